@@ -1,0 +1,159 @@
+/*
+ * anyseq.h - C ABI of the GB300 pairwise alignment library.
+ *
+ * The operation is the DP alignment of Sec. III-A of the AnySeq paper
+ * (arXiv 2002.04561): for a query Q = q_1..q_n (rows i) and a subject
+ * S = s_1..s_m (columns j),
+ *
+ *   E(i,j) = max(E(i-1,j) + extend, H(i-1,j) + open + extend)   Eq. 4
+ *   F(i,j) = max(F(i,j-1) + extend, H(i,j-1) + open + extend)   Eq. 5
+ *   H(i,j) = max(H(i-1,j-1) + sigma(q_i,s_j), E(i,j), F(i,j), nu) Eq. 1
+ *
+ * with the global (nu = -inf, optimum at (n,m)), local (nu = 0, optimum
+ * anywhere) and semi-global (row 0 and column 0 free, optimum in the last
+ * row or column) initialisations of Sec. III-A. A linear gap g (Eqs. 2, 3)
+ * is open = 0, extend = g. Scores are SIGNED: open, extend <= 0, and a gap
+ * of length k adds open + k*extend (the paper writes G_o = -open,
+ * G_e = -extend). The paper's one-pair interface construct_global_alignment
+ * (Sec. III-C) becomes a batch call and a long-pair call here.
+ *
+ * Conventions fixed by this library where the paper is silent:
+ *  - optimum cell on ties: the smallest i, then the smallest j;
+ *  - predecessor on ties: diagonal, then E (CIGAR I), then F (CIGAR D); a
+ *    local cell of value 0 ends the alignment; inside E/F opening is
+ *    preferred over extending;
+ *  - CIGAR words are BAM style (length << 4 | op) with op M = 0 (q_i with
+ *    s_j), I = 1 (q_i against a gap), D = 2 (s_j against a gap);
+ *  - beg_q/beg_s is the DP cell where the path starts (the alignment covers
+ *    q[beg_q+1 .. end_q] and s[beg_s+1 .. end_s]); an empty local alignment
+ *    has beg = end = (0,0).
+ *
+ * Pointers: every array argument may be host or device memory (the library
+ * asks the driver). Calls are asynchronous on the given CUDA stream when all
+ * arrays are device memory; when any output is host memory the call returns
+ * after the stream has finished. Inputs and outputs are owned by the caller
+ * and never freed by the library; scratch comes from the context, capped by
+ * its memory budget. All functions return an anyseq_status_t and never throw;
+ * anyseq_last_error() describes the last failure of the calling thread.
+ */
+#ifndef ANYSEQ_H
+#define ANYSEQ_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+    ANYSEQ_GLOBAL = 0,      /* Needleman-Wunsch: nu = -inf, optimum H(n,m) */
+    ANYSEQ_LOCAL = 1,       /* Smith-Waterman: nu = 0, optimum anywhere */
+    ANYSEQ_SEMIGLOBAL = 2   /* free end gaps: local initialisation, nu = -inf, optimum in last row/column */
+} anyseq_mode_t;
+
+typedef enum {
+    ANYSEQ_OK = 0,
+    ANYSEQ_ERR_ARG = 1,       /* bad pointer, size, scoring or mode */
+    ANYSEQ_ERR_ALPHABET = 2,  /* a code >= alphabet, or a non-ACGT letter */
+    ANYSEQ_ERR_BUDGET = 3,    /* scratch would exceed the context's memory budget */
+    ANYSEQ_ERR_CUDA = 4,      /* a CUDA runtime call failed */
+    ANYSEQ_ERR_TIMEOUT = 5,   /* a device-side wait exceeded its iteration limit */
+    ANYSEQ_ERR_CAPACITY = 6   /* the caller's CIGAR buffer is too small (*cigar_used = words needed) */
+} anyseq_status_t;
+
+enum {
+    ANYSEQ_WANT_SCORE = 1,    /* score (always computed) */
+    ANYSEQ_WANT_END = 2,      /* optimum cell (always computed) */
+    ANYSEQ_WANT_CIGAR = 4,    /* traceback to a CIGAR and the start cell */
+    ANYSEQ_BAND_LEARNED = 8   /* long/global pairs: try a learned band under a certificate first */
+};
+
+/* result flags */
+enum {
+    ANYSEQ_FLAG_INT32 = 1,        /* computed in 32-bit lanes (did not pass the int16 range test) */
+    ANYSEQ_FLAG_BAND_ACCEPTED = 2,/* a banded result was accepted by the certificate */
+    ANYSEQ_FLAG_FULL_FALLBACK = 4 /* band certificate failed at every width: full DP */
+    /* bits 8..15: number of band doublings */
+};
+
+typedef struct {
+    int32_t alphabet;        /* 4 for DNA (codes 0..3 = A,C,G,T) up to 32; codes must be < alphabet */
+    const int8_t *matrix;    /* alphabet x alphabet row-major, row = query letter (host memory); NULL: match/mismatch */
+    int32_t match, mismatch; /* used when matrix == NULL */
+    int32_t gap_open;        /* <= 0 */
+    int32_t gap_extend;      /* <= 0 */
+} anyseq_scoring_t;
+
+typedef struct {
+    int32_t score;
+    int32_t beg_q, beg_s;    /* start cell (WANT_CIGAR), else -1 */
+    int32_t end_q, end_s;    /* optimum cell */
+    uint32_t flags;
+    uint64_t cigar_off;      /* first word of this pair in the caller's CIGAR buffer */
+    uint32_t cigar_len;      /* number of words */
+    uint32_t reserved;
+} anyseq_result_t;
+
+typedef struct anyseq_ctx anyseq_ctx;
+
+/* Create a context on CUDA device 'device'. Scratch is allocated lazily and
+ * reused; its total never exceeds mem_budget_bytes (0 = 90% of free memory). */
+anyseq_status_t anyseq_create(anyseq_ctx **ctx, int device, size_t mem_budget_bytes);
+anyseq_status_t anyseq_destroy(anyseq_ctx *ctx);
+
+/*
+ * Align n_pairs independent pairs (inter-sequence parallelism, Sec. VI).
+ *   q, s          concatenated letter codes (uint8), pair p at q[q_off[p] .. q_off[p+1])
+ *   q_off, s_off  n_pairs + 1 non-decreasing offsets (int64)
+ *   sc            scoring (host struct); mode: anyseq_mode_t; want: ANYSEQ_WANT_* bits
+ *   out           n_pairs results (caller-owned)
+ *   cigar         with ANYSEQ_WANT_CIGAR: buffer of cigar_cap words; pair p's words start at
+ *                 out[p].cigar_off; *cigar_used (host) receives the total. Too small a buffer
+ *                 returns ANYSEQ_ERR_CAPACITY with *cigar_used = words needed; NULL/0 allowed otherwise.
+ *   cuda_stream   cudaStream_t (NULL = legacy default stream)
+ * Errors: ERR_ARG (null pointers, decreasing offsets, open/extend > 0, alphabet out of
+ * range, mode unknown), ERR_ALPHABET (a code >= alphabet), ERR_BUDGET, ERR_CUDA.
+ */
+anyseq_status_t anyseq_align_batch(anyseq_ctx *ctx,
+                                   const uint8_t *q, const int64_t *q_off,
+                                   const uint8_t *s, const int64_t *s_off,
+                                   int64_t n_pairs, const anyseq_scoring_t *sc,
+                                   int32_t mode, uint32_t want,
+                                   anyseq_result_t *out,
+                                   uint32_t *cigar, uint64_t cigar_cap, uint64_t *cigar_used,
+                                   void *cuda_stream);
+
+/*
+ * Align one long pair (intra-sequence parallelism: anti-diagonal wavefront of
+ * row stripes, Sec. IV-C), score in linear space, and with ANYSEQ_WANT_CIGAR
+ * the divide-and-conquer traceback of Sec. III-A (Myers-Miller for affine
+ * gaps). Only ANYSEQ_GLOBAL supports ANYSEQ_WANT_CIGAR. Arguments as for
+ * anyseq_align_batch with one pair of lengths n and m.
+ */
+anyseq_status_t anyseq_align_long(anyseq_ctx *ctx,
+                                  const uint8_t *q, int64_t n,
+                                  const uint8_t *s, int64_t m,
+                                  const anyseq_scoring_t *sc, int32_t mode, uint32_t want,
+                                  anyseq_result_t *out,
+                                  uint32_t *cigar, uint64_t cigar_cap, uint64_t *cigar_used,
+                                  void *cuda_stream);
+
+/* Tuning and test switches of a context: "force_int32" (0/1) routes every pair
+ * to 32-bit lanes. Unknown keys: ANYSEQ_ERR_ARG. */
+anyseq_status_t anyseq_set_option(anyseq_ctx *ctx, const char *key, int64_t value);
+
+/* Map ASCII A/C/G/T (either case) to codes 0..3; any other byte: ANYSEQ_ERR_ALPHABET.
+ * Host pointers only; synchronous. */
+anyseq_status_t anyseq_encode_dna(const char *ascii, uint8_t *codes, int64_t len);
+
+/* Description of the calling thread's last error (static storage, never NULL). */
+const char *anyseq_last_error(void);
+
+/* Library version string. */
+const char *anyseq_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* ANYSEQ_H */

@@ -1,0 +1,186 @@
+"""GB300 (sm_103a) pairwise DP alignment: Python binding of the C ABI.
+
+The binding only marshals arguments: it passes pointers of torch tensors (or
+numpy arrays for host buffers) and the current CUDA stream to the functions
+declared in include/anyseq.h, with the same names. Every step of the
+alignment runs in the CUDA library ``_lib/libanyseq.so``; there is no CPU
+fallback, and importing the binding fails loudly when the library is missing.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+import numpy as np
+
+from . import build as _build
+
+GLOBAL, LOCAL, SEMIGLOBAL = 0, 1, 2
+MODES = {"global": GLOBAL, "local": LOCAL, "semiglobal": SEMIGLOBAL}
+WANT_SCORE, WANT_END, WANT_CIGAR, BAND_LEARNED = 1, 2, 4, 8
+FLAG_INT32, FLAG_BAND_ACCEPTED, FLAG_FULL_FALLBACK = 1, 2, 4
+STATUS = {0: "OK", 1: "ERR_ARG", 2: "ERR_ALPHABET", 3: "ERR_BUDGET", 4: "ERR_CUDA",
+          5: "ERR_TIMEOUT", 6: "ERR_CAPACITY"}
+
+LIB_PATH = _build.LIB
+
+
+class AnyseqError(RuntimeError):
+    def __init__(self, status: int, msg: str):
+        super().__init__(f"{STATUS.get(status, status)}: {msg}")
+        self.status = status
+
+
+class Scoring(ctypes.Structure):
+    """anyseq_scoring_t. ``matrix`` (optional) must stay alive during calls."""
+    _fields_ = [("alphabet", ctypes.c_int32), ("matrix", ctypes.c_void_p),
+                ("match", ctypes.c_int32), ("mismatch", ctypes.c_int32),
+                ("gap_open", ctypes.c_int32), ("gap_extend", ctypes.c_int32)]
+
+    @classmethod
+    def make(cls, match=2, mismatch=-1, gap_open=0, gap_extend=-1, matrix=None, alphabet=4):
+        sc = cls()
+        sc.alphabet = alphabet
+        sc.match, sc.mismatch, sc.gap_open, sc.gap_extend = match, mismatch, gap_open, gap_extend
+        if matrix is not None:
+            sc._mat = np.ascontiguousarray(matrix, dtype=np.int8)
+            sc.matrix = sc._mat.ctypes.data
+            sc.alphabet = sc._mat.shape[0]
+        else:
+            sc.matrix = None
+        return sc
+
+
+class Result(ctypes.Structure):
+    _fields_ = [("score", ctypes.c_int32), ("beg_q", ctypes.c_int32), ("beg_s", ctypes.c_int32),
+                ("end_q", ctypes.c_int32), ("end_s", ctypes.c_int32), ("flags", ctypes.c_uint32),
+                ("cigar_off", ctypes.c_uint64), ("cigar_len", ctypes.c_uint32), ("reserved", ctypes.c_uint32)]
+
+
+RESULT_DTYPE = np.dtype([("score", np.int32), ("beg_q", np.int32), ("beg_s", np.int32),
+                         ("end_q", np.int32), ("end_s", np.int32), ("flags", np.uint32),
+                         ("cigar_off", np.uint64), ("cigar_len", np.uint32), ("reserved", np.uint32)])
+assert RESULT_DTYPE.itemsize == ctypes.sizeof(Result) == 40
+
+_lib = None
+EXPORTS = ["anyseq_create", "anyseq_destroy", "anyseq_align_batch", "anyseq_align_long",
+           "anyseq_set_option", "anyseq_encode_dna", "anyseq_last_error", "anyseq_version"]
+
+
+def load(build_if_missing: bool = False):
+    """Load libanyseq.so (optionally building it first). Raises if it is missing."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(LIB_PATH):
+        if not build_if_missing:
+            raise ImportError(f"CUDA library {LIB_PATH} is missing: run paper_2002_04561_gb300.build.build()")
+        _build.build()
+    lib = ctypes.CDLL(LIB_PATH)
+    P, I64, I32, U32, U64 = ctypes.c_void_p, ctypes.c_int64, ctypes.c_int32, ctypes.c_uint32, ctypes.c_uint64
+    lib.anyseq_create.argtypes = [ctypes.POINTER(P), ctypes.c_int, ctypes.c_size_t]
+    lib.anyseq_destroy.argtypes = [P]
+    lib.anyseq_align_batch.argtypes = [P, P, P, P, P, I64, P, I32, U32, P, P, U64, P, P]
+    lib.anyseq_align_long.argtypes = [P, P, I64, P, I64, P, I32, U32, P, P, U64, P, P]
+    lib.anyseq_set_option.argtypes = [P, ctypes.c_char_p, I64]
+    lib.anyseq_encode_dna.argtypes = [P, P, I64]
+    lib.anyseq_last_error.restype = ctypes.c_char_p
+    lib.anyseq_last_error.argtypes = []
+    lib.anyseq_version.restype = ctypes.c_char_p
+    for name in ["anyseq_create", "anyseq_destroy", "anyseq_align_batch", "anyseq_align_long",
+                 "anyseq_set_option", "anyseq_encode_dna"]:
+        getattr(lib, name).restype = ctypes.c_int
+    _lib = lib
+    return lib
+
+
+def _check(status: int):
+    if status != 0:
+        raise AnyseqError(status, load().anyseq_last_error().decode())
+
+
+def _ptr(x) -> int | None:
+    """Address of a torch tensor or numpy array (None for empty/None)."""
+    if x is None:
+        return None
+    if hasattr(x, "data_ptr"):
+        return x.data_ptr() if x.numel() else None
+    return x.ctypes.data if x.size else None
+
+
+def _stream_handle(stream):
+    if stream is None:
+        try:
+            import torch
+            if torch.cuda.is_available():
+                return torch.cuda.current_stream().cuda_stream
+        except ImportError:
+            pass
+        return None
+    return getattr(stream, "cuda_stream", stream)
+
+
+class Context:
+    """anyseq_ctx: device, scratch arena and memory budget."""
+
+    def __init__(self, device: int = 0, mem_budget: int = 0):
+        lib = load()
+        h = ctypes.c_void_p()
+        _check(lib.anyseq_create(ctypes.byref(h), device, mem_budget))
+        self.h = h
+        self.device = device
+
+    def close(self):
+        if getattr(self, "h", None):
+            load().anyseq_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def set_option(self, key: str, value: int):
+        _check(load().anyseq_set_option(self.h, key.encode(), int(value)))
+
+    def align_batch(self, q, q_off, s, s_off, scoring: Scoring, mode: int = GLOBAL,
+                    want: int = WANT_SCORE | WANT_END, out=None, cigar=None, stream=None):
+        """anyseq_align_batch. Arrays: torch tensors (device or host) or numpy (host).
+
+        Returns (out, cigar_used). ``out`` defaults to a host numpy array of RESULT_DTYPE.
+        """
+        n_pairs = len(q_off) - 1
+        if out is None:
+            out = np.zeros(n_pairs, dtype=RESULT_DTYPE)
+        used = ctypes.c_uint64(0)
+        cap = 0 if cigar is None else (cigar.numel() if hasattr(cigar, "numel") else cigar.size)
+        _check(load().anyseq_align_batch(
+            self.h, _ptr(q), _ptr(q_off), _ptr(s), _ptr(s_off), n_pairs, ctypes.byref(scoring), mode, want,
+            _ptr(out), _ptr(cigar), cap, ctypes.byref(used), _stream_handle(stream)))
+        return out, used.value
+
+    def align_long(self, q, s, scoring: Scoring, mode: int = GLOBAL, want: int = WANT_SCORE | WANT_END,
+                   out=None, cigar=None, stream=None):
+        """anyseq_align_long on one pair. Returns (out, cigar_used)."""
+        n = q.numel() if hasattr(q, "numel") else len(q)
+        m = s.numel() if hasattr(s, "numel") else len(s)
+        if out is None:
+            out = np.zeros(1, dtype=RESULT_DTYPE)
+        used = ctypes.c_uint64(0)
+        cap = 0 if cigar is None else (cigar.numel() if hasattr(cigar, "numel") else cigar.size)
+        _check(load().anyseq_align_long(
+            self.h, _ptr(q), n, _ptr(s), m, ctypes.byref(scoring), mode, want, _ptr(out), _ptr(cigar), cap,
+            ctypes.byref(used), _stream_handle(stream)))
+        return out, used.value
+
+
+def encode_dna(text: str) -> np.ndarray:
+    raw = text.encode("ascii")
+    out = np.zeros(len(raw), dtype=np.uint8)
+    _check(load().anyseq_encode_dna(raw, _ptr(out), len(raw)))
+    return out
+
+
+def version() -> str:
+    return load().anyseq_version().decode()

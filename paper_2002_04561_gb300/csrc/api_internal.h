@@ -1,0 +1,46 @@
+// Internal declarations of the host side: the context and its scratch arena.
+#pragma once
+#include <cstdint>
+#include <string>
+#include <vector>
+
+#include <cuda_runtime.h>
+
+#include "../../include/anyseq.h"
+
+struct anyseq_ctx {
+    struct Buf {
+        std::string name;
+        void *p;
+        size_t cap;
+    };
+    int device = 0;
+    int num_sms = 1;
+    size_t budget = 0;
+    size_t used = 0;
+    int force32 = 0;              // route every pair to 32-bit lanes (testing)
+    std::vector<Buf> bufs;        // device scratch, grown on demand, reused across calls
+    std::vector<Buf> pinned;      // pinned host staging
+    // Named device buffer of at least 'bytes'; contents are not preserved on growth.
+    void *get(const char *name, size_t bytes, anyseq_status_t *st);
+};
+
+namespace anyseq {
+
+struct BatchInput {
+    const uint8_t *q = nullptr, *s = nullptr;          // device
+    const int64_t *q_off = nullptr, *s_off = nullptr;  // device
+    int64_t n_pairs = 0, q_len = 0, s_len = 0, max_n = 0, max_m = 0;
+};
+
+anyseq_status_t fail(anyseq_status_t st, const char *fmt, ...);
+bool is_device_ptr(const void *p);
+anyseq_status_t check_scoring(const anyseq_scoring_t *sc, int32_t mode);
+int32_t sigma_host(const anyseq_scoring_t *sc, int a, int b);
+anyseq_status_t make_rowprof(const anyseq_scoring_t *sc, int32_t mode, uint32_t prof[5]);
+anyseq_status_t stage_input(anyseq_ctx *ctx, const char *name, const void *src, size_t bytes, cudaStream_t st,
+                            const void **dev);
+anyseq_status_t batch_scores(anyseq_ctx *ctx, const BatchInput &in, const anyseq_scoring_t *sc, int32_t mode,
+                             int32_t *score, int32_t *eq, int32_t *es, uint32_t *flags, cudaStream_t st);
+
+}  // namespace anyseq

@@ -1,0 +1,107 @@
+// Shared device helpers of the alignment kernels: score lanes (int32 or two
+// int16 halves), byte permutes for substitution scores, 2-bit sequence access.
+#pragma once
+#include <cstdint>
+#include <cuda_runtime.h>
+
+namespace anyseq {
+
+constexpr int GROUP = 16;        // lanes cooperating on one slot (one row chunk)
+constexpr int RING = 128;        // columns held by the per-group shared-memory rings
+constexpr int BLOCK = 32;        // ring refill / flush granularity in columns
+
+// Minus infinity of the recurrences (Sec. III-A). Far enough from the
+// representable minimum that adding one gap extension cannot wrap, and below
+// every real value allowed by the range tests of the host.
+constexpr int32_t NEG32 = -(1 << 29);
+constexpr int32_t NEG16 = -20000;
+
+enum Mode { GLOBAL = 0, LOCAL = 1, SEMIGLOBAL = 2 };
+
+// prmt.b32 in its default mode: selector nibbles 8..15 replicate the sign
+// bit of the selected byte, which turns an int8 into an int16/int32.
+__device__ __forceinline__ uint32_t prmt(uint32_t a, uint32_t b, uint32_t sel) {
+    uint32_t d;
+    asm("prmt.b32 %0, %1, %2, %3;" : "=r"(d) : "r"(a), "r"(b), "r"(sel));
+    return d;
+}
+
+// One 32-bit score lane holding one pair.
+struct CellI32 {
+    typedef int32_t T;
+    static constexpr int PAIRS = 1;
+    static constexpr int32_t NEG = NEG32;
+    __device__ __forceinline__ static T add(T a, T b) { return a + b; }
+    __device__ __forceinline__ static T addmax(T a, T b, T c) { return __viaddmax_s32(a, b, c); }
+    __device__ __forceinline__ static T max3(T a, T b, T c) { return __vimax3_s32(a, b, c); }
+    __device__ __forceinline__ static T max3relu(T a, T b, T c) { return __vimax3_s32_relu(a, b, c); }
+    __device__ __forceinline__ static T vmax(T a, T b) { return max(a, b); }
+    __device__ __forceinline__ static T make(int32_t lo, int32_t hi) { (void)hi; return lo; }
+    __device__ __forceinline__ static int32_t get(T v, int h) { (void)h; return v; }
+    // sigma from a row profile word (4 int8 scores indexed by subject code)
+    __device__ __forceinline__ static T sigma(uint32_t pa, uint32_t pb, uint32_t sel) {
+        (void)pb; return (int32_t)prmt(pa, pa, sel);
+    }
+    // selector that sign-extends byte code_a of the row profile to 32 bits
+    __device__ __forceinline__ static uint32_t selector(uint32_t ca, uint32_t cb) {
+        (void)cb;
+        uint32_t sgn = ca | 8u;
+        return ca | (sgn << 4) | (sgn << 8) | (sgn << 12);
+    }
+    // mask (all ones per half) where a > b
+    __device__ __forceinline__ static uint32_t gt(T a, T b) { return a > b ? 0xFFFFFFFFu : 0u; }
+    __device__ __forceinline__ static uint32_t as_u(T v) { return (uint32_t)v; }
+    __device__ __forceinline__ static T from_u(uint32_t v) { return (int32_t)v; }
+};
+
+// Two int16 score halves: the low half holds pair A, the high half pair B.
+struct CellI16x2 {
+    typedef uint32_t T;
+    static constexpr int PAIRS = 2;
+    static constexpr int32_t NEG = NEG16;
+    __device__ __forceinline__ static T add(T a, T b) { return __vadd2(a, b); }
+    __device__ __forceinline__ static T addmax(T a, T b, T c) { return __viaddmax_s16x2(a, b, c); }
+    __device__ __forceinline__ static T max3(T a, T b, T c) { return __vimax3_s16x2(a, b, c); }
+    __device__ __forceinline__ static T max3relu(T a, T b, T c) { return __vimax3_s16x2_relu(a, b, c); }
+    __device__ __forceinline__ static T vmax(T a, T b) { return __vmaxs2(a, b); }
+    __device__ __forceinline__ static T make(int32_t lo, int32_t hi) {
+        return ((uint32_t)lo & 0xFFFFu) | ((uint32_t)hi << 16);
+    }
+    __device__ __forceinline__ static int32_t get(T v, int h) { return (int32_t)(int16_t)(v >> (16 * h)); }
+    __device__ __forceinline__ static T sigma(uint32_t pa, uint32_t pb, uint32_t sel) { return prmt(pa, pb, sel); }
+    // low half: byte ca of pa sign-extended; high half: byte cb of pb sign-extended
+    __device__ __forceinline__ static uint32_t selector(uint32_t ca, uint32_t cb) {
+        uint32_t b4 = cb + 4u;
+        return ca | ((ca | 8u) << 4) | (b4 << 8) | ((b4 | 8u) << 12);
+    }
+    __device__ __forceinline__ static uint32_t gt(T a, T b) { return __vcmpgts2(a, b); }
+    __device__ __forceinline__ static uint32_t as_u(T v) { return v; }
+    __device__ __forceinline__ static T from_u(uint32_t v) { return v; }
+};
+
+// Letter at global position k of a 2-bit packed array (16 letters per word).
+__device__ __forceinline__ uint32_t code2(const uint32_t *packed, int64_t k) {
+    return (packed[k >> 4] >> (2 * (k & 15))) & 3u;
+}
+
+// 16 consecutive letters starting at global position k, as one 32-bit word
+// (letter t in bits 2t..2t+1). Reads two words and funnel-shifts.
+__device__ __forceinline__ uint32_t codes16(const uint32_t *packed, int64_t k, int64_t limit_words) {
+    int64_t w = k >> 4;
+    uint32_t lo = packed[w];
+    uint32_t hi = (w + 1 < limit_words) ? packed[w + 1] : 0u;
+    return __funnelshift_r(lo, hi, 2 * (uint32_t)(k & 15));
+}
+
+// Lexicographic key of an optimum candidate: larger score, then smaller i,
+// then smaller j wins (the tie rule of the optimum cell).
+__device__ __forceinline__ uint64_t end_key(int32_t score, int32_t i, int32_t j) {
+    return ((uint64_t)(uint32_t)(score + (1 << 21)) << 42) |
+           ((uint64_t)(uint32_t)((1 << 21) - 1 - i) << 21) |
+           (uint64_t)(uint32_t)((1 << 21) - 1 - j);
+}
+__device__ __forceinline__ int32_t key_score(uint64_t k) { return (int32_t)(k >> 42) - (1 << 21); }
+__device__ __forceinline__ int32_t key_i(uint64_t k) { return (1 << 21) - 1 - (int32_t)((k >> 21) & 0x1FFFFF); }
+__device__ __forceinline__ int32_t key_j(uint64_t k) { return (1 << 21) - 1 - (int32_t)(k & 0x1FFFFF); }
+
+}  // namespace anyseq

@@ -1,0 +1,155 @@
+// Input staging of the batched path: letter validation, 2-bit packing with
+// 128-bit loads, the int16 range test, and a counting sort of the pairs into
+// length buckets (longest first) that the persistent kernel consumes as its
+// work queue. Pairs with an empty sequence get their closed-form result here.
+#include "batch.h"
+#include "common.cuh"
+
+namespace anyseq {
+
+constexpr int NBUCKET = 65536;
+
+// one thread per output word: 16 letters (one 16-byte load when aligned)
+__global__ void pack2bit_kernel(const uint8_t *codes, int64_t len, uint32_t *out, int32_t alphabet,
+                                int32_t *bad) {
+    int64_t w = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    int64_t nw = (len + 15) >> 4;
+    for (; w < nw; w += (int64_t)gridDim.x * blockDim.x) {
+        int64_t k0 = w << 4;
+        uint8_t b[16];
+        if (k0 + 16 <= len && ((reinterpret_cast<uintptr_t>(codes + k0) & 15u) == 0)) {
+            uint4 v = *reinterpret_cast<const uint4 *>(codes + k0);
+            *reinterpret_cast<uint4 *>(b) = v;
+        } else {
+#pragma unroll
+            for (int t = 0; t < 16; t++) b[t] = (k0 + t < len) ? codes[k0 + t] : 0;
+        }
+        uint32_t word = 0;
+        int badv = 0;
+#pragma unroll
+        for (int t = 0; t < 16; t++) {
+            badv |= (b[t] >= alphabet);
+            word |= (uint32_t)(b[t] & 3u) << (2 * t);
+        }
+        if (out) out[w] = word;
+        if (badv) *bad = 1;
+    }
+}
+
+// bytes only (alphabets above 4): validation
+__global__ void validate_kernel(const uint8_t *codes, int64_t len, int32_t alphabet, int32_t *bad) {
+    int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    for (; k < len; k += (int64_t)gridDim.x * blockDim.x)
+        if (codes[k] >= alphabet) *bad = 1;
+}
+
+// 8-bit logarithmic length bucket, 8 sub-steps per octave.
+__device__ __forceinline__ uint32_t lbucket(int64_t x) {
+    if (x < 16) return (uint32_t)x;
+    int lg = 63 - __clzll(x);
+    uint32_t q = 16u + (uint32_t)(lg - 4) * 8u + (uint32_t)((x >> (lg - 3)) & 7);
+    return q > 255u ? 255u : q;
+}
+
+// Range test for exact int16 lanes: every H, E, F, Hoe and diagonal term of
+// the pair stays inside [-16000, 16000] (bounds from the recurrences: H is at
+// most max(sigma,0) * min(n,m); below, global H(i,j) is at least two gaps,
+// semi-global at least one, local at least 0; E/F add one more open+extend).
+__device__ __forceinline__ bool fits_int16(int64_t n, int64_t m, int32_t smax, int32_t smin, int32_t o, int32_t e,
+                                           int32_t mode) {
+    int64_t mn = n < m ? n : m;
+    int64_t hi = (int64_t)(smax > 0 ? smax : 0) * (mn + 1) + (smax > 0 ? smax : 0);
+    int64_t lo;
+    int64_t ox = o, ex = e, sm = smin < 0 ? smin : 0;
+    if (mode == GLOBAL) lo = 3 * ox + (n + m + 2) * ex + sm;
+    else if (mode == SEMIGLOBAL) lo = 2 * ox + (mn + 2) * ex + sm;
+    else lo = ox + 2 * ex + sm;
+    return hi <= 16000 && lo >= -16000;
+}
+
+__global__ void bin_kernel(PrepArgs P) {
+    int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    for (; p < P.n_pairs; p += (int64_t)gridDim.x * blockDim.x) {
+        int64_t n = P.q_off[p + 1] - P.q_off[p];
+        int64_t m = P.s_off[p + 1] - P.s_off[p];
+        if (n == 0 || m == 0) {
+            int32_t sc = 0;
+            if (P.mode == GLOBAL) sc = (n + m == 0) ? 0 : P.o + (int32_t)(n + m) * P.e;
+            P.score[p] = sc;
+            P.end_q[p] = P.mode == GLOBAL ? (int32_t)n : 0;
+            P.end_s[p] = P.mode == GLOBAL ? (int32_t)m : 0;
+            P.flags[p] = 0;
+            P.key[p] = 0xFFFFFFFFu;
+            unsigned long long pos = atomicAdd(reinterpret_cast<unsigned long long *>(&P.counts[2]), 1ull);
+            if (P.trivial) P.trivial[pos] = (int32_t)p;
+            continue;
+        }
+        uint32_t prec = (P.force32 || !fits_int16(n, m, P.smax, P.smin, P.o, P.e, P.mode)) ? 1u : 0u;
+        uint32_t k = prec * NBUCKET + (lbucket(n) << 8) + lbucket(m);
+        P.key[p] = k;
+        atomicAdd(&P.hist[k], 1u);
+        atomicAdd(reinterpret_cast<unsigned long long *>(&P.counts[prec]), 1ull);
+    }
+}
+
+// Exclusive offsets in DESCENDING key order within each precision class, in
+// place: hist[k] becomes the first list position of bucket k. One block.
+__global__ void scan_kernel(uint32_t *hist) {
+    __shared__ uint32_t part[1024];
+    const int t = threadIdx.x;
+    for (int cls = 0; cls < 2; cls++) {
+        uint32_t *h = hist + cls * NBUCKET;
+        const int per = NBUCKET / 1024;  // 64 buckets per thread, descending
+        // thread t owns reversed indices [t*per, (t+1)*per): key = NBUCKET-1-idx
+        uint32_t sum = 0;
+        for (int k = 0; k < per; k++) sum += h[NBUCKET - 1 - (t * per + k)];
+        part[t] = sum;
+        __syncthreads();
+        for (int off = 1; off < 1024; off <<= 1) {
+            uint32_t v = t >= off ? part[t - off] : 0u;
+            __syncthreads();
+            part[t] += v;
+            __syncthreads();
+        }
+        uint32_t run = part[t] - sum;
+        for (int k = 0; k < per; k++) {
+            int key = NBUCKET - 1 - (t * per + k);
+            uint32_t c = h[key];
+            h[key] = run;
+            run += c;
+        }
+        __syncthreads();
+    }
+}
+
+__global__ void scatter_kernel(PrepArgs P) {
+    int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    for (; p < P.n_pairs; p += (int64_t)gridDim.x * blockDim.x) {
+        uint32_t k = P.key[p];
+        if (k == 0xFFFFFFFFu) continue;
+        uint32_t pos = atomicAdd(&P.hist[k], 1u);
+        if (k < NBUCKET) P.list16[pos] = (int32_t)p;
+        else P.list32[pos] = (int32_t)p;
+    }
+}
+
+cudaError_t launch_prep(const PrepArgs &P, cudaStream_t st) {
+    const int T = 256;
+    auto blocks = [](int64_t work) { int64_t b = (work + 255) / 256; return (int)(b < 1 ? 1 : (b > 65535 ? 65535 : b)); };
+    cudaMemsetAsync(P.hist, 0, 2 * NBUCKET * sizeof(uint32_t), st);
+    cudaMemsetAsync(P.counts, 0, 3 * sizeof(int64_t), st);
+    cudaMemsetAsync(P.bad_code, 0, sizeof(int32_t), st);
+    if (P.alphabet <= 4) {
+        pack2bit_kernel<<<blocks((P.q_len + 15) / 16), T, 0, st>>>(P.q, P.q_len, P.q2, P.alphabet, P.bad_code);
+        pack2bit_kernel<<<blocks((P.s_len + 15) / 16), T, 0, st>>>(P.s, P.s_len, P.s2, P.alphabet, P.bad_code);
+    } else {
+        validate_kernel<<<blocks(P.q_len), T, 0, st>>>(P.q, P.q_len, P.alphabet, P.bad_code);
+        validate_kernel<<<blocks(P.s_len), T, 0, st>>>(P.s, P.s_len, P.alphabet, P.bad_code);
+    }
+    bin_kernel<<<blocks(P.n_pairs), T, 0, st>>>(P);
+    scan_kernel<<<1, 1024, 0, st>>>(P.hist);
+    scatter_kernel<<<blocks(P.n_pairs), T, 0, st>>>(P);
+    return cudaGetLastError();
+}
+
+}  // namespace anyseq

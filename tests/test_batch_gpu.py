@@ -1,0 +1,175 @@
+"""GPU parity of the batched path (anyseq_align_batch) with the CPU oracle.
+
+Scores and optimum cells must be bit-identical (integer work). Cases cover all
+three modes, linear and affine gaps, match/mismatch and matrix scoring, the
+int16x2 lanes and the forced 32-bit lanes, lengths that span several row
+chunks (256 rows per chunk) and ragged tails, empty sequences, scorings that
+fail the int16 range test, and a 20,000-pair sample of the full 262,144-pair
+short-read workload in the launch configuration the benchmark times.
+"""
+import numpy as np
+import pytest
+
+import oracle
+import synth
+
+pytestmark = pytest.mark.gpu
+
+torch = pytest.importorskip("torch")
+
+
+@pytest.fixture(scope="module")
+def pkg():
+    if not torch.cuda.is_available():
+        pytest.skip("no GPU")
+    import paper_2002_04561_gb300 as p
+    p.load(build_if_missing=True)
+    return p
+
+
+@pytest.fixture(scope="module")
+def ctx(pkg):
+    c = pkg.Context(0)
+    yield c
+    c.close()
+
+
+def dev(a):
+    return torch.from_numpy(np.ascontiguousarray(a)).cuda()
+
+
+def run(pkg, ctx, b, sc_args, mode, on_device=True, force32=False):
+    sc = pkg.Scoring.make(*sc_args[:4], matrix=sc_args[4] if len(sc_args) > 4 else None)
+    ctx.set_option("force_int32", int(force32))
+    try:
+        if on_device:
+            out = torch.zeros(b.n_pairs * 40, dtype=torch.uint8, device="cuda")
+            ctx.align_batch(dev(b.q), dev(b.q_off), dev(b.s), dev(b.s_off), sc, mode, out=out)
+            torch.cuda.synchronize()
+            return out.cpu().numpy().view(pkg.RESULT_DTYPE)
+        out, _ = ctx.align_batch(b.q, b.q_off, b.s, b.s_off, sc, mode)
+        return out
+    finally:
+        ctx.set_option("force_int32", 0)
+
+
+def oracle_of(b, sc_args, mode):
+    sc = oracle.Scoring(*sc_args[:4], matrix=sc_args[4] if len(sc_args) > 4 else None)
+    return oracle.score_batch(b, sc, mode)
+
+
+def assert_parity(res, want, b):
+    bad = np.nonzero((res["score"] != want[0]) | (res["end_q"] != want[1]) | (res["end_s"] != want[2]))[0]
+    if len(bad):
+        p = int(bad[0])
+        raise AssertionError(
+            f"{len(bad)} of {b.n_pairs} pairs differ; first pair {p} (n={b.q_len()[p]}, m={b.s_len()[p]}): "
+            f"gpu ({res['score'][p]}, {res['end_q'][p]}, {res['end_s'][p]}) "
+            f"oracle ({want[0][p]}, {want[1][p]}, {want[2][p]})")
+
+
+SCHEMES = [(2, -1, 0, -1), (1, -4, -6, -1), (2, -3, -5, -2), (3, -2, -4, -3)]
+MODES = [0, 1, 2]
+
+
+@pytest.mark.parametrize("mode", MODES)
+@pytest.mark.parametrize("sc_args", SCHEMES)
+@pytest.mark.parametrize("force32", [False, True])
+def test_random_pairs_parity(pkg, ctx, mode, sc_args, force32):
+    b = synth.random_pairs(700, 0, 600, seed=100 + mode, related=0.6)
+    res = run(pkg, ctx, b, sc_args, mode, force32=force32)
+    assert_parity(res, oracle_of(b, sc_args, mode), b)
+    if force32:
+        nonempty = (b.q_len() > 0) & (b.s_len() > 0)
+        assert np.all(res["flags"][nonempty] & 1)
+
+
+@pytest.mark.parametrize("mode", MODES)
+def test_matrix_scoring_parity(pkg, ctx, mode):
+    st = synth.Stream(77, 1)
+    mat = st.integers(-5, 6, 16).reshape(4, 4).astype(np.int8)
+    b = synth.random_pairs(400, 1, 300, seed=200 + mode)
+    args = (0, 0, -4, -1, mat)
+    assert_parity(run(pkg, ctx, b, args, mode), oracle_of(b, args, mode), b)
+
+
+EDGE_LENGTHS = [0, 1, 2, 15, 16, 17, 31, 32, 33, 255, 256, 257, 511, 512, 513, 1000]
+
+
+@pytest.mark.parametrize("mode", MODES)
+def test_edge_lengths(pkg, ctx, mode):
+    st = synth.Stream(300 + mode, 1)
+    pairs = []
+    for n in EDGE_LENGTHS:
+        for m in EDGE_LENGTHS:
+            if (n * m) % 7 == 0 or n in (0, 1) or m in (0, 1):
+                pairs.append((synth.random_codes(st, n, 4), synth.random_codes(st, m, 4)))
+    b = synth.from_pairs(pairs)
+    for sc_args in SCHEMES[:3]:
+        for force32 in (False, True):
+            assert_parity(run(pkg, ctx, b, sc_args, mode, force32=force32), oracle_of(b, sc_args, mode), b)
+
+
+def test_self_alignment_and_identical_pairs(pkg, ctx):
+    st = synth.Stream(400, 1)
+    pairs = [(x, x) for x in (synth.random_codes(st, int(n), 4) for n in st.integers(1, 700, 100))]
+    b = synth.from_pairs(pairs)
+    for mode in MODES:
+        res = run(pkg, ctx, b, (2, -3, -5, -2), mode)
+        assert np.array_equal(res["score"], 2 * b.q_len())
+
+
+def test_int16_range_test_routes_to_int32(pkg, ctx):
+    """Large match scores on long related pairs fail the int16 bound and must be
+    computed in 32-bit lanes with exact results."""
+    b = synth.random_pairs(200, 300, 900, seed=500, related=1.0, p_sub=0.02, p_indel=0.01)
+    args = (60, -60, -60, -10)
+    for mode in MODES:
+        res = run(pkg, ctx, b, args, mode)
+        assert_parity(res, oracle_of(b, args, mode), b)
+        assert np.all(res["flags"] & 1)
+
+
+def test_host_buffers_match_device_buffers(pkg, ctx):
+    b = synth.random_pairs(300, 0, 400, seed=600)
+    for mode in MODES:
+        a = run(pkg, ctx, b, SCHEMES[1], mode, on_device=True)
+        h = run(pkg, ctx, b, SCHEMES[1], mode, on_device=False)
+        assert np.array_equal(a["score"], h["score"]) and np.array_equal(a["end_s"], h["end_s"])
+
+
+def test_bad_letter_is_rejected(pkg, ctx):
+    b = synth.random_pairs(10, 5, 20, seed=700)
+    b.q[3] = 7
+    with pytest.raises(pkg.AnyseqError) as ei:
+        run(pkg, ctx, b, SCHEMES[0], 0)
+    assert ei.value.status == 2
+
+
+def test_bad_arguments_are_rejected(pkg, ctx):
+    b = synth.random_pairs(4, 5, 20, seed=701)
+    sc = pkg.Scoring.make(1, -1, 2, -1)  # positive open
+    with pytest.raises(pkg.AnyseqError) as ei:
+        ctx.align_batch(b.q, b.q_off, b.s, b.s_off, sc, 0)
+    assert ei.value.status == 1
+    with pytest.raises(pkg.AnyseqError):
+        ctx.align_batch(b.q, b.q_off, b.s, b.s_off, pkg.Scoring.make(1, -1, 0, -1), 7)
+    off = b.q_off.copy()
+    off[2], off[3] = off[3], off[2]
+    if off[2] > off[3]:
+        with pytest.raises(pkg.AnyseqError):
+            ctx.align_batch(b.q, off, b.s, b.s_off, pkg.Scoring.make(1, -1, 0, -1), 0)
+
+
+def test_short_read_workload_full_size_sampled(pkg, ctx):
+    """262,144 pairs, semi-global affine +1/-4/-6/-1, int16x2 lanes: every score is
+    checked against the oracle on a 20,000-pair sample of the full run."""
+    b = synth.short_reads()
+    args = (1, -4, -6, -1)
+    res = run(pkg, ctx, b, args, 2)
+    st = synth.Stream(800, 1)
+    idx = np.unique(st.integers(0, b.n_pairs - 1, 20000))
+    sub = b.subset(idx)
+    want = oracle_of(sub, args, 2)
+    assert_parity(res[idx], want, sub)
+    assert not np.any(res["flags"] & 1)  # all pairs passed the int16 range test
