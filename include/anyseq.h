@@ -140,8 +140,15 @@ anyseq_status_t anyseq_align_long(anyseq_ctx *ctx,
                                   void *cuda_stream);
 
 /* Tuning and test switches of a context: "force_int32" (0/1) routes every pair
- * to 32-bit lanes. Unknown keys: ANYSEQ_ERR_ARG. */
+ * to 32-bit lanes; "profile" (0/1) times the DP kernels of each call with CUDA
+ * events on the call's stream. Unknown keys: ANYSEQ_ERR_ARG. */
 anyseq_status_t anyseq_set_option(anyseq_ctx *ctx, const char *key, int64_t value);
+
+/* Statistics of the context's last call (host values, valid after the call's
+ * stream has finished): "launches" (kernels launched), "dp_ms" (time of the
+ * int16x2 DP kernel, needs "profile"), "dp32_ms" (32-bit lanes), "pairs16",
+ * "pairs32" (pairs per lane width). Unknown keys: ANYSEQ_ERR_ARG. */
+anyseq_status_t anyseq_get_stat(anyseq_ctx *ctx, const char *key, double *value);
 
 /* Map ASCII A/C/G/T (either case) to codes 0..3; any other byte: ANYSEQ_ERR_ALPHABET.
  * Host pointers only; synchronous. */

@@ -64,7 +64,8 @@ assert RESULT_DTYPE.itemsize == ctypes.sizeof(Result) == 40
 
 _lib = None
 EXPORTS = ["anyseq_create", "anyseq_destroy", "anyseq_align_batch", "anyseq_align_long",
-           "anyseq_set_option", "anyseq_encode_dna", "anyseq_last_error", "anyseq_version"]
+           "anyseq_set_option", "anyseq_get_stat", "anyseq_encode_dna", "anyseq_last_error",
+           "anyseq_version"]
 
 
 def load(build_if_missing: bool = False):
@@ -83,12 +84,13 @@ def load(build_if_missing: bool = False):
     lib.anyseq_align_batch.argtypes = [P, P, P, P, P, I64, P, I32, U32, P, P, U64, P, P]
     lib.anyseq_align_long.argtypes = [P, P, I64, P, I64, P, I32, U32, P, P, U64, P, P]
     lib.anyseq_set_option.argtypes = [P, ctypes.c_char_p, I64]
+    lib.anyseq_get_stat.argtypes = [P, ctypes.c_char_p, ctypes.POINTER(ctypes.c_double)]
     lib.anyseq_encode_dna.argtypes = [P, P, I64]
     lib.anyseq_last_error.restype = ctypes.c_char_p
     lib.anyseq_last_error.argtypes = []
     lib.anyseq_version.restype = ctypes.c_char_p
     for name in ["anyseq_create", "anyseq_destroy", "anyseq_align_batch", "anyseq_align_long",
-                 "anyseq_set_option", "anyseq_encode_dna"]:
+                 "anyseq_set_option", "anyseq_get_stat", "anyseq_encode_dna"]:
         getattr(lib, name).restype = ctypes.c_int
     _lib = lib
     return lib
@@ -143,6 +145,11 @@ class Context:
 
     def set_option(self, key: str, value: int):
         _check(load().anyseq_set_option(self.h, key.encode(), int(value)))
+
+    def stat(self, key: str) -> float:
+        v = ctypes.c_double(0)
+        _check(load().anyseq_get_stat(self.h, key.encode(), ctypes.byref(v)))
+        return v.value
 
     def align_batch(self, q, q_off, s, s_off, scoring: Scoring, mode: int = GLOBAL,
                     want: int = WANT_SCORE | WANT_END, out=None, cigar=None, stream=None):

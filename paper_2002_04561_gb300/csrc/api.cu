@@ -81,6 +81,7 @@ extern "C" anyseq_status_t anyseq_destroy(anyseq_ctx *ctx) {
     cudaSetDevice(ctx->device);
     for (auto &b : ctx->bufs) cudaFree(b.p);
     for (auto &h : ctx->pinned) cudaFreeHost(h.p);
+    for (auto &e : ctx->ev) if (e) cudaEventDestroy(e);
     delete ctx;
     return ANYSEQ_OK;
 }
@@ -88,7 +89,24 @@ extern "C" anyseq_status_t anyseq_destroy(anyseq_ctx *ctx) {
 extern "C" anyseq_status_t anyseq_set_option(anyseq_ctx *ctx, const char *key, int64_t value) {
     if (!ctx || !key) return fail(ANYSEQ_ERR_ARG, "ctx or key is NULL");
     if (!strcmp(key, "force_int32")) { ctx->force32 = value != 0; return ANYSEQ_OK; }
+    if (!strcmp(key, "profile")) {
+        ctx->profile = value != 0;
+        if (ctx->profile && !ctx->ev[0])
+            for (auto &e : ctx->ev) cudaEventCreate(&e);
+        return ANYSEQ_OK;
+    }
     return fail(ANYSEQ_ERR_ARG, "unknown option '%s'", key);
+}
+
+extern "C" anyseq_status_t anyseq_get_stat(anyseq_ctx *ctx, const char *key, double *value) {
+    if (!ctx || !key || !value) return fail(ANYSEQ_ERR_ARG, "ctx, key or value is NULL");
+    if (!strcmp(key, "launches")) *value = (double)ctx->launches;
+    else if (!strcmp(key, "dp_ms")) *value = ctx->dp_ms;
+    else if (!strcmp(key, "dp32_ms")) *value = ctx->dp32_ms;
+    else if (!strcmp(key, "pairs16")) *value = (double)ctx->pairs16;
+    else if (!strcmp(key, "pairs32")) *value = (double)ctx->pairs32;
+    else return fail(ANYSEQ_ERR_ARG, "unknown statistic '%s'", key);
+    return ANYSEQ_OK;
 }
 
 extern "C" anyseq_status_t anyseq_encode_dna(const char *ascii, uint8_t *codes, int64_t len) {
@@ -262,6 +280,7 @@ anyseq_status_t anyseq::batch_scores(anyseq_ctx *ctx, const BatchInput &in, cons
     P.score = score; P.end_q = eq; P.end_s = es; P.flags = flags;
     P.force32 = ctx->force32;
     CUDA_TRY(launch_prep(P, st));
+    ctx->launches += 5;  // pack/validate x2, bin, scan, scatter
 
     BatchArgs A;
     memset(&A, 0, sizeof(A));
@@ -284,12 +303,26 @@ anyseq_status_t anyseq::batch_scores(anyseq_ctx *ctx, const BatchInput &in, cons
             if (s2 != ANYSEQ_OK) return s2;
         }
         CUDA_TRY(cudaMemsetAsync(A.counter, 0, sizeof(int32_t), st));
+        if (ctx->profile) cudaEventRecord(ctx->ev[2 * cell32], st);
         CUDA_TRY(launch_batch(A, cell32, mode, grid, st));
+        if (ctx->profile) cudaEventRecord(ctx->ev[2 * cell32 + 1], st);
+        ctx->launches += 1;
     }
     // letter check (read after the kernels; an invalid code only affects its own scores)
     int32_t bad = 0;
+    int64_t hc[2] = {0, 0};
     CUDA_TRY(cudaMemcpyAsync(&bad, P.bad_code, sizeof(int32_t), cudaMemcpyDeviceToHost, st));
+    CUDA_TRY(cudaMemcpyAsync(hc, P.counts, 2 * sizeof(int64_t), cudaMemcpyDeviceToHost, st));
     CUDA_TRY(cudaStreamSynchronize(st));
+    ctx->pairs16 = hc[0];
+    ctx->pairs32 = hc[1];
+    if (ctx->profile) {
+        float a = 0, b = 0;
+        cudaEventElapsedTime(&a, ctx->ev[0], ctx->ev[1]);
+        cudaEventElapsedTime(&b, ctx->ev[2], ctx->ev[3]);
+        ctx->dp_ms = a;
+        ctx->dp32_ms = b;
+    }
     if (bad) return fail(ANYSEQ_ERR_ALPHABET, "a letter code is >= alphabet (%d)", sc->alphabet);
     return ANYSEQ_OK;
 }
@@ -311,6 +344,7 @@ extern "C" anyseq_status_t anyseq_align_batch(anyseq_ctx *ctx, const uint8_t *q,
     anyseq_status_t s2 = ANYSEQ_OK;
 
     // offsets: stage, then read totals and maxima
+    ctx->launches = 0;
     BatchInput in;
     in.n_pairs = n_pairs;
     const void *dq_off, *ds_off;
@@ -324,6 +358,7 @@ extern "C" anyseq_status_t anyseq_align_batch(anyseq_ctx *ctx, const uint8_t *q,
     CUDA_TRY(cudaMemsetAsync(stats, 0, 3 * sizeof(int64_t), st));
     len_stats_kernel<<<grid_for(n_pairs) > 1024 ? 1024 : grid_for(n_pairs), 256, 0, st>>>(in.q_off, in.s_off, n_pairs, stats);
     CUDA_TRY(cudaGetLastError());
+    ctx->launches += 1;
     CUDA_TRY(cudaMemcpyAsync(hstats, stats, 3 * sizeof(int64_t), cudaMemcpyDeviceToHost, st));
     CUDA_TRY(cudaMemcpyAsync(&hstats[3], in.q_off + n_pairs, sizeof(int64_t), cudaMemcpyDeviceToHost, st));
     CUDA_TRY(cudaMemcpyAsync(&hstats[4], in.s_off + n_pairs, sizeof(int64_t), cudaMemcpyDeviceToHost, st));
@@ -359,6 +394,7 @@ extern "C" anyseq_status_t anyseq_align_batch(anyseq_ctx *ctx, const uint8_t *q,
     }
     write_results_kernel<<<grid_for(n_pairs), 256, 0, st>>>(n_pairs, score, eq, es, flags, dout);
     CUDA_TRY(cudaGetLastError());
+    ctx->launches += 1;
     if (!out_dev) {
         CUDA_TRY(cudaMemcpyAsync(out, dout, n_pairs * sizeof(anyseq_result_t), cudaMemcpyDeviceToHost, st));
         CUDA_TRY(cudaStreamSynchronize(st));

@@ -19,6 +19,12 @@ struct anyseq_ctx {
     size_t budget = 0;
     size_t used = 0;
     int force32 = 0;              // route every pair to 32-bit lanes (testing)
+    int profile = 0;              // time the DP kernels with events
+    cudaEvent_t ev[4] = {nullptr, nullptr, nullptr, nullptr};
+    // statistics of the last call
+    int64_t launches = 0;
+    double dp_ms = 0, dp32_ms = 0;
+    int64_t pairs16 = 0, pairs32 = 0;
     std::vector<Buf> bufs;        // device scratch, grown on demand, reused across calls
     std::vector<Buf> pinned;      // pinned host staging
     // Named device buffer of at least 'bytes'; contents are not preserved on growth.

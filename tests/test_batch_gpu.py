@@ -122,8 +122,8 @@ def test_self_alignment_and_identical_pairs(pkg, ctx):
 def test_int16_range_test_routes_to_int32(pkg, ctx):
     """Large match scores on long related pairs fail the int16 bound and must be
     computed in 32-bit lanes with exact results."""
-    b = synth.random_pairs(200, 300, 900, seed=500, related=1.0, p_sub=0.02, p_indel=0.01)
-    args = (60, -60, -60, -10)
+    b = synth.random_pairs(200, 500, 900, seed=500, related=1.0, p_sub=0.02, p_indel=0.01)
+    args = (40, -40, -40, -5)  # 40 * 500 > 16000: every pair fails the int16 bound
     for mode in MODES:
         res = run(pkg, ctx, b, args, mode)
         assert_parity(res, oracle_of(b, args, mode), b)
