@@ -173,19 +173,30 @@ anyseq_status_t anyseq::make_rowprof(const anyseq_scoring_t *sc, int32_t mode, u
 }
 
 __global__ void len_stats_kernel(const int64_t *q_off, const int64_t *s_off, int64_t n_pairs, int64_t *stats) {
-    // stats: [0] max n, [1] max m, [2] bad-offset flag
+    // stats: [0] max n, [1] max m, [2] bad-offset flag; one atomic per block
+    __shared__ unsigned long long red[3][32];
     int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    unsigned long long mn = 0, mm = 0;
-    int bad = 0;
+    unsigned long long mn = 0, mm = 0, bad = 0;
     for (; p < n_pairs; p += (int64_t)gridDim.x * blockDim.x) {
         int64_t n = q_off[p + 1] - q_off[p], m = s_off[p + 1] - s_off[p];
         if (n < 0 || m < 0 || n >= (1 << 21) || m >= (1 << 21)) bad = 1;
         if (n > (int64_t)mn) mn = (unsigned long long)n;
         if (m > (int64_t)mm) mm = (unsigned long long)m;
     }
-    if (bad) atomicOr(reinterpret_cast<unsigned long long *>(&stats[2]), 1ull);
-    atomicMax(reinterpret_cast<unsigned long long *>(&stats[0]), mn);
-    atomicMax(reinterpret_cast<unsigned long long *>(&stats[1]), mm);
+    for (int off = 16; off; off >>= 1) {
+        mn = max(mn, __shfl_xor_sync(0xffffffffu, mn, off));
+        mm = max(mm, __shfl_xor_sync(0xffffffffu, mm, off));
+        bad |= __shfl_xor_sync(0xffffffffu, bad, off);
+    }
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5, nw = blockDim.x >> 5;
+    if (lane == 0) { red[0][w] = mn; red[1][w] = mm; red[2][w] = bad; }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        for (int k = 1; k < nw; k++) { mn = max(mn, red[0][k]); mm = max(mm, red[1][k]); bad |= red[2][k]; }
+        if (bad) atomicOr(reinterpret_cast<unsigned long long *>(&stats[2]), 1ull);
+        atomicMax(reinterpret_cast<unsigned long long *>(&stats[0]), mn);
+        atomicMax(reinterpret_cast<unsigned long long *>(&stats[1]), mm);
+    }
 }
 
 __global__ void write_results_kernel(int64_t n, const int32_t *score, const int32_t *eq, const int32_t *es,
@@ -263,6 +274,7 @@ anyseq_status_t anyseq::batch_scores(anyseq_ctx *ctx, const BatchInput &in, cons
     P.s2 = arena<uint32_t>(ctx, "s2", (in.s_len + 15) / 16 + 2, &s2);
     P.bad_code = arena<int32_t>(ctx, "bad", 4, &s2);
     P.hist = arena<uint32_t>(ctx, "hist", 2 * 65536, &s2);
+    P.tile_sum = arena<uint32_t>(ctx, "tile_sum", 256, &s2);
     P.key = arena<uint32_t>(ctx, "key", n + 1, &s2);
     P.list16 = arena<int32_t>(ctx, "list16", n + 1, &s2);
     P.list32 = arena<int32_t>(ctx, "list32", n + 1, &s2);
@@ -280,7 +292,7 @@ anyseq_status_t anyseq::batch_scores(anyseq_ctx *ctx, const BatchInput &in, cons
     P.score = score; P.end_q = eq; P.end_s = es; P.flags = flags;
     P.force32 = ctx->force32;
     CUDA_TRY(launch_prep(P, st));
-    ctx->launches += 5;  // pack/validate x2, bin, scan, scatter
+    ctx->launches += 6;  // pack/validate x2, bin, tile sums, tile scan, scatter
 
     BatchArgs A;
     memset(&A, 0, sizeof(A));
@@ -356,7 +368,7 @@ extern "C" anyseq_status_t anyseq_align_batch(anyseq_ctx *ctx, const uint8_t *q,
     if (s2 != ANYSEQ_OK) return s2;
     int64_t hstats[5];
     CUDA_TRY(cudaMemsetAsync(stats, 0, 3 * sizeof(int64_t), st));
-    len_stats_kernel<<<grid_for(n_pairs) > 1024 ? 1024 : grid_for(n_pairs), 256, 0, st>>>(in.q_off, in.s_off, n_pairs, stats);
+    len_stats_kernel<<<grid_for(n_pairs) > 304 ? 304 : grid_for(n_pairs), 256, 0, st>>>(in.q_off, in.s_off, n_pairs, stats);
     CUDA_TRY(cudaGetLastError());
     ctx->launches += 1;
     CUDA_TRY(cudaMemcpyAsync(hstats, stats, 3 * sizeof(int64_t), cudaMemcpyDeviceToHost, st));

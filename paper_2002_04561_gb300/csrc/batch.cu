@@ -16,13 +16,14 @@ __device__ __noinline__ void run_slot(const BatchArgs &A, GroupSmem *sm, const S
                                       int nch, int Mit, int g, int64_t gslot, int32_t *res) {
     typedef typename C::T T;
     const int32_t o = A.o, e = A.e, oe = A.o + A.e;
-    const T e2 = C::make(e, e), oe2 = C::make(oe, oe);
+    const uint32_t e_raw = C::raw(e), oe_raw = C::raw(oe);   // per-half constants of DPX add-max
+    const uint32_t oe_c = C::cst(oe);                        // packed constant of IADD
     const T NEGv = C::make(C::NEG, C::NEG);
     const int CH = GROUP * R;
     const int S = Mit + GROUP - 1;
     int32_t *scr = A.scratch ? A.scratch + gslot * 2 * (int64_t)A.scratch_cols : nullptr;
 
-    // optimum candidates per half, as keys (larger wins)
+    // optimum candidates per half as keys (larger wins)
     uint64_t best[2];
 #pragma unroll
     for (int h = 0; h < 2; h++) best[h] = end_key(0, 0, MODE == SEMIGLOBAL ? sl.m[h] : 0);
@@ -33,25 +34,26 @@ __device__ __noinline__ void run_slot(const BatchArgs &A, GroupSmem *sm, const S
         const int32_t rb = ch * CH + g * R + 1;  // padded row of register 0
         uint32_t profA[R], profB[R];
         T Hoe[R], F[R];
-        T rowmax[R];
-        uint32_t rowj[R];
+        T rowmax[MODE == LOCAL ? R : 1];
+        uint32_t rowj[MODE == LOCAL ? R : 1];   // first column of the row maximum (int16x2: one per half)
 #pragma unroll
         for (int r = 0; r < R; r++) {
-            int32_t h0[2];
-            uint32_t pw[2];
+            int32_t h0[2] = {0, 0};
+            uint32_t pw[2] = {A.rowprof[4], A.rowprof[4]};
 #pragma unroll
             for (int h = 0; h < C::PAIRS; h++) {
                 int32_t i = rb + r - sl.pad[h];
-                pw[h] = A.rowprof[4];
                 if (i >= 1 && sl.n[h] > 0) pw[h] = A.rowprof[letter(A.q2, sl.q0[h], sl.n[h], i - 1, sl.rev[h])];
                 h0[h] = col0(MODE, i, o, e, sl.tb[h]) + oe;
             }
             profA[r] = pw[0];
-            profB[r] = C::PAIRS == 2 ? pw[1] : pw[0];
-            Hoe[r] = C::make(h0[0], C::PAIRS == 2 ? h0[1] : h0[0]);
+            profB[r] = pw[1];
+            Hoe[r] = C::make(h0[0], h0[1]);
             F[r] = NEGv;
-            rowmax[r] = C::make(0, 0);
-            rowj[r] = 0;
+            if (MODE == LOCAL) {
+                rowmax[r] = C::make(oe, oe);  // Hoe of H = 0
+                rowj[r] = 0;
+            }
         }
         T diag0;
         {
@@ -60,11 +62,9 @@ __device__ __noinline__ void run_slot(const BatchArgs &A, GroupSmem *sm, const S
             for (int h = 0; h < 2; h++) d[h] = col0(MODE, rb - 1 - sl.pad[h], o, e, sl.tb[h]) + oe;
             diag0 = C::make(d[0], d[1]);
         }
-        // semi-global last-row tracking (lane 15, last chunk)
-        T lr_best = C::make(0, 0);
-        uint32_t lr_j = 0;
 
-        // --- ring fill / flush helpers (warp-cooperative, 16 lanes per group)
+        // --- ring fill (selectors, border of the previous chunk) and drain of
+        //     the bottom ring (border of this chunk, or the query's last row)
         auto fill = [&](int blk) {
 #pragma unroll
             for (int k = 0; k < 2; k++) {
@@ -81,13 +81,27 @@ __device__ __noinline__ void run_slot(const BatchArgs &A, GroupSmem *sm, const S
                 }
             }
         };
-        auto flush = [&](int blk) {
+        auto drain = [&](int blk) {
 #pragma unroll
             for (int k = 0; k < 2; k++) {
                 int c = blk * BLOCK + g + 16 * k;
                 if (blk >= 0 && c < Mit) {
-                    scr[2 * c] = sm->bot[2 * (c & (RING - 1))];
-                    scr[2 * c + 1] = sm->bot[2 * (c & (RING - 1)) + 1];
+                    int32_t hv = sm->bot[2 * (c & (RING - 1))];
+                    if (!last) {
+                        scr[2 * c] = hv;
+                        scr[2 * c + 1] = sm->bot[2 * (c & (RING - 1)) + 1];
+                    } else if (MODE != LOCAL) {
+                        // H(n, c+1) of each half: semi-global last-row candidate / global score
+#pragma unroll
+                        for (int h = 0; h < C::PAIRS; h++) {
+                            int32_t H = C::get(C::from_u((uint32_t)hv), h) - oe;
+                            if (MODE == SEMIGLOBAL && c < sl.m[h]) {
+                                uint64_t key = end_key(H, sl.n[h], c + 1);
+                                best[h] = key > best[h] ? key : best[h];
+                            }
+                            if (MODE == GLOBAL && c == sl.m[h] - 1) gscore[h] = H;
+                        }
+                    }
                 }
             }
         };
@@ -95,7 +109,7 @@ __device__ __noinline__ void run_slot(const BatchArgs &A, GroupSmem *sm, const S
         __syncwarp();
         fill(0);
         __syncwarp();
-        int flushed = 0;  // next bottom block to flush
+        int drained = 0;  // next bottom block to drain
 
         T last_hoe = NEGv, last_e = NEGv, prev_up = diag0;
         for (int s = 0; s < S; s++) {
@@ -103,17 +117,19 @@ __device__ __noinline__ void run_slot(const BatchArgs &A, GroupSmem *sm, const S
                 __syncwarp();
                 int k = s / BLOCK;
                 fill(k + 1);
-                if (!last && k - 2 >= flushed) { flush(k - 2); flushed = k - 1; }
+                if (k - 2 >= drained) { drain(k - 2); drained = k - 1; }
                 __syncwarp();
             }
             const int c = s - g;
+            // from lane g-1: Hoe of its last row and E of this lane's first row, column c
             T up_hoe = C::from_u(__shfl_up_sync(0xffffffffu, C::as_u(last_hoe), 1, GROUP));
             T up_e = C::from_u(__shfl_up_sync(0xffffffffu, C::as_u(last_e), 1, GROUP));
             if (g == 0) {
                 if (ch == 0) {
+                    // row 0: H(0, c+1); E below row 0 comes from H only (E(0, .) = -inf)
                     int32_t v = (MODE == GLOBAL ? o + (c + 1) * e : 0) + oe;
                     up_hoe = C::make(v, v);
-                    up_e = NEGv;
+                    up_e = up_hoe;
                 } else if (c >= 0 && c < Mit) {
                     up_hoe = C::from_u((uint32_t)sm->top[2 * (c & (RING - 1))]);
                     up_e = C::from_u((uint32_t)sm->top[2 * (c & (RING - 1)) + 1]);
@@ -123,51 +139,45 @@ __device__ __noinline__ void run_slot(const BatchArgs &A, GroupSmem *sm, const S
                 const uint32_t sel = sm->sel[c & (RING - 1)];
                 T diag = (c == 0) ? diag0 : prev_up;
                 prev_up = up_hoe;
-                T hu = up_hoe, eu = up_e;
+                T E = up_e;
                 uint32_t valid = 0, jj = 0;
                 if (MODE == LOCAL) {
                     valid = C::PAIRS == 2 ? ((c < sl.m[0] ? 0xFFFFu : 0u) | (c < sl.m[1] ? 0xFFFF0000u : 0u))
                                           : (c < sl.m[0] ? 0xFFFFFFFFu : 0u);
-                    jj = C::PAIRS == 2 ? ((uint32_t)(c + 1) | ((uint32_t)(c + 1) << 16)) : (uint32_t)(c + 1);
+                    jj = C::PAIRS == 2 ? (uint32_t)(c + 1) * 65537u : (uint32_t)(c + 1);
                 }
 #pragma unroll
                 for (int r = 0; r < R; r++) {
+                    // H(i,j) = max(H(i-1,j-1)+sigma, E(i,j), F(i,j) [,0]) kept as Hoe = H + o + e
                     T sg = C::sigma(profA[r], profB[r], sel);
-                    T En = C::addmax(eu, e2, hu);
-                    T Fn = C::addmax(F[r], e2, Hoe[r]);
-                    T Hd = C::add(diag, sg);
-                    T H = (MODE == LOCAL) ? C::max3relu(Hd, En, Fn) : C::max3(Hd, En, Fn);
+                    T Ad = C::addc(diag, C::as_u(sg));                 // H(i-1,j-1) + sigma
+                    F[r] = C::addmax(F[r], e_raw, Hoe[r]);             // Eq. 5
+                    T M = (MODE == LOCAL) ? C::maxrelu(Ad, F[r]) : C::vmax(Ad, F[r]);
+                    T X = C::addc(M, oe_c);                           // max(diag, F) + o + e
                     diag = Hoe[r];
-                    T Hn = C::add(H, oe2);
-                    Hoe[r] = Hn;
-                    F[r] = Fn;
-                    hu = Hn;
-                    eu = En;
+                    Hoe[r] = C::addmax(E, oe_raw, X);                  // H + o + e
+                    E = C::addmax(E, e_raw, X);                        // Eq. 4 for row i+1
                     if (MODE == LOCAL) {
-                        T Hm = C::from_u(C::as_u(H) & valid);
-                        uint32_t gm = C::gt(Hm, rowmax[r]);
-                        rowmax[r] = C::vmax(rowmax[r], Hm);
+                        // strict improvement of the row maximum at a valid column
+                        uint32_t gm;
+                        if (C::PAIRS == 2) {
+                            // invalid columns read -16000 (biased 16768): within 2^15 of every row maximum
+                            uint32_t Hm = (C::as_u(Hoe[r]) & valid) | (0x41804180u & ~valid);
+                            // per half: Hm - rowmax - 1 + 2^15 keeps bit 15 iff Hm > rowmax
+                            uint32_t d = Hm + 0x7FFF7FFFu - C::as_u(rowmax[r]);
+                            gm = prmt(d, 0u, 0xBB99u);                        // sign of bytes 1, 3 -> halves
+                            rowmax[r] = C::vmax(rowmax[r], C::from_u(Hm));
+                        } else {
+                            int32_t Hm = valid ? (int32_t)C::as_u(Hoe[r]) : (int32_t)C::NEG;
+                            gm = Hm > (int32_t)C::as_u(rowmax[r]) ? 0xFFFFFFFFu : 0u;
+                            rowmax[r] = C::vmax(rowmax[r], C::from_u((uint32_t)Hm));
+                        }
                         rowj[r] = (jj & gm) | (rowj[r] & ~gm);
                     }
                 }
-                last_hoe = hu;
-                last_e = eu;
-                // last row of the query: lane 15, last register, last chunk
-                if (MODE != LOCAL && last && g == GROUP - 1) {
-                    T H = C::add(hu, C::make(-oe, -oe));
-                    if (MODE == SEMIGLOBAL) {
-                        uint32_t v = C::PAIRS == 2 ? ((c < sl.m[0] ? 0xFFFFu : 0u) | (c < sl.m[1] ? 0xFFFF0000u : 0u))
-                                                   : (c < sl.m[0] ? 0xFFFFFFFFu : 0u);
-                        uint32_t gm = C::gt(H, lr_best) & v;
-                        lr_best = C::from_u((C::as_u(H) & gm) | (C::as_u(lr_best) & ~gm));
-                        uint32_t j2 = C::PAIRS == 2 ? ((uint32_t)(c + 1) | ((uint32_t)(c + 1) << 16)) : (uint32_t)(c + 1);
-                        lr_j = (j2 & gm) | (lr_j & ~gm);
-                    } else {
-                        if (c == sl.m[0] - 1) gscore[0] = C::get(H, 0);
-                        if (C::PAIRS == 2 && c == sl.m[1] - 1) gscore[1] = C::get(H, 1);
-                    }
-                }
-                if (!last && g == GROUP - 1) {
+                last_hoe = Hoe[R - 1];
+                last_e = E;
+                if (g == GROUP - 1) {
                     sm->bot[2 * (c & (RING - 1))] = (int32_t)C::as_u(last_hoe);
                     sm->bot[2 * (c & (RING - 1)) + 1] = (int32_t)C::as_u(last_e);
                 }
@@ -180,8 +190,7 @@ __device__ __noinline__ void run_slot(const BatchArgs &A, GroupSmem *sm, const S
                             for (int r = 0; r < R; r++) {
                                 int32_t i = rb + r - sl.pad[h];
                                 if (i >= 1) {
-                                    int32_t hv = C::get(Hoe[r], h) - oe;
-                                    uint64_t k = end_key(hv, i, sl.m[h]);
+                                    uint64_t k = end_key(C::get(Hoe[r], h) - oe, i, sl.m[h]);
                                     best[h] = k > best[h] ? k : best[h];
                                 }
                             }
@@ -190,12 +199,9 @@ __device__ __noinline__ void run_slot(const BatchArgs &A, GroupSmem *sm, const S
                 }
             }
         }
-        if (!last) {
-            __syncwarp();
-            int kend = (Mit - 1) / BLOCK;
-            for (int b = flushed; b <= kend; b++) flush(b);
-            __syncwarp();
-        }
+        __syncwarp();
+        for (int b = drained; b <= (Mit - 1) / BLOCK; b++) drain(b);
+        __syncwarp();
         if (MODE == LOCAL) {
 #pragma unroll
             for (int h = 0; h < C::PAIRS; h++) {
@@ -203,7 +209,7 @@ __device__ __noinline__ void run_slot(const BatchArgs &A, GroupSmem *sm, const S
                 for (int r = 0; r < R; r++) {
                     int32_t i = rb + r - sl.pad[h];
                     if (i >= 1) {
-                        int32_t v = C::get(rowmax[r], h);
+                        int32_t v = C::get(rowmax[r], h) - oe;
                         int32_t j = C::PAIRS == 2 ? (int32_t)((rowj[r] >> (16 * h)) & 0xFFFFu) : (int32_t)rowj[r];
                         if (v > 0) {
                             uint64_t k = end_key(v, i, j);
@@ -211,15 +217,6 @@ __device__ __noinline__ void run_slot(const BatchArgs &A, GroupSmem *sm, const S
                         }
                     }
                 }
-            }
-        }
-        if (MODE == SEMIGLOBAL && last && g == GROUP - 1) {
-#pragma unroll
-            for (int h = 0; h < C::PAIRS; h++) {
-                int32_t v = C::get(lr_best, h);
-                int32_t j = C::PAIRS == 2 ? (int32_t)((lr_j >> (16 * h)) & 0xFFFFu) : (int32_t)lr_j;
-                uint64_t k = end_key(v, sl.n[h], j);
-                best[h] = k > best[h] ? k : best[h];
             }
         }
     }
@@ -231,7 +228,9 @@ __device__ __noinline__ void run_slot(const BatchArgs &A, GroupSmem *sm, const S
             uint64_t other = __shfl_xor_sync(0xffffffffu, best[h], off, GROUP);
             best[h] = other > best[h] ? other : best[h];
         }
-        int32_t gs = __shfl_sync(0xffffffffu, gscore[h], GROUP - 1, GROUP);
+        int32_t gs = gscore[h];
+#pragma unroll
+        for (int off = 8; off >= 1; off >>= 1) gs |= __shfl_xor_sync(0xffffffffu, gs, off, GROUP);
         if (MODE == GLOBAL) {
             res[3 * h] = gs;
             res[3 * h + 1] = sl.n[h];
@@ -283,7 +282,9 @@ __global__ void __launch_bounds__(256, 2) batch_kernel(BatchArgs A) {
                 }
             }
         }
-        int nch = (nmax + 255) / 256;
+        // rows per lane: at most 16 (12 for local int16x2, which also keeps per-row maxima)
+        constexpr int RMAX = (MODE == LOCAL && C::PAIRS == 2) ? 12 : 16;
+        int nch = (nmax + GROUP * RMAX - 1) / (GROUP * RMAX);
         int R = (nmax + GROUP * nch - 1) / (GROUP * nch);
         R += R & 1;
         if (R < 2) R = 2;
@@ -298,8 +299,8 @@ __global__ void __launch_bounds__(256, 2) batch_kernel(BatchArgs A) {
             case 8: run_slot<C, MODE, 8>(A, sm, sl, nch, Mit, g, gslot, res); break;
             case 10: run_slot<C, MODE, 10>(A, sm, sl, nch, Mit, g, gslot, res); break;
             case 12: run_slot<C, MODE, 12>(A, sm, sl, nch, Mit, g, gslot, res); break;
-            case 14: run_slot<C, MODE, 14>(A, sm, sl, nch, Mit, g, gslot, res); break;
-            default: run_slot<C, MODE, 16>(A, sm, sl, nch, Mit, g, gslot, res); break;
+            case 14: run_slot<C, MODE, (RMAX < 14 ? RMAX : 14)>(A, sm, sl, nch, Mit, g, gslot, res); break;
+            default: run_slot<C, MODE, RMAX>(A, sm, sl, nch, Mit, g, gslot, res); break;
         }
         if (g == 0) {
 #pragma unroll

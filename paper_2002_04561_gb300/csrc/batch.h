@@ -34,6 +34,7 @@ struct PrepArgs {
     int32_t smax, smin, o, e, mode;
     // binning
     uint32_t *hist;                 // 2 * 65536 bucket counters
+    uint32_t *tile_sum;             // 128 per-tile sums of the bucket scan
     uint32_t *key;                  // per pair bucket (or 0xFFFFFFFF: trivial pair)
     int32_t *list16, *list32;       // sorted outputs
     int64_t *counts;                // [0] int16 pairs, [1] int32 pairs, [2] trivial pairs

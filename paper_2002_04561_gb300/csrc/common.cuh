@@ -26,55 +26,66 @@ __device__ __forceinline__ uint32_t prmt(uint32_t a, uint32_t b, uint32_t sel) {
     return d;
 }
 
-// One 32-bit score lane holding one pair.
+// Score lanes. Both traits keep the same six-step cell (see engine.cuh) and
+// split it between the two integer pipes of the SM: the additions of a
+// constant go to full-rate 32-bit IADD, the maxima to the half-rate DPX/VIMNMX
+// instructions (measured on sm_103: every max-type integer instruction issues
+// at 64 lanes per clock per SM, IADD at 128).
+
+// One signed 32-bit lane per pair.
 struct CellI32 {
     typedef int32_t T;
     static constexpr int PAIRS = 1;
     static constexpr int32_t NEG = NEG32;
-    __device__ __forceinline__ static T add(T a, T b) { return a + b; }
-    __device__ __forceinline__ static T addmax(T a, T b, T c) { return __viaddmax_s32(a, b, c); }
-    __device__ __forceinline__ static T max3(T a, T b, T c) { return __vimax3_s32(a, b, c); }
-    __device__ __forceinline__ static T max3relu(T a, T b, T c) { return __vimax3_s32_relu(a, b, c); }
-    __device__ __forceinline__ static T vmax(T a, T b) { return max(a, b); }
     __device__ __forceinline__ static T make(int32_t lo, int32_t hi) { (void)hi; return lo; }
     __device__ __forceinline__ static int32_t get(T v, int h) { (void)h; return v; }
-    // sigma from a row profile word (4 int8 scores indexed by subject code)
+    // packed constant for addc (a plain signed 32-bit value here)
+    __host__ __device__ __forceinline__ static uint32_t cst(int32_t c) { return (uint32_t)c; }
+    __device__ __forceinline__ static T addc(T a, uint32_t c) { return a + (int32_t)c; }
+    // raw per-lane constant for addmax
+    __device__ __forceinline__ static uint32_t raw(int32_t c) { return (uint32_t)c; }
+    __device__ __forceinline__ static T addmax(T a, uint32_t b, T c) { return __viaddmax_s32(a, (int32_t)b, c); }
+    __device__ __forceinline__ static T vmax(T a, T b) { return max(a, b); }
+    __device__ __forceinline__ static T maxrelu(T a, T b) { return __vimax_s32_relu(a, b); }
+    // sigma' >= 0 from a row profile word (4 bytes indexed by subject letter)
     __device__ __forceinline__ static T sigma(uint32_t pa, uint32_t pb, uint32_t sel) {
         (void)pb; return (int32_t)prmt(pa, pa, sel);
     }
-    // selector that sign-extends byte code_a of the row profile to 32 bits
     __device__ __forceinline__ static uint32_t selector(uint32_t ca, uint32_t cb) {
         (void)cb;
         uint32_t sgn = ca | 8u;
         return ca | (sgn << 4) | (sgn << 8) | (sgn << 12);
     }
-    // mask (all ones per half) where a > b
-    __device__ __forceinline__ static uint32_t gt(T a, T b) { return a > b ? 0xFFFFFFFFu : 0u; }
     __device__ __forceinline__ static uint32_t as_u(T v) { return (uint32_t)v; }
     __device__ __forceinline__ static T from_u(uint32_t v) { return (int32_t)v; }
 };
 
-// Two int16 score halves: the low half holds pair A, the high half pair B.
+// Two int16 halves per 32-bit word (low: pair A, high: pair B), each stored
+// with a bias of 2^15 as an unsigned 16-bit number. With every value inside
+// [-32768, 32767] a 32-bit IADD of a packed constant never carries or borrows
+// across the halves, so constant additions run on the full-rate adder while
+// the unsigned per-half maxima use VIMNMX/DPX.
 struct CellI16x2 {
     typedef uint32_t T;
     static constexpr int PAIRS = 2;
     static constexpr int32_t NEG = NEG16;
-    __device__ __forceinline__ static T add(T a, T b) { return __vadd2(a, b); }
-    __device__ __forceinline__ static T addmax(T a, T b, T c) { return __viaddmax_s16x2(a, b, c); }
-    __device__ __forceinline__ static T max3(T a, T b, T c) { return __vimax3_s16x2(a, b, c); }
-    __device__ __forceinline__ static T max3relu(T a, T b, T c) { return __vimax3_s16x2_relu(a, b, c); }
-    __device__ __forceinline__ static T vmax(T a, T b) { return __vmaxs2(a, b); }
     __device__ __forceinline__ static T make(int32_t lo, int32_t hi) {
-        return ((uint32_t)lo & 0xFFFFu) | ((uint32_t)hi << 16);
+        return ((uint32_t)(lo + 32768) & 0xFFFFu) | (((uint32_t)(hi + 32768) & 0xFFFFu) << 16);
     }
-    __device__ __forceinline__ static int32_t get(T v, int h) { return (int32_t)(int16_t)(v >> (16 * h)); }
+    __device__ __forceinline__ static int32_t get(T v, int h) { return (int32_t)((v >> (16 * h)) & 0xFFFFu) - 32768; }
+    __host__ __device__ __forceinline__ static uint32_t cst(int32_t c) { return (uint32_t)(c * 65537); }
+    __device__ __forceinline__ static T addc(T a, uint32_t c) { return a + c; }
+    __device__ __forceinline__ static uint32_t raw(int32_t c) { return ((uint32_t)c & 0xFFFFu) * 65537u; }
+    __device__ __forceinline__ static T addmax(T a, uint32_t b, T c) { return __viaddmax_u16x2(a, b, c); }
+    __device__ __forceinline__ static T vmax(T a, T b) { return __vmaxu2(a, b); }
+    __device__ __forceinline__ static T maxrelu(T a, T b) { return __vimax3_u16x2(a, b, 0x80008000u); }
     __device__ __forceinline__ static T sigma(uint32_t pa, uint32_t pb, uint32_t sel) { return prmt(pa, pb, sel); }
-    // low half: byte ca of pa sign-extended; high half: byte cb of pb sign-extended
+    // low half: byte ca of pa, high half: byte cb of pb; bytes are >= 0 so the
+    // sign replication fills zeros
     __device__ __forceinline__ static uint32_t selector(uint32_t ca, uint32_t cb) {
         uint32_t b4 = cb + 4u;
         return ca | ((ca | 8u) << 4) | (b4 << 8) | ((b4 | 8u) << 12);
     }
-    __device__ __forceinline__ static uint32_t gt(T a, T b) { return __vcmpgts2(a, b); }
     __device__ __forceinline__ static uint32_t as_u(T v) { return v; }
     __device__ __forceinline__ static T from_u(uint32_t v) { return v; }
 };

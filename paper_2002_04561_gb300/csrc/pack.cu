@@ -68,8 +68,13 @@ __device__ __forceinline__ bool fits_int16(int64_t n, int64_t m, int32_t smax, i
 }
 
 __global__ void bin_kernel(PrepArgs P) {
-    int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    for (; p < P.n_pairs; p += (int64_t)gridDim.x * blockDim.x) {
+    // grid-stride loop with a warp-uniform trip count (the shuffles below need the whole warp)
+    unsigned long long local[2] = {0, 0};
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    const int64_t base = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    for (int64_t p0 = (int64_t)blockIdx.x * blockDim.x; p0 < P.n_pairs; p0 += stride) {
+        const int64_t p = p0 + (base - (int64_t)blockIdx.x * blockDim.x);
+        if (p >= P.n_pairs) continue;
         int64_t n = P.q_off[p + 1] - P.q_off[p];
         int64_t m = P.s_off[p + 1] - P.s_off[p];
         if (n == 0 || m == 0) {
@@ -88,38 +93,70 @@ __global__ void bin_kernel(PrepArgs P) {
         uint32_t k = prec * NBUCKET + (lbucket(n) << 8) + lbucket(m);
         P.key[p] = k;
         atomicAdd(&P.hist[k], 1u);
-        atomicAdd(reinterpret_cast<unsigned long long *>(&P.counts[prec]), 1ull);
+        local[prec]++;
+    }
+    // one counter update per warp and class
+#pragma unroll
+    for (int c = 0; c < 2; c++) {
+        unsigned long long v = local[c];
+        for (int off = 16; off; off >>= 1) v += __shfl_xor_sync(0xffffffffu, v, off);
+        if ((threadIdx.x & 31) == 0 && v) atomicAdd(reinterpret_cast<unsigned long long *>(&P.counts[c]), v);
     }
 }
 
 // Exclusive offsets in DESCENDING key order within each precision class, in
-// place: hist[k] becomes the first list position of bucket k. One block.
-__global__ void scan_kernel(uint32_t *hist) {
-    __shared__ uint32_t part[1024];
-    const int t = threadIdx.x;
-    for (int cls = 0; cls < 2; cls++) {
-        uint32_t *h = hist + cls * NBUCKET;
-        const int per = NBUCKET / 1024;  // 64 buckets per thread, descending
-        // thread t owns reversed indices [t*per, (t+1)*per): key = NBUCKET-1-idx
-        uint32_t sum = 0;
-        for (int k = 0; k < per; k++) sum += h[NBUCKET - 1 - (t * per + k)];
-        part[t] = sum;
-        __syncthreads();
-        for (int off = 1; off < 1024; off <<= 1) {
-            uint32_t v = t >= off ? part[t - off] : 0u;
-            __syncthreads();
-            part[t] += v;
-            __syncthreads();
-        }
-        uint32_t run = part[t] - sum;
-        for (int k = 0; k < per; k++) {
-            int key = NBUCKET - 1 - (t * per + k);
-            uint32_t c = h[key];
-            h[key] = run;
-            run += c;
-        }
-        __syncthreads();
+// place: hist[k] becomes the first list position of bucket k. Two passes over
+// tiles of 1024 buckets (reversed order inside a class): tile sums, then a
+// block scan per tile offset by the sums of the earlier tiles of its class.
+constexpr int SCAN_TILE = 1024;
+constexpr int TILES_PER_CLASS = NBUCKET / SCAN_TILE;
+
+__device__ __forceinline__ uint32_t *tile_bucket(uint32_t *hist, int tile, int x) {
+    int cls = tile / TILES_PER_CLASS, t = tile % TILES_PER_CLASS;
+    return hist + cls * NBUCKET + (NBUCKET - 1 - (t * SCAN_TILE + x));
+}
+
+__global__ void tile_sum_kernel(uint32_t *hist, uint32_t *tile_sum) {
+    __shared__ uint32_t red[32];
+    uint32_t v = *tile_bucket(hist, blockIdx.x, threadIdx.x);
+    for (int off = 16; off; off >>= 1) v += __shfl_xor_sync(0xffffffffu, v, off);
+    if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = v;
+    __syncthreads();
+    if (threadIdx.x < 32) {
+        uint32_t w = red[threadIdx.x];
+        for (int off = 16; off; off >>= 1) w += __shfl_xor_sync(0xffffffffu, w, off);
+        if (threadIdx.x == 0) tile_sum[blockIdx.x] = w;
     }
+}
+
+__global__ void tile_scan_kernel(uint32_t *hist, const uint32_t *tile_sum) {
+    __shared__ uint32_t warp_tot[32];
+    __shared__ uint32_t base;
+    const int tile = blockIdx.x, x = threadIdx.x, lane = x & 31, w = x >> 5;
+    if (x == 0) {
+        uint32_t b = 0;
+        int first = (tile / TILES_PER_CLASS) * TILES_PER_CLASS;
+        for (int t = first; t < tile; t++) b += tile_sum[t];
+        base = b;
+    }
+    uint32_t *cell = tile_bucket(hist, tile, x);
+    uint32_t v = *cell, inc = v;
+    for (int off = 1; off < 32; off <<= 1) {
+        uint32_t y = __shfl_up_sync(0xffffffffu, inc, off);
+        if (lane >= off) inc += y;
+    }
+    if (lane == 31) warp_tot[w] = inc;
+    __syncthreads();
+    if (w == 0) {
+        uint32_t t = warp_tot[lane], ti = t;
+        for (int off = 1; off < 32; off <<= 1) {
+            uint32_t y = __shfl_up_sync(0xffffffffu, ti, off);
+            if (lane >= off) ti += y;
+        }
+        warp_tot[lane] = ti - t;
+    }
+    __syncthreads();
+    *cell = base + warp_tot[w] + inc - v;
 }
 
 __global__ void scatter_kernel(PrepArgs P) {
@@ -147,7 +184,8 @@ cudaError_t launch_prep(const PrepArgs &P, cudaStream_t st) {
         validate_kernel<<<blocks(P.s_len), T, 0, st>>>(P.s, P.s_len, P.alphabet, P.bad_code);
     }
     bin_kernel<<<blocks(P.n_pairs), T, 0, st>>>(P);
-    scan_kernel<<<1, 1024, 0, st>>>(P.hist);
+    tile_sum_kernel<<<2 * TILES_PER_CLASS, SCAN_TILE, 0, st>>>(P.hist, P.tile_sum);
+    tile_scan_kernel<<<2 * TILES_PER_CLASS, SCAN_TILE, 0, st>>>(P.hist, P.tile_sum);
     scatter_kernel<<<blocks(P.n_pairs), T, 0, st>>>(P);
     return cudaGetLastError();
 }
