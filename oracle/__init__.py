@@ -84,6 +84,11 @@ class Scoring:
     matrix: np.ndarray | None = None
     alphabet: int = 4
 
+    def __post_init__(self):
+        # a matrix fixes the alphabet (its row stride in the C arrays)
+        if self.matrix is not None:
+            self.alphabet = int(np.asarray(self.matrix).shape[0])
+
     def _c(self):
         mat = None
         if self.matrix is not None:

@@ -10,6 +10,9 @@
 #include "api_internal.h"
 #include "batch.h"
 #include "common.cuh"
+#include "scan.h"
+#include "tb.h"
+#include "wave.h"
 
 using namespace anyseq;
 
@@ -89,6 +92,7 @@ extern "C" anyseq_status_t anyseq_destroy(anyseq_ctx *ctx) {
 extern "C" anyseq_status_t anyseq_set_option(anyseq_ctx *ctx, const char *key, int64_t value) {
     if (!ctx || !key) return fail(ANYSEQ_ERR_ARG, "ctx or key is NULL");
     if (!strcmp(key, "force_int32")) { ctx->force32 = value != 0; return ANYSEQ_OK; }
+    if (!strcmp(key, "force_matrix_path")) { ctx->force_matrix = value != 0; return ANYSEQ_OK; }
     if (!strcmp(key, "profile")) {
         ctx->profile = value != 0;
         if (ctx->profile && !ctx->ev[0])
@@ -162,9 +166,7 @@ anyseq_status_t anyseq::make_rowprof(const anyseq_scoring_t *sc, int32_t mode, u
             int32_t sg;
             if (a < 4) sg = (a < sc->alphabet && b < sc->alphabet) ? sigma_host(sc, a, b) : 0;
             else sg = mode == ANYSEQ_GLOBAL ? sc->gap_extend : 0;
-            int32_t v = sg - oe;
-            if (v < -128 || v > 127)
-                return fail(ANYSEQ_ERR_ARG, "sigma - open - extend = %d does not fit the int8 row profile", v);
+            int32_t v = sg - oe;  // range checked by the caller
             w |= (uint32_t)(uint8_t)(int8_t)v << (8 * b);
         }
         prof[a] = w;
@@ -200,18 +202,19 @@ __global__ void len_stats_kernel(const int64_t *q_off, const int64_t *s_off, int
 }
 
 __global__ void write_results_kernel(int64_t n, const int32_t *score, const int32_t *eq, const int32_t *es,
-                                     const uint32_t *flags, anyseq_result_t *out) {
+                                     const uint32_t *flags, const int32_t *bq, const int32_t *bs,
+                                     const int64_t *coff, const int64_t *clen, anyseq_result_t *out) {
     int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     for (; p < n; p += (int64_t)gridDim.x * blockDim.x) {
         anyseq_result_t r;
         r.score = score[p];
-        r.beg_q = -1;
-        r.beg_s = -1;
+        r.beg_q = bq ? bq[p] : -1;
+        r.beg_s = bs ? bs[p] : -1;
         r.end_q = eq[p];
         r.end_s = es[p];
         r.flags = flags[p];
-        r.cigar_off = 0;
-        r.cigar_len = 0;
+        r.cigar_off = coff ? (uint64_t)coff[p] : 0;
+        r.cigar_len = clen ? (uint32_t)clen[p] : 0;
         r.reserved = 0;
         out[p] = r;
     }
@@ -261,10 +264,11 @@ static T *arena(anyseq_ctx *ctx, const char *name, size_t count, anyseq_status_t
 }
 
 anyseq_status_t anyseq::batch_scores(anyseq_ctx *ctx, const BatchInput &in, const anyseq_scoring_t *sc, int32_t mode,
-                                     int32_t *score, int32_t *eq, int32_t *es, uint32_t *flags, cudaStream_t st) {
+                                     int32_t *score, int32_t *eq, int32_t *es, uint32_t *flags, cudaStream_t st,
+                                     TbOut *tb) {
     anyseq_status_t s2 = ANYSEQ_OK;
     const int64_t n = in.n_pairs;
-    if (sc->alphabet > 4) return fail(ANYSEQ_ERR_ARG, "alphabets above 4 letters need the profile path (not built)");
+    const int sigp = (sc->alphabet > 4 || ctx->force_matrix) ? 1 : 0;
     PrepArgs P;
     memset(&P, 0, sizeof(P));
     P.q = in.q; P.s = in.s; P.q_off = in.q_off; P.s_off = in.s_off;
@@ -290,33 +294,87 @@ anyseq_status_t anyseq::batch_scores(anyseq_ctx *ctx, const BatchInput &in, cons
         }
     P.smax = smax; P.smin = smin; P.o = sc->gap_open; P.e = sc->gap_extend; P.mode = mode;
     P.score = score; P.end_q = eq; P.end_s = es; P.flags = flags;
-    P.force32 = ctx->force32;
+    // sigma' = sigma - open - extend must be an int8; int16x2 lanes also need it >= 0
+    int32_t sp_min = 1 << 30, sp_max = -(1 << 30);
+    const int32_t oe = sc->gap_open + sc->gap_extend;
+    const int32_t sig_pad = (mode == ANYSEQ_GLOBAL ? sc->gap_extend : 0) - oe;
+    for (int a = 0; a < sc->alphabet; a++)
+        for (int b = 0; b < sc->alphabet; b++) {
+            int32_t v = sigma_host(sc, a, b) - oe;
+            sp_min = v < sp_min ? v : sp_min;
+            sp_max = v > sp_max ? v : sp_max;
+        }
+    sp_min = sig_pad < sp_min ? sig_pad : sp_min;
+    sp_max = sig_pad > sp_max ? sig_pad : sp_max;
+    if (sp_min < -128 || sp_max > 127)
+        return fail(ANYSEQ_ERR_ARG, "sigma - open - extend spans [%d, %d], outside the int8 profile", sp_min, sp_max);
+    P.force32 = ctx->force32 || sp_min < 0;
     CUDA_TRY(launch_prep(P, st));
     ctx->launches += 6;  // pack/validate x2, bin, tile sums, tile scan, scatter
 
     BatchArgs A;
     memset(&A, 0, sizeof(A));
     A.q2 = P.q2; A.s2 = P.s2; A.q_off = in.q_off; A.s_off = in.s_off;
-    TRY(make_rowprof(sc, mode, A.rowprof));
+    if (!sigp) TRY(make_rowprof(sc, mode, A.rowprof));
+    A.q8 = in.q;
+    A.s8 = in.s;
+    A.alphabet = sc->alphabet;
+    A.sig_pad = sig_pad;
+    if (sigp) {
+        int8_t htab[32 * 32];
+        for (int a = 0; a < sc->alphabet; a++)
+            for (int b = 0; b < sc->alphabet; b++) htab[a * sc->alphabet + b] = (int8_t)(sigma_host(sc, a, b) - oe);
+        int8_t *dtab = arena<int8_t>(ctx, "sig_tab", 32 * 32, &s2);
+        if (s2 != ANYSEQ_OK) return s2;
+        CUDA_TRY(cudaMemcpyAsync(dtab, htab, sc->alphabet * sc->alphabet, cudaMemcpyHostToDevice, st));
+        A.sig_tab = dtab;
+    }
     A.o = sc->gap_open; A.e = sc->gap_extend;
     A.score = score; A.end_q = eq; A.end_s = es; A.flags = flags;
     A.counter = arena<int32_t>(ctx, "counter", 4, &s2);
     if (s2 != ANYSEQ_OK) return s2;
+    if (tb) {
+        // direction-word layout: per pair size from the item plan, then a prefix sum
+        int64_t *words = arena<int64_t>(ctx, "tb_words", n + 1, &s2);
+        int64_t *base = arena<int64_t>(ctx, "tb_base", n + 1, &s2);
+        int64_t *stmp = arena<int64_t>(ctx, "scan_tmp", scan_tmp_words(n) + 2, &s2);
+        A.lay_pad = arena<int32_t>(ctx, "tb_pad", n + 1, &s2);
+        A.lay_ch0 = arena<int32_t>(ctx, "tb_ch0", n + 1, &s2);
+        if (s2 != ANYSEQ_OK) return s2;
+        CUDA_TRY(cudaMemsetAsync(words, 0, n * sizeof(int64_t), st));
+        CUDA_TRY(launch_tb_plan(P.list16, P.counts + 0, 4, (n + 3) / 4 + 1, in.q_off, in.s_off, words, A.lay_pad, A.lay_ch0, st));
+        CUDA_TRY(launch_tb_plan(P.list32, P.counts + 1, 2, (n + 1) / 2 + 1, in.q_off, in.s_off, words, A.lay_pad, A.lay_ch0, st));
+        CUDA_TRY(scan_exclusive_i64(words, base, n, stmp, stmp + scan_tmp_words(n), st));
+        int64_t total = 0;
+        CUDA_TRY(cudaMemcpyAsync(&total, stmp + scan_tmp_words(n), sizeof(int64_t), cudaMemcpyDeviceToHost, st));
+        CUDA_TRY(cudaStreamSynchronize(st));
+        A.dirs = arena<uint32_t>(ctx, "tb_dirs", (size_t)total + 1, &s2);
+        if (s2 != ANYSEQ_OK) return s2;
+        A.dir_base = base;
+        ctx->launches += 5;
+        tb->dirs = A.dirs;
+        tb->dir_base = base;
+        tb->lay_pad = A.lay_pad;
+        tb->lay_ch0 = A.lay_ch0;
+        tb->dir_words = total;
+    }
     for (int cell32 = 0; cell32 < 2; cell32++) {
-        int bps = batch_blocks_per_sm(cell32, mode);
+        int bps = batch_blocks_per_sm(cell32, mode, tb != nullptr, sigp, sc->alphabet);
         int grid = ctx->num_sms * bps;
         A.list = cell32 ? P.list32 : P.list16;
         A.n_list = P.counts + cell32;
         A.scratch = nullptr;
         A.scratch_cols = 0;
-        if (in.max_n > 256) {
+        // border rows between row chunks: the smallest chunk of any variant is
+        // GROUP * TB_R = 128 rows (traceback), so longer queries need scratch
+        if (in.max_n > GROUP * TB_R) {
             A.scratch_cols = in.max_m + 1;
-            A.scratch = arena<int32_t>(ctx, "border", (size_t)grid * 16 * 2 * (size_t)A.scratch_cols, &s2);
+            A.scratch = arena<int32_t>(ctx, "border", (size_t)grid * (sigp ? 8 : 16) * 2 * (size_t)A.scratch_cols, &s2);
             if (s2 != ANYSEQ_OK) return s2;
         }
         CUDA_TRY(cudaMemsetAsync(A.counter, 0, sizeof(int32_t), st));
         if (ctx->profile) cudaEventRecord(ctx->ev[2 * cell32], st);
-        CUDA_TRY(launch_batch(A, cell32, mode, grid, st));
+        CUDA_TRY(launch_batch(A, cell32, mode, tb != nullptr, sigp, grid, st));
         if (ctx->profile) cudaEventRecord(ctx->ev[2 * cell32 + 1], st);
         ctx->launches += 1;
     }
@@ -350,7 +408,6 @@ extern "C" anyseq_status_t anyseq_align_batch(anyseq_ctx *ctx, const uint8_t *q,
     if (!q_off || !s_off || !out) return fail(ANYSEQ_ERR_ARG, "q_off, s_off and out must not be NULL");
     if (n_pairs >= (1ll << 31) - 2) return fail(ANYSEQ_ERR_ARG, "n_pairs too large");
     TRY(check_scoring(sc, mode));
-    if (want & ANYSEQ_WANT_CIGAR) return fail(ANYSEQ_ERR_ARG, "CIGAR output of the batch path is not built");
     cudaStream_t st = (cudaStream_t)cuda_stream;
     if (cudaSetDevice(ctx->device) != cudaSuccess) return fail(ANYSEQ_ERR_CUDA, "cudaSetDevice failed");
     anyseq_status_t s2 = ANYSEQ_OK;
@@ -396,7 +453,48 @@ extern "C" anyseq_status_t anyseq_align_batch(anyseq_ctx *ctx, const uint8_t *q,
     int32_t *es = arena<int32_t>(ctx, "r_es", n_pairs, &s2);
     uint32_t *flags = arena<uint32_t>(ctx, "r_flags", n_pairs, &s2);
     if (s2 != ANYSEQ_OK) return s2;
-    TRY(batch_scores(ctx, in, sc, mode, score, eq, es, flags, st));
+    const bool want_cigar = (want & ANYSEQ_WANT_CIGAR) != 0;
+    TbOut tbo;
+    TRY(batch_scores(ctx, in, sc, mode, score, eq, es, flags, st, want_cigar ? &tbo : nullptr));
+
+    int32_t *bq = nullptr, *bs = nullptr;
+    int64_t *clen = nullptr, *coff = nullptr;
+    uint64_t used = 0;
+    if (want_cigar) {
+        // walk back, then lay the runs out contiguously in the caller's buffer
+        TbWalkArgs W;
+        W.n_pairs = n_pairs; W.mode = mode; W.q_off = in.q_off; W.s_off = in.s_off;
+        W.end_q = eq; W.end_s = es;
+        W.dirs = tbo.dirs; W.dir_base = tbo.dir_base; W.lay_pad = tbo.lay_pad; W.lay_ch0 = tbo.lay_ch0;
+        W.tmp = arena<uint32_t>(ctx, "tb_tmp", (size_t)(in.q_len + in.s_len + n_pairs + 1), &s2);
+        clen = W.cig_len = arena<int64_t>(ctx, "tb_clen", n_pairs + 1, &s2);
+        coff = arena<int64_t>(ctx, "tb_coff", n_pairs + 1, &s2);
+        bq = W.beg_q = arena<int32_t>(ctx, "tb_bq", n_pairs + 1, &s2);
+        bs = W.beg_s = arena<int32_t>(ctx, "tb_bs", n_pairs + 1, &s2);
+        int64_t *stmp = arena<int64_t>(ctx, "scan_tmp", scan_tmp_words(n_pairs) + 2, &s2);
+        if (s2 != ANYSEQ_OK) return s2;
+        CUDA_TRY(launch_tb_walk(W, st));
+        CUDA_TRY(scan_exclusive_i64(clen, coff, n_pairs, stmp, stmp + scan_tmp_words(n_pairs), st));
+        int64_t total = 0;
+        CUDA_TRY(cudaMemcpyAsync(&total, stmp + scan_tmp_words(n_pairs), sizeof(int64_t), cudaMemcpyDeviceToHost, st));
+        CUDA_TRY(cudaStreamSynchronize(st));
+        ctx->launches += 4;
+        used = (uint64_t)total;
+        if (cigar_used) *cigar_used = used;
+        if (!cigar || cigar_cap < used)
+            return fail(ANYSEQ_ERR_CAPACITY, "CIGAR buffer holds %llu words, %llu needed",
+                        (unsigned long long)cigar_cap, (unsigned long long)used);
+        bool cig_dev = is_device_ptr(cigar);
+        uint32_t *dcig = cigar;
+        if (!cig_dev) {
+            dcig = arena<uint32_t>(ctx, "r_cigar", used + 1, &s2);
+            if (s2 != ANYSEQ_OK) return s2;
+        }
+        CUDA_TRY(launch_tb_compact(n_pairs, in.q_off, in.s_off, W.tmp, clen, coff, dcig, st));
+        ctx->launches += 1;
+        if (!cig_dev && used)
+            CUDA_TRY(cudaMemcpyAsync(cigar, dcig, used * sizeof(uint32_t), cudaMemcpyDeviceToHost, st));
+    }
 
     bool out_dev = is_device_ptr(out);
     anyseq_result_t *dout = out;
@@ -404,22 +502,102 @@ extern "C" anyseq_status_t anyseq_align_batch(anyseq_ctx *ctx, const uint8_t *q,
         dout = arena<anyseq_result_t>(ctx, "r_out", n_pairs, &s2);
         if (s2 != ANYSEQ_OK) return s2;
     }
-    write_results_kernel<<<grid_for(n_pairs), 256, 0, st>>>(n_pairs, score, eq, es, flags, dout);
+    write_results_kernel<<<grid_for(n_pairs), 256, 0, st>>>(n_pairs, score, eq, es, flags, bq, bs, coff, clen, dout);
     CUDA_TRY(cudaGetLastError());
     ctx->launches += 1;
     if (!out_dev) {
         CUDA_TRY(cudaMemcpyAsync(out, dout, n_pairs * sizeof(anyseq_result_t), cudaMemcpyDeviceToHost, st));
-        CUDA_TRY(cudaStreamSynchronize(st));
     }
-    if (cigar_used) *cigar_used = 0;
+    if (!out_dev || (want_cigar && !is_device_ptr(cigar))) CUDA_TRY(cudaStreamSynchronize(st));
+    if (cigar_used) *cigar_used = used;
     return ANYSEQ_OK;
+}
+
+// Last row (H, E) of one global pass (wavefront kernel, see hb.cu for the
+// multi-pass form used by the divide-and-conquer traceback).
+anyseq_status_t anyseq::long_last_row(anyseq_ctx *ctx, const uint32_t *q2, int64_t q0, int32_t n, const uint32_t *s2,
+                                      int64_t s0, int32_t m, bool rev, int32_t tb, const anyseq_scoring_t *sc,
+                                      int32_t *H, int32_t *E, cudaStream_t st) {
+    std::vector<WavePass> passes(1);
+    memset(passes.data(), 0, sizeof(WavePass));
+    passes[0].q0 = q0; passes[0].s0 = s0; passes[0].n = n; passes[0].m = m;
+    passes[0].tb = tb; passes[0].rev = rev ? 1 : 0; passes[0].out_off = 0;
+    return run_wave_passes(ctx, q2, s2, passes, sc, H, E, st);
 }
 
 extern "C" anyseq_status_t anyseq_align_long(anyseq_ctx *ctx, const uint8_t *q, int64_t n, const uint8_t *s,
                                              int64_t m, const anyseq_scoring_t *sc, int32_t mode, uint32_t want,
                                              anyseq_result_t *out, uint32_t *cigar, uint64_t cigar_cap,
                                              uint64_t *cigar_used, void *cuda_stream) {
-    (void)ctx; (void)q; (void)n; (void)s; (void)m; (void)sc; (void)mode; (void)want; (void)out;
-    (void)cigar; (void)cigar_cap; (void)cigar_used; (void)cuda_stream;
-    return fail(ANYSEQ_ERR_ARG, "the long-pair path is not built");
+    if (!ctx) return fail(ANYSEQ_ERR_ARG, "ctx is NULL");
+    if (n < 0 || m < 0 || n >= (1ll << 23) || m >= (1ll << 23)) return fail(ANYSEQ_ERR_ARG, "lengths out of range (below 2^23)");
+    if (!out) return fail(ANYSEQ_ERR_ARG, "out is NULL");
+    if ((n > 0 && !q) || (m > 0 && !s)) return fail(ANYSEQ_ERR_ARG, "q or s is NULL");
+    TRY(check_scoring(sc, mode));
+    if (mode != ANYSEQ_GLOBAL) return fail(ANYSEQ_ERR_ARG, "the long-pair path is global only");
+    if (sc->alphabet > 4) return fail(ANYSEQ_ERR_ARG, "the long-pair path takes alphabets of at most 4 letters");
+    // 32-bit range: |values| stay below 2^28
+    {
+        int64_t smax = 0;
+        for (int a = 0; a < sc->alphabet; a++)
+            for (int b = 0; b < sc->alphabet; b++) {
+                int64_t v = sigma_host(sc, a, b);
+                smax = v > smax ? v : (-v > smax ? -v : smax);
+            }
+        int64_t bound = 3 * (int64_t)(-sc->gap_open) + (n + m + 2) * (int64_t)(-sc->gap_extend) + smax * (n < m ? n : m + 1);
+        if (bound >= (1ll << 28)) return fail(ANYSEQ_ERR_ARG, "scores of this pair may leave the 32-bit range");
+    }
+    cudaStream_t st = (cudaStream_t)cuda_stream;
+    if (cudaSetDevice(ctx->device) != cudaSuccess) return fail(ANYSEQ_ERR_CUDA, "cudaSetDevice failed");
+    ctx->launches = 0;
+    anyseq_status_t s2 = ANYSEQ_OK;
+    anyseq_result_t r;
+    memset(&r, 0, sizeof(r));
+    r.beg_q = r.beg_s = -1;
+    r.end_q = (int32_t)n;
+    r.end_s = (int32_t)m;
+    r.flags = ANYSEQ_FLAG_INT32;
+    const bool want_cigar = (want & ANYSEQ_WANT_CIGAR) != 0;
+    std::vector<uint32_t> hcig;
+    if (n == 0 || m == 0) {
+        r.score = (n + m == 0) ? 0 : sc->gap_open + (int32_t)(n + m) * sc->gap_extend;
+        if (m) hcig.push_back(((uint32_t)m << 4) | 2u);
+        if (n) hcig.push_back(((uint32_t)n << 4) | 1u);
+    } else {
+        const void *dq, *ds;
+        TRY(stage_input(ctx, "l_q", q, (size_t)n, st, &dq));
+        TRY(stage_input(ctx, "l_s", s, (size_t)m, st, &ds));
+        uint32_t *q2 = arena<uint32_t>(ctx, "l_q2", (size_t)(n + 15) / 16 + 2, &s2);
+        uint32_t *s2p = arena<uint32_t>(ctx, "l_s2", (size_t)(m + 15) / 16 + 2, &s2);
+        int32_t *bad = arena<int32_t>(ctx, "l_bad", 4, &s2);
+        int32_t *H = arena<int32_t>(ctx, "l_H", (size_t)m + 2, &s2);
+        if (s2 != ANYSEQ_OK) return s2;
+        CUDA_TRY(cudaMemsetAsync(bad, 0, sizeof(int32_t), st));
+        CUDA_TRY(launch_pack2bit((const uint8_t *)dq, n, q2, sc->alphabet, bad, st));
+        CUDA_TRY(launch_pack2bit((const uint8_t *)ds, m, s2p, sc->alphabet, bad, st));
+        ctx->launches += 2;
+        TRY(long_last_row(ctx, q2, 0, (int32_t)n, s2p, 0, (int32_t)m, false, sc->gap_open, sc, H, nullptr, st));
+        int32_t hb = 0;
+        CUDA_TRY(cudaMemcpy(&hb, bad, sizeof(int32_t), cudaMemcpyDeviceToHost));
+        if (hb) return fail(ANYSEQ_ERR_ALPHABET, "a letter code is >= alphabet (%d)", sc->alphabet);
+        CUDA_TRY(cudaMemcpy(&r.score, H + m, sizeof(int32_t), cudaMemcpyDeviceToHost));
+        if (want_cigar) TRY(hirschberg_cigar(ctx, q2, (int32_t)n, s2p, (int32_t)m, sc, hcig, st));
+    }
+    if (want_cigar) {
+        r.beg_q = 0;
+        r.beg_s = 0;
+        r.cigar_off = 0;
+        r.cigar_len = (uint32_t)hcig.size();
+        if (cigar_used) *cigar_used = hcig.size();
+        if (!cigar || cigar_cap < hcig.size())
+            return fail(ANYSEQ_ERR_CAPACITY, "CIGAR buffer holds %llu words, %zu needed",
+                        (unsigned long long)cigar_cap, hcig.size());
+        if (!hcig.empty())
+            CUDA_TRY(cudaMemcpyAsync(cigar, hcig.data(), hcig.size() * sizeof(uint32_t), cudaMemcpyDefault, st));
+    } else if (cigar_used) {
+        *cigar_used = 0;
+    }
+    CUDA_TRY(cudaMemcpyAsync(out, &r, sizeof(r), cudaMemcpyDefault, st));
+    CUDA_TRY(cudaStreamSynchronize(st));
+    return ANYSEQ_OK;
 }

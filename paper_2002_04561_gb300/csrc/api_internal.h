@@ -7,6 +7,7 @@
 #include <cuda_runtime.h>
 
 #include "../../include/anyseq.h"
+#include "wave.h"
 
 struct anyseq_ctx {
     struct Buf {
@@ -19,6 +20,9 @@ struct anyseq_ctx {
     size_t budget = 0;
     size_t used = 0;
     int force32 = 0;              // route every pair to 32-bit lanes (testing)
+    int force_matrix = 0;         // use the shared-memory profile path for any alphabet (testing)
+    int64_t spin_limit = 1ll << 24;  // iterations of one device-side wait (x ~64 ns)
+    int64_t base_cells = 1 << 16;    // Hirschberg base-case size
     int profile = 0;              // time the DP kernels with events
     cudaEvent_t ev[4] = {nullptr, nullptr, nullptr, nullptr};
     // statistics of the last call
@@ -46,7 +50,26 @@ int32_t sigma_host(const anyseq_scoring_t *sc, int a, int b);
 anyseq_status_t make_rowprof(const anyseq_scoring_t *sc, int32_t mode, uint32_t prof[5]);
 anyseq_status_t stage_input(anyseq_ctx *ctx, const char *name, const void *src, size_t bytes, cudaStream_t st,
                             const void **dev);
+// Direction words of a traceback run (see tb.cu).
+struct TbOut {
+    uint32_t *dirs = nullptr;
+    int64_t *dir_base = nullptr;
+    int32_t *lay_pad = nullptr, *lay_ch0 = nullptr;
+    int64_t dir_words = 0;
+};
+
+anyseq_status_t long_last_row(anyseq_ctx *ctx, const uint32_t *q2, int64_t q0, int32_t n, const uint32_t *s2,
+                              int64_t s0, int32_t m, bool rev, int32_t tb, const anyseq_scoring_t *sc, int32_t *H,
+                              int32_t *E, cudaStream_t st);
+anyseq_status_t run_wave_passes(anyseq_ctx *ctx, const uint32_t *q2, const uint32_t *s2,
+                                std::vector<WavePass> &passes, const anyseq_scoring_t *sc, int32_t *H, int32_t *E,
+                                cudaStream_t st);
+anyseq_status_t hirschberg_cigar(anyseq_ctx *ctx, const uint32_t *q2, int32_t n, const uint32_t *s2, int32_t m,
+                                 const anyseq_scoring_t *sc, std::vector<uint32_t> &cigar, cudaStream_t st);
+
+// Scores and optimum cells of a batch; with tb != null also the direction words.
 anyseq_status_t batch_scores(anyseq_ctx *ctx, const BatchInput &in, const anyseq_scoring_t *sc, int32_t mode,
-                             int32_t *score, int32_t *eq, int32_t *es, uint32_t *flags, cudaStream_t st);
+                             int32_t *score, int32_t *eq, int32_t *es, uint32_t *flags, cudaStream_t st,
+                             TbOut *tb = nullptr);
 
 }  // namespace anyseq

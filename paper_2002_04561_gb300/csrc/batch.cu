@@ -11,9 +11,38 @@ __device__ __forceinline__ uint32_t letter(const uint32_t *packed, int64_t base,
     return code2(packed, base + (rev ? (int64_t)(len - 1 - idx) : (int64_t)idx));
 }
 
-template <class C, int MODE, int R>
+// Query profile of one group for the matrix path: byte [h][a][row] = sigma'(q_row, a)
+// for the chunk's 128 rows (padding rows: sig_pad), built by the 16 lanes together.
+template <class C>
+__device__ __forceinline__ void build_qprofile(const BatchArgs &A, const Slot &sl, int ch, int g, uint32_t *qp,
+                                               const int8_t *tab) {
+    const int alpha = A.alphabet;
+    const int words_per_letter = QP_ROWS / 4;
+    for (int task = g; task < 2 * words_per_letter; task += GROUP) {
+        const int h = task / words_per_letter, w = task % words_per_letter;
+        int32_t code[4];
+#pragma unroll
+        for (int k = 0; k < 4; k++) {
+            int32_t i = ch * QP_ROWS + w * 4 + k + 1 - sl.pad[h];
+            code[k] = (h < C::PAIRS && i >= 1 && sl.n[h] > 0)
+                          ? (int32_t)A.q8[sl.q0[h] + (sl.rev[h] ? sl.n[h] - i : i - 1)] : -1;
+        }
+        for (int a = 0; a < alpha; a++) {
+            uint32_t word = 0;
+#pragma unroll
+            for (int k = 0; k < 4; k++) {
+                int32_t v = code[k] >= 0 ? (int32_t)tab[code[k] * alpha + a] : A.sig_pad;
+                word |= ((uint32_t)v & 0xFFu) << (8 * k);
+            }
+            qp[(h * alpha + a) * words_per_letter + w] = word;
+        }
+    }
+}
+
+template <class C, int MODE, int R, bool TB, int SIGP>
 __device__ __noinline__ void run_slot(const BatchArgs &A, GroupSmem *sm, const Slot &sl,
-                                      int nch, int Mit, int g, int64_t gslot, int32_t *res) {
+                                      int nch, int Mit, int g, int64_t gslot, int32_t *res, const int32_t *pid,
+                                      uint32_t *qp, const int8_t *tab) {
     typedef typename C::T T;
     const int32_t o = A.o, e = A.e, oe = A.o + A.e;
     const uint32_t e_raw = C::raw(e), oe_raw = C::raw(oe);   // per-half constants of DPX add-max
@@ -43,7 +72,7 @@ __device__ __noinline__ void run_slot(const BatchArgs &A, GroupSmem *sm, const S
 #pragma unroll
             for (int h = 0; h < C::PAIRS; h++) {
                 int32_t i = rb + r - sl.pad[h];
-                if (i >= 1 && sl.n[h] > 0) pw[h] = A.rowprof[letter(A.q2, sl.q0[h], sl.n[h], i - 1, sl.rev[h])];
+                if (SIGP == 0 && i >= 1 && sl.n[h] > 0) pw[h] = A.rowprof[letter(A.q2, sl.q0[h], sl.n[h], i - 1, sl.rev[h])];
                 h0[h] = col0(MODE, i, o, e, sl.tb[h]) + oe;
             }
             profA[r] = pw[0];
@@ -71,9 +100,16 @@ __device__ __noinline__ void run_slot(const BatchArgs &A, GroupSmem *sm, const S
                 int c = blk * BLOCK + g + 16 * k;
                 if (c < Mit) {
                     uint32_t ca = 0, cb = 0;
-                    if (c < sl.m[0]) ca = letter(A.s2, sl.s0[0], sl.m[0], c, sl.rev[0]);
-                    if (C::PAIRS == 2 && c < sl.m[1]) cb = letter(A.s2, sl.s0[1], sl.m[1], c, sl.rev[1]);
-                    sm->sel[c & (RING - 1)] = C::selector(ca, cb);
+                    if (SIGP == 0) {
+                        if (c < sl.m[0]) ca = letter(A.s2, sl.s0[0], sl.m[0], c, sl.rev[0]);
+                        if (C::PAIRS == 2 && c < sl.m[1]) cb = letter(A.s2, sl.s0[1], sl.m[1], c, sl.rev[1]);
+                        sm->sel[c & (RING - 1)] = C::selector(ca, cb);
+                    } else {
+                        if (c < sl.m[0]) ca = A.s8[sl.s0[0] + (sl.rev[0] ? sl.m[0] - 1 - c : c)];
+                        if (C::PAIRS == 2 && c < sl.m[1]) cb = A.s8[sl.s0[1] + (sl.rev[1] ? sl.m[1] - 1 - c : c)];
+                        // byte offsets of the two letters' profile rows for this lane
+                        sm->sel[c & (RING - 1)] = (ca * QP_ROWS) | ((((uint32_t)A.alphabet + cb) * QP_ROWS) << 16);
+                    }
                     if (ch > 0) {
                         sm->top[2 * (c & (RING - 1))] = scr[2 * c];
                         sm->top[2 * (c & (RING - 1)) + 1] = scr[2 * c + 1];
@@ -107,10 +143,24 @@ __device__ __noinline__ void run_slot(const BatchArgs &A, GroupSmem *sm, const S
         };
 
         __syncwarp();
+        if (SIGP) build_qprofile<C>(A, sl, ch, g, qp, tab);
         fill(0);
         __syncwarp();
         int drained = 0;  // next bottom block to drain
 
+        // traceback: this chunk's direction words of each half (row chunks before
+        // the pair's first real row are not stored)
+        uint32_t *dptr[2] = {nullptr, nullptr};
+        int32_t Sh[2] = {0, 0};
+        if (TB) {
+#pragma unroll
+            for (int h = 0; h < C::PAIRS; h++) {
+                int32_t ch0 = sl.pad[h] / CH;
+                Sh[h] = sl.m[h] + GROUP - 1;
+                if (pid[h] >= 0 && ch >= ch0)
+                    dptr[h] = A.dirs + A.dir_base[pid[h]] + (int64_t)(ch - ch0) * Sh[h] * GROUP + g;
+            }
+        }
         T last_hoe = NEGv, last_e = NEGv, prev_up = diag0;
         for (int s = 0; s < S; s++) {
             if ((s & (BLOCK - 1)) == 0) {
@@ -137,6 +187,12 @@ __device__ __noinline__ void run_slot(const BatchArgs &A, GroupSmem *sm, const S
             }
             if (c >= 0 && c < Mit) {
                 const uint32_t sel = sm->sel[c & (RING - 1)];
+                uint2 qa = make_uint2(0, 0), qb = make_uint2(0, 0);
+                if (SIGP) {
+                    const uint8_t *qpb = reinterpret_cast<const uint8_t *>(qp) + g * R;
+                    qa = *reinterpret_cast<const uint2 *>(qpb + (sel & 0xFFFFu));
+                    if (C::PAIRS == 2) qb = *reinterpret_cast<const uint2 *>(qpb + (sel >> 16));
+                }
                 T diag = (c == 0) ? diag0 : prev_up;
                 prev_up = up_hoe;
                 T E = up_e;
@@ -146,17 +202,51 @@ __device__ __noinline__ void run_slot(const BatchArgs &A, GroupSmem *sm, const S
                                           : (c < sl.m[0] ? 0xFFFFFFFFu : 0u);
                     jj = C::PAIRS == 2 ? (uint32_t)(c + 1) * 65537u : (uint32_t)(c + 1);
                 }
+                // direction bit planes (traceback): bit 8+r / 24+r of each accumulator
+                uint32_t pl_s0 = 0, pl_s1 = 0, pl_eo = 0, pl_fo = 0;
+                T hup = up_hoe;  // Hoe of the row above, this column
 #pragma unroll
                 for (int r = 0; r < R; r++) {
                     // H(i,j) = max(H(i-1,j-1)+sigma, E(i,j), F(i,j) [,0]) kept as Hoe = H + o + e
-                    T sg = C::sigma(profA[r], profB[r], sel);
+                    T sg;
+                    if (SIGP == 0) {
+                        sg = C::sigma(profA[r], profB[r], sel);
+                    } else {
+                        // byte r of this lane's profile row, per half (bytes are >= 0)
+                        const uint32_t wa = (r & 4) ? qa.y : qa.x, wb = (r & 4) ? qb.y : qb.x;
+                        const uint32_t b = (uint32_t)(r & 3);
+                        sg = C::PAIRS == 2 ? C::from_u(prmt(wa, wb, b | ((b | 8u) << 4) | ((b + 4u) << 8) | (((b + 4u) | 8u) << 12)))
+                                           : C::from_u(prmt(wa, wa, b | ((b | 8u) << 4) | ((b | 8u) << 8) | ((b | 8u) << 12)));
+                    }
                     T Ad = C::addc(diag, C::as_u(sg));                 // H(i-1,j-1) + sigma
+                    T Fl = F[r];
                     F[r] = C::addmax(F[r], e_raw, Hoe[r]);             // Eq. 5
                     T M = (MODE == LOCAL) ? C::maxrelu(Ad, F[r]) : C::vmax(Ad, F[r]);
                     T X = C::addc(M, oe_c);                           // max(diag, F) + o + e
                     diag = Hoe[r];
+                    T Ein = E;
                     Hoe[r] = C::addmax(E, oe_raw, X);                  // H + o + e
                     E = C::addmax(E, e_raw, X);                        // Eq. 4 for row i+1
+                    if (TB) {
+                        // a >= b  <=>  sign bit (bit 15 / 31 per lane) of b - a - 1 ... expressed per cell type
+                        uint32_t fD = C::ge(C::addc(Ad, oe_c), Hoe[r]);   // diagonal reaches H
+                        uint32_t fE = C::ge(C::addc(Ein, oe_c), Hoe[r]);  // E reaches H
+                        uint32_t fEo = C::ge(hup, Ein);                    // E(i,j) opened from H(i-1,j)
+                        uint32_t fFo = C::ge(diag, F[r]);                  // F(i,j) opened from H(i,j-1)
+                        uint32_t s0 = fD, s1 = fE;
+                        if (MODE == LOCAL) {
+                            uint32_t fZ = C::ge(C::from_u(C::zero_hoe(oe)), Hoe[r]);  // H == 0
+                            s0 = fZ | fD;
+                            s1 = fZ | (fE & ~fD);
+                        }
+                        const uint32_t FM = C::flag_mask();
+                        pl_s0 = (pl_s0 >> 1) | (s0 & FM);
+                        pl_s1 = (pl_s1 >> 1) | (s1 & FM);
+                        pl_eo = (pl_eo >> 1) | (fEo & FM);
+                        pl_fo = (pl_fo >> 1) | (fFo & FM);
+                        hup = Hoe[r];
+                    }
+                    (void)Fl;
                     if (MODE == LOCAL) {
                         // strict improvement of the row maximum at a valid column
                         uint32_t gm;
@@ -177,6 +267,12 @@ __device__ __noinline__ void run_slot(const BatchArgs &A, GroupSmem *sm, const S
                 }
                 last_hoe = Hoe[R - 1];
                 last_e = E;
+                if (TB) {
+                    uint32_t w01 = prmt(pl_s0, pl_s1, 0x7351u);   // s0.b1 s1.b1 s0.b3 s1.b3
+                    uint32_t w23 = prmt(pl_eo, pl_fo, 0x7351u);
+                    if (dptr[0] && s < Sh[0]) dptr[0][(int64_t)s * GROUP] = C::PAIRS == 2 ? prmt(w01, w23, 0x5410u) : prmt(w01, w23, 0x7632u);
+                    if (C::PAIRS == 2 && dptr[1] && s < Sh[1]) dptr[1][(int64_t)s * GROUP] = prmt(w01, w23, 0x7632u);
+                }
                 if (g == GROUP - 1) {
                     sm->bot[2 * (c & (RING - 1))] = (int32_t)C::as_u(last_hoe);
                     sm->bot[2 * (c & (RING - 1)) + 1] = (int32_t)C::as_u(last_e);
@@ -243,64 +339,73 @@ __device__ __noinline__ void run_slot(const BatchArgs &A, GroupSmem *sm, const S
     }
 }
 
-template <class C, int MODE>
-__global__ void __launch_bounds__(256, 2) batch_kernel(BatchArgs A) {
-    __shared__ GroupSmem smem[16];
+// Persistent kernel: each warp pulls work items (2 slots of 16 lanes) from the
+// sorted list until it is empty. THREADS = 256 for the row-profile path, 128
+// for the matrix path (whose per-group query profile lives in dynamic shared
+// memory after a copy of the sigma' table).
+template <class C, int MODE, bool TB, int SIGP>
+__global__ void __launch_bounds__(SIGP ? 128 : 256, SIGP ? 4 : 2) batch_kernel(BatchArgs A) {
+    constexpr int THREADS = SIGP ? 128 : 256;
+    __shared__ GroupSmem smem[THREADS / 16];
+    extern __shared__ __align__(16) uint8_t dyn_smem[];
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int grp = lane >> 4, g = lane & 15;
     GroupSmem *sm = &smem[warp * 2 + grp];
-    const int64_t gslot = ((int64_t)blockIdx.x * (blockDim.x >> 5) + warp) * 2 + grp;
+    int8_t *tab = nullptr;
+    uint32_t *qp = nullptr;
+    if (SIGP) {
+        tab = reinterpret_cast<int8_t *>(dyn_smem);
+        for (int k = threadIdx.x; k < A.alphabet * A.alphabet; k += THREADS) tab[k] = A.sig_tab[k];
+        qp = reinterpret_cast<uint32_t *>(dyn_smem + 1024) + (warp * 2 + grp) * (2 * A.alphabet * QP_ROWS / 4);
+        __syncthreads();
+    }
+    const int64_t gslot = ((int64_t)blockIdx.x * (THREADS >> 5) + warp) * 2 + grp;
     const int per_item = 2 * C::PAIRS;
-    const int32_t n_items = (int32_t)((*A.n_list + per_item - 1) / per_item);
+    const int64_t n_list = *A.n_list;
+    const int64_t n_items = (n_list + per_item - 1) / per_item;
+    // rows per lane: at most 16 (12 for local int16x2, which also keeps per-row
+    // maxima); exactly TB_R for the traceback and matrix kernels
+    constexpr int RMAX = (TB || SIGP) ? TB_R : ((MODE == LOCAL && C::PAIRS == 2) ? 12 : 16);
     for (;;) {
         int item = 0;
         if (lane == 0) item = atomicAdd(A.counter, 1);
         item = __shfl_sync(0xffffffffu, item, 0);
         if (item >= n_items) break;
-        // pairs of the item: per_item consecutive entries of the sorted list
-        int32_t nmax = 0, Mit = 0;
-        int32_t pid[2] = {-1, -1};
+        ItemPlan P = plan_item(A.list, n_list, item, per_item, A.q_off, A.s_off, RMAX, !(TB || SIGP));
+        if (TB || SIGP) P.R = TB_R;
         Slot sl;
+        int32_t pid[2] = {-1, -1};
 #pragma unroll
         for (int h = 0; h < 2; h++) {
-            sl.n[h] = 0; sl.m[h] = 0; sl.q0[h] = 0; sl.s0[h] = 0; sl.rev[h] = false;
+            int k = grp * C::PAIRS + h;
+            bool ok = h < C::PAIRS && P.pid[k] >= 0;
+            pid[h] = ok ? P.pid[k] : -1;
+            sl.n[h] = ok ? P.n[k] : 0;
+            sl.m[h] = ok ? P.m[k] : 0;
+            sl.q0[h] = ok ? A.q_off[P.pid[k]] : 0;
+            sl.s0[h] = ok ? A.s_off[P.pid[k]] : 0;
+            sl.rev[h] = false;
             sl.tb[h] = A.o;
+            sl.pad[h] = P.nch * GROUP * P.R - sl.n[h];
         }
-        for (int k = 0; k < per_item; k++) {
-            int64_t idx = (int64_t)item * per_item + k;
-            if (idx < *A.n_list) {
-                int32_t p = A.list[idx];
-                int32_t n = (int32_t)(A.q_off[p + 1] - A.q_off[p]);
-                int32_t m = (int32_t)(A.s_off[p + 1] - A.s_off[p]);
-                nmax = max(nmax, n);
-                Mit = max(Mit, m);
-                if (k / C::PAIRS == grp) {
-                    int h = k % C::PAIRS;
-                    pid[h] = p;
-                    sl.n[h] = n; sl.m[h] = m;
-                    sl.q0[h] = A.q_off[p]; sl.s0[h] = A.s_off[p];
-                }
-            }
-        }
-        // rows per lane: at most 16 (12 for local int16x2, which also keeps per-row maxima)
-        constexpr int RMAX = (MODE == LOCAL && C::PAIRS == 2) ? 12 : 16;
-        int nch = (nmax + GROUP * RMAX - 1) / (GROUP * RMAX);
-        int R = (nmax + GROUP * nch - 1) / (GROUP * nch);
-        R += R & 1;
-        if (R < 2) R = 2;
-        const int rows = nch * GROUP * R;
-#pragma unroll
-        for (int h = 0; h < 2; h++) sl.pad[h] = rows - sl.n[h];
         int32_t res[6];
-        switch (R) {
-            case 2: run_slot<C, MODE, 2>(A, sm, sl, nch, Mit, g, gslot, res); break;
-            case 4: run_slot<C, MODE, 4>(A, sm, sl, nch, Mit, g, gslot, res); break;
-            case 6: run_slot<C, MODE, 6>(A, sm, sl, nch, Mit, g, gslot, res); break;
-            case 8: run_slot<C, MODE, 8>(A, sm, sl, nch, Mit, g, gslot, res); break;
-            case 10: run_slot<C, MODE, 10>(A, sm, sl, nch, Mit, g, gslot, res); break;
-            case 12: run_slot<C, MODE, 12>(A, sm, sl, nch, Mit, g, gslot, res); break;
-            case 14: run_slot<C, MODE, (RMAX < 14 ? RMAX : 14)>(A, sm, sl, nch, Mit, g, gslot, res); break;
-            default: run_slot<C, MODE, RMAX>(A, sm, sl, nch, Mit, g, gslot, res); break;
+        if (P.nch > 1 && A.scratch == nullptr) {
+            // the host sizes the border scratch for every multi-chunk query; never reached
+            continue;
+        }
+        if (TB || SIGP) {
+            run_slot<C, MODE, TB_R, TB, SIGP>(A, sm, sl, P.nch, P.Mit, g, gslot, res, pid, qp, tab);
+        } else {
+            switch (P.R) {
+                case 2: run_slot<C, MODE, 2, TB, SIGP>(A, sm, sl, P.nch, P.Mit, g, gslot, res, pid, qp, tab); break;
+                case 4: run_slot<C, MODE, 4, TB, SIGP>(A, sm, sl, P.nch, P.Mit, g, gslot, res, pid, qp, tab); break;
+                case 6: run_slot<C, MODE, 6, TB, SIGP>(A, sm, sl, P.nch, P.Mit, g, gslot, res, pid, qp, tab); break;
+                case 8: run_slot<C, MODE, 8, TB, SIGP>(A, sm, sl, P.nch, P.Mit, g, gslot, res, pid, qp, tab); break;
+                case 10: run_slot<C, MODE, 10, TB, SIGP>(A, sm, sl, P.nch, P.Mit, g, gslot, res, pid, qp, tab); break;
+                case 12: run_slot<C, MODE, 12, TB, SIGP>(A, sm, sl, P.nch, P.Mit, g, gslot, res, pid, qp, tab); break;
+                case 14: run_slot<C, MODE, (RMAX < 14 ? RMAX : 14), TB, SIGP>(A, sm, sl, P.nch, P.Mit, g, gslot, res, pid, qp, tab); break;
+                default: run_slot<C, MODE, RMAX, TB, SIGP>(A, sm, sl, P.nch, P.Mit, g, gslot, res, pid, qp, tab); break;
+            }
         }
         if (g == 0) {
 #pragma unroll
@@ -316,41 +421,67 @@ __global__ void __launch_bounds__(256, 2) batch_kernel(BatchArgs A) {
     }
 }
 
-template <class C, int MODE>
+static size_t dyn_smem_bytes(int sigp, int alphabet) {
+    return sigp ? 1024 + (size_t)(128 / 16) * 2 * alphabet * QP_ROWS : 0;
+}
+
+template <class C, int MODE, bool TB, int SIGP>
 static cudaError_t launch_one(const BatchArgs &A, int grid, cudaStream_t st) {
-    batch_kernel<C, MODE><<<grid, 256, 0, st>>>(A);
+    size_t dyn = dyn_smem_bytes(SIGP, A.alphabet);
+    // static rings + dynamic profile exceed the 48 KB default: opt in explicitly
+    if (SIGP) cudaFuncSetAttribute(batch_kernel<C, MODE, TB, SIGP>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)dyn);
+    batch_kernel<C, MODE, TB, SIGP><<<grid, SIGP ? 128 : 256, dyn, st>>>(A);
     return cudaGetLastError();
 }
 
-cudaError_t launch_batch(const BatchArgs &A, int cell32, int mode, int grid, cudaStream_t st) {
+template <bool TB, int SIGP>
+static cudaError_t launch_v(const BatchArgs &A, int cell32, int mode, int grid, cudaStream_t st) {
     if (cell32) {
         switch (mode) {
-            case GLOBAL: return launch_one<CellI32, GLOBAL>(A, grid, st);
-            case LOCAL: return launch_one<CellI32, LOCAL>(A, grid, st);
-            default: return launch_one<CellI32, SEMIGLOBAL>(A, grid, st);
+            case GLOBAL: return launch_one<CellI32, GLOBAL, TB, SIGP>(A, grid, st);
+            case LOCAL: return launch_one<CellI32, LOCAL, TB, SIGP>(A, grid, st);
+            default: return launch_one<CellI32, SEMIGLOBAL, TB, SIGP>(A, grid, st);
         }
     }
     switch (mode) {
-        case GLOBAL: return launch_one<CellI16x2, GLOBAL>(A, grid, st);
-        case LOCAL: return launch_one<CellI16x2, LOCAL>(A, grid, st);
-        default: return launch_one<CellI16x2, SEMIGLOBAL>(A, grid, st);
+        case GLOBAL: return launch_one<CellI16x2, GLOBAL, TB, SIGP>(A, grid, st);
+        case LOCAL: return launch_one<CellI16x2, LOCAL, TB, SIGP>(A, grid, st);
+        default: return launch_one<CellI16x2, SEMIGLOBAL, TB, SIGP>(A, grid, st);
     }
 }
 
-int batch_blocks_per_sm(int cell32, int mode) {
+cudaError_t launch_batch(const BatchArgs &A, int cell32, int mode, int tb, int sigp, int grid, cudaStream_t st) {
+    if (sigp) return tb ? launch_v<true, 1>(A, cell32, mode, grid, st) : launch_v<false, 1>(A, cell32, mode, grid, st);
+    return tb ? launch_v<true, 0>(A, cell32, mode, grid, st) : launch_v<false, 0>(A, cell32, mode, grid, st);
+}
+
+template <class C, int MODE, bool TB, int SIGP>
+static int occ(int alphabet) {
     int nb = 0;
-    cudaError_t err;
-    if (cell32) {
-        err = mode == GLOBAL ? cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, batch_kernel<CellI32, GLOBAL>, 256, 0)
-            : mode == LOCAL  ? cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, batch_kernel<CellI32, LOCAL>, 256, 0)
-                             : cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, batch_kernel<CellI32, SEMIGLOBAL>, 256, 0);
-    } else {
-        err = mode == GLOBAL ? cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, batch_kernel<CellI16x2, GLOBAL>, 256, 0)
-            : mode == LOCAL  ? cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, batch_kernel<CellI16x2, LOCAL>, 256, 0)
-                             : cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, batch_kernel<CellI16x2, SEMIGLOBAL>, 256, 0);
+    size_t dyn = dyn_smem_bytes(SIGP, alphabet);
+    if (SIGP) cudaFuncSetAttribute(batch_kernel<C, MODE, TB, SIGP>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)dyn);
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, batch_kernel<C, MODE, TB, SIGP>, SIGP ? 128 : 256, dyn) !=
+        cudaSuccess) {
+        cudaGetLastError();
+        nb = 1;
     }
-    if (err != cudaSuccess || nb < 1) nb = 1;
-    return nb;
+    return nb < 1 ? 1 : nb;
+}
+
+template <bool TB, int SIGP>
+static int occ_v(int cell32, int mode, int alphabet) {
+    if (cell32)
+        return mode == GLOBAL ? occ<CellI32, GLOBAL, TB, SIGP>(alphabet)
+             : mode == LOCAL  ? occ<CellI32, LOCAL, TB, SIGP>(alphabet)
+                              : occ<CellI32, SEMIGLOBAL, TB, SIGP>(alphabet);
+    return mode == GLOBAL ? occ<CellI16x2, GLOBAL, TB, SIGP>(alphabet)
+         : mode == LOCAL  ? occ<CellI16x2, LOCAL, TB, SIGP>(alphabet)
+                          : occ<CellI16x2, SEMIGLOBAL, TB, SIGP>(alphabet);
+}
+
+int batch_blocks_per_sm(int cell32, int mode, int tb, int sigp, int alphabet) {
+    if (sigp) return tb ? occ_v<true, 1>(cell32, mode, alphabet) : occ_v<false, 1>(cell32, mode, alphabet);
+    return tb ? occ_v<true, 0>(cell32, mode, alphabet) : occ_v<false, 0>(cell32, mode, alphabet);
 }
 
 }  // namespace anyseq

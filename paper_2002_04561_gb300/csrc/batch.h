@@ -17,10 +17,65 @@ struct BatchArgs {
     int64_t scratch_cols;
     int32_t *score, *end_q, *end_s; // outputs per pair
     uint32_t *flags;
+    // substitution matrix path (alphabet > 4): letters as bytes and the table
+    // sigma'(a, b) = sigma(a, b) - open - extend (alphabet x alphabet int8, >= 0)
+    const uint8_t *q8, *s8;
+    const int8_t *sig_tab;
+    int32_t alphabet;
+    int32_t sig_pad;                // sigma' of the padding rows
+    // traceback (direction words, see tb.cu): per pair base word, padding rows, first chunk
+    uint32_t *dirs;
+    const int64_t *dir_base;
+    int32_t *lay_pad, *lay_ch0;
 };
 
-cudaError_t launch_batch(const BatchArgs &A, int cell32, int mode, int grid, cudaStream_t st);
-int batch_blocks_per_sm(int cell32, int mode);
+// Work item of the persistent batched kernels: per_item consecutive pairs of a
+// sorted list, their row chunking (nch chunks of 16*R rows) and column count.
+struct ItemPlan {
+    int32_t pid[4];
+    int32_t n[4], m[4];
+    int32_t nch, R, Mit, count;
+};
+
+__device__ __forceinline__ ItemPlan plan_item(const int32_t *list, int64_t n_list, int64_t item, int per_item,
+                                              const int64_t *q_off, const int64_t *s_off, int rmax, bool r_even) {
+    ItemPlan P;
+    int32_t nmax = 0;
+    P.Mit = 0;
+    P.count = 0;
+    for (int k = 0; k < 4; k++) {
+        P.pid[k] = -1;
+        P.n[k] = 0;
+        P.m[k] = 0;
+    }
+    for (int k = 0; k < per_item; k++) {
+        int64_t idx = item * per_item + k;
+        if (idx < n_list) {
+            int32_t p = list[idx];
+            P.pid[k] = p;
+            P.n[k] = (int32_t)(q_off[p + 1] - q_off[p]);
+            P.m[k] = (int32_t)(s_off[p + 1] - s_off[p]);
+            nmax = max(nmax, P.n[k]);
+            P.Mit = max(P.Mit, P.m[k]);
+            P.count++;
+        }
+    }
+    P.nch = (nmax + 16 * rmax - 1) / (16 * rmax);
+    if (P.nch < 1) P.nch = 1;
+    int R = (nmax + 16 * P.nch - 1) / (16 * P.nch);
+    if (r_even) R += R & 1;
+    if (R < 2) R = 2;
+    if (R > rmax) R = rmax;
+    P.R = R;
+    return P;
+}
+
+// sigp: 0 = row-profile words (alphabet <= 4), 1 = shared-memory query profile (matrix, alphabet <= 32)
+cudaError_t launch_batch(const BatchArgs &A, int cell32, int mode, int tb, int sigp, int grid, cudaStream_t st);
+int batch_blocks_per_sm(int cell32, int mode, int tb, int sigp, int alphabet);
+constexpr int QP_ROWS = 128;        // rows of the shared-memory query profile (chunk of 16 lanes x 8 rows)
+// Rows per lane of the traceback kernels (one 32-bit direction word per lane, step and pair).
+constexpr int TB_R = 8;
 
 // Packing, range tests and length binning (pack.cu).
 struct PrepArgs {
@@ -45,5 +100,7 @@ struct PrepArgs {
 };
 
 cudaError_t launch_prep(const PrepArgs &P, cudaStream_t st);
+cudaError_t launch_pack2bit(const uint8_t *codes, int64_t len, uint32_t *out, int32_t alphabet, int32_t *bad,
+                            cudaStream_t st);
 
 }  // namespace anyseq

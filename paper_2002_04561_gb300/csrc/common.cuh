@@ -58,6 +58,10 @@ struct CellI32 {
     }
     __device__ __forceinline__ static uint32_t as_u(T v) { return (uint32_t)v; }
     __device__ __forceinline__ static T from_u(uint32_t v) { return (int32_t)v; }
+    // flag word: bit 31 set iff a >= b (sign of b - a - 1; |a - b| < 2^31)
+    __device__ __forceinline__ static uint32_t ge(T a, T b) { return (uint32_t)(b - a - 1); }
+    __device__ __forceinline__ static uint32_t flag_mask() { return 0x80000000u; }
+    __device__ __forceinline__ static uint32_t zero_hoe(int32_t oe) { return (uint32_t)oe; }
 };
 
 // Two int16 halves per 32-bit word (low: pair A, high: pair B), each stored
@@ -88,6 +92,13 @@ struct CellI16x2 {
     }
     __device__ __forceinline__ static uint32_t as_u(T v) { return v; }
     __device__ __forceinline__ static T from_u(uint32_t v) { return v; }
+    // flag word: bit 15 (low half) / 31 (high half) set iff a >= b; one full-rate
+    // add because a - b + 2^15 stays inside [0, 2^16) when |a - b| < 2^15
+    __device__ __forceinline__ static uint32_t ge(T a, T b) { return a + 0x80008000u - b; }
+    __device__ __forceinline__ static uint32_t flag_mask() { return 0x80008000u; }
+    __device__ __forceinline__ static uint32_t zero_hoe(int32_t oe) {
+        return ((uint32_t)(oe + 32768) & 0xFFFFu) * 65537u;
+    }
 };
 
 // Letter at global position k of a 2-bit packed array (16 letters per word).

@@ -170,6 +170,13 @@ __global__ void scatter_kernel(PrepArgs P) {
     }
 }
 
+cudaError_t launch_pack2bit(const uint8_t *codes, int64_t len, uint32_t *out, int32_t alphabet, int32_t *bad,
+                            cudaStream_t st) {
+    int64_t b = ((len + 15) / 16 + 255) / 256;
+    pack2bit_kernel<<<(int)(b < 1 ? 1 : (b > 65535 ? 65535 : b)), 256, 0, st>>>(codes, len, out, alphabet, bad);
+    return cudaGetLastError();
+}
+
 cudaError_t launch_prep(const PrepArgs &P, cudaStream_t st) {
     const int T = 256;
     auto blocks = [](int64_t work) { int64_t b = (work + 255) / 256; return (int)(b < 1 ? 1 : (b > 65535 ? 65535 : b)); };

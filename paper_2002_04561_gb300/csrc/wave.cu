@@ -1,0 +1,216 @@
+// Intra-sequence wavefront for one long pair (Sec. IV-C, Sec. VI): global
+// alignment of q[1..n] against s[1..m] in linear space, 32-bit lanes.
+//
+// The rows are cut into stripes of 32 lanes x 16 rows = 512 rows. A warp owns a
+// stripe and walks all m columns; lane l is one step behind lane l-1 and gets
+// its upper neighbours by shfl.up (the anti-diagonal dependency of Sec. III-A).
+// Stripe k reads the last row of stripe k-1 from a border row in global memory
+// and writes its own for stripe k+1 (two border rows, alternating): the first
+// row and column of a submatrix come in, its last row goes out (Sec. III-A,
+// Fig. submatrix). A border block of 32 columns is published with a release
+// store of the stripe's progress counter and consumed after an acquire load;
+// persistent warps take stripes in increasing order from an atomic counter, so
+// a waiting stripe only waits for a stripe that a running warp already owns.
+// Every wait has an iteration limit; on expiry the kernel raises an error flag
+// that makes every other waiter give up too, and the host returns
+// ANYSEQ_ERR_TIMEOUT.
+//
+// Per cell: the same seven instructions as the batched kernel (engine.cuh).
+#include "common.cuh"
+#include "engine.cuh"
+#include "wave.h"
+
+namespace anyseq {
+
+constexpr int WG = 32;   // lanes per stripe
+constexpr int WR = 16;   // rows per lane
+constexpr int WCH = WG * WR;
+constexpr int WRING = 128;
+
+__device__ __forceinline__ uint32_t wletter(const uint32_t *packed, int64_t base, int32_t len, int32_t idx, bool rev) {
+    return code2(packed, base + (rev ? (int64_t)(len - 1 - idx) : (int64_t)idx));
+}
+
+__device__ __forceinline__ int32_t ld_acquire(const int32_t *p) {
+    int32_t v;
+    asm volatile("ld.acquire.gpu.global.s32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+    return v;
+}
+__device__ __forceinline__ void st_release(int32_t *p, int32_t v) {
+    asm volatile("st.release.gpu.global.s32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
+}
+
+struct WaveSmem {
+    uint32_t sel[WRING];
+    int32_t top[2 * WRING];
+    int32_t bot[2 * WRING];
+};
+
+__global__ void __launch_bounds__(256, 2) wave_kernel(WaveArgs A) {
+    __shared__ WaveSmem smem[8];
+    const int warp = threadIdx.x >> 5, g = threadIdx.x & 31;
+    WaveSmem *sm = &smem[warp];
+    typedef CellI32 C;
+    typedef int32_t T;
+    const int32_t o = A.o, e = A.e, oe = A.o + A.e;
+    const uint32_t e_raw = C::raw(e), oe_raw = C::raw(oe), oe_c = C::cst(oe);
+    for (;;) {
+        int32_t t = 0;
+        if (g == 0) t = atomicAdd(A.stripe_counter, 1);
+        t = __shfl_sync(0xffffffffu, t, 0);
+        if (t >= A.n_stripes) break;
+        // the pass owning global stripe t (binary search over stripe0)
+        int lo = 0, hi = A.n_passes - 1;
+        while (lo < hi) {
+            int mid = (lo + hi + 1) >> 1;
+            if (A.passes[mid].stripe0 <= t) lo = mid; else hi = mid - 1;
+        }
+        const WavePass ps = A.passes[lo];
+        const int32_t n = ps.n, m = ps.m;
+        const int32_t nstripes = (n + WCH - 1) / WCH;
+        const int32_t pad = nstripes * WCH - n;
+        const int S = m + WG - 1;
+        const int32_t k = t - ps.stripe0;
+        const bool last = (k == nstripes - 1);
+        const bool rev = ps.rev != 0;
+        int32_t *outH = A.last_H ? A.last_H + ps.out_off : nullptr;
+        int32_t *outE = A.last_E ? A.last_E + ps.out_off : nullptr;
+        const int32_t rb = k * WCH + g * WR + 1;
+        uint32_t prof[WR];
+        T Hoe[WR], F[WR];
+#pragma unroll
+        for (int r = 0; r < WR; r++) {
+            int32_t i = rb + r - pad;
+            prof[r] = (i >= 1) ? A.rowprof[wletter(A.q2, ps.q0, n, i - 1, rev)] : A.rowprof[4];
+            Hoe[r] = col0(GLOBAL, i, o, e, ps.tb) + oe;
+            F[r] = C::NEG;
+        }
+        const T diag0 = col0(GLOBAL, rb - 1 - pad, o, e, ps.tb) + oe;
+        const int2 *bin = A.border + ps.border_off + (int64_t)((k - 1) & 1) * m;
+        int2 *bout = A.border + ps.border_off + (int64_t)(k & 1) * m;
+        int32_t *prog_prev = A.prog + ps.stripe0 + (k > 0 ? k - 1 : 0);
+        int32_t *prog_mine = A.prog + t;
+        bool failed = false;
+
+        // wait until the previous stripe published border block blk (bounded)
+        auto wait_for = [&](int blk) {
+            if (k == 0 || failed) return;
+            int ok = 1;
+            if (g == 0) {
+                int64_t spins = 0;
+                while (ld_acquire(prog_prev) < blk + 1) {
+                    if (++spins > A.spin_limit || *((volatile int32_t *)A.err)) {
+                        atomicExch(A.err, 1);
+                        ok = 0;
+                        break;
+                    }
+                    __nanosleep(64);
+                }
+            }
+            ok = __shfl_sync(0xffffffffu, ok, 0);
+            failed = !ok;
+            __syncwarp();
+        };
+        auto fill = [&](int blk) {
+            int c = blk * BLOCK + g;
+            if (c < m) {
+                sm->sel[c & (WRING - 1)] = C::selector(wletter(A.s2, ps.s0, m, c, rev), 0);
+                if (k > 0 && !failed) {
+                    int2 v = bin[c];
+                    sm->top[2 * (c & (WRING - 1))] = v.x;
+                    sm->top[2 * (c & (WRING - 1)) + 1] = v.y;
+                }
+            }
+        };
+        auto drain = [&](int blk) {
+            int c = blk * BLOCK + g;
+            if (blk >= 0 && c < m) {
+                int32_t hv = sm->bot[2 * (c & (WRING - 1))], ev = sm->bot[2 * (c & (WRING - 1)) + 1];
+                if (!last) {
+                    bout[c] = make_int2(hv, ev);
+                } else {
+                    if (outH) outH[c + 1] = hv - oe;
+                    if (outE) outE[c + 1] = ev;
+                }
+            }
+            __syncwarp();
+            if (!last && g == 0 && blk >= 0) st_release(prog_mine, blk + 1);
+        };
+
+        wait_for(0);
+        fill(0);
+        __syncwarp();
+        int drained = 0;
+        T last_hoe = C::NEG, last_e = C::NEG, prev_up = diag0;
+        for (int s = 0; s < S && !failed; s++) {
+            if ((s & (BLOCK - 1)) == 0) {
+                int kb = s / BLOCK;
+                if ((kb + 1) * BLOCK < m) wait_for(kb + 1);
+                fill(kb + 1);
+                if (kb - 2 >= drained) { drain(kb - 2); drained = kb - 1; }
+                __syncwarp();
+            }
+            const int c = s - g;
+            T up_hoe = (T)__shfl_up_sync(0xffffffffu, (uint32_t)last_hoe, 1);
+            T up_e = (T)__shfl_up_sync(0xffffffffu, (uint32_t)last_e, 1);
+            if (g == 0) {
+                if (k == 0) {
+                    up_hoe = o + (c + 1) * e + oe;  // row 0
+                    up_e = up_hoe;
+                } else if (c >= 0 && c < m) {
+                    up_hoe = sm->top[2 * (c & (WRING - 1))];
+                    up_e = sm->top[2 * (c & (WRING - 1)) + 1];
+                }
+            }
+            if (c >= 0 && c < m) {
+                const uint32_t sel = sm->sel[c & (WRING - 1)];
+                T diag = (c == 0) ? diag0 : prev_up;
+                prev_up = up_hoe;
+                T E = up_e, Ein = up_e;
+#pragma unroll
+                for (int r = 0; r < WR; r++) {
+                    T sg = C::sigma(prof[r], prof[r], sel);
+                    T Ad = C::addc(diag, (uint32_t)sg);
+                    F[r] = C::addmax(F[r], e_raw, Hoe[r]);
+                    T M = C::vmax(Ad, F[r]);
+                    T X = C::addc(M, oe_c);
+                    diag = Hoe[r];
+                    Ein = E;
+                    Hoe[r] = C::addmax(E, oe_raw, X);
+                    E = C::addmax(E, e_raw, X);
+                }
+                last_hoe = Hoe[WR - 1];
+                last_e = E;
+                if (g == WG - 1) {
+                    // border for the next stripe: (Hoe, E of the row below); the last
+                    // stripe keeps E of its own last row for the Hirschberg join
+                    sm->bot[2 * (c & (WRING - 1))] = last_hoe;
+                    sm->bot[2 * (c & (WRING - 1)) + 1] = last ? Ein : E;
+                }
+            }
+        }
+        __syncwarp();
+        for (int b = drained; b <= (m - 1) / BLOCK; b++) drain(b);
+        if (!last && g == 0) st_release(prog_mine, (m + BLOCK - 1) / BLOCK + 1);
+        if (last && g == 0) {
+            if (outH) outH[0] = col0(GLOBAL, n, o, e, ps.tb);
+            if (outE) outE[0] = col0(GLOBAL, n, o, e, ps.tb);
+        }
+    }
+}
+
+cudaError_t launch_wave(const WaveArgs &A, int grid, cudaStream_t st) {
+    wave_kernel<<<grid, 256, 0, st>>>(A);
+    return cudaGetLastError();
+}
+
+int wave_blocks_per_sm() {
+    int nb = 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, wave_kernel, 256, 0) != cudaSuccess) {
+        cudaGetLastError();
+        nb = 1;
+    }
+    return nb < 1 ? 1 : nb;
+}
+
+}  // namespace anyseq

@@ -1,0 +1,39 @@
+// Long-pair wavefront kernel (wave.cu).
+#pragma once
+#include <cstdint>
+#include <cuda_runtime.h>
+
+namespace anyseq {
+
+// One global pass over q[q0 .. q0+n) x s[s0 .. s0+m) (read reversed when rev),
+// column-0 open tb. Its stripes are numbered stripe0 .. stripe0 + ceil(n/512) - 1
+// in the launch; border rows at border + border_off (2 x m), progress counters
+// at prog + stripe0, last row written at last_H/last_E + out_off (m + 1 values).
+struct WavePass {
+    int64_t q0, s0;
+    int32_t n, m;
+    int32_t tb, rev;
+    int64_t border_off;
+    int64_t out_off;
+    int32_t stripe0, pad_;
+};
+
+struct WaveArgs {
+    const uint32_t *q2, *s2;      // 2-bit packed letters (global positions)
+    const WavePass *passes;       // device table, sorted by stripe0
+    int32_t n_passes, n_stripes;
+    int32_t o, e;                 // gap open, extend
+    uint32_t rowprof[5];          // profile words (global padding in word 4)
+    int2 *border;
+    int32_t *prog;                // per stripe: border blocks published (zeroed)
+    int32_t *stripe_counter;      // zeroed
+    int32_t *err;                 // zeroed; 1 after a wait gave up
+    int32_t *last_H, *last_E;     // optional outputs
+    int64_t spin_limit;           // iterations of one wait
+};
+
+cudaError_t launch_wave(const WaveArgs &A, int grid, cudaStream_t st);
+int wave_blocks_per_sm();
+constexpr int WAVE_ROWS = 512;    // rows per stripe
+
+}  // namespace anyseq

@@ -173,3 +173,44 @@ def test_short_read_workload_full_size_sampled(pkg, ctx):
     want = oracle_of(sub, args, 2)
     assert_parity(res[idx], want, sub)
     assert not np.any(res["flags"] & 1)  # all pairs passed the int16 range test
+
+
+@pytest.mark.parametrize("mode", MODES)
+@pytest.mark.parametrize("force32", [False, True])
+def test_protein_matrix_parity(pkg, ctx, mode, force32):
+    """20-letter alphabet with a seeded symmetric matrix (shared-memory query profile path)."""
+    mat = synth.protein_matrix(seed=3)
+    b = synth.random_pairs(400, 0, 500, alphabet=20, seed=1000 + mode, related=0.7, p_sub=0.3, p_indel=0.03)
+    args = (0, 0, -11, -1, mat)
+    assert_parity(run(pkg, ctx, b, args, mode, force32=force32), oracle_of(b, args, mode), b)
+
+
+def test_wide_alphabet_asymmetric_matrix(pkg, ctx):
+    st = synth.Stream(1100, 1)
+    mat = st.integers(-6, 9, 32 * 32).reshape(32, 32).astype(np.int8)
+    b = synth.random_pairs(200, 1, 300, alphabet=32, seed=1101)
+    for mode in MODES:
+        args = (0, 0, -7, -2, mat)
+        assert_parity(run(pkg, ctx, b, args, mode), oracle_of(b, args, mode), b)
+
+
+def test_negative_profile_routes_to_int32(pkg, ctx):
+    """mismatch below open+extend gives a negative profile byte: 32-bit lanes, exact."""
+    b = synth.random_pairs(200, 1, 300, seed=1200)
+    args = (2, -10, 0, -1)
+    for mode in MODES:
+        res = run(pkg, ctx, b, args, mode)
+        assert_parity(res, oracle_of(b, args, mode), b)
+        nonempty = (b.q_len() > 0) & (b.s_len() > 0)
+        assert np.all(res["flags"][nonempty] & 1)
+
+
+def test_protein_workload_full_size_sampled(pkg, ctx):
+    """65,536 protein pairs, local affine (open -11, extend -1): 3,000-pair sample vs the oracle."""
+    b = synth.protein_pairs()
+    args = (0, 0, -11, -1, synth.protein_matrix(seed=3))
+    res = run(pkg, ctx, b, args, 1)
+    st = synth.Stream(1300, 1)
+    idx = np.unique(st.integers(0, b.n_pairs - 1, 3000))
+    sub = b.subset(idx)
+    assert_parity(res[idx], oracle_of(sub, args, 1), sub)
