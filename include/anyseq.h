@@ -142,8 +142,11 @@ anyseq_status_t anyseq_align_long(anyseq_ctx *ctx,
 /* Tuning and test switches of a context: "force_int32" (0/1) routes every pair
  * to 32-bit lanes; "force_matrix_path" (0/1) scores every alphabet through the
  * shared-memory profile kernels (as used above 4 letters); "profile" (0/1) times
- * the DP kernels of each call with CUDA events on the call's stream. Unknown
- * keys: ANYSEQ_ERR_ARG. */
+ * the DP kernels of each call with CUDA events on the call's stream;
+ * "hirschberg_base_cells" (default 65536) is the subproblem size below which the
+ * divide-and-conquer traceback switches to a full matrix; "spin_limit" (default
+ * 2^24) bounds every device-side wait of the wavefront (ANYSEQ_ERR_TIMEOUT).
+ * Unknown keys: ANYSEQ_ERR_ARG. */
 anyseq_status_t anyseq_set_option(anyseq_ctx *ctx, const char *key, int64_t value);
 
 /* Statistics of the context's last call (host values, valid after the call's

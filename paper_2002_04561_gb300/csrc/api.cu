@@ -93,6 +93,16 @@ extern "C" anyseq_status_t anyseq_set_option(anyseq_ctx *ctx, const char *key, i
     if (!ctx || !key) return fail(ANYSEQ_ERR_ARG, "ctx or key is NULL");
     if (!strcmp(key, "force_int32")) { ctx->force32 = value != 0; return ANYSEQ_OK; }
     if (!strcmp(key, "force_matrix_path")) { ctx->force_matrix = value != 0; return ANYSEQ_OK; }
+    if (!strcmp(key, "hirschberg_base_cells")) {
+        if (value < 1) return fail(ANYSEQ_ERR_ARG, "hirschberg_base_cells must be >= 1");
+        ctx->base_cells = value;
+        return ANYSEQ_OK;
+    }
+    if (!strcmp(key, "spin_limit")) {
+        if (value < 1) return fail(ANYSEQ_ERR_ARG, "spin_limit must be >= 1");
+        ctx->spin_limit = value;
+        return ANYSEQ_OK;
+    }
     if (!strcmp(key, "profile")) {
         ctx->profile = value != 0;
         if (ctx->profile && !ctx->ev[0])

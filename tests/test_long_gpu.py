@@ -1,0 +1,106 @@
+"""GPU parity of the long-pair path (anyseq_align_long): the anti-diagonal
+stripe wavefront (score) and the divide-and-conquer traceback (CIGAR).
+
+* scores equal the oracle's linear-space global score for lengths that span
+  one to many 512-row stripes, ragged tails and n != m;
+* the CIGAR equals the oracle's Hirschberg (Myers-Miller) CIGAR under the same
+  midpoint rule, for small and large base sizes;
+* every CIGAR re-scores to the reported score (a property that holds at any
+  size), including a 200 kbp pair shaped like the long-genome workload.
+"""
+import numpy as np
+import pytest
+
+import oracle
+import synth
+from brute import rescore_cigar
+
+pytestmark = pytest.mark.gpu
+torch = pytest.importorskip("torch")
+
+
+@pytest.fixture(scope="module")
+def pkg():
+    if not torch.cuda.is_available():
+        pytest.skip("no GPU")
+    import paper_2002_04561_gb300 as p
+    p.load(build_if_missing=True)
+    return p
+
+
+@pytest.fixture(scope="module")
+def ctx(pkg):
+    c = pkg.Context(0)
+    yield c
+    c.close()
+
+
+C4 = (2, -3, -5, -2)
+
+
+def related(n, m_extra, seed, p_sub=0.05, p_indel=0.01):
+    st = synth.Stream(seed, 1)
+    q = synth.random_codes(st, n, 4)
+    s, _ = synth.mutate(q, np.array([0, n], np.int64), p_sub, p_indel, 0.3, 4, st)
+    return q, s[: max(0, len(s) + m_extra)]
+
+
+@pytest.mark.parametrize("n", [1, 5, 511, 512, 513, 1500, 3000])
+def test_long_score_parity(pkg, ctx, n):
+    for k, extra in enumerate([0, -3, 7]):
+        q, s = related(n, extra, seed=2000 + n + k)
+        out, _ = ctx.align_long(q, s, pkg.Scoring.make(*C4))
+        assert out["score"][0] == oracle.score(q, s, oracle.Scoring(*C4))[0]
+
+
+def test_long_score_unrelated_and_skewed(pkg, ctx):
+    st = synth.Stream(2100, 1)
+    for n, m in [(2000, 700), (700, 2000), (1025, 1), (1, 1025), (4096, 4096)]:
+        q = synth.random_codes(st, n, 4)
+        s = synth.random_codes(st, m, 4)
+        for args in (C4, (2, -1, 0, -1), (1, -4, -6, -1)):
+            out, _ = ctx.align_long(q, s, pkg.Scoring.make(*args))
+            assert out["score"][0] == oracle.score(q, s, oracle.Scoring(*args))[0], (n, m, args)
+
+
+def long_cigar(pkg, ctx, q, s, args):
+    cap = len(q) + len(s) + 4
+    cig = np.zeros(cap, dtype=np.uint32)
+    out, used = ctx.align_long(q, s, pkg.Scoring.make(*args), want=pkg.WANT_SCORE | pkg.WANT_CIGAR, cigar=cig)
+    return out[0], cig[:used]
+
+
+@pytest.mark.parametrize("base", [16, 1024, 1 << 16])
+def test_hirschberg_cigar_parity(pkg, ctx, base):
+    ctx.set_option("hirschberg_base_cells", base)
+    try:
+        for k, (n, extra) in enumerate([(40, 3), (700, -5), (1300, 11), (2600, 0)]):
+            for args in (C4, (2, -1, 0, -1), (3, -2, -4, -3)):
+                q, s = related(n, extra, seed=2200 + k)
+                res, cig = long_cigar(pkg, ctx, q, s, args)
+                want, _ = oracle.hirschberg(q, s, oracle.Scoring(*args), base)
+                assert np.array_equal(cig, want), (n, args, oracle.cigar_string(cig)[:60], oracle.cigar_string(want)[:60])
+                assert rescore_cigar(cig, q, s, (0, 0), oracle.Scoring(*args))[0] == res["score"]
+    finally:
+        ctx.set_option("hirschberg_base_cells", 1 << 16)
+
+
+def test_hirschberg_unrelated_pairs(pkg, ctx):
+    st = synth.Stream(2300, 1)
+    for n, m in [(900, 300), (300, 900), (1200, 1250)]:
+        q = synth.random_codes(st, n, 4)
+        s = synth.random_codes(st, m, 4)
+        res, cig = long_cigar(pkg, ctx, q, s, C4)
+        want, _ = oracle.hirschberg(q, s, oracle.Scoring(*C4))
+        assert np.array_equal(cig, want)
+
+
+def test_long_pair_60kbp_rescores(pkg, ctx):
+    """A 60 kbp pair shaped like the long-genome workload (1 % substitutions,
+    0.1 % indels, one 10 kbp inversion): the Hirschberg CIGAR re-scores to the
+    score of the wavefront pass, which equals the oracle's score."""
+    b = synth.long_pair(seed=4, n=60_000, inversion=10_000, n_inversions=1)
+    q, s = b.pair(0)
+    res, cig = long_cigar(pkg, ctx, q, s, C4)
+    assert rescore_cigar(cig, q, s, (0, 0), oracle.Scoring(*C4))[0] == res["score"]
+    assert res["score"] == oracle.score(q, s, oracle.Scoring(*C4))[0]
