@@ -139,6 +139,42 @@ anyseq_status_t anyseq_align_long(anyseq_ctx *ctx,
                                   uint32_t *cigar, uint64_t cigar_cap, uint64_t *cigar_used,
                                   void *cuda_stream);
 
+/*
+ * Learned band (an extension of the global alignment that keeps results exact).
+ * With ANYSEQ_BAND_LEARNED, anyseq_align_batch (global mode, scores) first runs
+ * a banded DP around a band proposed by a small network from k-mer diagonal
+ * features, accepts the banded score only under an exit certificate (no path
+ * that leaves the band can score more), doubles the band otherwise, and falls
+ * back to the full DP when the band would cover half of the matrix. Results are
+ * identical to the full DP; flags tell which route each pair took. The context
+ * must hold a model (anyseq_band_train or anyseq_band_model_load/set).
+ */
+#define ANYSEQ_BAND_FEATURES 64
+#define ANYSEQ_BAND_PARAMS 25090   /* W1 64x128, b1 128, W2 128x128, b2 128, W3 128x2, b3 2 (row-major, float) */
+
+/* 64 k-mer diagonal features per pair (k = 12, DNA codes 0..3): hits of sampled
+ * query k-mers in the subject binned by their offset from the straight line
+ * (0,0)-(n,m), divided by the number of sampled query k-mers. features: n_pairs x 64 floats. */
+anyseq_status_t anyseq_band_features(anyseq_ctx *ctx, const uint8_t *q, const int64_t *q_off, const uint8_t *s,
+                                     const int64_t *s_off, int64_t n_pairs, float *features, void *cuda_stream);
+/* Network parameters (float master copy; compute uses their bfloat16 rounding). */
+anyseq_status_t anyseq_band_model_get(anyseq_ctx *ctx, float *params, int64_t count);
+anyseq_status_t anyseq_band_model_set(anyseq_ctx *ctx, const float *params, int64_t count);
+anyseq_status_t anyseq_band_model_save(anyseq_ctx *ctx, const char *path);
+anyseq_status_t anyseq_band_model_load(anyseq_ctx *ctx, const char *path);
+/* Network outputs y (B x 2: band centre, log half-width) for features x (B x 64). */
+anyseq_status_t anyseq_band_forward(anyseq_ctx *ctx, const float *x, int64_t B, float *y, void *cuda_stream);
+/* Mean loss and its gradient (ANYSEQ_BAND_PARAMS floats) for targets (B x 2). */
+anyseq_status_t anyseq_band_gradient(anyseq_ctx *ctx, const float *x, const float *targets, int64_t B,
+                                     float *grad, float *loss, void *cuda_stream);
+/* Train the network on the GPU from example pairs: targets are the centre of
+ * the optimal path (full DP traceback) and the smallest doubling width whose
+ * band passes the certificate. epochs over the pairs in batches of 1024 with
+ * Adam at learning rate lr; the final mean loss goes to *loss (may be NULL). */
+anyseq_status_t anyseq_band_train(anyseq_ctx *ctx, const uint8_t *q, const int64_t *q_off, const uint8_t *s,
+                                  const int64_t *s_off, int64_t n_pairs, const anyseq_scoring_t *sc, int32_t epochs,
+                                  float lr, float *loss, void *cuda_stream);
+
 /* Tuning and test switches of a context: "force_int32" (0/1) routes every pair
  * to 32-bit lanes; "force_matrix_path" (0/1) scores every alphabet through the
  * shared-memory profile kernels (as used above 4 letters); "profile" (0/1) times
@@ -152,7 +188,9 @@ anyseq_status_t anyseq_set_option(anyseq_ctx *ctx, const char *key, int64_t valu
 /* Statistics of the context's last call (host values, valid after the call's
  * stream has finished): "launches" (kernels launched), "dp_ms" (time of the
  * int16x2 DP kernel, needs "profile"), "dp32_ms" (32-bit lanes), "pairs16",
- * "pairs32" (pairs per lane width). Unknown keys: ANYSEQ_ERR_ARG. */
+ * "pairs32" (pairs per lane width); with ANYSEQ_BAND_LEARNED also "band_cells"
+ * (cells relaxed by banded passes), "band_accepted", "band_fallback" (pairs),
+ * "band_rounds". Unknown keys: ANYSEQ_ERR_ARG. */
 anyseq_status_t anyseq_get_stat(anyseq_ctx *ctx, const char *key, double *value);
 
 /* Map ASCII A/C/G/T (either case) to codes 0..3; any other byte: ANYSEQ_ERR_ALPHABET.

@@ -6,15 +6,17 @@ relative to the straight line from (0, 0) to (n, m):
 
 * k = 12 letters of a DNA sequence (codes 0..3) form a 24-bit key, first
   letter in the lowest bits;
-* the query contributes the k-mers starting at positions i = 0, 4, 8, ...;
-  a key seen at several such positions keeps the smallest one;
+* the query contributes the k-mers starting at positions i = 0, t, 2t, ...
+  with stride t = 4 * ceil(n / 16384) (at most 4,097 sampled k-mers); a key
+  seen at several such positions keeps the smallest one;
 * every subject k-mer start j whose key occurs in the query gives a hit
   (i, j) with the integer deviation D = (j - i) * n - (m - n) * i (that is n
   times the offset from the straight line);
 * magnitude bucket of |D| / n (integer division): 0 for 0, otherwise
   1 + 2 * floor(log2(x)) + (second highest bit of x), capped at 31; bin
   32 + bucket for D >= 0 and 31 - bucket for D < 0;
-* counts divided by the number of hits in float32 (all zero without hits).
+* counts divided by the number of sampled query k-mers in float32 (all zero
+  when a sequence is shorter than k), so the total mass measures similarity.
 
 All binning is integer arithmetic, so any correct implementation produces the
 same bins; the one float operation is a correctly rounded float32 division.
@@ -26,6 +28,10 @@ import numpy as np
 K = 12
 STRIDE = 4
 NBINS = 64
+
+
+def stride(n: int) -> int:
+    return STRIDE * max(1, -(-n // 16384))
 
 
 def bucket(x: int) -> int:
@@ -55,7 +61,7 @@ def histogram_counts(q, s) -> np.ndarray:
         return counts
     qk = kmer_keys(q)
     first: dict[int, int] = {}
-    for i in range(0, len(qk), STRIDE):
+    for i in range(0, len(qk), stride(n)):
         first.setdefault(int(qk[i]), i)
     for j, key in enumerate(kmer_keys(s)):
         i = first.get(int(key))
@@ -67,12 +73,17 @@ def histogram_counts(q, s) -> np.ndarray:
     return counts
 
 
+def sampled(n: int) -> int:
+    """Number of sampled query k-mers."""
+    return 0 if n < K else (n - K) // stride(n) + 1
+
+
 def features(q, s) -> np.ndarray:
     counts = histogram_counts(q, s)
-    total = counts.sum()
-    if total == 0:
+    nk = sampled(len(q)) if len(s) >= K else 0
+    if nk == 0:
         return np.zeros(NBINS, dtype=np.float32)
-    return (counts.astype(np.float32) / np.float32(total)).astype(np.float32)
+    return (counts.astype(np.float32) / np.float32(nk)).astype(np.float32)
 
 
 def features_batch(batch) -> np.ndarray:

@@ -65,7 +65,11 @@ assert RESULT_DTYPE.itemsize == ctypes.sizeof(Result) == 40
 _lib = None
 EXPORTS = ["anyseq_create", "anyseq_destroy", "anyseq_align_batch", "anyseq_align_long",
            "anyseq_set_option", "anyseq_get_stat", "anyseq_encode_dna", "anyseq_last_error",
-           "anyseq_version"]
+           "anyseq_version", "anyseq_band_features", "anyseq_band_model_get", "anyseq_band_model_set",
+           "anyseq_band_model_save", "anyseq_band_model_load", "anyseq_band_forward",
+           "anyseq_band_gradient", "anyseq_band_train"]
+BAND_FEATURES = 64
+BAND_PARAMS = 25090
 
 
 def load(build_if_missing: bool = False):
@@ -86,11 +90,22 @@ def load(build_if_missing: bool = False):
     lib.anyseq_set_option.argtypes = [P, ctypes.c_char_p, I64]
     lib.anyseq_get_stat.argtypes = [P, ctypes.c_char_p, ctypes.POINTER(ctypes.c_double)]
     lib.anyseq_encode_dna.argtypes = [P, P, I64]
+    F32 = ctypes.c_float
+    lib.anyseq_band_features.argtypes = [P, P, P, P, P, I64, P, P]
+    lib.anyseq_band_model_get.argtypes = [P, P, I64]
+    lib.anyseq_band_model_set.argtypes = [P, P, I64]
+    lib.anyseq_band_model_save.argtypes = [P, ctypes.c_char_p]
+    lib.anyseq_band_model_load.argtypes = [P, ctypes.c_char_p]
+    lib.anyseq_band_forward.argtypes = [P, P, I64, P, P]
+    lib.anyseq_band_gradient.argtypes = [P, P, P, I64, P, P, P]
+    lib.anyseq_band_train.argtypes = [P, P, P, P, P, I64, P, I32, F32, P, P]
     lib.anyseq_last_error.restype = ctypes.c_char_p
     lib.anyseq_last_error.argtypes = []
     lib.anyseq_version.restype = ctypes.c_char_p
     for name in ["anyseq_create", "anyseq_destroy", "anyseq_align_batch", "anyseq_align_long",
-                 "anyseq_set_option", "anyseq_get_stat", "anyseq_encode_dna"]:
+                 "anyseq_set_option", "anyseq_get_stat", "anyseq_encode_dna", "anyseq_band_features",
+                 "anyseq_band_model_get", "anyseq_band_model_set", "anyseq_band_model_save",
+                 "anyseq_band_model_load", "anyseq_band_forward", "anyseq_band_gradient", "anyseq_band_train"]:
         getattr(lib, name).restype = ctypes.c_int
     _lib = lib
     return lib
@@ -180,6 +195,53 @@ class Context:
             self.h, _ptr(q), n, _ptr(s), m, ctypes.byref(scoring), mode, want, _ptr(out), _ptr(cigar), cap,
             ctypes.byref(used), _stream_handle(stream)))
         return out, used.value
+
+
+    # ---------------------------------------------------------------- learned band
+    def band_features(self, q, q_off, s, s_off, out=None, stream=None):
+        n_pairs = len(q_off) - 1
+        if out is None:
+            out = np.zeros((n_pairs, BAND_FEATURES), dtype=np.float32)
+        _check(load().anyseq_band_features(self.h, _ptr(q), _ptr(q_off), _ptr(s), _ptr(s_off), n_pairs,
+                                           _ptr(out), _stream_handle(stream)))
+        return out
+
+    def band_model_get(self) -> np.ndarray:
+        out = np.zeros(BAND_PARAMS, dtype=np.float32)
+        _check(load().anyseq_band_model_get(self.h, _ptr(out), BAND_PARAMS))
+        return out
+
+    def band_model_set(self, params):
+        params = np.ascontiguousarray(params, dtype=np.float32)
+        _check(load().anyseq_band_model_set(self.h, _ptr(params), params.size))
+
+    def band_model_save(self, path: str):
+        _check(load().anyseq_band_model_save(self.h, path.encode()))
+
+    def band_model_load(self, path: str):
+        _check(load().anyseq_band_model_load(self.h, path.encode()))
+
+    def band_forward(self, x, stream=None) -> np.ndarray:
+        x = np.ascontiguousarray(x, dtype=np.float32)
+        y = np.zeros((x.shape[0], 2), dtype=np.float32)
+        _check(load().anyseq_band_forward(self.h, _ptr(x), x.shape[0], _ptr(y), _stream_handle(stream)))
+        return y
+
+    def band_gradient(self, x, targets, stream=None):
+        x = np.ascontiguousarray(x, dtype=np.float32)
+        t = np.ascontiguousarray(targets, dtype=np.float32)
+        g = np.zeros(BAND_PARAMS, dtype=np.float32)
+        loss = ctypes.c_float(0)
+        _check(load().anyseq_band_gradient(self.h, _ptr(x), _ptr(t), x.shape[0], _ptr(g), ctypes.byref(loss),
+                                           _stream_handle(stream)))
+        return float(loss.value), g
+
+    def band_train(self, q, q_off, s, s_off, scoring: Scoring, epochs: int = 30, lr: float = 1e-3, stream=None):
+        loss = ctypes.c_float(0)
+        _check(load().anyseq_band_train(self.h, _ptr(q), _ptr(q_off), _ptr(s), _ptr(s_off), len(q_off) - 1,
+                                        ctypes.byref(scoring), epochs, lr, ctypes.byref(loss),
+                                        _stream_handle(stream)))
+        return float(loss.value)
 
 
 def encode_dna(text: str) -> np.ndarray:

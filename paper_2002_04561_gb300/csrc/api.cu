@@ -85,6 +85,7 @@ extern "C" anyseq_status_t anyseq_destroy(anyseq_ctx *ctx) {
     for (auto &b : ctx->bufs) cudaFree(b.p);
     for (auto &h : ctx->pinned) cudaFreeHost(h.p);
     for (auto &e : ctx->ev) if (e) cudaEventDestroy(e);
+    if (ctx->mlp) cudaFree(ctx->mlp);
     delete ctx;
     return ANYSEQ_OK;
 }
@@ -119,6 +120,10 @@ extern "C" anyseq_status_t anyseq_get_stat(anyseq_ctx *ctx, const char *key, dou
     else if (!strcmp(key, "dp32_ms")) *value = ctx->dp32_ms;
     else if (!strcmp(key, "pairs16")) *value = (double)ctx->pairs16;
     else if (!strcmp(key, "pairs32")) *value = (double)ctx->pairs32;
+    else if (!strcmp(key, "band_cells")) *value = (double)ctx->band_cells;
+    else if (!strcmp(key, "band_accepted")) *value = (double)ctx->band_accepted;
+    else if (!strcmp(key, "band_fallback")) *value = (double)ctx->band_fallback;
+    else if (!strcmp(key, "band_rounds")) *value = (double)ctx->band_rounds;
     else return fail(ANYSEQ_ERR_ARG, "unknown statistic '%s'", key);
     return ANYSEQ_OK;
 }
@@ -319,6 +324,7 @@ anyseq_status_t anyseq::batch_scores(anyseq_ctx *ctx, const BatchInput &in, cons
     if (sp_min < -128 || sp_max > 127)
         return fail(ANYSEQ_ERR_ARG, "sigma - open - extend spans [%d, %d], outside the int8 profile", sp_min, sp_max);
     P.force32 = ctx->force32 || sp_min < 0;
+    P.select = in.select;
     CUDA_TRY(launch_prep(P, st));
     ctx->launches += 6;  // pack/validate x2, bin, tile sums, tile scan, scatter
 
@@ -407,24 +413,9 @@ anyseq_status_t anyseq::batch_scores(anyseq_ctx *ctx, const BatchInput &in, cons
     return ANYSEQ_OK;
 }
 
-extern "C" anyseq_status_t anyseq_align_batch(anyseq_ctx *ctx, const uint8_t *q, const int64_t *q_off,
-                                              const uint8_t *s, const int64_t *s_off, int64_t n_pairs,
-                                              const anyseq_scoring_t *sc, int32_t mode, uint32_t want,
-                                              anyseq_result_t *out, uint32_t *cigar, uint64_t cigar_cap,
-                                              uint64_t *cigar_used, void *cuda_stream) {
-    if (!ctx) return fail(ANYSEQ_ERR_ARG, "ctx is NULL");
-    if (n_pairs < 0) return fail(ANYSEQ_ERR_ARG, "n_pairs < 0");
-    if (n_pairs == 0) { if (cigar_used) *cigar_used = 0; return ANYSEQ_OK; }
-    if (!q_off || !s_off || !out) return fail(ANYSEQ_ERR_ARG, "q_off, s_off and out must not be NULL");
-    if (n_pairs >= (1ll << 31) - 2) return fail(ANYSEQ_ERR_ARG, "n_pairs too large");
-    TRY(check_scoring(sc, mode));
-    cudaStream_t st = (cudaStream_t)cuda_stream;
-    if (cudaSetDevice(ctx->device) != cudaSuccess) return fail(ANYSEQ_ERR_CUDA, "cudaSetDevice failed");
+anyseq_status_t anyseq::stage_batch(anyseq_ctx *ctx, const uint8_t *q, const int64_t *q_off, const uint8_t *s,
+                                    const int64_t *s_off, int64_t n_pairs, BatchInput &in, cudaStream_t st) {
     anyseq_status_t s2 = ANYSEQ_OK;
-
-    // offsets: stage, then read totals and maxima
-    ctx->launches = 0;
-    BatchInput in;
     in.n_pairs = n_pairs;
     const void *dq_off, *ds_off;
     TRY(stage_input(ctx, "in_qoff", q_off, (n_pairs + 1) * sizeof(int64_t), st, &dq_off));
@@ -458,6 +449,29 @@ extern "C" anyseq_status_t anyseq_align_batch(anyseq_ctx *ctx, const uint8_t *q,
     in.q = (const uint8_t *)dq;
     in.s = (const uint8_t *)ds;
 
+    return ANYSEQ_OK;
+}
+
+extern "C" anyseq_status_t anyseq_align_batch(anyseq_ctx *ctx, const uint8_t *q, const int64_t *q_off,
+                                              const uint8_t *s, const int64_t *s_off, int64_t n_pairs,
+                                              const anyseq_scoring_t *sc, int32_t mode, uint32_t want,
+                                              anyseq_result_t *out, uint32_t *cigar, uint64_t cigar_cap,
+                                              uint64_t *cigar_used, void *cuda_stream) {
+    if (!ctx) return fail(ANYSEQ_ERR_ARG, "ctx is NULL");
+    if (n_pairs < 0) return fail(ANYSEQ_ERR_ARG, "n_pairs < 0");
+    if (n_pairs == 0) { if (cigar_used) *cigar_used = 0; return ANYSEQ_OK; }
+    if (!q_off || !s_off || !out) return fail(ANYSEQ_ERR_ARG, "q_off, s_off and out must not be NULL");
+    if (n_pairs >= (1ll << 31) - 2) return fail(ANYSEQ_ERR_ARG, "n_pairs too large");
+    TRY(check_scoring(sc, mode));
+    cudaStream_t st = (cudaStream_t)cuda_stream;
+    if (cudaSetDevice(ctx->device) != cudaSuccess) return fail(ANYSEQ_ERR_CUDA, "cudaSetDevice failed");
+    anyseq_status_t s2 = ANYSEQ_OK;
+
+    // offsets: stage, then read totals and maxima
+    ctx->launches = 0;
+    BatchInput in;
+    TRY(stage_batch(ctx, q, q_off, s, s_off, n_pairs, in, st));
+
     int32_t *score = arena<int32_t>(ctx, "r_score", n_pairs, &s2);
     int32_t *eq = arena<int32_t>(ctx, "r_eq", n_pairs, &s2);
     int32_t *es = arena<int32_t>(ctx, "r_es", n_pairs, &s2);
@@ -465,7 +479,11 @@ extern "C" anyseq_status_t anyseq_align_batch(anyseq_ctx *ctx, const uint8_t *q,
     if (s2 != ANYSEQ_OK) return s2;
     const bool want_cigar = (want & ANYSEQ_WANT_CIGAR) != 0;
     TbOut tbo;
-    TRY(batch_scores(ctx, in, sc, mode, score, eq, es, flags, st, want_cigar ? &tbo : nullptr));
+    if ((want & ANYSEQ_BAND_LEARNED) && !want_cigar && mode == ANYSEQ_GLOBAL && sc->alphabet <= 4) {
+        TRY(band_scores(ctx, in, sc, score, eq, es, flags, st));
+    } else {
+        TRY(batch_scores(ctx, in, sc, mode, score, eq, es, flags, st, want_cigar ? &tbo : nullptr));
+    }
 
     int32_t *bq = nullptr, *bs = nullptr;
     int64_t *clen = nullptr, *coff = nullptr;

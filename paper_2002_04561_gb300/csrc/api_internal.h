@@ -23,6 +23,10 @@ struct anyseq_ctx {
     int force_matrix = 0;         // use the shared-memory profile path for any alphabet (testing)
     int64_t spin_limit = 1ll << 24;  // iterations of one device-side wait (x ~64 ns)
     int64_t base_cells = 1 << 16;    // Hirschberg base-case size
+    // band network (device): float master, bfloat16 copies, gradients, Adam moments
+    float *mlp = nullptr;
+    bool mlp_ready = false;
+    int64_t band_cells = 0, band_accepted = 0, band_fallback = 0, band_rounds = 0;
     int profile = 0;              // time the DP kernels with events
     cudaEvent_t ev[4] = {nullptr, nullptr, nullptr, nullptr};
     // statistics of the last call
@@ -41,6 +45,7 @@ struct BatchInput {
     const uint8_t *q = nullptr, *s = nullptr;          // device
     const int64_t *q_off = nullptr, *s_off = nullptr;  // device
     int64_t n_pairs = 0, q_len = 0, s_len = 0, max_n = 0, max_m = 0;
+    const uint8_t *select = nullptr;                   // optional subset of pairs (device)
 };
 
 anyseq_status_t fail(anyseq_status_t st, const char *fmt, ...);
@@ -58,6 +63,10 @@ struct TbOut {
     int64_t dir_words = 0;
 };
 
+anyseq_status_t stage_batch(anyseq_ctx *ctx, const uint8_t *q, const int64_t *q_off, const uint8_t *s,
+                            const int64_t *s_off, int64_t n_pairs, BatchInput &in, cudaStream_t st);
+anyseq_status_t band_scores(anyseq_ctx *ctx, const BatchInput &in, const anyseq_scoring_t *sc, int32_t *score,
+                            int32_t *eq, int32_t *es, uint32_t *flags, cudaStream_t st);
 anyseq_status_t long_last_row(anyseq_ctx *ctx, const uint32_t *q2, int64_t q0, int32_t n, const uint32_t *s2,
                               int64_t s0, int32_t m, bool rev, int32_t tb, const anyseq_scoring_t *sc, int32_t *H,
                               int32_t *E, cudaStream_t st);

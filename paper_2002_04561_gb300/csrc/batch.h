@@ -97,6 +97,7 @@ struct PrepArgs {
     int32_t *score, *end_q, *end_s; // for trivial pairs
     uint32_t *flags;
     int32_t force32;                // route every pair to 32-bit lanes
+    const uint8_t *select;          // optional: only pairs with select[p] != 0 are touched
 };
 
 cudaError_t launch_prep(const PrepArgs &P, cudaStream_t st);

@@ -75,6 +75,7 @@ __global__ void bin_kernel(PrepArgs P) {
     for (int64_t p0 = (int64_t)blockIdx.x * blockDim.x; p0 < P.n_pairs; p0 += stride) {
         const int64_t p = p0 + (base - (int64_t)blockIdx.x * blockDim.x);
         if (p >= P.n_pairs) continue;
+        if (P.select && !P.select[p]) { P.key[p] = 0xFFFFFFFFu; continue; }
         int64_t n = P.q_off[p + 1] - P.q_off[p];
         int64_t m = P.s_off[p + 1] - P.s_off[p];
         if (n == 0 || m == 0) {
