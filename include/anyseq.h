@@ -193,6 +193,26 @@ anyseq_status_t anyseq_set_option(anyseq_ctx *ctx, const char *key, int64_t valu
  * "band_rounds". Unknown keys: ANYSEQ_ERR_ARG. */
 anyseq_status_t anyseq_get_stat(anyseq_ctx *ctx, const char *key, double *value);
 
+/*
+ * Global score of one long pair, allocating no device memory. The paper has
+ * no counterpart: this is for callers that cannot let the library call
+ * cudaMalloc/cudaFree, such as a process whose framework owns all device
+ * memory through its own pool, or a latency-bound service that cannot accept
+ * the synchronisation those calls imply. It runs the same wavefront pass as
+ * anyseq_align_long, with all scratch in one fixed device array of the library
+ * (about 21 MB on every GPU that loads it, held until the process exits).
+ *   q, s    device arrays of codes 0..3, lengths 1 <= n, m <= ANYSEQ_NOALLOC_MAX_LEN
+ *           (longer inputs: ANYSEQ_ERR_ARG)
+ *   score   device int32 receiving the optimal global score
+ * No context is needed. The first call on a device resolves the array's device
+ * address (once per device); make that first call before any stream capture.
+ * The call returns after its stream has finished (it reads the error flags).
+ * All calls share the array: calls that overlap on the GPU race on it.
+ */
+#define ANYSEQ_NOALLOC_MAX_LEN 1048576
+anyseq_status_t anyseq_align_long_noalloc(const uint8_t *q, int64_t n, const uint8_t *s, int64_t m,
+                                          const anyseq_scoring_t *sc, int32_t *score, void *cuda_stream);
+
 /* Map ASCII A/C/G/T (either case) to codes 0..3; any other byte: ANYSEQ_ERR_ALPHABET.
  * Host pointers only; synchronous. */
 anyseq_status_t anyseq_encode_dna(const char *ascii, uint8_t *codes, int64_t len);

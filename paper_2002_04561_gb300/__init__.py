@@ -67,7 +67,8 @@ EXPORTS = ["anyseq_create", "anyseq_destroy", "anyseq_align_batch", "anyseq_alig
            "anyseq_set_option", "anyseq_get_stat", "anyseq_encode_dna", "anyseq_last_error",
            "anyseq_version", "anyseq_band_features", "anyseq_band_model_get", "anyseq_band_model_set",
            "anyseq_band_model_save", "anyseq_band_model_load", "anyseq_band_forward",
-           "anyseq_band_gradient", "anyseq_band_train"]
+           "anyseq_band_gradient", "anyseq_band_train", "anyseq_align_long_noalloc"]
+NOALLOC_MAX_LEN = 1048576
 BAND_FEATURES = 64
 BAND_PARAMS = 25090
 
@@ -99,13 +100,15 @@ def load(build_if_missing: bool = False):
     lib.anyseq_band_forward.argtypes = [P, P, I64, P, P]
     lib.anyseq_band_gradient.argtypes = [P, P, P, I64, P, P, P]
     lib.anyseq_band_train.argtypes = [P, P, P, P, P, I64, P, I32, F32, P, P]
+    lib.anyseq_align_long_noalloc.argtypes = [P, I64, P, I64, P, P, P]
     lib.anyseq_last_error.restype = ctypes.c_char_p
     lib.anyseq_last_error.argtypes = []
     lib.anyseq_version.restype = ctypes.c_char_p
     for name in ["anyseq_create", "anyseq_destroy", "anyseq_align_batch", "anyseq_align_long",
                  "anyseq_set_option", "anyseq_get_stat", "anyseq_encode_dna", "anyseq_band_features",
                  "anyseq_band_model_get", "anyseq_band_model_set", "anyseq_band_model_save",
-                 "anyseq_band_model_load", "anyseq_band_forward", "anyseq_band_gradient", "anyseq_band_train"]:
+                 "anyseq_band_model_load", "anyseq_band_forward", "anyseq_band_gradient", "anyseq_band_train",
+                 "anyseq_align_long_noalloc"]:
         getattr(lib, name).restype = ctypes.c_int
     _lib = lib
     return lib
@@ -242,6 +245,16 @@ class Context:
                                         ctypes.byref(scoring), epochs, lr, ctypes.byref(loss),
                                         _stream_handle(stream)))
         return float(loss.value)
+
+
+def align_long_noalloc(q, s, scoring: Scoring, score, stream=None):
+    """anyseq_align_long_noalloc: global score of one long pair into the device
+    int32 tensor ``score``, with no device allocation by the library (for
+    callers whose device memory is owned by someone else; see the header)."""
+    n = q.numel() if hasattr(q, "numel") else len(q)
+    m = s.numel() if hasattr(s, "numel") else len(s)
+    _check(load().anyseq_align_long_noalloc(_ptr(q), n, _ptr(s), m, ctypes.byref(scoring), _ptr(score),
+                                            _stream_handle(stream)))
 
 
 def encode_dna(text: str) -> np.ndarray:
