@@ -11,7 +11,10 @@ Prints one JSON line. ``value`` is cell updates per second (GCUPS) with inputs
 resident in device memory; ``e2e`` is the same metric through the C ABI with
 pinned host buffers, host-device copies inside the timed region; ``roofline``
 is the DP kernel's cell rate against the integer-issue bound
-SMs x clock x 128 lane-ops per clock / (3.5 ops per cell for int16x2 affine);
+SMs x clock x 64 lane-ops per clock / (3.5 ops per cell for int16x2 affine):
+the DPX add-max, per-half max and byte-permute instructions the recurrence
+needs issue at 64 lanes per clock per SM on GB300 (measured with instruction
+counters; the nominal 128 would halve every fraction, reported beside it);
 ``cpu_baseline`` is the CPU oracle on the host cores on a bounded sample.
 ``--impl reference`` times the CPU oracle itself on the same workload.
 """
@@ -39,7 +42,8 @@ WORKLOAD = "short_reads_262144_semiglobal_affine"
 SCORING = (1, -4, -6, -1)
 MODE = 2  # semi-global
 I_ALG = 3.5  # algorithmic integer ops per cell, int16x2 affine (fixed before measuring)
-LANE_OPS_PER_CLK = 128  # 4 SM sub-partitions x 32 lanes
+LANE_OPS_PER_CLK = 64  # measured issue rate of DPX / VIMNMX / PRMT on sm_103 (lanes per clock per SM)
+NOMINAL_LANE_OPS = 128  # 4 SM sub-partitions x 32 lanes
 L2_BYTES = 129 * 2**20
 
 
@@ -224,11 +228,88 @@ def run_reference(args, ws, rank):
     print(json.dumps(line), flush=True)
 
 
+def timed_events(fn, reps, stream):
+    """Mean milliseconds of fn over reps runs, CUDA events on the stream, after one warm-up."""
+    import torch
+    fn()
+    torch.cuda.synchronize()
+    a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    a.record(stream)
+    for _ in range(reps):
+        fn()
+    b.record(stream)
+    b.synchronize()
+    return a.elapsed_time(b) / reps
+
+
+def secondary_workloads(pkg, ctx, device):
+    """The other workloads of the method, one line each (not the headline)."""
+    import torch
+    stream = torch.cuda.current_stream()
+    dev = lambda a: torch.from_numpy(np.ascontiguousarray(a)).to(device)
+    out = {}
+    # single 1,000 x 1,100 global pair with CIGAR (latency)
+    b = synth.single_pair()
+    sc = pkg.Scoring.make(2, -1, 0, -2)
+    cig = torch.zeros(4096, dtype=torch.int32, device=device)
+    res = torch.zeros(40, dtype=torch.uint8, device=device)
+    args = (dev(b.q), dev(b.q_off), dev(b.s), dev(b.s_off))
+    ms = timed_events(lambda: ctx.align_batch(*args, sc, pkg.GLOBAL, want=7, out=res, cigar=cig), 20, stream)
+    out["single_pair_1000x1100_cigar"] = {"us": 1e3 * ms, "GCUPS": b.cells() / ms / 1e6}
+    # protein, local affine, score and CIGAR
+    b = synth.protein_pairs()
+    sc = pkg.Scoring.make(0, 0, -11, -1, matrix=synth.protein_matrix(3))
+    args = (dev(b.q), dev(b.q_off), dev(b.s), dev(b.s_off))
+    res = torch.zeros(b.n_pairs * 40, dtype=torch.uint8, device=device)
+    ms = timed_events(lambda: ctx.align_batch(*args, sc, pkg.LOCAL, out=res), 5, stream)
+    cap = int(b.q_len().sum() + b.s_len().sum() + b.n_pairs)
+    cig = torch.zeros(cap, dtype=torch.int32, device=device)
+    ms2 = timed_events(lambda: ctx.align_batch(*args, sc, pkg.LOCAL, want=7, out=res, cigar=cig), 3, stream)
+    out["protein_65536_local_affine"] = {"score_ms": ms, "score_GCUPS": b.cells() / ms / 1e6,
+                                         "cigar_ms": ms2, "cigar_GCUPS": b.cells() / ms2 / 1e6}
+    # 1 Mbp x 1 Mbp global affine: wavefront score, divide-and-conquer CIGAR
+    b = synth.long_pair()
+    qd, sd = dev(b.q), dev(b.s)
+    sc = pkg.Scoring.make(2, -3, -5, -2)
+    ms = timed_events(lambda: ctx.align_long(qd, sd, sc), 2, stream)
+    hcig = np.zeros(len(b.q) + len(b.s) + 4, np.uint32)
+    t0 = time.perf_counter()
+    r, used = ctx.align_long(qd, sd, sc, want=7, cigar=hcig)
+    hb_s = time.perf_counter() - t0
+    out["long_pair_1Mbp_global_affine"] = {"score_s": ms / 1e3, "score_GCUPS": b.cells() / ms / 1e6,
+                                           "cigar_total_s": hb_s, "cigar_words": int(used),
+                                           "score": int(r["score"][0])}
+    del qd, sd
+    # learned band vs full DP on 65,536 pairs of 1-10 kbp (scores must be equal)
+    train = synth.band_pairs(n_pairs=2048, seed=105)
+    sc = pkg.Scoring.make(2, -3, -5, -2)
+    t0 = time.perf_counter()
+    loss = ctx.band_train(train.q, train.q_off, train.s, train.s_off, sc, epochs=40, lr=1e-3)
+    train_s = time.perf_counter() - t0
+    b = synth.band_pairs()
+    args = (dev(b.q), dev(b.q_off), dev(b.s), dev(b.s_off))
+    full = torch.zeros(b.n_pairs * 40, dtype=torch.uint8, device=device)
+    band = torch.zeros(b.n_pairs * 40, dtype=torch.uint8, device=device)
+    ms_full = timed_events(lambda: ctx.align_batch(*args, sc, pkg.GLOBAL, out=full), 2, stream)
+    ms_band = timed_events(lambda: ctx.align_batch(*args, sc, pkg.GLOBAL, want=1 | pkg.BAND_LEARNED, out=band), 2,
+                           stream)
+    fr = full.cpu().numpy().view(pkg.RESULT_DTYPE)
+    br = band.cpu().numpy().view(pkg.RESULT_DTYPE)
+    out["band_65536_1_10kbp_global_affine"] = {
+        "pairs_per_s_full_dp": b.n_pairs / ms_full * 1e3, "pairs_per_s_learned_band": b.n_pairs / ms_band * 1e3,
+        "speedup": ms_full / ms_band, "scores_equal": bool(np.array_equal(fr["score"], br["score"])),
+        "band_accepted": int(((br["flags"] & pkg.FLAG_BAND_ACCEPTED) != 0).sum()),
+        "full_dp_fallback": int(((br["flags"] & pkg.FLAG_FULL_FALLBACK) != 0).sum()),
+        "full_dp_GCUPS": b.cells() / ms_full / 1e6, "train_s": train_s, "train_loss": loss}
+    return out
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=10)
-    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--steps", type=int, default=60)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--no-extra", action="store_true", help="skip the secondary workloads")
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     args = ap.parse_args()
@@ -260,12 +341,11 @@ def main():
     def step():
         ctx.align_batch(q, q_off, s, s_off, sc, MODE, out=out)
 
+    clocks = ClockSampler(local)
+    clocks.start()  # samples warm-up and timed steps (the timed region alone is shorter than the 200 ms period)
     for _ in range(max(3, args.warmup)):
         step()
     torch.cuda.synchronize()
-
-    clocks = ClockSampler(local)
-    clocks.start()
     barrier(ws)
     torch.cuda.synchronize()
     step_ms, dp_ms, launches = [], [], 0
@@ -318,7 +398,8 @@ def main():
             "frac": achieved / peak_gcups, "traffic": profiled_traffic(),
             "peak_basis": f"{n_sm} SMs x {f_max / 1e6:.0f} MHz (max) x {LANE_OPS_PER_CLK} lane-ops/clk / "
                           f"{I_ALG} ops per cell",
-            "kernel": "batch_kernel<CellI16x2, SEMIGLOBAL>", "kernel_ms": dp_avg}
+            "kernel": "batch_kernel<CellI16x2, SEMIGLOBAL>", "kernel_ms": dp_avg,
+            "frac_nominal_128": achieved / (peak_gcups * NOMINAL_LANE_OPS / LANE_OPS_PER_CLK)}
     if clk.get("sm_mhz"):
         roof["frac_at_sampled_clock"] = achieved / (n_sm * clk["sm_mhz"] * 1e6 * LANE_OPS_PER_CLK / I_ALG / 1e9)
 
@@ -337,6 +418,10 @@ def main():
     }
     if rank == 0 and ws == 1 and not args.no_cpu_baseline:
         line["cpu_baseline"] = cpu_baseline(batch)
+    if rank == 0 and not args.no_extra:
+        del q, q_off, s, s_off, out
+        torch.cuda.empty_cache()
+        line["workloads"] = secondary_workloads(pkg, ctx, device)
     if rank == 0:
         print(json.dumps(line), flush=True)
     ctx.close()
