@@ -310,6 +310,7 @@ def main():
     ap.add_argument("--steps", type=int, default=60)
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--no-extra", action="store_true", help="skip the secondary workloads")
+    ap.add_argument("--pairs", type=int, default=262144, help="pairs per GPU (profiling runs use fewer)")
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     args = ap.parse_args()
@@ -329,7 +330,7 @@ def main():
     ctx = pkg.Context(local)
     ctx.set_option("profile", 1)
 
-    batch = synth.short_reads(seed=2 + 1000 * rank)
+    batch = synth.short_reads(n_pairs=args.pairs, seed=2 + 1000 * rank)
     cells = batch.cells()
     dev = lambda a: torch.from_numpy(np.ascontiguousarray(a)).to(device)
     q, q_off, s, s_off = dev(batch.q), dev(batch.q_off), dev(batch.s), dev(batch.s_off)
@@ -407,7 +408,8 @@ def main():
         "metric": METRIC, "value": value, "unit": "GCUPS", "n_gpus": ws, "steps": args.steps,
         "warmup": max(3, args.warmup), "ms_per_step": total_ms / args.steps, "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "int16x2", "data": "synthetic",
-        "config": {"workload": WORKLOAD, "n_pairs_per_gpu": batch.n_pairs, "cells_per_gpu": cells,
+        "config": {"workload": WORKLOAD if args.pairs == 262144 else f"short_reads_{args.pairs}_semiglobal_affine",
+                   "n_pairs_per_gpu": batch.n_pairs, "cells_per_gpu": cells,
                    "query_len": "100-250", "target": "query + 4% sub + 1% indel + 20bp flanks",
                    "scoring": "semiglobal +1/-4 open -6 extend -1", "l2": "flushed between steps (258 MB write)",
                    "pairs_per_s": batch.n_pairs * ws * args.steps / (total_ms / 1e3)},
