@@ -104,3 +104,20 @@ def test_long_pair_60kbp_rescores(pkg, ctx):
     res, cig = long_cigar(pkg, ctx, q, s, C4)
     assert rescore_cigar(cig, q, s, (0, 0), oracle.Scoring(*C4))[0] == res["score"]
     assert res["score"] == oracle.score(q, s, oracle.Scoring(*C4))[0]
+
+
+def test_wavefront_wait_limit_reports_timeout(pkg, ctx):
+    """A wait limit of one iteration makes a stripe give up on its predecessor:
+    the kernel raises its error flag, every stripe returns, the call reports
+    ANYSEQ_ERR_TIMEOUT, and the context keeps working afterwards."""
+    q, s = related(5000, 0, seed=2400)
+    ctx.set_option("spin_limit", 1)
+    try:
+        with pytest.raises(pkg.AnyseqError) as ei:
+            for _ in range(20):  # a stripe that finds its border already published does not wait
+                ctx.align_long(q, s, pkg.Scoring.make(*C4))
+        assert ei.value.status == 5
+    finally:
+        ctx.set_option("spin_limit", 1 << 24)
+    out, _ = ctx.align_long(q, s, pkg.Scoring.make(*C4))
+    assert out["score"][0] == oracle.score(q, s, oracle.Scoring(*C4))[0]
