@@ -246,6 +246,60 @@ def timed_events(fn, reps, stream):
     return a.elapsed_time(b) / reps
 
 
+def serving_workload(pkg, n_requests: int = 3000, load: float = 0.8):
+    """The serving mix (70 % 100-300 bp, 25 % 1-10 kbp, 5 % 50-200 kbp, global
+    affine +2/-3/-5/-2) through the native request queue: capacity with every
+    request queued at once, then Poisson arrivals at `load` x capacity; latency
+    from submit to completion as the server measures it."""
+    import queue
+    import threading
+    sc = pkg.Scoring.make(2, -3, -5, -2)
+    arr = synth.serving_mix(n_requests, rate_per_s=1.0)
+    pairs = [arr.batch.pair(k) for k in range(n_requests)]
+    cells = arr.batch.cells()
+
+    def run(times):
+        srv = pkg.Server(sc, mode=pkg.GLOBAL, max_wait_us=500, max_batch_pairs=8192)
+        try:
+            tq = queue.Queue()
+
+            def submitter():
+                t0 = time.perf_counter()
+                for k in range(n_requests):
+                    if times is not None:
+                        delay = t0 + times[k] - time.perf_counter()
+                        if delay > 0:
+                            time.sleep(delay)
+                    tq.put(srv.submit(*pairs[k]))
+
+            start = time.perf_counter()
+            th = threading.Thread(target=submitter)
+            th.start()
+            lat = np.zeros(n_requests)
+            for k in range(n_requests):
+                _, lat[k] = srv.wait(tq.get())
+            th.join()
+            wall = time.perf_counter() - start
+            return wall, lat * 1e-6, srv.stat("batches"), srv.stat("long_pairs")
+        finally:
+            srv.close()
+
+    run(None)  # warm-up: builds the context's scratch
+    wall, _, _, _ = run(None)
+    capacity = n_requests / wall
+    rate = load * capacity
+    wall, lat, batches, longs = run(arr.times / rate)
+    res = {"requests": n_requests, "capacity_req_per_s": capacity, "capacity_GCUPS": cells / (n_requests / capacity) / 1e9,
+           "offered_req_per_s": rate, "achieved_req_per_s": n_requests / wall,
+           "p50_ms": float(np.percentile(lat, 50)), "p99_ms": float(np.percentile(lat, 99)),
+           "batches": int(batches), "wavefront_pairs": int(longs)}
+    for kind, name in enumerate(("short", "medium", "long")):
+        sel = arr.kind == kind
+        res[f"{name}_p50_ms"] = float(np.percentile(lat[sel], 50))
+        res[f"{name}_p99_ms"] = float(np.percentile(lat[sel], 99))
+    return res
+
+
 def secondary_workloads(pkg, ctx, device):
     """The other workloads of the method, one line each (not the headline)."""
     import torch
@@ -305,6 +359,8 @@ def secondary_workloads(pkg, ctx, device):
         "band_accepted": int(((br["flags"] & pkg.FLAG_BAND_ACCEPTED) != 0).sum()),
         "full_dp_fallback": int(((br["flags"] & pkg.FLAG_FULL_FALLBACK) != 0).sum()),
         "full_dp_GCUPS": b.cells() / ms_full / 1e6, "train_s": train_s, "train_loss": loss}
+    # serving: Poisson arrivals through the native request queue
+    out["serving_mix_3000_global_affine"] = serving_workload(pkg)
     return out
 
 

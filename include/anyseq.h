@@ -223,6 +223,50 @@ const char *anyseq_last_error(void);
 /* Library version string. */
 const char *anyseq_version(void);
 
+/* ------------------------------------------------------------------------
+ * Serving (not in the paper, whose interface aligns one pair per call): a
+ * request queue drained by one worker thread that owns a context and a CUDA
+ * stream. Pairs are submitted one at a time from any thread and aligned in
+ * micro-batches: the worker waits at most max_wait_us after the oldest queued
+ * request (or until max_batch_pairs are queued), then aligns the batch's small
+ * pairs with one anyseq_align_batch call and, in global mode, every pair of at
+ * least long_cells cells with anyseq_align_long (whole-GPU wavefront), in
+ * arrival order. Results carry score and optimum cell.
+ * Admission: the letters of queued and running requests never exceed
+ * mem_budget_bytes; a submit beyond it returns ANYSEQ_ERR_BUDGET and queues
+ * nothing (the caller may retry later). Device scratch is the context's,
+ * grown on demand within 90% of free device memory.
+ * ------------------------------------------------------------------------ */
+typedef struct anyseq_server anyseq_server;
+
+typedef struct {
+    int32_t device;               /* CUDA device of the worker */
+    int32_t mode;                 /* anyseq_mode_t of every request */
+    anyseq_scoring_t scoring;     /* copied, including the matrix */
+    int64_t max_batch_pairs;      /* 0: 65536 */
+    int64_t max_wait_us;          /* batching window after the oldest queued request; 0: 200 */
+    int64_t long_cells;           /* n*m from which a global pair takes the wavefront path; 0: 2^22 */
+    size_t mem_budget_bytes;      /* letters held by queued and running requests; 0: 1 GiB */
+} anyseq_server_config_t;
+
+/* Start the worker. Errors: ERR_ARG (bad scoring or limits), ERR_CUDA. */
+anyseq_status_t anyseq_server_create(anyseq_server **srv, const anyseq_server_config_t *cfg);
+/* Queue one pair (host letter codes, copied before return); *ticket names it.
+ * Errors: ERR_ARG, ERR_BUDGET (admission refused). Thread-safe. */
+anyseq_status_t anyseq_server_submit(anyseq_server *srv, const uint8_t *q, int64_t n,
+                                     const uint8_t *s, int64_t m, uint64_t *ticket);
+/* Wait for a ticket (timeout_us < 0: no limit). On return other than
+ * ERR_TIMEOUT the ticket is released: *out holds its result and *latency_ns
+ * (optional) the time from submit to completion. ERR_TIMEOUT keeps the ticket;
+ * an alignment error of the pair is returned as its status. Thread-safe. */
+anyseq_status_t anyseq_server_wait(anyseq_server *srv, uint64_t ticket, int64_t timeout_us,
+                                   anyseq_result_t *out, int64_t *latency_ns);
+/* "completed", "batches", "long_pairs", "rejected", "queued", "held_bytes", "busy_ms". */
+anyseq_status_t anyseq_server_stat(anyseq_server *srv, const char *key, double *value);
+/* Finish every queued request, stop the worker, free the context; tickets not
+ * yet waited for are dropped. */
+anyseq_status_t anyseq_server_destroy(anyseq_server *srv);
+
 #ifdef __cplusplus
 }
 #endif

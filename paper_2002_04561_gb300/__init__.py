@@ -67,10 +67,19 @@ EXPORTS = ["anyseq_create", "anyseq_destroy", "anyseq_align_batch", "anyseq_alig
            "anyseq_set_option", "anyseq_get_stat", "anyseq_encode_dna", "anyseq_last_error",
            "anyseq_version", "anyseq_band_features", "anyseq_band_model_get", "anyseq_band_model_set",
            "anyseq_band_model_save", "anyseq_band_model_load", "anyseq_band_forward",
-           "anyseq_band_gradient", "anyseq_band_train", "anyseq_align_long_noalloc"]
+           "anyseq_band_gradient", "anyseq_band_train", "anyseq_align_long_noalloc",
+           "anyseq_server_create", "anyseq_server_submit", "anyseq_server_wait", "anyseq_server_stat",
+           "anyseq_server_destroy"]
 NOALLOC_MAX_LEN = 1048576
 BAND_FEATURES = 64
 BAND_PARAMS = 25090
+
+
+class ServerConfig(ctypes.Structure):
+    """anyseq_server_config_t."""
+    _fields_ = [("device", ctypes.c_int32), ("mode", ctypes.c_int32), ("scoring", Scoring),
+                ("max_batch_pairs", ctypes.c_int64), ("max_wait_us", ctypes.c_int64),
+                ("long_cells", ctypes.c_int64), ("mem_budget_bytes", ctypes.c_size_t)]
 
 
 def load(build_if_missing: bool = False):
@@ -101,6 +110,11 @@ def load(build_if_missing: bool = False):
     lib.anyseq_band_gradient.argtypes = [P, P, P, I64, P, P, P]
     lib.anyseq_band_train.argtypes = [P, P, P, P, P, I64, P, I32, F32, P, P]
     lib.anyseq_align_long_noalloc.argtypes = [P, I64, P, I64, P, P, P]
+    lib.anyseq_server_create.argtypes = [ctypes.POINTER(P), ctypes.POINTER(ServerConfig)]
+    lib.anyseq_server_submit.argtypes = [P, P, I64, P, I64, ctypes.POINTER(U64)]
+    lib.anyseq_server_wait.argtypes = [P, U64, I64, P, ctypes.POINTER(I64)]
+    lib.anyseq_server_stat.argtypes = [P, ctypes.c_char_p, ctypes.POINTER(ctypes.c_double)]
+    lib.anyseq_server_destroy.argtypes = [P]
     lib.anyseq_last_error.restype = ctypes.c_char_p
     lib.anyseq_last_error.argtypes = []
     lib.anyseq_version.restype = ctypes.c_char_p
@@ -108,7 +122,8 @@ def load(build_if_missing: bool = False):
                  "anyseq_set_option", "anyseq_get_stat", "anyseq_encode_dna", "anyseq_band_features",
                  "anyseq_band_model_get", "anyseq_band_model_set", "anyseq_band_model_save",
                  "anyseq_band_model_load", "anyseq_band_forward", "anyseq_band_gradient", "anyseq_band_train",
-                 "anyseq_align_long_noalloc"]:
+                 "anyseq_align_long_noalloc", "anyseq_server_create", "anyseq_server_submit",
+                 "anyseq_server_wait", "anyseq_server_stat", "anyseq_server_destroy"]:
         getattr(lib, name).restype = ctypes.c_int
     _lib = lib
     return lib
@@ -266,3 +281,48 @@ def encode_dna(text: str) -> np.ndarray:
 
 def version() -> str:
     return load().anyseq_version().decode()
+
+
+class Server:
+    """anyseq_server: a request queue drained in micro-batches by a native worker
+    thread (score and optimum cell per pair). ``submit`` and ``wait`` may be
+    called from any thread; both release the GIL while in the library."""
+
+    def __init__(self, scoring: Scoring, mode: int = GLOBAL, device: int = 0, max_batch_pairs: int = 0,
+                 max_wait_us: int = 0, long_cells: int = 0, mem_budget: int = 0):
+        lib = load()
+        self._cfg = ServerConfig(device, mode, scoring, max_batch_pairs, max_wait_us, long_cells, mem_budget)
+        self._scoring = scoring  # keeps a matrix alive until the server has copied it
+        h = ctypes.c_void_p()
+        _check(lib.anyseq_server_create(ctypes.byref(h), ctypes.byref(self._cfg)))
+        self.h = h
+
+    def submit(self, q, s) -> int:
+        q = np.ascontiguousarray(q, dtype=np.uint8)
+        s = np.ascontiguousarray(s, dtype=np.uint8)
+        t = ctypes.c_uint64(0)
+        _check(load().anyseq_server_submit(self.h, _ptr(q), q.size, _ptr(s), s.size, ctypes.byref(t)))
+        return t.value
+
+    def wait(self, ticket: int, timeout_us: int = -1):
+        """Returns (result record, latency in ns)."""
+        out = np.zeros(1, dtype=RESULT_DTYPE)
+        lat = ctypes.c_int64(0)
+        _check(load().anyseq_server_wait(self.h, ticket, timeout_us, _ptr(out), ctypes.byref(lat)))
+        return out[0], lat.value
+
+    def stat(self, key: str) -> float:
+        v = ctypes.c_double(0)
+        _check(load().anyseq_server_stat(self.h, key.encode(), ctypes.byref(v)))
+        return v.value
+
+    def close(self):
+        if getattr(self, "h", None):
+            load().anyseq_server_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

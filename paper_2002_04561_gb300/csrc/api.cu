@@ -375,8 +375,7 @@ anyseq_status_t anyseq::batch_scores(anyseq_ctx *ctx, const BatchInput &in, cons
         tb->dir_words = total;
     }
     for (int cell32 = 0; cell32 < 2; cell32++) {
-        int bps = batch_blocks_per_sm(cell32, mode, tb != nullptr, sigp, sc->alphabet);
-        int grid = ctx->num_sms * bps;
+        const int grid = ctx->num_sms * batch_blocks_per_sm(cell32, mode, tb != nullptr, sigp, sc->alphabet);
         A.list = cell32 ? P.list32 : P.list16;
         A.n_list = P.counts + cell32;
         A.scratch = nullptr;

@@ -6,6 +6,11 @@
 
 namespace anyseq {
 
+// Byte offset of the last-column buffers inside the dynamic shared memory.
+__host__ __device__ __forceinline__ size_t lc_offset(int sigp, int alphabet) {
+    return sigp ? 1024 + (size_t)(128 / GROUP) * 2 * (alphabet + 1) * QP_ROWS : 0;
+}
+
 __device__ __forceinline__ uint32_t letter(const uint32_t *packed, int64_t base, int32_t len, int32_t idx, bool rev) {
     // idx is 0-based inside the sequence
     return code2(packed, base + (rev ? (int64_t)(len - 1 - idx) : (int64_t)idx));
@@ -13,6 +18,8 @@ __device__ __forceinline__ uint32_t letter(const uint32_t *packed, int64_t base,
 
 // Query profile of one group for the matrix path: byte [h][a][row] = sigma'(q_row, a)
 // for the chunk's 128 rows (padding rows: sig_pad), built by the 16 lanes together.
+// Letter a = alphabet is a null letter with sigma' = 0 (sigma = open + extend),
+// read by the columns past the end of a pair.
 template <class C>
 __device__ __forceinline__ void build_qprofile(const BatchArgs &A, const Slot &sl, int ch, int g, uint32_t *qp,
                                                const int8_t *tab) {
@@ -27,22 +34,29 @@ __device__ __forceinline__ void build_qprofile(const BatchArgs &A, const Slot &s
             code[k] = (h < C::PAIRS && i >= 1 && sl.n[h] > 0)
                           ? (int32_t)A.q8[sl.q0[h] + (sl.rev[h] ? sl.n[h] - i : i - 1)] : -1;
         }
-        for (int a = 0; a < alpha; a++) {
+        for (int a = 0; a <= alpha; a++) {
             uint32_t word = 0;
 #pragma unroll
             for (int k = 0; k < 4; k++) {
-                int32_t v = code[k] >= 0 ? (int32_t)tab[code[k] * alpha + a] : A.sig_pad;
+                int32_t v = a == alpha ? 0 : code[k] >= 0 ? (int32_t)tab[code[k] * alpha + a] : A.sig_pad;
                 word |= ((uint32_t)v & 0xFFu) << (8 * k);
             }
-            qp[(h * alpha + a) * words_per_letter + w] = word;
+            qp[(h * (alpha + 1) + a) * words_per_letter + w] = word;
         }
     }
 }
 
+// lc (semi-global only): the group's last-column buffer, 2 x GROUP x R words.
+// At the step where lane g reaches column m_h - 1 of half h it stores its R
+// row words there; the candidates H(i, m_h) are ranked after the chunk, so
+// the step loop carries no per-row work for them.
+// Local mode keeps, per row, the running maximum and the first column where it
+// occurs (four instructions per cell pair); the optimum is ranked after each
+// chunk.
 template <class C, int MODE, int R, bool TB, int SIGP>
 __device__ __noinline__ void run_slot(const BatchArgs &A, GroupSmem *sm, const Slot &sl,
                                       int nch, int Mit, int g, int64_t gslot, int32_t *res, const int32_t *pid,
-                                      uint32_t *qp, const int8_t *tab) {
+                                      uint32_t *qp, const int8_t *tab, uint32_t *lc) {
     typedef typename C::T T;
     const int32_t o = A.o, e = A.e, oe = A.o + A.e;
     const uint32_t e_raw = C::raw(e), oe_raw = C::raw(oe);   // per-half constants of DPX add-max
@@ -63,8 +77,8 @@ __device__ __noinline__ void run_slot(const BatchArgs &A, GroupSmem *sm, const S
         const int32_t rb = ch * CH + g * R + 1;  // padded row of register 0
         uint32_t profA[R], profB[R];
         T Hoe[R], F[R];
-        T rowmax[MODE == LOCAL ? R : 1];
-        uint32_t rowj[MODE == LOCAL ? R : 1];   // first column of the row maximum (int16x2: one per half)
+        T rowmax[MODE == LOCAL ? R : 1];   // Hoe of the row maximum so far
+        uint32_t rowj[MODE == LOCAL ? R : 1];  // its first column (int16x2: one per half)
 #pragma unroll
         for (int r = 0; r < R; r++) {
             int32_t h0[2] = {0, 0};
@@ -99,21 +113,30 @@ __device__ __noinline__ void run_slot(const BatchArgs &A, GroupSmem *sm, const S
             for (int k = 0; k < 2; k++) {
                 int c = blk * BLOCK + g + 16 * k;
                 if (c < Mit) {
-                    uint32_t ca = 0, cb = 0;
+                    // columns past the end of a pair read a zero sigma' (sigma = open + extend):
+                    // their values stay below the pair's optimum (only the local kernel looks at them)
                     if (SIGP == 0) {
+                        uint32_t ca = 0, cb = 0;
                         if (c < sl.m[0]) ca = letter(A.s2, sl.s0[0], sl.m[0], c, sl.rev[0]);
                         if (C::PAIRS == 2 && c < sl.m[1]) cb = letter(A.s2, sl.s0[1], sl.m[1], c, sl.rev[1]);
-                        sm->sel[c & (RING - 1)] = C::selector(ca, cb);
+                        sm->sel[c & (RING - 1)] = C::null_past_end(C::selector(ca, cb), c < sl.m[0], c < sl.m[1]);
                     } else {
+                        const uint32_t alpha = (uint32_t)A.alphabet;
+                        uint32_t ca = alpha, cb = alpha;
                         if (c < sl.m[0]) ca = A.s8[sl.s0[0] + (sl.rev[0] ? sl.m[0] - 1 - c : c)];
                         if (C::PAIRS == 2 && c < sl.m[1]) cb = A.s8[sl.s0[1] + (sl.rev[1] ? sl.m[1] - 1 - c : c)];
                         // byte offsets of the two letters' profile rows for this lane
-                        sm->sel[c & (RING - 1)] = (ca * QP_ROWS) | ((((uint32_t)A.alphabet + cb) * QP_ROWS) << 16);
+                        sm->sel[c & (RING - 1)] = (ca * QP_ROWS) | (((alpha + 1 + cb) * QP_ROWS) << 16);
                     }
+                    int2 tv;
                     if (ch > 0) {
-                        sm->top[2 * (c & (RING - 1))] = scr[2 * c];
-                        sm->top[2 * (c & (RING - 1)) + 1] = scr[2 * c + 1];
+                        tv = make_int2(scr[2 * c], scr[2 * c + 1]);
+                    } else {
+                        // row 0: H(0, c+1); E below row 0 comes from H only (E(0, .) = -inf)
+                        const int32_t v = (MODE == GLOBAL ? o + (c + 1) * e : 0) + oe;
+                        tv.x = tv.y = (int32_t)C::as_u(C::make(v, v));
                     }
+                    reinterpret_cast<int2 *>(sm->top)[c & (RING - 1)] = tv;
                 }
             }
         };
@@ -161,31 +184,32 @@ __device__ __noinline__ void run_slot(const BatchArgs &A, GroupSmem *sm, const S
                     dptr[h] = A.dirs + A.dir_base[pid[h]] + (int64_t)(ch - ch0) * Sh[h] * GROUP + g;
             }
         }
+        // diag starts as H(i0-1, 0) and afterwards is the Hoe that came down at the
+        // previous column (prev_up changes only at valid columns)
         T last_hoe = NEGv, last_e = NEGv, prev_up = diag0;
-        for (int s = 0; s < S; s++) {
-            if ((s & (BLOCK - 1)) == 0) {
-                __syncwarp();
-                int k = s / BLOCK;
-                fill(k + 1);
-                if (k - 2 >= drained) { drain(k - 2); drained = k - 1; }
-                __syncwarp();
-            }
+        const int ev0 = sl.m[0] - 1, ev1 = C::PAIRS == 2 ? sl.m[1] - 1 : -1;  // last-column steps (+g)
+        for (int s0 = 0; s0 < S; s0 += BLOCK) {
+          __syncwarp();
+          {
+            const int k = s0 / BLOCK;
+            fill(k + 1);
+            if (k - 2 >= drained) { drain(k - 2); drained = k - 1; }
+          }
+          __syncwarp();
+          const int s1 = min(S, s0 + BLOCK);
+          for (int s = s0; s < s1; s++) {
             const int c = s - g;
-            // from lane g-1: Hoe of its last row and E of this lane's first row, column c
+            // from lane g-1: Hoe of its last row and E of this lane's first row, column c;
+            // lane 0 reads the row above the chunk from the top ring (any column: the
+            // ring index is masked, and invalid columns are not used)
             T up_hoe = C::from_u(__shfl_up_sync(0xffffffffu, C::as_u(last_hoe), 1, GROUP));
             T up_e = C::from_u(__shfl_up_sync(0xffffffffu, C::as_u(last_e), 1, GROUP));
             if (g == 0) {
-                if (ch == 0) {
-                    // row 0: H(0, c+1); E below row 0 comes from H only (E(0, .) = -inf)
-                    int32_t v = (MODE == GLOBAL ? o + (c + 1) * e : 0) + oe;
-                    up_hoe = C::make(v, v);
-                    up_e = up_hoe;
-                } else if (c >= 0 && c < Mit) {
-                    up_hoe = C::from_u((uint32_t)sm->top[2 * (c & (RING - 1))]);
-                    up_e = C::from_u((uint32_t)sm->top[2 * (c & (RING - 1)) + 1]);
-                }
+                const int2 tv = reinterpret_cast<const int2 *>(sm->top)[c & (RING - 1)];
+                up_hoe = C::from_u((uint32_t)tv.x);
+                up_e = C::from_u((uint32_t)tv.y);
             }
-            if (c >= 0 && c < Mit) {
+            if ((unsigned)c < (unsigned)Mit) {
                 const uint32_t sel = sm->sel[c & (RING - 1)];
                 uint2 qa = make_uint2(0, 0), qb = make_uint2(0, 0);
                 if (SIGP) {
@@ -193,15 +217,10 @@ __device__ __noinline__ void run_slot(const BatchArgs &A, GroupSmem *sm, const S
                     qa = *reinterpret_cast<const uint2 *>(qpb + (sel & 0xFFFFu));
                     if (C::PAIRS == 2) qb = *reinterpret_cast<const uint2 *>(qpb + (sel >> 16));
                 }
-                T diag = (c == 0) ? diag0 : prev_up;
+                T diag = prev_up;
                 prev_up = up_hoe;
                 T E = up_e;
-                uint32_t valid = 0, jj = 0;
-                if (MODE == LOCAL) {
-                    valid = C::PAIRS == 2 ? ((c < sl.m[0] ? 0xFFFFu : 0u) | (c < sl.m[1] ? 0xFFFF0000u : 0u))
-                                          : (c < sl.m[0] ? 0xFFFFFFFFu : 0u);
-                    jj = C::PAIRS == 2 ? (uint32_t)(c + 1) * 65537u : (uint32_t)(c + 1);
-                }
+                const uint32_t jj = C::PAIRS == 2 ? (uint32_t)(c + 1) * 65537u : (uint32_t)(c + 1);
                 // direction bit planes (traceback): bit 8+r / 24+r of each accumulator
                 uint32_t pl_s0 = 0, pl_s1 = 0, pl_eo = 0, pl_fo = 0;
                 T hup = up_hoe;  // Hoe of the row above, this column
@@ -248,21 +267,10 @@ __device__ __noinline__ void run_slot(const BatchArgs &A, GroupSmem *sm, const S
                     }
                     (void)Fl;
                     if (MODE == LOCAL) {
-                        // strict improvement of the row maximum at a valid column
-                        uint32_t gm;
-                        if (C::PAIRS == 2) {
-                            // invalid columns read -16000 (biased 16768): within 2^15 of every row maximum
-                            uint32_t Hm = (C::as_u(Hoe[r]) & valid) | (0x41804180u & ~valid);
-                            // per half: Hm - rowmax - 1 + 2^15 keeps bit 15 iff Hm > rowmax
-                            uint32_t d = Hm + 0x7FFF7FFFu - C::as_u(rowmax[r]);
-                            gm = prmt(d, 0u, 0xBB99u);                        // sign of bytes 1, 3 -> halves
-                            rowmax[r] = C::vmax(rowmax[r], C::from_u(Hm));
-                        } else {
-                            int32_t Hm = valid ? (int32_t)C::as_u(Hoe[r]) : (int32_t)C::NEG;
-                            gm = Hm > (int32_t)C::as_u(rowmax[r]) ? 0xFFFFFFFFu : 0u;
-                            rowmax[r] = C::vmax(rowmax[r], C::from_u((uint32_t)Hm));
-                        }
+                        // strict improvement of the row maximum: the column of its first occurrence
+                        const uint32_t gm = C::gt_mask(Hoe[r], rowmax[r]);
                         rowj[r] = (jj & gm) | (rowj[r] & ~gm);
+                        rowmax[r] = C::vmax(rowmax[r], Hoe[r]);
                     }
                 }
                 last_hoe = Hoe[R - 1];
@@ -273,44 +281,51 @@ __device__ __noinline__ void run_slot(const BatchArgs &A, GroupSmem *sm, const S
                     if (dptr[0] && s < Sh[0]) dptr[0][(int64_t)s * GROUP] = C::PAIRS == 2 ? prmt(w01, w23, 0x5410u) : prmt(w01, w23, 0x7632u);
                     if (C::PAIRS == 2 && dptr[1] && s < Sh[1]) dptr[1][(int64_t)s * GROUP] = prmt(w01, w23, 0x7632u);
                 }
-                if (g == GROUP - 1) {
-                    sm->bot[2 * (c & (RING - 1))] = (int32_t)C::as_u(last_hoe);
-                    sm->bot[2 * (c & (RING - 1)) + 1] = (int32_t)C::as_u(last_e);
+                if (g == GROUP - 1)
+                    reinterpret_cast<int2 *>(sm->bot)[c & (RING - 1)] =
+                        make_int2((int32_t)C::as_u(last_hoe), (int32_t)C::as_u(last_e));
+                // semi-global: this lane's rows of the last column of a half (once per chunk)
+                if (MODE == SEMIGLOBAL && (c == ev0 || c == ev1)) {
+#pragma unroll
+                    for (int r = 0; r < R; r++) {
+                        if (c == ev0) lc[g * R + r] = C::as_u(Hoe[r]);
+                        if (c == ev1) lc[(GROUP + g) * R + r] = C::as_u(Hoe[r]);
+                    }
                 }
-                // semi-global: last column candidates at c == m-1
-                if (MODE == SEMIGLOBAL) {
+            }
+          }
+        }
+        __syncwarp();
+        for (int b = drained; b <= (Mit - 1) / BLOCK; b++) drain(b);
+        __syncwarp();
+        if (MODE == SEMIGLOBAL) {
+            // last-column candidates H(i, m_h) of this lane's rows
 #pragma unroll
-                    for (int h = 0; h < C::PAIRS; h++) {
-                        if (c == sl.m[h] - 1) {
+            for (int h = 0; h < C::PAIRS; h++) {
+                if (sl.m[h] > 0) {
 #pragma unroll
-                            for (int r = 0; r < R; r++) {
-                                int32_t i = rb + r - sl.pad[h];
-                                if (i >= 1) {
-                                    uint64_t k = end_key(C::get(Hoe[r], h) - oe, i, sl.m[h]);
-                                    best[h] = k > best[h] ? k : best[h];
-                                }
-                            }
+                    for (int r = 0; r < R; r++) {
+                        const int32_t i = rb + r - sl.pad[h];
+                        if (i >= 1) {
+                            const uint64_t k = end_key(C::get(C::from_u(lc[(h * GROUP + g) * R + r]), h) - oe, i, sl.m[h]);
+                            best[h] = k > best[h] ? k : best[h];
                         }
                     }
                 }
             }
         }
-        __syncwarp();
-        for (int b = drained; b <= (Mit - 1) / BLOCK; b++) drain(b);
-        __syncwarp();
         if (MODE == LOCAL) {
+            // every row's maximum, at the first column it occurs (columns past the end of a
+            // half never win: their values do not exceed a real cell earlier in row-major order)
 #pragma unroll
             for (int h = 0; h < C::PAIRS; h++) {
 #pragma unroll
                 for (int r = 0; r < R; r++) {
-                    int32_t i = rb + r - sl.pad[h];
-                    if (i >= 1) {
-                        int32_t v = C::get(rowmax[r], h) - oe;
-                        int32_t j = C::PAIRS == 2 ? (int32_t)((rowj[r] >> (16 * h)) & 0xFFFFu) : (int32_t)rowj[r];
-                        if (v > 0) {
-                            uint64_t k = end_key(v, i, j);
-                            best[h] = k > best[h] ? k : best[h];
-                        }
+                    const int32_t i = rb + r - sl.pad[h], v = C::get(rowmax[r], h) - oe;
+                    const int32_t j = C::PAIRS == 2 ? (int32_t)((rowj[r] >> (16 * h)) & 0xFFFFu) : (int32_t)rowj[r];
+                    if (i >= 1 && v > 0) {
+                        const uint64_t k = end_key(v, i, j);
+                        best[h] = k > best[h] ? k : best[h];
                     }
                 }
             }
@@ -356,16 +371,19 @@ __global__ void __launch_bounds__(SIGP ? 128 : 256, SIGP ? 4 : 2) batch_kernel(B
     if (SIGP) {
         tab = reinterpret_cast<int8_t *>(dyn_smem);
         for (int k = threadIdx.x; k < A.alphabet * A.alphabet; k += THREADS) tab[k] = A.sig_tab[k];
-        qp = reinterpret_cast<uint32_t *>(dyn_smem + 1024) + (warp * 2 + grp) * (2 * A.alphabet * QP_ROWS / 4);
+        qp = reinterpret_cast<uint32_t *>(dyn_smem + 1024) + (warp * 2 + grp) * (2 * (A.alphabet + 1) * QP_ROWS / 4);
         __syncthreads();
     }
     const int64_t gslot = ((int64_t)blockIdx.x * (THREADS >> 5) + warp) * 2 + grp;
+    // rows per lane: at most 16 (12 for local int16x2, which also keeps per-row
+    // maxima and columns); exactly TB_R for the traceback and matrix kernels
+    constexpr int RMAX = (TB || SIGP) ? TB_R : ((MODE == LOCAL && C::PAIRS == 2) ? 12 : 16);
+    uint32_t *lc = nullptr;
+    if (MODE == SEMIGLOBAL)
+        lc = reinterpret_cast<uint32_t *>(dyn_smem + lc_offset(SIGP, A.alphabet)) + (warp * 2 + grp) * 2 * GROUP * RMAX;
     const int per_item = 2 * C::PAIRS;
     const int64_t n_list = *A.n_list;
     const int64_t n_items = (n_list + per_item - 1) / per_item;
-    // rows per lane: at most 16 (12 for local int16x2, which also keeps per-row
-    // maxima); exactly TB_R for the traceback and matrix kernels
-    constexpr int RMAX = (TB || SIGP) ? TB_R : ((MODE == LOCAL && C::PAIRS == 2) ? 12 : 16);
     for (;;) {
         int item = 0;
         if (lane == 0) item = atomicAdd(A.counter, 1);
@@ -394,17 +412,17 @@ __global__ void __launch_bounds__(SIGP ? 128 : 256, SIGP ? 4 : 2) batch_kernel(B
             continue;
         }
         if (TB || SIGP) {
-            run_slot<C, MODE, TB_R, TB, SIGP>(A, sm, sl, P.nch, P.Mit, g, gslot, res, pid, qp, tab);
+            run_slot<C, MODE, TB_R, TB, SIGP>(A, sm, sl, P.nch, P.Mit, g, gslot, res, pid, qp, tab, lc);
         } else {
             switch (P.R) {
-                case 2: run_slot<C, MODE, 2, TB, SIGP>(A, sm, sl, P.nch, P.Mit, g, gslot, res, pid, qp, tab); break;
-                case 4: run_slot<C, MODE, 4, TB, SIGP>(A, sm, sl, P.nch, P.Mit, g, gslot, res, pid, qp, tab); break;
-                case 6: run_slot<C, MODE, 6, TB, SIGP>(A, sm, sl, P.nch, P.Mit, g, gslot, res, pid, qp, tab); break;
-                case 8: run_slot<C, MODE, 8, TB, SIGP>(A, sm, sl, P.nch, P.Mit, g, gslot, res, pid, qp, tab); break;
-                case 10: run_slot<C, MODE, 10, TB, SIGP>(A, sm, sl, P.nch, P.Mit, g, gslot, res, pid, qp, tab); break;
-                case 12: run_slot<C, MODE, 12, TB, SIGP>(A, sm, sl, P.nch, P.Mit, g, gslot, res, pid, qp, tab); break;
-                case 14: run_slot<C, MODE, (RMAX < 14 ? RMAX : 14), TB, SIGP>(A, sm, sl, P.nch, P.Mit, g, gslot, res, pid, qp, tab); break;
-                default: run_slot<C, MODE, RMAX, TB, SIGP>(A, sm, sl, P.nch, P.Mit, g, gslot, res, pid, qp, tab); break;
+                case 2: run_slot<C, MODE, 2, TB, SIGP>(A, sm, sl, P.nch, P.Mit, g, gslot, res, pid, qp, tab, lc); break;
+                case 4: run_slot<C, MODE, 4, TB, SIGP>(A, sm, sl, P.nch, P.Mit, g, gslot, res, pid, qp, tab, lc); break;
+                case 6: run_slot<C, MODE, 6, TB, SIGP>(A, sm, sl, P.nch, P.Mit, g, gslot, res, pid, qp, tab, lc); break;
+                case 8: run_slot<C, MODE, 8, TB, SIGP>(A, sm, sl, P.nch, P.Mit, g, gslot, res, pid, qp, tab, lc); break;
+                case 10: run_slot<C, MODE, 10, TB, SIGP>(A, sm, sl, P.nch, P.Mit, g, gslot, res, pid, qp, tab, lc); break;
+                case 12: run_slot<C, MODE, 12, TB, SIGP>(A, sm, sl, P.nch, P.Mit, g, gslot, res, pid, qp, tab, lc); break;
+                case 14: run_slot<C, MODE, (RMAX < 14 ? RMAX : 14), TB, SIGP>(A, sm, sl, P.nch, P.Mit, g, gslot, res, pid, qp, tab, lc); break;
+                default: run_slot<C, MODE, RMAX, TB, SIGP>(A, sm, sl, P.nch, P.Mit, g, gslot, res, pid, qp, tab, lc); break;
             }
         }
         if (g == 0) {
@@ -421,67 +439,66 @@ __global__ void __launch_bounds__(SIGP ? 128 : 256, SIGP ? 4 : 2) batch_kernel(B
     }
 }
 
-static size_t dyn_smem_bytes(int sigp, int alphabet) {
-    return sigp ? 1024 + (size_t)(128 / 16) * 2 * alphabet * QP_ROWS : 0;
+// Dynamic shared memory: [sigma table (1 KB) + per-group query profiles] for the
+// matrix path, then the per-group last-column buffers of the semi-global kernels.
+static size_t dyn_smem_bytes(int sigp, int alphabet, int mode, bool tb) {
+    const int groups = (sigp ? 128 : 256) / GROUP;
+    const int rmax = (tb || sigp) ? TB_R : 16;
+    return lc_offset(sigp, alphabet) + (mode == SEMIGLOBAL ? (size_t)groups * 2 * GROUP * rmax * 4 : 0);
 }
 
+// One instantiation: launch (occupancy == false) or blocks per SM (occupancy == true).
 template <class C, int MODE, bool TB, int SIGP>
-static cudaError_t launch_one(const BatchArgs &A, int grid, cudaStream_t st) {
-    size_t dyn = dyn_smem_bytes(SIGP, A.alphabet);
-    // static rings + dynamic profile exceed the 48 KB default: opt in explicitly
-    if (SIGP) cudaFuncSetAttribute(batch_kernel<C, MODE, TB, SIGP>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)dyn);
-    batch_kernel<C, MODE, TB, SIGP><<<grid, SIGP ? 128 : 256, dyn, st>>>(A);
-    return cudaGetLastError();
+static int run_one(const BatchArgs *A, int alphabet, int grid, cudaStream_t st, bool occupancy, cudaError_t *err) {
+    auto kern = batch_kernel<C, MODE, TB, SIGP>;
+    const size_t dyn = dyn_smem_bytes(SIGP, alphabet, MODE, TB);
+    // static rings + dynamic buffers may exceed the 48 KB default: opt in explicitly
+    if (dyn) cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)dyn);
+    if (occupancy) {
+        int nb = 0;
+        if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, kern, SIGP ? 128 : 256, dyn) != cudaSuccess) {
+            cudaGetLastError();
+            nb = 1;
+        }
+        return nb < 1 ? 1 : nb;
+    }
+    kern<<<grid, SIGP ? 128 : 256, dyn, st>>>(*A);
+    *err = cudaGetLastError();
+    return 0;
 }
 
-template <bool TB, int SIGP>
-static cudaError_t launch_v(const BatchArgs &A, int cell32, int mode, int grid, cudaStream_t st) {
-    if (cell32) {
-        switch (mode) {
-            case GLOBAL: return launch_one<CellI32, GLOBAL, TB, SIGP>(A, grid, st);
-            case LOCAL: return launch_one<CellI32, LOCAL, TB, SIGP>(A, grid, st);
-            default: return launch_one<CellI32, SEMIGLOBAL, TB, SIGP>(A, grid, st);
-        }
-    }
+template <class C, bool TB, int SIGP>
+static int run_mode(const BatchArgs *A, int mode, int alphabet, int grid, cudaStream_t st, bool occ, cudaError_t *err) {
     switch (mode) {
-        case GLOBAL: return launch_one<CellI16x2, GLOBAL, TB, SIGP>(A, grid, st);
-        case LOCAL: return launch_one<CellI16x2, LOCAL, TB, SIGP>(A, grid, st);
-        default: return launch_one<CellI16x2, SEMIGLOBAL, TB, SIGP>(A, grid, st);
+        case GLOBAL: return run_one<C, GLOBAL, TB, SIGP>(A, alphabet, grid, st, occ, err);
+        case LOCAL: return run_one<C, LOCAL, TB, SIGP>(A, alphabet, grid, st, occ, err);
+        default: return run_one<C, SEMIGLOBAL, TB, SIGP>(A, alphabet, grid, st, occ, err);
     }
+}
+
+static int dispatch(const BatchArgs *A, int cell32, int mode, int tb, int sigp, int alphabet, int grid,
+                    cudaStream_t st, bool occ, cudaError_t *err) {
+    if (cell32) {
+        if (sigp) return tb ? run_mode<CellI32, true, 1>(A, mode, alphabet, grid, st, occ, err)
+                            : run_mode<CellI32, false, 1>(A, mode, alphabet, grid, st, occ, err);
+        return tb ? run_mode<CellI32, true, 0>(A, mode, alphabet, grid, st, occ, err)
+                  : run_mode<CellI32, false, 0>(A, mode, alphabet, grid, st, occ, err);
+    }
+    if (sigp) return tb ? run_mode<CellI16x2, true, 1>(A, mode, alphabet, grid, st, occ, err)
+                        : run_mode<CellI16x2, false, 1>(A, mode, alphabet, grid, st, occ, err);
+    return tb ? run_mode<CellI16x2, true, 0>(A, mode, alphabet, grid, st, occ, err)
+              : run_mode<CellI16x2, false, 0>(A, mode, alphabet, grid, st, occ, err);
 }
 
 cudaError_t launch_batch(const BatchArgs &A, int cell32, int mode, int tb, int sigp, int grid, cudaStream_t st) {
-    if (sigp) return tb ? launch_v<true, 1>(A, cell32, mode, grid, st) : launch_v<false, 1>(A, cell32, mode, grid, st);
-    return tb ? launch_v<true, 0>(A, cell32, mode, grid, st) : launch_v<false, 0>(A, cell32, mode, grid, st);
-}
-
-template <class C, int MODE, bool TB, int SIGP>
-static int occ(int alphabet) {
-    int nb = 0;
-    size_t dyn = dyn_smem_bytes(SIGP, alphabet);
-    if (SIGP) cudaFuncSetAttribute(batch_kernel<C, MODE, TB, SIGP>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)dyn);
-    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, batch_kernel<C, MODE, TB, SIGP>, SIGP ? 128 : 256, dyn) !=
-        cudaSuccess) {
-        cudaGetLastError();
-        nb = 1;
-    }
-    return nb < 1 ? 1 : nb;
-}
-
-template <bool TB, int SIGP>
-static int occ_v(int cell32, int mode, int alphabet) {
-    if (cell32)
-        return mode == GLOBAL ? occ<CellI32, GLOBAL, TB, SIGP>(alphabet)
-             : mode == LOCAL  ? occ<CellI32, LOCAL, TB, SIGP>(alphabet)
-                              : occ<CellI32, SEMIGLOBAL, TB, SIGP>(alphabet);
-    return mode == GLOBAL ? occ<CellI16x2, GLOBAL, TB, SIGP>(alphabet)
-         : mode == LOCAL  ? occ<CellI16x2, LOCAL, TB, SIGP>(alphabet)
-                          : occ<CellI16x2, SEMIGLOBAL, TB, SIGP>(alphabet);
+    cudaError_t err = cudaSuccess;
+    dispatch(&A, cell32, mode, tb, sigp, A.alphabet, grid, st, false, &err);
+    return err;
 }
 
 int batch_blocks_per_sm(int cell32, int mode, int tb, int sigp, int alphabet) {
-    if (sigp) return tb ? occ_v<true, 1>(cell32, mode, alphabet) : occ_v<false, 1>(cell32, mode, alphabet);
-    return tb ? occ_v<true, 0>(cell32, mode, alphabet) : occ_v<false, 0>(cell32, mode, alphabet);
+    cudaError_t err = cudaSuccess;
+    return dispatch(nullptr, cell32, mode, tb, sigp, alphabet, 0, nullptr, true, &err);
 }
 
 }  // namespace anyseq

@@ -61,7 +61,14 @@ struct CellI32 {
     // flag word: bit 31 set iff a >= b (sign of b - a - 1; |a - b| < 2^31)
     __device__ __forceinline__ static uint32_t ge(T a, T b) { return (uint32_t)(b - a - 1); }
     __device__ __forceinline__ static uint32_t flag_mask() { return 0x80000000u; }
+    // all ones where a > b
+    __device__ __forceinline__ static uint32_t gt_mask(T a, T b) { return a > b ? 0xFFFFFFFFu : 0u; }
     __device__ __forceinline__ static uint32_t zero_hoe(int32_t oe) { return (uint32_t)oe; }
+    // selector of a column past the end of the pair: the sign byte of profile byte 0
+    // in all four bytes (sigma' = 0 or -1)
+    __device__ __forceinline__ static uint32_t null_past_end(uint32_t sel, bool va, bool vb) {
+        (void)vb; return va ? sel : 0x8888u;
+    }
 };
 
 // Two int16 halves per 32-bit word (low: pair A, high: pair B), each stored
@@ -96,6 +103,14 @@ struct CellI16x2 {
     // add because a - b + 2^15 stays inside [0, 2^16) when |a - b| < 2^15
     __device__ __forceinline__ static uint32_t ge(T a, T b) { return a + 0x80008000u - b; }
     __device__ __forceinline__ static uint32_t flag_mask() { return 0x80008000u; }
+    // all ones in each half where a > b: a - b - 1 + 2^15 has bit 15 set (no borrow
+    // across halves while |a - b| < 2^15), and prmt replicates the sign of bytes 1 and 3
+    __device__ __forceinline__ static uint32_t gt_mask(T a, T b) { return prmt(a + 0x7FFF7FFFu - b, 0u, 0xBB99u); }
+    // selector nibbles 8 of a half past the end of its pair: the sign of profile
+    // byte 0, which is >= 0, in both bytes (sigma' = 0)
+    __device__ __forceinline__ static uint32_t null_past_end(uint32_t sel, bool va, bool vb) {
+        return (va ? (sel & 0x00FFu) : 0x0088u) | (vb ? (sel & 0xFF00u) : 0x8800u);
+    }
     __device__ __forceinline__ static uint32_t zero_hoe(int32_t oe) {
         return ((uint32_t)(oe + 32768) & 0xFFFFu) * 65537u;
     }

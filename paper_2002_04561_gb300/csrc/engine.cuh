@@ -30,7 +30,7 @@
 namespace anyseq {
 
 // Per-group shared memory: subject selectors, top and bottom border rings.
-struct GroupSmem {
+struct __align__(16) GroupSmem {
     uint32_t sel[RING];
     int32_t top[2 * RING];  // (Hoe, E) of the row above the chunk
     int32_t bot[2 * RING];  // (Hoe, E) of the chunk's last row

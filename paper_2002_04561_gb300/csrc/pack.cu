@@ -64,7 +64,8 @@ __device__ __forceinline__ bool fits_int16(int64_t n, int64_t m, int32_t smax, i
     if (mode == GLOBAL) lo = 3 * ox + (n + m + 2) * ex + sm;
     else if (mode == SEMIGLOBAL) lo = 2 * ox + (mn + 2) * ex + sm;
     else lo = ox + 2 * ex + sm;
-    return hi <= 16000 && lo >= -16000;
+    // local mode packs the optimum column of both halves into 16 bits each
+    return hi <= 16000 && lo >= -16000 && (mode != LOCAL || m < 65535);
 }
 
 __global__ void bin_kernel(PrepArgs P) {

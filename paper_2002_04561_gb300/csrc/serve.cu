@@ -1,0 +1,278 @@
+// Serving runtime: a request queue in front of the alignment paths (not in the
+// paper; its GPU mapping aligns one pair or one batch per call).
+//
+// Callers submit single pairs from any thread. One worker thread owns a
+// context and a CUDA stream and drains the queue in micro-batches: it waits at
+// most max_wait_us after the oldest queued request (or until max_batch_pairs
+// are queued), then aligns every small pair of the batch with one
+// anyseq_align_batch call (inter-sequence parallelism) and every pair of at
+// least long_cells cells with the whole-GPU wavefront of anyseq_align_long
+// (intra-sequence parallelism, global mode), in arrival order. Admission: the
+// letters of queued and running requests may not exceed mem_budget_bytes; a
+// submit that would exceed it is refused with ANYSEQ_ERR_BUDGET.
+#include <chrono>
+#include <condition_variable>
+#include <cstring>
+#include <deque>
+#include <mutex>
+#include <string>
+#include <thread>
+#include <unordered_map>
+#include <vector>
+
+#include <cuda_runtime.h>
+
+#include "../../include/anyseq.h"
+#include "api_internal.h"
+
+namespace {
+
+int64_t now_ns() {
+    return std::chrono::duration_cast<std::chrono::nanoseconds>(std::chrono::steady_clock::now().time_since_epoch())
+        .count();
+}
+
+struct Request {
+    uint64_t ticket = 0;
+    std::vector<uint8_t> q, s;
+    int64_t t_submit = 0, t_done = 0;
+    anyseq_result_t res{};
+    anyseq_status_t status = ANYSEQ_OK;
+    std::string error;  // the worker's message when status != ANYSEQ_OK
+    bool done = false;
+};
+
+}  // namespace
+
+struct anyseq_server {
+    anyseq_server_config_t cfg{};
+    std::vector<int8_t> matrix;  // copy of the scoring matrix
+    anyseq_scoring_t sc{};
+    anyseq_ctx *ctx = nullptr;
+    cudaStream_t stream = nullptr;
+    std::thread worker;
+    std::mutex mu;
+    std::condition_variable cv_work, cv_done;
+    std::deque<Request *> queue;
+    std::unordered_map<uint64_t, Request *> live;
+    uint64_t next_ticket = 1;
+    size_t held_bytes = 0;  // letters of queued and running requests
+    bool stop = false;
+    anyseq_status_t worker_status = ANYSEQ_OK;
+    // statistics
+    int64_t completed = 0, batches = 0, long_pairs = 0, rejected = 0;
+    double busy_ms = 0;
+};
+
+namespace {
+
+void run_batch(anyseq_server *S, std::vector<Request *> &reqs) {
+    std::vector<Request *> small, big;
+    for (Request *r : reqs) {
+        const double cells = (double)r->q.size() * (double)r->s.size();
+        const bool is_long = S->cfg.mode == ANYSEQ_GLOBAL && cells >= (double)S->cfg.long_cells && !r->q.empty() &&
+                             !r->s.empty();
+        (is_long ? big : small).push_back(r);
+    }
+    if (!small.empty()) {
+        std::vector<int64_t> qo(small.size() + 1, 0), so(small.size() + 1, 0);
+        for (size_t k = 0; k < small.size(); k++) {
+            qo[k + 1] = qo[k] + (int64_t)small[k]->q.size();
+            so[k + 1] = so[k] + (int64_t)small[k]->s.size();
+        }
+        std::vector<uint8_t> q((size_t)qo.back() + 1), s((size_t)so.back() + 1);
+        for (size_t k = 0; k < small.size(); k++) {
+            if (!small[k]->q.empty()) memcpy(q.data() + qo[k], small[k]->q.data(), small[k]->q.size());
+            if (!small[k]->s.empty()) memcpy(s.data() + so[k], small[k]->s.data(), small[k]->s.size());
+        }
+        std::vector<anyseq_result_t> out(small.size());
+        uint64_t used = 0;
+        const anyseq_status_t st =
+            anyseq_align_batch(S->ctx, q.data(), qo.data(), s.data(), so.data(), (int64_t)small.size(), &S->sc,
+                               S->cfg.mode, ANYSEQ_WANT_SCORE | ANYSEQ_WANT_END, out.data(), nullptr, 0, &used,
+                               S->stream);
+        const int64_t t = now_ns();
+        for (size_t k = 0; k < small.size(); k++) {
+            small[k]->res = out[k];
+            small[k]->status = st;
+            if (st != ANYSEQ_OK) small[k]->error = anyseq_last_error();
+            small[k]->t_done = t;
+        }
+    }
+    for (Request *r : big) {
+        uint64_t used = 0;
+        r->status = anyseq_align_long(S->ctx, r->q.data(), (int64_t)r->q.size(), r->s.data(), (int64_t)r->s.size(),
+                                      &S->sc, ANYSEQ_GLOBAL, ANYSEQ_WANT_SCORE | ANYSEQ_WANT_END, &r->res, nullptr, 0,
+                                      &used, S->stream);
+        if (r->status != ANYSEQ_OK) r->error = anyseq_last_error();
+        r->t_done = now_ns();
+    }
+    std::lock_guard<std::mutex> lock(S->mu);
+    for (Request *r : reqs) {
+        r->done = true;
+        S->held_bytes -= r->q.size() + r->s.size();
+        r->q.clear();
+        r->q.shrink_to_fit();
+        r->s.clear();
+        r->s.shrink_to_fit();
+    }
+    S->completed += (int64_t)reqs.size();
+    S->long_pairs += (int64_t)big.size();
+    S->batches += 1;
+    S->cv_done.notify_all();
+}
+
+void worker_main(anyseq_server *S) {
+    if (cudaSetDevice(S->cfg.device) != cudaSuccess) {
+        std::lock_guard<std::mutex> lock(S->mu);
+        S->worker_status = ANYSEQ_ERR_CUDA;
+        return;
+    }
+    for (;;) {
+        std::vector<Request *> batch;
+        {
+            std::unique_lock<std::mutex> lock(S->mu);
+            S->cv_work.wait(lock, [&] { return S->stop || !S->queue.empty(); });
+            if (S->queue.empty()) break;  // stop requested and nothing left
+            // batching window: until the oldest request has waited max_wait_us or the batch is full
+            const int64_t deadline = S->queue.front()->t_submit + S->cfg.max_wait_us * 1000;
+            while (!S->stop && (int64_t)S->queue.size() < S->cfg.max_batch_pairs) {
+                const int64_t left = deadline - now_ns();
+                if (left <= 0) break;
+                S->cv_work.wait_for(lock, std::chrono::nanoseconds(left));
+            }
+            while (!S->queue.empty() && (int64_t)batch.size() < S->cfg.max_batch_pairs) {
+                batch.push_back(S->queue.front());
+                S->queue.pop_front();
+            }
+        }
+        const int64_t t0 = now_ns();
+        run_batch(S, batch);
+        std::lock_guard<std::mutex> lock(S->mu);
+        S->busy_ms += (double)(now_ns() - t0) * 1e-6;
+    }
+}
+
+}  // namespace
+
+extern "C" anyseq_status_t anyseq_server_create(anyseq_server **out, const anyseq_server_config_t *cfg) {
+    if (!out || !cfg) return anyseq::fail(ANYSEQ_ERR_ARG, "server and config must not be NULL");
+    *out = nullptr;
+    const anyseq_status_t sc_st = anyseq::check_scoring(&cfg->scoring, cfg->mode);
+    if (sc_st != ANYSEQ_OK) return sc_st;
+    if (cfg->max_batch_pairs < 0 || cfg->max_wait_us < 0 || cfg->long_cells < 0)
+        return anyseq::fail(ANYSEQ_ERR_ARG, "negative server limits");
+    anyseq_server *S = new anyseq_server();
+    S->cfg = *cfg;
+    if (S->cfg.max_batch_pairs == 0) S->cfg.max_batch_pairs = 65536;
+    if (S->cfg.max_wait_us == 0) S->cfg.max_wait_us = 200;
+    if (S->cfg.long_cells == 0) S->cfg.long_cells = 1ll << 22;
+    if (S->cfg.mem_budget_bytes == 0) S->cfg.mem_budget_bytes = (size_t)1 << 30;
+    S->sc = cfg->scoring;
+    if (cfg->scoring.matrix) {
+        const int a = cfg->scoring.alphabet;
+        S->matrix.assign(cfg->scoring.matrix, cfg->scoring.matrix + (size_t)a * a);
+        S->sc.matrix = S->matrix.data();
+    }
+    anyseq_status_t st = anyseq_create(&S->ctx, cfg->device, 0);
+    if (st != ANYSEQ_OK) {
+        delete S;
+        return st;
+    }
+    if (cudaSetDevice(cfg->device) != cudaSuccess ||
+        cudaStreamCreateWithFlags(&S->stream, cudaStreamNonBlocking) != cudaSuccess) {
+        cudaGetLastError();
+        anyseq_destroy(S->ctx);
+        delete S;
+        return anyseq::fail(ANYSEQ_ERR_CUDA, "could not create the server's stream");
+    }
+    S->worker = std::thread(worker_main, S);
+    *out = S;
+    return ANYSEQ_OK;
+}
+
+extern "C" anyseq_status_t anyseq_server_submit(anyseq_server *S, const uint8_t *q, int64_t n, const uint8_t *s,
+                                                int64_t m, uint64_t *ticket) {
+    if (!S || !ticket) return anyseq::fail(ANYSEQ_ERR_ARG, "server and ticket must not be NULL");
+    if (n < 0 || m < 0 || (n > 0 && !q) || (m > 0 && !s)) return anyseq::fail(ANYSEQ_ERR_ARG, "bad pair");
+    Request *r = new Request();
+    r->q.assign(q, q + n);
+    r->s.assign(s, s + m);
+    std::lock_guard<std::mutex> lock(S->mu);
+    if (S->worker_status != ANYSEQ_OK) {
+        delete r;
+        return anyseq::fail(S->worker_status, "the server's worker failed to start");
+    }
+    if (S->stop) {
+        delete r;
+        return anyseq::fail(ANYSEQ_ERR_ARG, "the server is shutting down");
+    }
+    const size_t bytes = (size_t)n + (size_t)m;
+    if (S->held_bytes + bytes > S->cfg.mem_budget_bytes) {
+        S->rejected += 1;
+        delete r;
+        return anyseq::fail(ANYSEQ_ERR_BUDGET, "request of %zu letters exceeds the server's budget (%zu held of %zu)",
+                            bytes, S->held_bytes, S->cfg.mem_budget_bytes);
+    }
+    S->held_bytes += bytes;
+    r->ticket = S->next_ticket++;
+    r->t_submit = now_ns();
+    S->live[r->ticket] = r;
+    S->queue.push_back(r);
+    *ticket = r->ticket;
+    S->cv_work.notify_one();
+    return ANYSEQ_OK;
+}
+
+extern "C" anyseq_status_t anyseq_server_wait(anyseq_server *S, uint64_t ticket, int64_t timeout_us,
+                                              anyseq_result_t *out, int64_t *latency_ns) {
+    if (!S || !out) return anyseq::fail(ANYSEQ_ERR_ARG, "server and out must not be NULL");
+    std::unique_lock<std::mutex> lock(S->mu);
+    auto it = S->live.find(ticket);
+    if (it == S->live.end()) return anyseq::fail(ANYSEQ_ERR_ARG, "unknown ticket %llu", (unsigned long long)ticket);
+    Request *r = it->second;
+    auto ready = [&] { return r->done; };
+    if (timeout_us < 0) {
+        S->cv_done.wait(lock, ready);
+    } else if (!S->cv_done.wait_for(lock, std::chrono::microseconds(timeout_us), ready)) {
+        return anyseq::fail(ANYSEQ_ERR_TIMEOUT, "ticket %llu not finished within %lld us", (unsigned long long)ticket,
+                            (long long)timeout_us);
+    }
+    *out = r->res;
+    if (latency_ns) *latency_ns = r->t_done - r->t_submit;
+    const anyseq_status_t st = r->status;
+    const std::string msg = r->error;
+    S->live.erase(it);
+    delete r;
+    if (st != ANYSEQ_OK) return anyseq::fail(st, "%s", msg.c_str());
+    return ANYSEQ_OK;
+}
+
+extern "C" anyseq_status_t anyseq_server_stat(anyseq_server *S, const char *key, double *value) {
+    if (!S || !key || !value) return anyseq::fail(ANYSEQ_ERR_ARG, "server, key and value must not be NULL");
+    std::lock_guard<std::mutex> lock(S->mu);
+    if (!strcmp(key, "completed")) *value = (double)S->completed;
+    else if (!strcmp(key, "batches")) *value = (double)S->batches;
+    else if (!strcmp(key, "long_pairs")) *value = (double)S->long_pairs;
+    else if (!strcmp(key, "rejected")) *value = (double)S->rejected;
+    else if (!strcmp(key, "queued")) *value = (double)S->queue.size();
+    else if (!strcmp(key, "held_bytes")) *value = (double)S->held_bytes;
+    else if (!strcmp(key, "busy_ms")) *value = S->busy_ms;
+    else return anyseq::fail(ANYSEQ_ERR_ARG, "unknown server statistic '%s'", key);
+    return ANYSEQ_OK;
+}
+
+extern "C" anyseq_status_t anyseq_server_destroy(anyseq_server *S) {
+    if (!S) return ANYSEQ_OK;
+    {
+        std::lock_guard<std::mutex> lock(S->mu);
+        S->stop = true;
+        S->cv_work.notify_all();
+    }
+    if (S->worker.joinable()) S->worker.join();
+    for (auto &kv : S->live) delete kv.second;
+    if (S->stream) cudaStreamDestroy(S->stream);
+    anyseq_status_t st = anyseq_destroy(S->ctx);
+    delete S;
+    return st;
+}

@@ -49,3 +49,28 @@ def test_host_only_calls(lib):
     with pytest.raises(pkg.AnyseqError) as ei:
         pkg.encode_dna("ACGN")
     assert ei.value.status == 2
+
+
+def test_binding_structs_match_c_layout(tmp_path):
+    """sizeof/offsetof of the header's structs as the C compiler lays them out,
+    against the ctypes and numpy views the binding passes across the ABI."""
+    import subprocess
+
+    import paper_2002_04561_gb300 as pkg
+    src = tmp_path / "layout.c"
+    src.write_text(f'''#include <stddef.h>
+#include <stdio.h>
+#include "{ROOT}/include/anyseq.h"
+int main(void) {{
+  printf("%zu %zu %zu\\n", sizeof(anyseq_scoring_t), sizeof(anyseq_result_t), sizeof(anyseq_server_config_t));
+  printf("%zu %zu %zu %zu\\n", offsetof(anyseq_scoring_t, matrix), offsetof(anyseq_result_t, cigar_off),
+         offsetof(anyseq_server_config_t, scoring), offsetof(anyseq_server_config_t, mem_budget_bytes));
+  return 0;
+}}
+''')
+    exe = tmp_path / "layout"
+    subprocess.check_call(["gcc", "-std=c99", "-o", str(exe), str(src)])
+    sizes, offs = [list(map(int, line.split())) for line in subprocess.check_output([str(exe)]).decode().split("\n")[:2]]
+    assert sizes == [ctypes.sizeof(pkg.Scoring), pkg.RESULT_DTYPE.itemsize, ctypes.sizeof(pkg.ServerConfig)]
+    assert offs == [pkg.Scoring.matrix.offset, pkg.RESULT_DTYPE.fields["cigar_off"][1],
+                    pkg.ServerConfig.scoring.offset, pkg.ServerConfig.mem_budget_bytes.offset]

@@ -214,3 +214,42 @@ def test_protein_workload_full_size_sampled(pkg, ctx):
     idx = np.unique(st.integers(0, b.n_pairs - 1, 3000))
     sub = b.subset(idx)
     assert_parity(res[idx], oracle_of(sub, args, 1), sub)
+
+
+def designed_optimum_pairs(seed=7100):
+    """Pairs whose optimum sits where the kernel's bookkeeping is most delicate:
+    semi-global optima in the last column (query = subject + tail), local
+    optima tied between two rows (query = X + junk + X against X) or two
+    columns (X against X + junk + X), and motif repeats with many equal
+    cells. Lengths vary so the two halves of a lane word differ in length."""
+    st = synth.Stream(seed, 1)
+    pairs = []
+    for k in range(480):
+        L = int(st.integers(3, 60, 1)[0])
+        X = synth.random_codes(st, L, 4)
+        junk = synth.random_codes(st, int(st.integers(0, 90, 1)[0]), 4)
+        tail = synth.random_codes(st, int(st.integers(1, 200, 1)[0]), 4)
+        kind = k % 6
+        if kind == 0:
+            pairs.append((np.concatenate([X, tail]), X))
+        elif kind == 1:
+            pairs.append((np.concatenate([tail, X]), X))
+        elif kind == 2:
+            pairs.append((np.concatenate([X, junk, X]), X))
+        elif kind == 3:
+            pairs.append((X, np.concatenate([X, junk, X])))
+        elif kind == 4:
+            motif = synth.random_codes(st, 3, 4)
+            reps = int(st.integers(2, 40, 1)[0])
+            pairs.append((np.tile(motif, reps), np.tile(motif, reps + int(st.integers(0, 5, 1)[0]))))
+        else:
+            pairs.append((np.concatenate([junk, X, tail]), np.concatenate([X, junk[: len(junk) // 2]])))
+    return synth.from_pairs(pairs)
+
+
+@pytest.mark.parametrize("mode", MODES)
+@pytest.mark.parametrize("force32", [False, True])
+def test_designed_optimum_cells(pkg, ctx, mode, force32):
+    b = designed_optimum_pairs()
+    for sc_args in SCHEMES + [(1, -1, 0, 0)]:
+        assert_parity(run(pkg, ctx, b, sc_args, mode, force32=force32), oracle_of(b, sc_args, mode), b)
