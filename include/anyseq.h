@@ -230,8 +230,9 @@ const char *anyseq_version(void);
  * micro-batches: the worker waits at most max_wait_us after the oldest queued
  * request (or until max_batch_pairs are queued), then aligns the batch's small
  * pairs with one anyseq_align_batch call and, in global mode, every pair of at
- * least long_cells cells with anyseq_align_long (whole-GPU wavefront), in
- * arrival order. Results carry score and optimum cell.
+ * least long_cells cells with the wavefront of anyseq_align_long, all of them in
+ * one launch (their stripes run side by side). Results carry score and optimum
+ * cell.
  * Admission: the letters of queued and running requests never exceed
  * mem_budget_bytes; a submit beyond it returns ANYSEQ_ERR_BUDGET and queues
  * nothing (the caller may retry later). Device scratch is the context's,

@@ -540,6 +540,65 @@ extern "C" anyseq_status_t anyseq_align_batch(anyseq_ctx *ctx, const uint8_t *q,
     return ANYSEQ_OK;
 }
 
+// 32-bit range of the wavefront: every |value| of the pair stays below 2^28.
+bool anyseq::long_range_ok(const anyseq_scoring_t *sc, int64_t n, int64_t m) {
+    int64_t smax = 0;
+    for (int a = 0; a < sc->alphabet; a++)
+        for (int b = 0; b < sc->alphabet; b++) {
+            int64_t v = sigma_host(sc, a, b);
+            smax = v > smax ? v : (-v > smax ? -v : smax);
+        }
+    const int64_t bound = 3 * (int64_t)(-sc->gap_open) + (n + m + 2) * (int64_t)(-sc->gap_extend) + smax * (n < m ? n : m + 1);
+    return bound < (1ll << 28);
+}
+
+// Global scores of several long pairs in one wavefront launch (one pass per
+// pair; their stripes run side by side). Host letters and offsets; every pair
+// non-empty and inside the 32-bit range test of anyseq_align_long.
+anyseq_status_t anyseq::long_scores(anyseq_ctx *ctx, const uint8_t *q, const int64_t *q_off, const uint8_t *s,
+                                    const int64_t *s_off, int64_t count, const anyseq_scoring_t *sc, int32_t *scores,
+                                    cudaStream_t st) {
+    if (count <= 0) return ANYSEQ_OK;
+    anyseq_status_t s2 = ANYSEQ_OK;
+    const int64_t nq = q_off[count], ns = s_off[count];
+    std::vector<WavePass> passes((size_t)count);
+    int64_t out = 0;
+    for (int64_t k = 0; k < count; k++) {
+        WavePass &p = passes[(size_t)k];
+        memset(&p, 0, sizeof(p));
+        p.q0 = q_off[k];
+        p.s0 = s_off[k];
+        p.n = (int32_t)(q_off[k + 1] - q_off[k]);
+        p.m = (int32_t)(s_off[k + 1] - s_off[k]);
+        if (p.n <= 0 || p.m <= 0) return fail(ANYSEQ_ERR_ARG, "long_scores: empty pair %lld", (long long)k);
+        p.tb = sc->gap_open;
+        p.out_off = out;
+        out += p.m + 1;
+    }
+    const void *dq, *ds;
+    TRY(stage_input(ctx, "ls_q", q, (size_t)nq, st, &dq));
+    TRY(stage_input(ctx, "ls_s", s, (size_t)ns, st, &ds));
+    uint32_t *q2 = arena<uint32_t>(ctx, "ls_q2", (size_t)(nq + 15) / 16 + 2, &s2);
+    uint32_t *s2p = arena<uint32_t>(ctx, "ls_s2", (size_t)(ns + 15) / 16 + 2, &s2);
+    int32_t *bad = arena<int32_t>(ctx, "ls_bad", 4, &s2);
+    int32_t *H = arena<int32_t>(ctx, "ls_H", (size_t)out + 2, &s2);
+    if (s2 != ANYSEQ_OK) return s2;
+    CUDA_TRY(cudaMemsetAsync(bad, 0, sizeof(int32_t), st));
+    CUDA_TRY(launch_pack2bit((const uint8_t *)dq, nq, q2, sc->alphabet, bad, st));
+    CUDA_TRY(launch_pack2bit((const uint8_t *)ds, ns, s2p, sc->alphabet, bad, st));
+    ctx->launches += 2;
+    TRY(run_wave_passes(ctx, q2, s2p, passes, sc, H, nullptr, st));
+    int32_t hb = 0;
+    CUDA_TRY(cudaMemcpyAsync(&hb, bad, sizeof(int32_t), cudaMemcpyDeviceToHost, st));
+    for (int64_t k = 0; k < count; k++) {
+        const WavePass &p = passes[(size_t)k];
+        CUDA_TRY(cudaMemcpyAsync(&scores[k], H + p.out_off + p.m, sizeof(int32_t), cudaMemcpyDeviceToHost, st));
+    }
+    CUDA_TRY(cudaStreamSynchronize(st));
+    if (hb) return fail(ANYSEQ_ERR_ALPHABET, "a letter code is >= alphabet (%d)", sc->alphabet);
+    return ANYSEQ_OK;
+}
+
 // Last row (H, E) of one global pass (wavefront kernel, see hb.cu for the
 // multi-pass form used by the divide-and-conquer traceback).
 anyseq_status_t anyseq::long_last_row(anyseq_ctx *ctx, const uint32_t *q2, int64_t q0, int32_t n, const uint32_t *s2,
@@ -563,17 +622,7 @@ extern "C" anyseq_status_t anyseq_align_long(anyseq_ctx *ctx, const uint8_t *q, 
     TRY(check_scoring(sc, mode));
     if (mode != ANYSEQ_GLOBAL) return fail(ANYSEQ_ERR_ARG, "the long-pair path is global only");
     if (sc->alphabet > 4) return fail(ANYSEQ_ERR_ARG, "the long-pair path takes alphabets of at most 4 letters");
-    // 32-bit range: |values| stay below 2^28
-    {
-        int64_t smax = 0;
-        for (int a = 0; a < sc->alphabet; a++)
-            for (int b = 0; b < sc->alphabet; b++) {
-                int64_t v = sigma_host(sc, a, b);
-                smax = v > smax ? v : (-v > smax ? -v : smax);
-            }
-        int64_t bound = 3 * (int64_t)(-sc->gap_open) + (n + m + 2) * (int64_t)(-sc->gap_extend) + smax * (n < m ? n : m + 1);
-        if (bound >= (1ll << 28)) return fail(ANYSEQ_ERR_ARG, "scores of this pair may leave the 32-bit range");
-    }
+    if (!long_range_ok(sc, n, m)) return fail(ANYSEQ_ERR_ARG, "scores of this pair may leave the 32-bit range");
     cudaStream_t st = (cudaStream_t)cuda_stream;
     if (cudaSetDevice(ctx->device) != cudaSuccess) return fail(ANYSEQ_ERR_CUDA, "cudaSetDevice failed");
     ctx->launches = 0;

@@ -67,6 +67,10 @@ anyseq_status_t stage_batch(anyseq_ctx *ctx, const uint8_t *q, const int64_t *q_
                             const int64_t *s_off, int64_t n_pairs, BatchInput &in, cudaStream_t st);
 anyseq_status_t band_scores(anyseq_ctx *ctx, const BatchInput &in, const anyseq_scoring_t *sc, int32_t *score,
                             int32_t *eq, int32_t *es, uint32_t *flags, cudaStream_t st);
+bool long_range_ok(const anyseq_scoring_t *sc, int64_t n, int64_t m);
+anyseq_status_t long_scores(anyseq_ctx *ctx, const uint8_t *q, const int64_t *q_off, const uint8_t *s,
+                            const int64_t *s_off, int64_t count, const anyseq_scoring_t *sc, int32_t *scores,
+                            cudaStream_t st);
 anyseq_status_t long_last_row(anyseq_ctx *ctx, const uint32_t *q2, int64_t q0, int32_t n, const uint32_t *s2,
                               int64_t s0, int32_t m, bool rev, int32_t tb, const anyseq_scoring_t *sc, int32_t *H,
                               int32_t *E, cudaStream_t st);

@@ -217,7 +217,19 @@ __device__ __noinline__ void run_slot(const BatchArgs &A, GroupSmem *sm, const S
                     qa = *reinterpret_cast<const uint2 *>(qpb + (sel & 0xFFFFu));
                     if (C::PAIRS == 2) qb = *reinterpret_cast<const uint2 *>(qpb + (sel >> 16));
                 }
-                T diag = prev_up;
+                // sigma' of row r at this column
+                auto sigma_r = [&](int r) -> uint32_t {
+                    if (SIGP == 0) return C::as_u(C::sigma(profA[r], profB[r], sel));
+                    // byte r of this lane's profile row, per half (bytes are >= 0)
+                    const uint32_t wa = (r & 4) ? qa.y : qa.x, wb = (r & 4) ? qb.y : qb.x;
+                    const uint32_t b = (uint32_t)(r & 3);
+                    return C::PAIRS == 2 ? prmt(wa, wb, b | ((b | 8u) << 4) | ((b + 4u) << 8) | (((b + 4u) | 8u) << 12))
+                                         : prmt(wa, wa, b | ((b | 8u) << 4) | ((b | 8u) << 8) | ((b | 8u) << 12));
+                };
+                // H(i-1,j-1) + sigma of row 0; every later row takes the old Hoe of the row
+                // above (its upper-left neighbour) before that register is overwritten, so
+                // the row registers update in place
+                T Ad = C::addc(prev_up, sigma_r(0));
                 prev_up = up_hoe;
                 T E = up_e;
                 const uint32_t jj = C::PAIRS == 2 ? (uint32_t)(c + 1) * 65537u : (uint32_t)(c + 1);
@@ -227,23 +239,14 @@ __device__ __noinline__ void run_slot(const BatchArgs &A, GroupSmem *sm, const S
 #pragma unroll
                 for (int r = 0; r < R; r++) {
                     // H(i,j) = max(H(i-1,j-1)+sigma, E(i,j), F(i,j) [,0]) kept as Hoe = H + o + e
-                    T sg;
-                    if (SIGP == 0) {
-                        sg = C::sigma(profA[r], profB[r], sel);
-                    } else {
-                        // byte r of this lane's profile row, per half (bytes are >= 0)
-                        const uint32_t wa = (r & 4) ? qa.y : qa.x, wb = (r & 4) ? qb.y : qb.x;
-                        const uint32_t b = (uint32_t)(r & 3);
-                        sg = C::PAIRS == 2 ? C::from_u(prmt(wa, wb, b | ((b | 8u) << 4) | ((b + 4u) << 8) | (((b + 4u) | 8u) << 12)))
-                                           : C::from_u(prmt(wa, wa, b | ((b | 8u) << 4) | ((b | 8u) << 8) | ((b | 8u) << 12)));
-                    }
-                    T Ad = C::addc(diag, C::as_u(sg));                 // H(i-1,j-1) + sigma
-                    T Fl = F[r];
-                    F[r] = C::addmax(F[r], e_raw, Hoe[r]);             // Eq. 5
-                    T M = (MODE == LOCAL) ? C::maxrelu(Ad, F[r]) : C::vmax(Ad, F[r]);
-                    T X = C::addc(M, oe_c);                           // max(diag, F) + o + e
-                    diag = Hoe[r];
-                    T Ein = E;
+                    F[r] = C::addmax(F[r], e_raw, Hoe[r]);             // Eq. 5 (Hoe[r]: the left neighbour)
+                    const T M = (MODE == LOCAL) ? C::maxrelu(Ad, F[r]) : C::vmax(Ad, F[r]);
+                    const T X = C::addc(M, oe_c);                     // max(diag, F) + o + e
+                    T Adn = Ad;
+                    if (r + 1 < R) Adn = C::addc(Hoe[r], sigma_r(r + 1));
+                    uint32_t fFo = 0;
+                    if (TB) fFo = C::ge(Hoe[r], F[r]);                // F(i,j) opened from H(i,j-1)
+                    const T Ein = E;
                     Hoe[r] = C::addmax(E, oe_raw, X);                  // H + o + e
                     E = C::addmax(E, e_raw, X);                        // Eq. 4 for row i+1
                     if (TB) {
@@ -251,7 +254,6 @@ __device__ __noinline__ void run_slot(const BatchArgs &A, GroupSmem *sm, const S
                         uint32_t fD = C::ge(C::addc(Ad, oe_c), Hoe[r]);   // diagonal reaches H
                         uint32_t fE = C::ge(C::addc(Ein, oe_c), Hoe[r]);  // E reaches H
                         uint32_t fEo = C::ge(hup, Ein);                    // E(i,j) opened from H(i-1,j)
-                        uint32_t fFo = C::ge(diag, F[r]);                  // F(i,j) opened from H(i,j-1)
                         uint32_t s0 = fD, s1 = fE;
                         if (MODE == LOCAL) {
                             uint32_t fZ = C::ge(C::from_u(C::zero_hoe(oe)), Hoe[r]);  // H == 0
@@ -265,13 +267,13 @@ __device__ __noinline__ void run_slot(const BatchArgs &A, GroupSmem *sm, const S
                         pl_fo = (pl_fo >> 1) | (fFo & FM);
                         hup = Hoe[r];
                     }
-                    (void)Fl;
                     if (MODE == LOCAL) {
                         // strict improvement of the row maximum: the column of its first occurrence
                         const uint32_t gm = C::gt_mask(Hoe[r], rowmax[r]);
                         rowj[r] = (jj & gm) | (rowj[r] & ~gm);
                         rowmax[r] = C::vmax(rowmax[r], Hoe[r]);
                     }
+                    Ad = Adn;
                 }
                 last_hoe = Hoe[R - 1];
                 last_e = E;

@@ -6,8 +6,8 @@
 // most max_wait_us after the oldest queued request (or until max_batch_pairs
 // are queued), then aligns every small pair of the batch with one
 // anyseq_align_batch call (inter-sequence parallelism) and every pair of at
-// least long_cells cells with the whole-GPU wavefront of anyseq_align_long
-// (intra-sequence parallelism, global mode), in arrival order. Admission: the
+// least long_cells cells with the wavefront of anyseq_align_long (intra-sequence
+// parallelism, global mode), all of them in one launch. Admission: the
 // letters of queued and running requests may not exceed mem_budget_bytes; a
 // submit that would exceed it is refused with ANYSEQ_ERR_BUDGET.
 #include <chrono>
@@ -71,7 +71,8 @@ void run_batch(anyseq_server *S, std::vector<Request *> &reqs) {
     for (Request *r : reqs) {
         const double cells = (double)r->q.size() * (double)r->s.size();
         const bool is_long = S->cfg.mode == ANYSEQ_GLOBAL && cells >= (double)S->cfg.long_cells && !r->q.empty() &&
-                             !r->s.empty();
+                             !r->s.empty() && S->sc.alphabet <= 4 &&
+                             anyseq::long_range_ok(&S->sc, (int64_t)r->q.size(), (int64_t)r->s.size());
         (is_long ? big : small).push_back(r);
     }
     if (!small.empty()) {
@@ -99,13 +100,35 @@ void run_batch(anyseq_server *S, std::vector<Request *> &reqs) {
             small[k]->t_done = t;
         }
     }
-    for (Request *r : big) {
-        uint64_t used = 0;
-        r->status = anyseq_align_long(S->ctx, r->q.data(), (int64_t)r->q.size(), r->s.data(), (int64_t)r->s.size(),
-                                      &S->sc, ANYSEQ_GLOBAL, ANYSEQ_WANT_SCORE | ANYSEQ_WANT_END, &r->res, nullptr, 0,
-                                      &used, S->stream);
-        if (r->status != ANYSEQ_OK) r->error = anyseq_last_error();
-        r->t_done = now_ns();
+    if (!big.empty()) {
+        // every long pair of the batch in one wavefront launch
+        std::vector<int64_t> qo(big.size() + 1, 0), so(big.size() + 1, 0);
+        for (size_t k = 0; k < big.size(); k++) {
+            qo[k + 1] = qo[k] + (int64_t)big[k]->q.size();
+            so[k + 1] = so[k] + (int64_t)big[k]->s.size();
+        }
+        std::vector<uint8_t> q((size_t)qo.back()), s((size_t)so.back());
+        for (size_t k = 0; k < big.size(); k++) {
+            memcpy(q.data() + qo[k], big[k]->q.data(), big[k]->q.size());
+            memcpy(s.data() + so[k], big[k]->s.data(), big[k]->s.size());
+        }
+        std::vector<int32_t> scores(big.size(), 0);
+        const anyseq_status_t st = anyseq::long_scores(S->ctx, q.data(), qo.data(), s.data(), so.data(),
+                                                       (int64_t)big.size(), &S->sc, scores.data(), S->stream);
+        const std::string msg = st != ANYSEQ_OK ? anyseq_last_error() : "";
+        const int64_t t = now_ns();
+        for (size_t k = 0; k < big.size(); k++) {
+            Request *r = big[k];
+            memset(&r->res, 0, sizeof(r->res));
+            r->res.score = scores[k];
+            r->res.beg_q = r->res.beg_s = -1;
+            r->res.end_q = (int32_t)r->q.size();
+            r->res.end_s = (int32_t)r->s.size();
+            r->res.flags = ANYSEQ_FLAG_INT32;
+            r->status = st;
+            r->error = msg;
+            r->t_done = t;
+        }
     }
     std::lock_guard<std::mutex> lock(S->mu);
     for (Request *r : reqs) {

@@ -164,17 +164,17 @@ __global__ void __launch_bounds__(256, 2) wave_kernel(WaveArgs A) {
             }
             if (c >= 0 && c < m) {
                 const uint32_t sel = sm->sel[c & (WRING - 1)];
-                T diag = (c == 0) ? diag0 : prev_up;
+                // prev_up is diag0 until the first valid column; each later row takes the
+                // old Hoe of the row above before that register is overwritten
+                T Ad = C::addc(prev_up, (uint32_t)C::sigma(prof[0], prof[0], sel));
                 prev_up = up_hoe;
                 T E = up_e, Ein = up_e;
 #pragma unroll
                 for (int r = 0; r < WR; r++) {
-                    T sg = C::sigma(prof[r], prof[r], sel);
-                    T Ad = C::addc(diag, (uint32_t)sg);
                     F[r] = C::addmax(F[r], e_raw, Hoe[r]);
-                    T M = C::vmax(Ad, F[r]);
-                    T X = C::addc(M, oe_c);
-                    diag = Hoe[r];
+                    const T M = C::vmax(Ad, F[r]);
+                    const T X = C::addc(M, oe_c);
+                    if (r + 1 < WR) Ad = C::addc(Hoe[r], (uint32_t)C::sigma(prof[r + 1], prof[r + 1], sel));
                     Ein = E;
                     Hoe[r] = C::addmax(E, oe_raw, X);
                     E = C::addmax(E, e_raw, X);
