@@ -53,10 +53,22 @@ struct Runs {
     }
 };
 
-// One thread per pair: walk the direction words from the optimum cell.
-__global__ void tb_walk_kernel(TbWalkArgs W) {
-    for (int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; p < W.n_pairs;
-         p += (int64_t)gridDim.x * blockDim.x) {
+// One warp per pair: the walk from the optimum cell is sequential and every
+// step moves up or left, so the warp stages a window of direction words ahead of
+// the walker into shared memory (rows i-31..i, columns j-31..j: one load per
+// lane and row group of 8 rows, all independent) and lane 0 walks inside it;
+// leaving the window triggers the next load. This turns one dependent global
+// load per step into one per window.
+constexpr int TBW = 32;                  // window height and width (cells)
+constexpr int TBG = TBW / TB_R + 1;      // row groups a window can touch
+constexpr int TB_WARPS = 8;              // warps per block of the walk
+
+__global__ void __launch_bounds__(TB_WARPS * 32) tb_walk_kernel(TbWalkArgs W) {
+    __shared__ uint32_t win[TB_WARPS][TBG][TBW];
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    uint32_t(*wn)[TBW] = win[wid];
+    const int64_t nw = (int64_t)gridDim.x * TB_WARPS;
+    for (int64_t p = (int64_t)blockIdx.x * TB_WARPS + wid; p < W.n_pairs; p += nw) {
         const int32_t n = (int32_t)(W.q_off[p + 1] - W.q_off[p]);
         const int32_t m = (int32_t)(W.s_off[p + 1] - W.s_off[p]);
         Runs rl;
@@ -76,57 +88,84 @@ __global__ void tb_walk_kernel(TbWalkArgs W) {
             const uint32_t *dw = W.dirs + W.dir_base[p];
             const int32_t pad = W.lay_pad[p], ch0 = W.lay_ch0[p];
             const int64_t S = m + GROUP - 1;
-            auto word = [&](int32_t ii, int32_t jj, int32_t &r) -> uint32_t {
-                int32_t ip = ii + pad - 1;
-                int32_t ch = ip / (GROUP * TB_R);
-                int32_t gl = (ip % (GROUP * TB_R)) / TB_R;
-                r = ip % TB_R;
-                int64_t s = (int64_t)(jj - 1) + gl;
-                return dw[((int64_t)(ch - ch0) * S + s) * GROUP + gl];
-            };
             int state = 0;  // 0: H, 1: E, 2: F
+            bool done = false;
             // every step moves up or left within two iterations; the bound and the
             // boundary checks keep a corrupt word from leaving the pair's words
-            for (int64_t guard = 2 * ((int64_t)n + m) + 4; guard > 0; guard--) {
-                if (state != 0 && (i <= 0 || j <= 0)) break;
-                if (state == 0) {
-                    if (i == 0 && j == 0) break;
-                    if (W.mode != GLOBAL) {
-                        if (i == 0 || j == 0) break;
-                    } else {
-                        if (j == 0) { rl.push(1u, (uint32_t)i); i = 0; break; }
-                        if (i == 0) { rl.push(2u, (uint32_t)j); j = 0; break; }
+            int64_t guard = 2 * ((int64_t)n + m) + 4;
+            while (!done) {
+                // stage the window below-right of (i, j): rows i_lo..i, columns j_lo..j
+                const int32_t i_lo = max(1, i - TBW + 1), j_lo = max(1, j - TBW + 1);
+                const int32_t rg_lo = (i_lo + pad - 1) / TB_R;  // row group of the window's top row
+                if (i >= 1 && j >= 1) {
+                    const int32_t rg_hi = (i + pad - 1) / TB_R;
+                    const int32_t jj = j - lane;
+                    if (jj >= j_lo) {
+                        for (int32_t rg = rg_lo; rg <= rg_hi; rg++) {
+                            const int32_t ch = rg / GROUP, gl = rg % GROUP;
+                            const int64_t s = (int64_t)(jj - 1) + gl;
+                            wn[rg - rg_lo][lane] = dw[((int64_t)(ch - ch0) * S + s) * GROUP + gl];
+                        }
                     }
-                    int32_t r;
-                    uint32_t w = word(i, j, r);
-                    uint32_t s0 = (w >> r) & 1u, s1 = (w >> (8 + r)) & 1u;
-                    if (W.mode == LOCAL) {
-                        if (s0 && s1) break;  // H = 0: the local alignment starts here
-                        if (s0) { rl.push(0u, 1u); i--; j--; }
-                        else state = s1 ? 1 : 2;
-                    } else {
-                        if (s0) { rl.push(0u, 1u); i--; j--; }
-                        else state = s1 ? 1 : 2;
-                    }
-                } else if (state == 1) {
-                    int32_t r;
-                    uint32_t w = word(i, j, r);
-                    rl.push(1u, 1u);
-                    if ((w >> (16 + r)) & 1u) state = 0;
-                    i--;
-                } else {
-                    int32_t r;
-                    uint32_t w = word(i, j, r);
-                    rl.push(2u, 1u);
-                    if ((w >> (24 + r)) & 1u) state = 0;
-                    j--;
                 }
+                __syncwarp();
+                if (lane == 0) {
+                    const int32_t jtop = j;  // the window's right column (j moves while walking)
+                    // the word of (ii, jj) inside the window, r = its row bit
+                    auto word = [&](int32_t ii, int32_t jj, int32_t &r) -> uint32_t {
+                        const int32_t ip = ii + pad - 1;
+                        r = ip % TB_R;
+                        return wn[ip / TB_R - rg_lo][jtop - jj];
+                    };
+                    auto inside = [&](int32_t ii, int32_t jj) { return ii >= i_lo && jj >= j_lo && jj <= jtop; };
+                    for (; guard > 0; guard--) {
+                        if (state != 0 && (i <= 0 || j <= 0)) { done = true; break; }
+                        if (state == 0) {
+                            if (i == 0 && j == 0) { done = true; break; }
+                            if (W.mode != GLOBAL) {
+                                if (i == 0 || j == 0) { done = true; break; }
+                            } else {
+                                if (j == 0) { rl.push(1u, (uint32_t)i); i = 0; done = true; break; }
+                                if (i == 0) { rl.push(2u, (uint32_t)j); j = 0; done = true; break; }
+                            }
+                            if (!inside(i, j)) break;  // next window
+                            int32_t r;
+                            const uint32_t w = word(i, j, r);
+                            const uint32_t s0 = (w >> r) & 1u, s1 = (w >> (8 + r)) & 1u;
+                            if (W.mode == LOCAL && s0 && s1) { done = true; break; }  // H = 0: the alignment starts here
+                            if (s0) { rl.push(0u, 1u); i--; j--; }
+                            else state = s1 ? 1 : 2;
+                        } else {
+                            if (!inside(i, j)) break;
+                            int32_t r;
+                            const uint32_t w = word(i, j, r);
+                            if (state == 1) {
+                                rl.push(1u, 1u);
+                                if ((w >> (16 + r)) & 1u) state = 0;
+                                i--;
+                            } else {
+                                rl.push(2u, 1u);
+                                if ((w >> (24 + r)) & 1u) state = 0;
+                                j--;
+                            }
+                        }
+                    }
+                    if (guard <= 0) done = true;
+                }
+                __syncwarp();
+                i = __shfl_sync(0xffffffffu, i, 0);
+                j = __shfl_sync(0xffffffffu, j, 0);
+                state = __shfl_sync(0xffffffffu, state, 0);
+                done = __shfl_sync(0xffffffffu, (int)done, 0) != 0;
+                guard = __shfl_sync(0xffffffffu, guard, 0);
             }
         }
-        rl.flush();
-        W.cig_len[p] = rl.k;
-        W.beg_q[p] = i;
-        W.beg_s[p] = j;
+        if (lane == 0) {
+            rl.flush();
+            W.cig_len[p] = rl.k;
+            W.beg_q[p] = i;
+            W.beg_s[p] = j;
+        }
     }
 }
 
@@ -140,7 +179,6 @@ __global__ void tb_compact_kernel(int64_t n_pairs, const int64_t *q_off, const i
         for (int64_t t = 0; t < len; t++) out[off + t] = src[len - 1 - t];
     }
 }
-
 static int grid_of(int64_t work) {
     int64_t b = (work + 255) / 256;
     return (int)(b < 1 ? 1 : (b > 65535 ? 65535 : b));
@@ -154,7 +192,9 @@ cudaError_t launch_tb_plan(const int32_t *list, const int64_t *n_list, int per_i
 }
 
 cudaError_t launch_tb_walk(const TbWalkArgs &W, cudaStream_t st) {
-    tb_walk_kernel<<<grid_of(W.n_pairs), 256, 0, st>>>(W);
+    int64_t blocks = (W.n_pairs + TB_WARPS - 1) / TB_WARPS;
+    blocks = blocks < 1 ? 1 : (blocks > 65535 ? 65535 : blocks);
+    tb_walk_kernel<<<(int)blocks, TB_WARPS * 32, 0, st>>>(W);
     return cudaGetLastError();
 }
 
