@@ -148,17 +148,34 @@ constexpr int BCH = GROUP * BR;    // rows per chunk
 
 __device__ __forceinline__ int64_t floor_div(int64_t a, int64_t b) { return a >= 0 ? a / b : -((-a + b - 1) / b); }
 
+// Band of a pair: around the line from (0,0) to (n,m), row i keeps the
+// columns within w(i) of the line shifted by c(i), with c(i) = c (n-i)/n and
+// w(i) = wm + (w - wm) (n-i)/n, wm = min(w, BAND_WMIN): both taper linearly to
+// the end cell. An exit at row i must beat the banded score by about the
+// shortfall of the remaining n - i rows against all-match scoring (the
+// certificate's bound), so the margin the band needs shrinks with the rows left;
+// the optimal path starts and ends on the line, so the shift tapers too.
+constexpr int32_t BAND_WMIN = 16;
+
 // DP-column interval [lo, hi] of the chunk holding real rows [ilo, ihi]
 // (rows <= 0 stand for row 0); the first chunk starts at column 0 and the last
-// one ends at column m so that (0,0) and (n,m) are inside.
+// one ends at column m so that (0,0) and (n,m) are inside. The left edge is the
+// smallest left edge of the rows from ilo to n and the right edge the largest
+// right edge of the rows up to ihi, so consecutive chunks form a staircase.
 __device__ __forceinline__ void chunk_cols(int64_t n, int64_t m, int32_t c, int32_t w, int64_t ilo, int64_t ihi,
                                            bool first, bool last, int32_t &lo, int32_t &hi) {
     // a chunk that holds padding rows (copies of row 0) starts at column 0
     if (ilo <= 0) first = true;
     ilo = ilo < 0 ? 0 : ilo;
     ihi = ihi < 0 ? 0 : ihi;
-    int64_t l = -floor_div(-(ilo * m + (int64_t)(c - w) * n), n);  // ceil
-    int64_t h = floor_div(ihi * m + (int64_t)(c + w) * n, n);
+    const int64_t nn = n > 0 ? n : 1;
+    const int64_t wm = w < BAND_WMIN ? w : BAND_WMIN;
+    // n * (left edge + wm) and n * (right edge - wm) of row i are linear in i
+    auto left_num = [&](int64_t i) { return i * m + ((int64_t)c - w + wm) * (n - i); };
+    auto right_num = [&](int64_t i) { return i * m + ((int64_t)c + w - wm) * (n - i); };
+    const int64_t ln = min(left_num(ilo), left_num(n)), rn = max(right_num(0), right_num(ihi));
+    int64_t l = -floor_div(-ln, nn) - wm;  // ceil
+    int64_t h = floor_div(rn, nn) + wm;
     if (first || l < 0) l = 0;
     if (last || h > m) h = m;
     if (l > m) l = m;

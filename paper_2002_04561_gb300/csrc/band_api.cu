@@ -33,6 +33,13 @@ static T *arena_b(anyseq_ctx *ctx, const char *name, size_t count, anyseq_status
 static constexpr int64_t NP = MLP_NPARAM;
 static constexpr int32_t MIN_W = 16;
 
+// Cells of a band of top half-width w over n rows (the half-width tapers
+// linearly to min(w, 16) at the last row, see chunk_cols).
+__host__ __device__ inline double band_area(int64_t n, int32_t w) {
+    const double wm = w < 16 ? (double)w : 16.0;
+    return ((double)w + wm + 1.0) * (double)n;
+}
+
 static MlpDev mlp_dev(anyseq_ctx *ctx) {
     MlpDev P;
     P.master = ctx->mlp;
@@ -102,9 +109,11 @@ __global__ void band_plan_kernel(const float *y, const int64_t *q_off, const int
         lw = fminf(fmaxf(lw, 0.0f), 20.0f);
         int32_t w = (int32_t)ceilf(expf(lw));
         w = w < MIN_W ? MIN_W : w;
+        // the path starts on the line: a shift beyond the top half-width cannot hold it
+        c = fminf(fmaxf(c, -(float)w), (float)w);
         centre[p] = (int32_t)rintf(c);
         width[p] = w;
-        const bool too_wide = (2.0 * w + 1.0) * (double)n > 0.5 * (double)n * (double)m;
+        const bool too_wide = band_area(n, w) > 0.5 * (double)n * (double)m;
         if (n == 0 || m == 0 || too_wide) {
             full[p] = 1;
         } else {
@@ -133,7 +142,7 @@ __global__ void band_round_kernel(const int32_t *list, int64_t n_list, const int
         } else {
             const int32_t w = width[p] * 2;
             width[p] = w;
-            if ((2.0 * w + 1.0) * (double)n > 0.5 * (double)n * (double)m) {
+            if (band_area(n, w) > 0.5 * (double)n * (double)m) {
                 full[p] = 1;
             } else {
                 unsigned long long pos = atomicAdd(reinterpret_cast<unsigned long long *>(next_count), 1ull);
@@ -453,7 +462,7 @@ extern "C" anyseq_status_t anyseq_band_train(anyseq_ctx *ctx, const uint8_t *q, 
                 wcert[p] = hw[p];
             } else {
                 hw[p] *= 2;
-                if ((2.0 * hw[p] + 1.0) * (double)qn <= 0.5 * (double)qn * (double)sm) next.push_back(p);
+                if (band_area(qn, hw[p]) <= 0.5 * (double)qn * (double)sm) next.push_back(p);
             }
         }
         pending.swap(next);

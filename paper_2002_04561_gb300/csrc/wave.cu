@@ -40,7 +40,7 @@ __device__ __forceinline__ void st_release(int32_t *p, int32_t v) {
     asm volatile("st.release.gpu.global.s32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
 }
 
-struct WaveSmem {
+struct __align__(16) WaveSmem {
     uint32_t sel[WRING];
     int32_t top[2 * WRING];
     int32_t bot[2 * WRING];
@@ -115,17 +115,20 @@ __global__ void __launch_bounds__(256, 2) wave_kernel(WaveArgs A) {
             int c = blk * BLOCK + g;
             if (c < m) {
                 sm->sel[c & (WRING - 1)] = C::selector(wletter(A.s2, ps.s0, m, c, rev), 0);
-                if (k > 0 && !failed) {
-                    int2 v = bin[c];
-                    sm->top[2 * (c & (WRING - 1))] = v.x;
-                    sm->top[2 * (c & (WRING - 1)) + 1] = v.y;
+                if (k == 0) {
+                    // row 0: H(0, c+1); E below row 0 comes from H only (E(0, .) = -inf)
+                    const int32_t v = o + (c + 1) * e + oe;
+                    reinterpret_cast<int2 *>(sm->top)[c & (WRING - 1)] = make_int2(v, v);
+                } else if (!failed) {
+                    reinterpret_cast<int2 *>(sm->top)[c & (WRING - 1)] = bin[c];
                 }
             }
         };
         auto drain = [&](int blk) {
             int c = blk * BLOCK + g;
             if (blk >= 0 && c < m) {
-                int32_t hv = sm->bot[2 * (c & (WRING - 1))], ev = sm->bot[2 * (c & (WRING - 1)) + 1];
+                const int2 b2 = reinterpret_cast<const int2 *>(sm->bot)[c & (WRING - 1)];
+                const int32_t hv = b2.x, ev = b2.y;
                 if (!last) {
                     bout[c] = make_int2(hv, ev);
                 } else {
@@ -142,27 +145,27 @@ __global__ void __launch_bounds__(256, 2) wave_kernel(WaveArgs A) {
         __syncwarp();
         int drained = 0;
         T last_hoe = C::NEG, last_e = C::NEG, prev_up = diag0;
-        for (int s = 0; s < S && !failed; s++) {
-            if ((s & (BLOCK - 1)) == 0) {
-                int kb = s / BLOCK;
-                if ((kb + 1) * BLOCK < m) wait_for(kb + 1);
-                fill(kb + 1);
-                if (kb - 2 >= drained) { drain(kb - 2); drained = kb - 1; }
-                __syncwarp();
-            }
+        for (int s0 = 0; s0 < S && !failed; s0 += BLOCK) {
+          {
+            const int kb = s0 / BLOCK;
+            if ((kb + 1) * BLOCK < m) wait_for(kb + 1);
+            fill(kb + 1);
+            if (kb - 2 >= drained) { drain(kb - 2); drained = kb - 1; }
+            __syncwarp();
+          }
+          const int s1 = min(S, s0 + BLOCK);
+          for (int s = s0; s < s1; s++) {
             const int c = s - g;
             T up_hoe = (T)__shfl_up_sync(0xffffffffu, (uint32_t)last_hoe, 1);
             T up_e = (T)__shfl_up_sync(0xffffffffu, (uint32_t)last_e, 1);
             if (g == 0) {
-                if (k == 0) {
-                    up_hoe = o + (c + 1) * e + oe;  // row 0
-                    up_e = up_hoe;
-                } else if (c >= 0 && c < m) {
-                    up_hoe = sm->top[2 * (c & (WRING - 1))];
-                    up_e = sm->top[2 * (c & (WRING - 1)) + 1];
-                }
+                // the row above the stripe (row 0 for the first stripe); the ring index is
+                // masked, and invalid columns are not used
+                const int2 tv = reinterpret_cast<const int2 *>(sm->top)[c & (WRING - 1)];
+                up_hoe = tv.x;
+                up_e = tv.y;
             }
-            if (c >= 0 && c < m) {
+            if ((unsigned)c < (unsigned)m) {
                 const uint32_t sel = sm->sel[c & (WRING - 1)];
                 // prev_up is diag0 until the first valid column; each later row takes the
                 // old Hoe of the row above before that register is overwritten
@@ -184,10 +187,10 @@ __global__ void __launch_bounds__(256, 2) wave_kernel(WaveArgs A) {
                 if (g == WG - 1) {
                     // border for the next stripe: (Hoe, E of the row below); the last
                     // stripe keeps E of its own last row for the Hirschberg join
-                    sm->bot[2 * (c & (WRING - 1))] = last_hoe;
-                    sm->bot[2 * (c & (WRING - 1)) + 1] = last ? Ein : E;
+                    reinterpret_cast<int2 *>(sm->bot)[c & (WRING - 1)] = make_int2(last_hoe, last ? Ein : E);
                 }
             }
+          }
         }
         __syncwarp();
         for (int b = drained; b <= (m - 1) / BLOCK; b++) drain(b);
