@@ -181,8 +181,11 @@ anyseq_status_t anyseq_band_train(anyseq_ctx *ctx, const uint8_t *q, const int64
  * the DP kernels of each call with CUDA events on the call's stream;
  * "hirschberg_base_cells" (default 65536) is the subproblem size below which the
  * divide-and-conquer traceback switches to a full matrix; "spin_limit" (default
- * 2^24) bounds every device-side wait of the wavefront (ANYSEQ_ERR_TIMEOUT).
- * Unknown keys: ANYSEQ_ERR_ARG. */
+ * 2^24) bounds every device-side wait of the wavefront (ANYSEQ_ERR_TIMEOUT);
+ * "band_max_doublings" (default 1) is how often ANYSEQ_BAND_LEARNED doubles a
+ * band that fails its certificate before the full DP; "band_area_pct" (default
+ * 35) sends a pair whose band would exceed that share of its matrix to the full
+ * DP. Unknown keys: ANYSEQ_ERR_ARG. */
 anyseq_status_t anyseq_set_option(anyseq_ctx *ctx, const char *key, int64_t value);
 
 /* Statistics of the context's last call (host values, valid after the call's
@@ -190,7 +193,9 @@ anyseq_status_t anyseq_set_option(anyseq_ctx *ctx, const char *key, int64_t valu
  * int16x2 DP kernel, needs "profile"), "dp32_ms" (32-bit lanes), "pairs16",
  * "pairs32" (pairs per lane width); with ANYSEQ_BAND_LEARNED also "band_cells"
  * (cells relaxed by banded passes), "band_accepted", "band_fallback" (pairs),
- * "band_rounds". Unknown keys: ANYSEQ_ERR_ARG. */
+ * "band_rounds", and the host time of its phases "band_plan_ms" (packing,
+ * features, network, band plan), "band_pass_ms" (banded passes with the
+ * certificate), "band_full_ms" (full DP of the rest). Unknown keys: ANYSEQ_ERR_ARG. */
 anyseq_status_t anyseq_get_stat(anyseq_ctx *ctx, const char *key, double *value);
 
 /*
@@ -222,6 +227,35 @@ const char *anyseq_last_error(void);
 
 /* Library version string. */
 const char *anyseq_version(void);
+
+/* ------------------------------------------------------------------------
+ * Graph plans (batching, not in the paper): one batch shape of
+ * anyseq_align_batch (offsets, scoring, mode; score and optimum cell) whose
+ * whole launch sequence is captured once in a CUDA graph and replayed. The
+ * plan owns device buffers for the letters and the results and a private
+ * context, so nothing else can move the scratch the graph points at.
+ *   1. anyseq_plan_create: host offsets (copied), scoring (copied), mode.
+ *   2. anyseq_plan_buffers: device pointers of the plan's letter arrays
+ *      (q_off[n_pairs] and s_off[n_pairs] bytes) and of its n_pairs results.
+ *      Fill the letters (any stream, ordered before the run) before each run.
+ *   3. anyseq_plan_run: enqueue one run on cuda_stream. The first run executes
+ *      the batched path once (sizing the scratch; it synchronises), then
+ *      captures it; every later run is one graph launch and does not
+ *      synchronise.
+ *   4. anyseq_plan_wait: synchronise cuda_stream and report the run's letter
+ *      check (ERR_ALPHABET if a code was >= alphabet).
+ * Runs of one plan must not overlap. Errors: ERR_ARG, ERR_ALPHABET, ERR_CUDA.
+ * ------------------------------------------------------------------------ */
+typedef struct anyseq_plan anyseq_plan;
+
+anyseq_status_t anyseq_plan_create(anyseq_plan **plan, int device, const int64_t *q_off,
+                                   const int64_t *s_off, int64_t n_pairs,
+                                   const anyseq_scoring_t *sc, int32_t mode);
+anyseq_status_t anyseq_plan_buffers(anyseq_plan *plan, uint8_t **q, uint8_t **s,
+                                    anyseq_result_t **out);
+anyseq_status_t anyseq_plan_run(anyseq_plan *plan, void *cuda_stream);
+anyseq_status_t anyseq_plan_wait(anyseq_plan *plan, void *cuda_stream);
+anyseq_status_t anyseq_plan_destroy(anyseq_plan *plan);
 
 /* ------------------------------------------------------------------------
  * Serving (not in the paper, whose interface aligns one pair per call): a

@@ -69,7 +69,8 @@ EXPORTS = ["anyseq_create", "anyseq_destroy", "anyseq_align_batch", "anyseq_alig
            "anyseq_band_model_save", "anyseq_band_model_load", "anyseq_band_forward",
            "anyseq_band_gradient", "anyseq_band_train", "anyseq_align_long_noalloc",
            "anyseq_server_create", "anyseq_server_submit", "anyseq_server_wait", "anyseq_server_stat",
-           "anyseq_server_destroy"]
+           "anyseq_server_destroy", "anyseq_plan_create", "anyseq_plan_buffers", "anyseq_plan_run",
+           "anyseq_plan_wait", "anyseq_plan_destroy"]
 NOALLOC_MAX_LEN = 1048576
 BAND_FEATURES = 64
 BAND_PARAMS = 25090
@@ -115,6 +116,11 @@ def load(build_if_missing: bool = False):
     lib.anyseq_server_wait.argtypes = [P, U64, I64, P, ctypes.POINTER(I64)]
     lib.anyseq_server_stat.argtypes = [P, ctypes.c_char_p, ctypes.POINTER(ctypes.c_double)]
     lib.anyseq_server_destroy.argtypes = [P]
+    lib.anyseq_plan_create.argtypes = [ctypes.POINTER(P), ctypes.c_int, P, P, I64, P, I32]
+    lib.anyseq_plan_buffers.argtypes = [P, ctypes.POINTER(P), ctypes.POINTER(P), ctypes.POINTER(P)]
+    lib.anyseq_plan_run.argtypes = [P, P]
+    lib.anyseq_plan_wait.argtypes = [P, P]
+    lib.anyseq_plan_destroy.argtypes = [P]
     lib.anyseq_last_error.restype = ctypes.c_char_p
     lib.anyseq_last_error.argtypes = []
     lib.anyseq_version.restype = ctypes.c_char_p
@@ -123,7 +129,8 @@ def load(build_if_missing: bool = False):
                  "anyseq_band_model_get", "anyseq_band_model_set", "anyseq_band_model_save",
                  "anyseq_band_model_load", "anyseq_band_forward", "anyseq_band_gradient", "anyseq_band_train",
                  "anyseq_align_long_noalloc", "anyseq_server_create", "anyseq_server_submit",
-                 "anyseq_server_wait", "anyseq_server_stat", "anyseq_server_destroy"]:
+                 "anyseq_server_wait", "anyseq_server_stat", "anyseq_server_destroy", "anyseq_plan_create",
+                 "anyseq_plan_buffers", "anyseq_plan_run", "anyseq_plan_wait", "anyseq_plan_destroy"]:
         getattr(lib, name).restype = ctypes.c_int
     _lib = lib
     return lib
@@ -319,6 +326,60 @@ class Server:
     def close(self):
         if getattr(self, "h", None):
             load().anyseq_server_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+class Plan:
+    """anyseq_plan: one batch shape of align_batch captured in a CUDA graph.
+
+    ``q``, ``s`` and ``out`` are torch uint8 views of the plan's device buffers
+    (letters in, 40-byte result records out); ``run`` replays the graph on the
+    current stream, ``wait`` synchronises and checks the letters."""
+
+    def __init__(self, q_off, s_off, scoring: Scoring, mode: int = GLOBAL, device: int = 0):
+        import torch
+        lib = load()
+        q_off = np.ascontiguousarray(q_off, dtype=np.int64)
+        s_off = np.ascontiguousarray(s_off, dtype=np.int64)
+        self._scoring = scoring
+        h = ctypes.c_void_p()
+        _check(lib.anyseq_plan_create(ctypes.byref(h), device, _ptr(q_off), _ptr(s_off), len(q_off) - 1,
+                                      ctypes.byref(scoring), mode))
+        self.h = h
+        self.n_pairs = len(q_off) - 1
+        pq, ps, po = ctypes.c_void_p(), ctypes.c_void_p(), ctypes.c_void_p()
+        _check(lib.anyseq_plan_buffers(h, ctypes.byref(pq), ctypes.byref(ps), ctypes.byref(po)))
+        dev = torch.device("cuda", device)
+
+        def view(ptr, nbytes):
+            # a torch view of plan-owned device memory (no copy, no ownership)
+            class _Arr:
+                __cuda_array_interface__ = {"shape": (nbytes,), "typestr": "|u1", "data": (ptr or 0, False),
+                                            "version": 3, "strides": None}
+            return torch.as_tensor(_Arr(), device=dev)
+
+        self.q = view(pq.value, int(q_off[-1]))
+        self.s = view(ps.value, int(s_off[-1]))
+        self.out = view(po.value, self.n_pairs * RESULT_DTYPE.itemsize)
+
+    def run(self, stream=None):
+        _check(load().anyseq_plan_run(self.h, _stream_handle(stream)))
+
+    def wait(self, stream=None):
+        _check(load().anyseq_plan_wait(self.h, _stream_handle(stream)))
+
+    def results(self):
+        return self.out.cpu().numpy().view(RESULT_DTYPE)
+
+    def close(self):
+        if getattr(self, "h", None):
+            load().anyseq_plan_destroy(self.h)
             self.h = None
 
     def __del__(self):

@@ -99,6 +99,16 @@ extern "C" anyseq_status_t anyseq_set_option(anyseq_ctx *ctx, const char *key, i
         ctx->base_cells = value;
         return ANYSEQ_OK;
     }
+    if (!strcmp(key, "band_max_doublings")) {
+        if (value < 0 || value > 16) return fail(ANYSEQ_ERR_ARG, "band_max_doublings must be in 0..16");
+        ctx->band_max_doublings = (int32_t)value;
+        return ANYSEQ_OK;
+    }
+    if (!strcmp(key, "band_area_pct")) {
+        if (value < 1 || value > 100) return fail(ANYSEQ_ERR_ARG, "band_area_pct must be in 1..100");
+        ctx->band_area_pct = (int32_t)value;
+        return ANYSEQ_OK;
+    }
     if (!strcmp(key, "spin_limit")) {
         if (value < 1) return fail(ANYSEQ_ERR_ARG, "spin_limit must be >= 1");
         ctx->spin_limit = value;
@@ -124,6 +134,9 @@ extern "C" anyseq_status_t anyseq_get_stat(anyseq_ctx *ctx, const char *key, dou
     else if (!strcmp(key, "band_accepted")) *value = (double)ctx->band_accepted;
     else if (!strcmp(key, "band_fallback")) *value = (double)ctx->band_fallback;
     else if (!strcmp(key, "band_rounds")) *value = (double)ctx->band_rounds;
+    else if (!strcmp(key, "band_plan_ms")) *value = ctx->band_plan_ms;
+    else if (!strcmp(key, "band_pass_ms")) *value = ctx->band_pass_ms;
+    else if (!strcmp(key, "band_full_ms")) *value = ctx->band_full_ms;
     else return fail(ANYSEQ_ERR_ARG, "unknown statistic '%s'", key);
     return ANYSEQ_OK;
 }
@@ -240,6 +253,12 @@ static int grid_for(int64_t work) {
     return (int)(b < 1 ? 1 : (b > 65535 ? 65535 : b));
 }
 
+cudaError_t anyseq::launch_write_results(int64_t n, const int32_t *score, const int32_t *eq, const int32_t *es,
+                                         const uint32_t *flags, anyseq_result_t *out, cudaStream_t st) {
+    write_results_kernel<<<grid_for(n), 256, 0, st>>>(n, score, eq, es, flags, nullptr, nullptr, nullptr, nullptr, out);
+    return cudaGetLastError();
+}
+
 // --------------------------------------------------------------- batch path
 
 anyseq_status_t anyseq::stage_input(anyseq_ctx *ctx, const char *name, const void *src, size_t bytes,
@@ -280,7 +299,7 @@ static T *arena(anyseq_ctx *ctx, const char *name, size_t count, anyseq_status_t
 
 anyseq_status_t anyseq::batch_scores(anyseq_ctx *ctx, const BatchInput &in, const anyseq_scoring_t *sc, int32_t mode,
                                      int32_t *score, int32_t *eq, int32_t *es, uint32_t *flags, cudaStream_t st,
-                                     TbOut *tb) {
+                                     TbOut *tb, bool capture) {
     anyseq_status_t s2 = ANYSEQ_OK;
     const int64_t n = in.n_pairs;
     const int sigp = (sc->alphabet > 4 || ctx->force_matrix) ? 1 : 0;
@@ -342,7 +361,8 @@ anyseq_status_t anyseq::batch_scores(anyseq_ctx *ctx, const BatchInput &in, cons
             for (int b = 0; b < sc->alphabet; b++) htab[a * sc->alphabet + b] = (int8_t)(sigma_host(sc, a, b) - oe);
         int8_t *dtab = arena<int8_t>(ctx, "sig_tab", 32 * 32, &s2);
         if (s2 != ANYSEQ_OK) return s2;
-        CUDA_TRY(cudaMemcpyAsync(dtab, htab, sc->alphabet * sc->alphabet, cudaMemcpyHostToDevice, st));
+        // a graph capture re-uses the table an uncaptured run of the same plan left in place
+        if (!capture) CUDA_TRY(cudaMemcpyAsync(dtab, htab, sc->alphabet * sc->alphabet, cudaMemcpyHostToDevice, st));
         A.sig_tab = dtab;
     }
     A.o = sc->gap_open; A.e = sc->gap_extend;
@@ -388,10 +408,15 @@ anyseq_status_t anyseq::batch_scores(anyseq_ctx *ctx, const BatchInput &in, cons
             if (s2 != ANYSEQ_OK) return s2;
         }
         CUDA_TRY(cudaMemsetAsync(A.counter, 0, sizeof(int32_t), st));
-        if (ctx->profile) cudaEventRecord(ctx->ev[2 * cell32], st);
+        if (ctx->profile && !capture) cudaEventRecord(ctx->ev[2 * cell32], st);
         CUDA_TRY(launch_batch(A, cell32, mode, tb != nullptr, sigp, grid, st));
-        if (ctx->profile) cudaEventRecord(ctx->ev[2 * cell32 + 1], st);
+        if (ctx->profile && !capture) cudaEventRecord(ctx->ev[2 * cell32 + 1], st);
         ctx->launches += 1;
+    }
+    // a graph capture ends here: the caller reads the letter check after the replay
+    if (capture) {
+        ctx->bad_code = P.bad_code;
+        return ANYSEQ_OK;
     }
     // letter check (read after the kernels; an invalid code only affects its own scores)
     int32_t bad = 0;

@@ -27,12 +27,16 @@ struct anyseq_ctx {
     float *mlp = nullptr;
     bool mlp_ready = false;
     int64_t band_cells = 0, band_accepted = 0, band_fallback = 0, band_rounds = 0;
+    double band_plan_ms = 0, band_pass_ms = 0, band_full_ms = 0;  // phases of the last banded call
+    int32_t band_max_doublings = 1;  // doublings after the predicted width before the full DP
+    int32_t band_area_pct = 35;      // a band above this share of the matrix goes to the full DP
     int profile = 0;              // time the DP kernels with events
     cudaEvent_t ev[4] = {nullptr, nullptr, nullptr, nullptr};
     // statistics of the last call
     int64_t launches = 0;
     double dp_ms = 0, dp32_ms = 0;
     int64_t pairs16 = 0, pairs32 = 0;
+    int32_t *bad_code = nullptr;  // letter-check flag of the last captured batch (graph plans)
     std::vector<Buf> bufs;        // device scratch, grown on demand, reused across calls
     std::vector<Buf> pinned;      // pinned host staging
     // Named device buffer of at least 'bytes'; contents are not preserved on growth.
@@ -48,6 +52,9 @@ struct BatchInput {
     const uint8_t *select = nullptr;                   // optional subset of pairs (device)
 };
 
+// 40-byte result records from the per-pair score and optimum-cell arrays (no CIGAR)
+cudaError_t launch_write_results(int64_t n, const int32_t *score, const int32_t *eq, const int32_t *es,
+                                 const uint32_t *flags, anyseq_result_t *out, cudaStream_t st);
 anyseq_status_t fail(anyseq_status_t st, const char *fmt, ...);
 bool is_device_ptr(const void *p);
 anyseq_status_t check_scoring(const anyseq_scoring_t *sc, int32_t mode);
@@ -83,6 +90,6 @@ anyseq_status_t hirschberg_cigar(anyseq_ctx *ctx, const uint32_t *q2, int32_t n,
 // Scores and optimum cells of a batch; with tb != null also the direction words.
 anyseq_status_t batch_scores(anyseq_ctx *ctx, const BatchInput &in, const anyseq_scoring_t *sc, int32_t mode,
                              int32_t *score, int32_t *eq, int32_t *es, uint32_t *flags, cudaStream_t st,
-                             TbOut *tb = nullptr);
+                             TbOut *tb = nullptr, bool capture = false);
 
 }  // namespace anyseq

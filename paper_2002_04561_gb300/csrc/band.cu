@@ -226,6 +226,7 @@ __global__ void __launch_bounds__(256, 2) band_kernel(BandArgs A) {
         const int32_t pad = nch * BCH - n;
         int64_t best_exit = INT64_MIN / 4;  // X, per lane
         int32_t score = 0;
+        int64_t cells = 0;                  // relaxed cells of this pair (lane 0)
         int32_t pa = 0, pb = 0;  // previous chunk's computed columns (c in [pa, pb))
         for (int ch = 0; ch < nch; ch++) {
             const bool last = ch == nch - 1;
@@ -244,6 +245,7 @@ __global__ void __launch_bounds__(256, 2) band_kernel(BandArgs A) {
             if (!have) { a = 0; b = 0; }
             const int32_t W = b - a;
             const int32_t Wmax = max(W, __shfl_xor_sync(0xffffffffu, W, 16));
+            cells += (int64_t)W * BCH;
             const int S = Wmax + GROUP - 1;
             uint32_t prof[BR];
             T Hoe[BR], F[BR];
@@ -409,6 +411,7 @@ __global__ void __launch_bounds__(256, 2) band_kernel(BandArgs A) {
             score |= __shfl_xor_sync(0xffffffffu, score, off, GROUP);
         }
         if (g == 0 && have) {
+            if (A.cells) atomicAdd(A.cells, (unsigned long long)cells);
             A.score[p] = score;
             const bool ok = A.strict ? (int64_t)score > best_exit : (int64_t)score >= best_exit;
             A.accept[p] = ok ? 1 : 0;

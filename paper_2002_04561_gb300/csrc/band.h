@@ -22,6 +22,7 @@ struct BandArgs {
     int64_t scratch_cols;
     int32_t *score;                 // per pair
     int32_t *accept;                // per pair: 1 if the certificate holds
+    unsigned long long *cells;      // device: cells relaxed by the pass (optional)
 };
 
 cudaError_t launch_band(const BandArgs &A, int grid, cudaStream_t st);

@@ -1,6 +1,7 @@
 // Learned band: C ABI entry points, training driver and the banded route of
 // anyseq_align_batch (features -> network -> banded DP with certificate ->
 // doubling -> full DP). See band.cu for the band and the certificate.
+#include <chrono>
 #include <cmath>
 #include <cstdio>
 #include <cstring>
@@ -100,7 +101,8 @@ static anyseq_status_t set_params(anyseq_ctx *ctx, const float *h, cudaStream_t 
 // Band proposal from the network output; pairs whose band would cover half of
 // the matrix (or with an empty sequence) go straight to the full DP.
 __global__ void band_plan_kernel(const float *y, const int64_t *q_off, const int64_t *s_off, int64_t n_pairs,
-                                 int32_t *centre, int32_t *width, uint8_t *full, int32_t *list, int64_t *count) {
+                                 double max_area, int32_t *centre, int32_t *width, uint8_t *full, int32_t *list,
+                                 int64_t *count) {
     for (int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; p < n_pairs;
          p += (int64_t)gridDim.x * blockDim.x) {
         const int64_t n = q_off[p + 1] - q_off[p], m = s_off[p + 1] - s_off[p];
@@ -113,7 +115,7 @@ __global__ void band_plan_kernel(const float *y, const int64_t *q_off, const int
         c = fminf(fmaxf(c, -(float)w), (float)w);
         centre[p] = (int32_t)rintf(c);
         width[p] = w;
-        const bool too_wide = band_area(n, w) > 0.5 * (double)n * (double)m;
+        const bool too_wide = band_area(n, w) > max_area * (double)n * (double)m;
         if (n == 0 || m == 0 || too_wide) {
             full[p] = 1;
         } else {
@@ -128,8 +130,8 @@ __global__ void band_plan_kernel(const float *y, const int64_t *q_off, const int
 // their band or move to the full DP.
 __global__ void band_round_kernel(const int32_t *list, int64_t n_list, const int64_t *q_off, const int64_t *s_off,
                                   const int32_t *bscore, const int32_t *accept, int32_t *width, uint8_t *full,
-                                  int32_t *next, int64_t *next_count, int32_t round, int32_t *score, int32_t *eq,
-                                  int32_t *es, uint32_t *flags) {
+                                  int32_t *next, int64_t *next_count, int32_t round, int32_t last_round,
+                                  double max_area, int32_t *score, int32_t *eq, int32_t *es, uint32_t *flags) {
     for (int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; k < n_list;
          k += (int64_t)gridDim.x * blockDim.x) {
         const int32_t p = list[k];
@@ -142,7 +144,7 @@ __global__ void band_round_kernel(const int32_t *list, int64_t n_list, const int
         } else {
             const int32_t w = width[p] * 2;
             width[p] = w;
-            if (band_area(n, w) > 0.5 * (double)n * (double)m) {
+            if (last_round || band_area(n, w) > max_area * (double)n * (double)m) {
                 full[p] = 1;
             } else {
                 unsigned long long pos = atomicAdd(reinterpret_cast<unsigned long long *>(next_count), 1ull);
@@ -166,6 +168,11 @@ __global__ void band_targets_kernel(const int32_t *dmin, const int32_t *dmax, co
         target[2 * p + 1] = logf((float)wcert[p]);
         (void)centre;
     }
+}
+
+// host wall clock in ms (the banded route synchronises between its phases)
+static double now_ms() {
+    return std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now().time_since_epoch()).count();
 }
 
 static int grid_of(int64_t work) {
@@ -218,9 +225,16 @@ static anyseq_status_t banded_pass(anyseq_ctx *ctx, const BatchInput &in, const 
     if (s2st != ANYSEQ_OK) return s2st;
     A.score = bscore;
     A.accept = accept;
+    A.cells = reinterpret_cast<unsigned long long *>(arena_b<int64_t>(ctx, "b_cells", 2, &s2st));
+    if (s2st != ANYSEQ_OK) return s2st;
+    BCUDA(cudaMemsetAsync(A.cells, 0, sizeof(int64_t), st));
     BCUDA(cudaMemsetAsync(A.counter, 0, sizeof(int32_t), st));
     BCUDA(launch_band(A, grid, st));
     ctx->launches += 1;
+    int64_t hc = 0;
+    BCUDA(cudaMemcpyAsync(&hc, A.cells, sizeof(int64_t), cudaMemcpyDeviceToHost, st));
+    BCUDA(cudaStreamSynchronize(st));
+    ctx->band_cells += hc;
     return ANYSEQ_OK;
 }
 
@@ -231,6 +245,8 @@ anyseq_status_t anyseq::band_scores(anyseq_ctx *ctx, const BatchInput &in, const
     if (!ctx->mlp_ready) return fail(ANYSEQ_ERR_ARG, "ANYSEQ_BAND_LEARNED needs a band model (train, load or set one)");
     anyseq_status_t s2st = ANYSEQ_OK;
     const int64_t n = in.n_pairs;
+    BCUDA(cudaStreamSynchronize(st));
+    const double t_start = now_ms();
     uint32_t *q2, *s2;
     BTRY(pack_batch(ctx, in, sc->alphabet, &q2, &s2, st));
     float *feat = arena_b<float>(ctx, "b_feat", (size_t)n * MLP_IN + 1, &s2st);
@@ -247,12 +263,15 @@ anyseq_status_t anyseq::band_scores(anyseq_ctx *ctx, const BatchInput &in, const
     BCUDA(launch_kmer_hist(q2, s2, in.q_off, in.s_off, nullptr, n, feat, st));
     BCUDA(launch_mlp_forward(mlp_dev(ctx), feat, n, y, st));
     BCUDA(cudaMemsetAsync(cnt, 0, 2 * sizeof(int64_t), st));
-    band_plan_kernel<<<grid_of(n), 256, 0, st>>>(y, in.q_off, in.s_off, n, centre, width, full, listA, cnt);
+    const double max_area = ctx->band_area_pct / 100.0;
+    band_plan_kernel<<<grid_of(n), 256, 0, st>>>(y, in.q_off, in.s_off, n, max_area, centre, width, full, listA, cnt);
     BCUDA(cudaGetLastError());
     ctx->launches += 3;
     int64_t n_list = 0;
     BCUDA(cudaMemcpyAsync(&n_list, cnt, sizeof(int64_t), cudaMemcpyDeviceToHost, st));
     BCUDA(cudaStreamSynchronize(st));
+    const double t_plan = now_ms();
+    ctx->band_plan_ms = t_plan - t_start;
     ctx->band_cells = 0;
     ctx->band_rounds = 0;
     ctx->band_accepted = 0;
@@ -262,7 +281,9 @@ anyseq_status_t anyseq::band_scores(anyseq_ctx *ctx, const BatchInput &in, const
         BTRY(banded_pass(ctx, in, sc, q2, s2, listA, n_list, centre, width, false, bscore, accept, st));
         BCUDA(cudaMemsetAsync(cnt + 1, 0, sizeof(int64_t), st));
         band_round_kernel<<<grid_of(n_list), 256, 0, st>>>(listA, n_list, in.q_off, in.s_off, bscore, accept, width,
-                                                           full, listB, cnt + 1, round, score, eq, es, flags);
+                                                           full, listB, cnt + 1, round,
+                                                           round >= ctx->band_max_doublings ? 1 : 0, max_area, score,
+                                                           eq, es, flags);
         BCUDA(cudaGetLastError());
         ctx->launches += 1;
         int64_t next = 0;
@@ -273,6 +294,8 @@ anyseq_status_t anyseq::band_scores(anyseq_ctx *ctx, const BatchInput &in, const
         n_list = next;
         round++;
     }
+    const double t_bands = now_ms();
+    ctx->band_pass_ms = t_bands - t_plan;
     // everything not accepted: the full DP, restricted to the marked pairs
     BatchInput sub = in;
     sub.select = full;
@@ -287,6 +310,7 @@ anyseq_status_t anyseq::band_scores(anyseq_ctx *ctx, const BatchInput &in, const
     for (int64_t p = 0; p < n; p++) nf += hfull[p] != 0;
     ctx->band_fallback = nf;
     ctx->band_accepted = n - nf;
+    ctx->band_full_ms = now_ms() - t_bands;
     (void)n_first;
     return ANYSEQ_OK;
 }
