@@ -143,8 +143,6 @@ cudaError_t launch_path_extent(const int64_t *q_off, const int64_t *s_off, const
 
 // ----------------------------------------------------------------- banded DP
 
-constexpr int BR = 8;              // rows per lane
-constexpr int BCH = GROUP * BR;    // rows per chunk
 
 __device__ __forceinline__ int64_t floor_div(int64_t a, int64_t b) { return a >= 0 ? a / b : -((-a + b - 1) / b); }
 
@@ -184,38 +182,30 @@ __device__ __forceinline__ void chunk_cols(int64_t n, int64_t m, int32_t c, int3
     hi = (int32_t)h;
 }
 
-__device__ __forceinline__ int32_t ubound(int64_t n, int64_t m, int64_t i, int64_t j, int32_t mmax, int32_t e) {
-    int64_t di = n - i, dj = m - j;
-    int64_t mn = di < dj ? di : dj, df = di > dj ? di - dj : dj - di;
-    return (int32_t)(mmax * mn + e * df);
+// Bound of the certificate from cell (i, j) to (n, m). In 32-bit arithmetic:
+// pairs of the banded route run in 32-bit lanes (|values| < 2^28), and the
+// bound is at most Mmax * 2^21 < 2^28.
+__device__ __forceinline__ int32_t ubound(int32_t n, int32_t m, int32_t i, int32_t j, int32_t mmax, int32_t e) {
+    const int32_t di = n - i, dj = m - j;
+    const int32_t mn = di < dj ? di : dj, df = di > dj ? di - dj : dj - di;
+    return mmax * mn + e * df;
 }
 
-struct BandSmem {
+struct __align__(16) BandSmem {
     uint32_t sel[RING];
     int32_t top[2 * RING];
     int32_t bot[2 * RING];
 };
 
-// Two slots of 16 lanes per warp, one pair per slot (32-bit lanes, global).
-__global__ void __launch_bounds__(256, 2) band_kernel(BandArgs A) {
-    __shared__ BandSmem smem[16];
+// One pair per 16-lane slot (32-bit lanes, global mode), chunks of GROUP * BR
+// rows over the band's column window; both slots of a warp run the same BR.
+template <int BR>
+__device__ __noinline__ void band_slot(const BandArgs &A, BandSmem *sm, int32_t *scr, int g, bool have, int32_t p) {
     typedef CellI32 C;
     typedef int32_t T;
-    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, grp = lane >> 4, g = lane & 15;
-    BandSmem *sm = &smem[warp * 2 + grp];
+    constexpr int BCH = GROUP * BR;  // rows per chunk
     const int32_t o = A.o, e = A.e, oe = o + e;
     const uint32_t e_raw = C::raw(e), oe_raw = C::raw(oe), oe_c = C::cst(oe);
-    const int64_t gslot = ((int64_t)blockIdx.x * 8 + warp) * 2 + grp;
-    int32_t *scr = A.scratch + gslot * 2 * (int64_t)A.scratch_cols;
-    const int64_t n_items = (A.n_list + 1) / 2;
-    for (;;) {
-        int item = 0;
-        if (lane == 0) item = atomicAdd(A.counter, 1);
-        item = __shfl_sync(0xffffffffu, item, 0);
-        if (item >= n_items) break;
-        const int64_t li = (int64_t)item * 2 + grp;
-        const bool have = li < A.n_list;
-        const int32_t p = have ? A.list[li] : -1;
         const int64_t q0 = have ? A.q_off[p] : 0, s0 = have ? A.s_off[p] : 0;
         const int32_t n = have ? (int32_t)(A.q_off[p + 1] - q0) : 0;
         const int32_t m = have ? (int32_t)(A.s_off[p + 1] - s0) : 0;
@@ -224,7 +214,7 @@ __global__ void __launch_bounds__(256, 2) band_kernel(BandArgs A) {
         int32_t nmax = max(n, __shfl_xor_sync(0xffffffffu, n, 16));
         const int32_t nch = nmax > 0 ? (nmax + BCH - 1) / BCH : 1;
         const int32_t pad = nch * BCH - n;
-        int64_t best_exit = INT64_MIN / 4;  // X, per lane
+        int32_t best_exit = INT32_MIN / 2;  // X, per lane
         int32_t score = 0;
         int64_t cells = 0;                  // relaxed cells of this pair (lane 0)
         int32_t pa = 0, pb = 0;  // previous chunk's computed columns (c in [pa, pb))
@@ -266,20 +256,20 @@ __global__ void __launch_bounds__(256, 2) band_kernel(BandArgs A) {
                 const bool holds_row0 = pad == 0 ? ch == 0 : (ch * BCH < pad && (ch + 1) * BCH >= pad);
                 if (holds_row0 && hi < m) {
                     int64_t h0 = hi == 0 ? 0 : o + (int64_t)hi * e;
-                    int64_t v = o + (int64_t)(hi + 1) * e + ubound(n, m, 0, hi + 1, A.mmax, e);
+                    int32_t v = o + (hi + 1) * e + ubound(n, m, 0, hi + 1, A.mmax, e);
                     best_exit = max(best_exit, v);
                     // diagonal into (1, hi+1): inside only if row 1 opens the next chunk and keeps that column
                     const bool row1_next = (ch + 1) * BCH < pad + 1;
                     const bool inside = row1_next && !last && hi + 1 >= nlo && hi + 1 <= nhi;
-                    if (n >= 1 && !inside) best_exit = max(best_exit, h0 + A.mmax + (int64_t)ubound(n, m, 1, hi + 1, A.mmax, e));
+                    if (n >= 1 && !inside) best_exit = max(best_exit, (int32_t)h0 + A.mmax + ubound(n, m, 1, hi + 1, A.mmax, e));
                 }
                 int64_t ir = (int64_t)(ch + 1) * BCH - pad;  // last row of this chunk
                 if (!last && left_in && nlo >= 1 && ir >= 0 && ir < n) {
                     int64_t hd = col0(GLOBAL, (int32_t)(ir + 1), o, e, o);  // H(ir+1, 0) via column 0
-                    best_exit = max(best_exit, hd + (int64_t)ubound(n, m, ir + 1, 0, A.mmax, e));
+                    best_exit = max(best_exit, (int32_t)hd + ubound(n, m, (int32_t)ir + 1, 0, A.mmax, e));
                     if (nlo >= 2) {
                         int64_t hr = col0(GLOBAL, (int32_t)ir, o, e, o);
-                        best_exit = max(best_exit, hr + A.mmax + (int64_t)ubound(n, m, ir + 1, 1, A.mmax, e));
+                        best_exit = max(best_exit, (int32_t)hr + A.mmax + ubound(n, m, (int32_t)ir + 1, 1, A.mmax, e));
                     }
                 }
             }
@@ -291,11 +281,15 @@ __global__ void __launch_bounds__(256, 2) band_kernel(BandArgs A) {
                     if (cr < W) {
                         int c = a + cr;
                         sm->sel[cr & (RING - 1)] = C::selector(code2(A.s2, s0 + c), 0);
+                        int2 tv;
                         if (ch > 0) {
-                            bool in = c >= pa && c < pb;
-                            sm->top[2 * (cr & (RING - 1))] = in ? scr[2 * c] : C::NEG;
-                            sm->top[2 * (cr & (RING - 1)) + 1] = in ? scr[2 * c + 1] : C::NEG;
+                            const bool in = c >= pa && c < pb;
+                            tv = in ? make_int2(scr[2 * c], scr[2 * c + 1]) : make_int2(C::NEG, C::NEG);
+                        } else {
+                            // row 0: H(0, c+1); E below row 0 comes from H only
+                            tv.x = tv.y = o + (c + 1) * e + oe;
                         }
+                        reinterpret_cast<int2 *>(sm->top)[cr & (RING - 1)] = tv;
                     }
                 }
             };
@@ -305,7 +299,8 @@ __global__ void __launch_bounds__(256, 2) band_kernel(BandArgs A) {
                     int cr = blk * BLOCK + g + 16 * k;
                     if (blk >= 0 && cr < W) {
                         int c = a + cr;
-                        int32_t hv = sm->bot[2 * (cr & (RING - 1))], ev = sm->bot[2 * (cr & (RING - 1)) + 1];
+                        const int2 b2 = reinterpret_cast<const int2 *>(sm->bot)[cr & (RING - 1)];
+                        const int32_t hv = b2.x, ev = b2.y;
                         if (!last) {
                             scr[2 * c] = hv;
                             scr[2 * c + 1] = ev;
@@ -314,10 +309,10 @@ __global__ void __launch_bounds__(256, 2) band_kernel(BandArgs A) {
                             int64_t ir = (int64_t)(ch + 1) * BCH - pad;  // this chunk's last row
                             const int64_t j = c + 1;
                             if (j < nlo && ir >= 0 && ir < n) {
-                                int64_t v = (int64_t)ev + ubound(n, m, ir + 1, j, A.mmax, e);
+                                int32_t v = ev + ubound(n, m, (int32_t)ir + 1, (int32_t)j, A.mmax, e);
                                 best_exit = v > best_exit ? v : best_exit;
                                 if (j + 1 < nlo) {
-                                    int64_t v2 = (int64_t)(hv - oe) + A.mmax + ubound(n, m, ir + 1, j + 1, A.mmax, e);
+                                    int32_t v2 = (hv - oe) + A.mmax + ubound(n, m, (int32_t)ir + 1, (int32_t)j + 1, A.mmax, e);
                                     best_exit = v2 > best_exit ? v2 : best_exit;
                                 }
                             }
@@ -331,50 +326,45 @@ __global__ void __launch_bounds__(256, 2) band_kernel(BandArgs A) {
             fill(0);
             __syncwarp();
             int drained = 0;
+            // prev_up is diag0 until the first valid column
             T last_hoe = C::NEG, last_e = C::NEG, prev_up = diag0;
-            for (int s = 0; s < S; s++) {
-                if ((s & (BLOCK - 1)) == 0) {
-                    __syncwarp();
-                    int kb = s / BLOCK;
-                    fill(kb + 1);
-                    if (kb - 2 >= drained) { drain(kb - 2); drained = kb - 1; }
-                    __syncwarp();
-                }
+            for (int s0b = 0; s0b < S; s0b += BLOCK) {
+              __syncwarp();
+              {
+                const int kb = s0b / BLOCK;
+                fill(kb + 1);
+                if (kb - 2 >= drained) { drain(kb - 2); drained = kb - 1; }
+              }
+              __syncwarp();
+              const int s1b = min(S, s0b + BLOCK);
+              for (int s = s0b; s < s1b; s++) {
                 const int cr = s - g;
-                const int c = a + cr;
                 T up_hoe = (T)__shfl_up_sync(0xffffffffu, (uint32_t)last_hoe, 1, GROUP);
                 T up_e = (T)__shfl_up_sync(0xffffffffu, (uint32_t)last_e, 1, GROUP);
                 if (g == 0) {
-                    if (ch == 0) {
-                        up_hoe = o + (c + 1) * e + oe;
-                        up_e = up_hoe;
-                    } else if (cr >= 0 && cr < W) {
-                        up_hoe = sm->top[2 * (cr & (RING - 1))];
-                        up_e = sm->top[2 * (cr & (RING - 1)) + 1];
-                    }
+                    // the row above the chunk (row 0 for the first); the ring index is masked
+                    const int2 tv = reinterpret_cast<const int2 *>(sm->top)[cr & (RING - 1)];
+                    up_hoe = tv.x;
+                    up_e = tv.y;
                 }
-                if (cr >= 0 && cr < W) {
+                if ((unsigned)cr < (unsigned)W) {
                     const uint32_t sel = sm->sel[cr & (RING - 1)];
-                    T diag = (cr == 0) ? diag0 : prev_up;
+                    T Ad = C::addc(prev_up, (uint32_t)C::sigma(prof[0], prof[0], sel));
                     prev_up = up_hoe;
                     T E = up_e;
 #pragma unroll
                     for (int r = 0; r < BR; r++) {
-                        T sg = C::sigma(prof[r], prof[r], sel);
-                        T Ad = C::addc(diag, (uint32_t)sg);
                         F[r] = C::addmax(F[r], e_raw, Hoe[r]);
-                        T M = C::vmax(Ad, F[r]);
-                        T X = C::addc(M, oe_c);
-                        diag = Hoe[r];
+                        const T M = C::vmax(Ad, F[r]);
+                        const T X = C::addc(M, oe_c);
+                        if (r + 1 < BR) Ad = C::addc(Hoe[r], (uint32_t)C::sigma(prof[r + 1], prof[r + 1], sel));
                         Hoe[r] = C::addmax(E, oe_raw, X);
                         E = C::addmax(E, e_raw, X);
                     }
                     last_hoe = Hoe[BR - 1];
                     last_e = E;
-                    if (g == GROUP - 1) {
-                        sm->bot[2 * (cr & (RING - 1))] = last_hoe;
-                        sm->bot[2 * (cr & (RING - 1)) + 1] = last_e;
-                    }
+                    if (g == GROUP - 1)
+                        reinterpret_cast<int2 *>(sm->bot)[cr & (RING - 1)] = make_int2(last_hoe, last_e);
                     // right exits from DP column hi = b (the chunk's last computed column)
                     if (cr == W - 1 && b < m) {
 #pragma unroll
@@ -383,19 +373,20 @@ __global__ void __launch_bounds__(256, 2) band_kernel(BandArgs A) {
                             if (i >= 1) {
                                 int32_t H = Hoe[r] - oe;
                                 int32_t Fn = max(F[r] + e, Hoe[r]);  // F(i, hi + 1)
-                                int64_t v = (int64_t)Fn + ubound(n, m, i, b + 1, A.mmax, e);
+                                int32_t v = Fn + ubound(n, m, (int32_t)i, b + 1, A.mmax, e);
                                 best_exit = v > best_exit ? v : best_exit;
                                 // diagonal to (i+1, hi+1): outside unless row i+1 opens the next chunk
                                 bool next_row_in_next = (r == BR - 1 && g == GROUP - 1);
                                 bool inside = next_row_in_next && !last && b + 1 >= nlo && b + 1 <= nhi;
                                 if (i + 1 <= n && !inside) {
-                                    int64_t v2 = (int64_t)H + A.mmax + ubound(n, m, i + 1, b + 1, A.mmax, e);
+                                    int32_t v2 = H + A.mmax + ubound(n, m, (int32_t)i + 1, b + 1, A.mmax, e);
                                     best_exit = v2 > best_exit ? v2 : best_exit;
                                 }
                             }
                         }
                     }
                 }
+              }
             }
             __syncwarp();
             for (int bk = drained; bk <= (Wmax - 1) / BLOCK; bk++) drain(bk);
@@ -406,16 +397,42 @@ __global__ void __launch_bounds__(256, 2) band_kernel(BandArgs A) {
         // reduce over the 16 lanes
 #pragma unroll
         for (int off = 8; off >= 1; off >>= 1) {
-            int64_t ox = __shfl_xor_sync(0xffffffffu, best_exit, off, GROUP);
+            int32_t ox = __shfl_xor_sync(0xffffffffu, best_exit, off, GROUP);
             best_exit = ox > best_exit ? ox : best_exit;
             score |= __shfl_xor_sync(0xffffffffu, score, off, GROUP);
         }
         if (g == 0 && have) {
             if (A.cells) atomicAdd(A.cells, (unsigned long long)cells);
             A.score[p] = score;
-            const bool ok = A.strict ? (int64_t)score > best_exit : (int64_t)score >= best_exit;
+            const bool ok = A.strict ? score > best_exit : score >= best_exit;
             A.accept[p] = ok ? 1 : 0;
         }
+}
+
+// Two slots of 16 lanes per warp, one pair per slot. Rows per lane follow the
+// warp's wider band: a chunk's column window spans the band plus the band's
+// drift over the chunk's rows, so tall chunks suit wide bands and short chunks
+// narrow ones.
+__global__ void __launch_bounds__(256, 2) band_kernel(BandArgs A) {
+    __shared__ BandSmem smem[16];
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, grp = lane >> 4, g = lane & 15;
+    BandSmem *sm = &smem[warp * 2 + grp];
+    const int64_t gslot = ((int64_t)blockIdx.x * 8 + warp) * 2 + grp;
+    int32_t *scr = A.scratch + gslot * 2 * (int64_t)A.scratch_cols;
+    const int64_t n_items = (A.n_list + 1) / 2;
+    for (;;) {
+        int item = 0;
+        if (lane == 0) item = atomicAdd(A.counter, 1);
+        item = __shfl_sync(0xffffffffu, item, 0);
+        if (item >= n_items) break;
+        const int64_t li = (int64_t)item * 2 + grp;
+        const bool have = li < A.n_list;
+        const int32_t p = have ? A.list[li] : -1;
+        int32_t bw = have ? A.width[p] : 0;
+        bw = max(bw, __shfl_xor_sync(0xffffffffu, bw, 16));
+        if (bw >= 192) band_slot<12>(A, sm, scr, g, have, p);
+        else if (bw >= 96) band_slot<8>(A, sm, scr, g, have, p);
+        else band_slot<4>(A, sm, scr, g, have, p);
     }
 }
 
