@@ -182,10 +182,12 @@ anyseq_status_t anyseq_band_train(anyseq_ctx *ctx, const uint8_t *q, const int64
  * "hirschberg_base_cells" (default 65536) is the subproblem size below which the
  * divide-and-conquer traceback switches to a full matrix; "spin_limit" (default
  * 2^24) bounds every device-side wait of the wavefront (ANYSEQ_ERR_TIMEOUT);
- * "band_max_doublings" (default 1) is how often ANYSEQ_BAND_LEARNED doubles a
+ * "band_max_doublings" (default 0) is how often ANYSEQ_BAND_LEARNED doubles a
  * band that fails its certificate before the full DP; "band_area_pct" (default
- * 35) sends a pair whose band would exceed that share of its matrix to the full
- * DP. Unknown keys: ANYSEQ_ERR_ARG. */
+ * 60) sends a pair whose band would exceed that share of its matrix to the full
+ * DP, "band_area16_pct" (default 15) the same for pairs that pass the int16
+ * range test (the full DP runs those two per 32-bit lane). Unknown keys:
+ * ANYSEQ_ERR_ARG. */
 anyseq_status_t anyseq_set_option(anyseq_ctx *ctx, const char *key, int64_t value);
 
 /* Statistics of the context's last call (host values, valid after the call's

@@ -109,6 +109,11 @@ extern "C" anyseq_status_t anyseq_set_option(anyseq_ctx *ctx, const char *key, i
         ctx->band_area_pct = (int32_t)value;
         return ANYSEQ_OK;
     }
+    if (!strcmp(key, "band_area16_pct")) {
+        if (value < 1 || value > 100) return fail(ANYSEQ_ERR_ARG, "band_area16_pct must be in 1..100");
+        ctx->band_area16_pct = (int32_t)value;
+        return ANYSEQ_OK;
+    }
     if (!strcmp(key, "spin_limit")) {
         if (value < 1) return fail(ANYSEQ_ERR_ARG, "spin_limit must be >= 1");
         ctx->spin_limit = value;

@@ -28,8 +28,9 @@ struct anyseq_ctx {
     bool mlp_ready = false;
     int64_t band_cells = 0, band_accepted = 0, band_fallback = 0, band_rounds = 0;
     double band_plan_ms = 0, band_pass_ms = 0, band_full_ms = 0;  // phases of the last banded call
-    int32_t band_max_doublings = 1;  // doublings after the predicted width before the full DP
-    int32_t band_area_pct = 35;      // a band above this share of the matrix goes to the full DP
+    int32_t band_max_doublings = 0;  // doublings after the predicted width before the full DP
+    int32_t band_area_pct = 60;      // a band above this share of the matrix goes to the full DP
+    int32_t band_area16_pct = 15;    // the same for pairs the full DP runs in int16x2 lanes
     int profile = 0;              // time the DP kernels with events
     cudaEvent_t ev[4] = {nullptr, nullptr, nullptr, nullptr};
     // statistics of the last call

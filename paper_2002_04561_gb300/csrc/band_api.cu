@@ -1,6 +1,7 @@
 // Learned band: C ABI entry points, training driver and the banded route of
 // anyseq_align_batch (features -> network -> banded DP with certificate ->
 // doubling -> full DP). See band.cu for the band and the certificate.
+#include <algorithm>
 #include <chrono>
 #include <cmath>
 #include <cstdio>
@@ -100,8 +101,19 @@ static anyseq_status_t set_params(anyseq_ctx *ctx, const float *h, cudaStream_t 
 
 // Band proposal from the network output; pairs whose band would cover half of
 // the matrix (or with an empty sequence) go straight to the full DP.
+// Largest band (share of the pair's matrix) worth a banded pass: the full DP
+// runs pairs that pass the int16 range test two per 32-bit lane, the banded
+// kernel always one, so their bands must be narrower to pay off.
+struct BandCaps {
+    double area32, area16;
+    int32_t smax, smin, o, e;
+};
+__device__ __forceinline__ double band_cap(const BandCaps &K, int64_t n, int64_t m) {
+    return fits_int16(n, m, K.smax, K.smin, K.o, K.e, GLOBAL) ? K.area16 : K.area32;
+}
+
 __global__ void band_plan_kernel(const float *y, const int64_t *q_off, const int64_t *s_off, int64_t n_pairs,
-                                 double max_area, int32_t *centre, int32_t *width, uint8_t *full, int32_t *list,
+                                 BandCaps caps, int32_t *centre, int32_t *width, uint8_t *full, int32_t *list,
                                  int64_t *count) {
     for (int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; p < n_pairs;
          p += (int64_t)gridDim.x * blockDim.x) {
@@ -115,7 +127,7 @@ __global__ void band_plan_kernel(const float *y, const int64_t *q_off, const int
         c = fminf(fmaxf(c, -(float)w), (float)w);
         centre[p] = (int32_t)rintf(c);
         width[p] = w;
-        const bool too_wide = band_area(n, w) > max_area * (double)n * (double)m;
+        const bool too_wide = band_area(n, w) > band_cap(caps, n, m) * (double)n * (double)m;
         if (n == 0 || m == 0 || too_wide) {
             full[p] = 1;
         } else {
@@ -131,7 +143,7 @@ __global__ void band_plan_kernel(const float *y, const int64_t *q_off, const int
 __global__ void band_round_kernel(const int32_t *list, int64_t n_list, const int64_t *q_off, const int64_t *s_off,
                                   const int32_t *bscore, const int32_t *accept, int32_t *width, uint8_t *full,
                                   int32_t *next, int64_t *next_count, int32_t round, int32_t last_round,
-                                  double max_area, int32_t *score, int32_t *eq, int32_t *es, uint32_t *flags) {
+                                  BandCaps caps, int32_t *score, int32_t *eq, int32_t *es, uint32_t *flags) {
     for (int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; k < n_list;
          k += (int64_t)gridDim.x * blockDim.x) {
         const int32_t p = list[k];
@@ -144,7 +156,7 @@ __global__ void band_round_kernel(const int32_t *list, int64_t n_list, const int
         } else {
             const int32_t w = width[p] * 2;
             width[p] = w;
-            if (last_round || band_area(n, w) > max_area * (double)n * (double)m) {
+            if (last_round || band_area(n, w) > band_cap(caps, n, m) * (double)n * (double)m) {
                 full[p] = 1;
             } else {
                 unsigned long long pos = atomicAdd(reinterpret_cast<unsigned long long *>(next_count), 1ull);
@@ -197,6 +209,25 @@ static anyseq_status_t pack_batch(anyseq_ctx *ctx, const BatchInput &in, int32_t
     BCUDA(cudaMemcpyAsync(&hb, bad, sizeof(int32_t), cudaMemcpyDeviceToHost, st));
     BCUDA(cudaStreamSynchronize(st));
     if (hb) return fail(ANYSEQ_ERR_ALPHABET, "a letter code is >= alphabet (%d)", alphabet);
+    return ANYSEQ_OK;
+}
+
+// Order a pass's pairs longest first (query, then subject length): the two
+// slots of a warp share its chunk count and step count, so pairs of similar
+// size side by side keep both busy, as the length binning of the full DP does.
+static anyseq_status_t sort_by_length(const std::vector<int64_t> &hq, const std::vector<int64_t> &hs, int32_t *list,
+                                      int64_t n_list, cudaStream_t st) {
+    if (n_list < 2) return ANYSEQ_OK;
+    std::vector<int32_t> h((size_t)n_list);
+    BCUDA(cudaMemcpyAsync(h.data(), list, (size_t)n_list * sizeof(int32_t), cudaMemcpyDeviceToHost, st));
+    BCUDA(cudaStreamSynchronize(st));
+    std::stable_sort(h.begin(), h.end(), [&](int32_t a, int32_t b) {
+        const int64_t na = hq[a + 1] - hq[a], nb = hq[b + 1] - hq[b];
+        if (na != nb) return na > nb;
+        return hs[a + 1] - hs[a] > hs[b + 1] - hs[b];
+    });
+    BCUDA(cudaMemcpyAsync(list, h.data(), (size_t)n_list * sizeof(int32_t), cudaMemcpyHostToDevice, st));
+    BCUDA(cudaStreamSynchronize(st));
     return ANYSEQ_OK;
 }
 
@@ -263,8 +294,20 @@ anyseq_status_t anyseq::band_scores(anyseq_ctx *ctx, const BatchInput &in, const
     BCUDA(launch_kmer_hist(q2, s2, in.q_off, in.s_off, nullptr, n, feat, st));
     BCUDA(launch_mlp_forward(mlp_dev(ctx), feat, n, y, st));
     BCUDA(cudaMemsetAsync(cnt, 0, 2 * sizeof(int64_t), st));
-    const double max_area = ctx->band_area_pct / 100.0;
-    band_plan_kernel<<<grid_of(n), 256, 0, st>>>(y, in.q_off, in.s_off, n, max_area, centre, width, full, listA, cnt);
+    BandCaps caps;
+    caps.area32 = ctx->band_area_pct / 100.0;
+    caps.area16 = ctx->band_area16_pct / 100.0;
+    caps.smax = -(1 << 30);
+    caps.smin = 1 << 30;
+    for (int a = 0; a < sc->alphabet; a++)
+        for (int b = 0; b < sc->alphabet; b++) {
+            caps.smax = std::max(caps.smax, sigma_host(sc, a, b));
+            caps.smin = std::min(caps.smin, sigma_host(sc, a, b));
+        }
+    caps.o = sc->gap_open;
+    caps.e = sc->gap_extend;
+    if (ctx->force32) caps.area16 = caps.area32;
+    band_plan_kernel<<<grid_of(n), 256, 0, st>>>(y, in.q_off, in.s_off, n, caps, centre, width, full, listA, cnt);
     BCUDA(cudaGetLastError());
     ctx->launches += 3;
     int64_t n_list = 0;
@@ -277,12 +320,17 @@ anyseq_status_t anyseq::band_scores(anyseq_ctx *ctx, const BatchInput &in, const
     ctx->band_accepted = 0;
     int32_t round = 0;
     const int64_t n_first = n_list;
+    std::vector<int64_t> hq((size_t)n + 1), hs((size_t)n + 1);
+    BCUDA(cudaMemcpyAsync(hq.data(), in.q_off, ((size_t)n + 1) * sizeof(int64_t), cudaMemcpyDeviceToHost, st));
+    BCUDA(cudaMemcpyAsync(hs.data(), in.s_off, ((size_t)n + 1) * sizeof(int64_t), cudaMemcpyDeviceToHost, st));
+    BCUDA(cudaStreamSynchronize(st));
     while (n_list > 0) {
+        BTRY(sort_by_length(hq, hs, listA, n_list, st));
         BTRY(banded_pass(ctx, in, sc, q2, s2, listA, n_list, centre, width, false, bscore, accept, st));
         BCUDA(cudaMemsetAsync(cnt + 1, 0, sizeof(int64_t), st));
         band_round_kernel<<<grid_of(n_list), 256, 0, st>>>(listA, n_list, in.q_off, in.s_off, bscore, accept, width,
                                                            full, listB, cnt + 1, round,
-                                                           round >= ctx->band_max_doublings ? 1 : 0, max_area, score,
+                                                           round >= ctx->band_max_doublings ? 1 : 0, caps, score,
                                                            eq, es, flags);
         BCUDA(cudaGetLastError());
         ctx->launches += 1;

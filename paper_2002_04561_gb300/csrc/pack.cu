@@ -51,22 +51,6 @@ __device__ __forceinline__ uint32_t lbucket(int64_t x) {
     return q > 255u ? 255u : q;
 }
 
-// Range test for exact int16 lanes: every H, E, F, Hoe and diagonal term of
-// the pair stays inside [-16000, 16000] (bounds from the recurrences: H is at
-// most max(sigma,0) * min(n,m); below, global H(i,j) is at least two gaps,
-// semi-global at least one, local at least 0; E/F add one more open+extend).
-__device__ __forceinline__ bool fits_int16(int64_t n, int64_t m, int32_t smax, int32_t smin, int32_t o, int32_t e,
-                                           int32_t mode) {
-    int64_t mn = n < m ? n : m;
-    int64_t hi = (int64_t)(smax > 0 ? smax : 0) * (mn + 1) + (smax > 0 ? smax : 0);
-    int64_t lo;
-    int64_t ox = o, ex = e, sm = smin < 0 ? smin : 0;
-    if (mode == GLOBAL) lo = 3 * ox + (n + m + 2) * ex + sm;
-    else if (mode == SEMIGLOBAL) lo = 2 * ox + (mn + 2) * ex + sm;
-    else lo = ox + 2 * ex + sm;
-    // local mode packs the optimum column of both halves into 16 bits each
-    return hi <= 16000 && lo >= -16000 && (mode != LOCAL || m < 65535);
-}
 
 __global__ void bin_kernel(PrepArgs P) {
     // grid-stride loop with a warp-uniform trip count (the shuffles below need the whole warp)
