@@ -364,6 +364,21 @@ def secondary_workloads(pkg, ctx, device):
     return out
 
 
+def profile_long(n: int):
+    """One global long pair of the long-pair generator's shape, scored twice by
+    the wavefront (a small case for ncu captures of the wavefront kernel)."""
+    import torch
+    pkg.load(build_if_missing=True)
+    ctx = pkg.Context(0)
+    b = synth.long_pair(n=n, inversion=max(1, n // 50))
+    q, s = torch.from_numpy(b.q).cuda(), torch.from_numpy(b.s).cuda()
+    sc = pkg.Scoring.make(2, -3, -5, -2)
+    for _ in range(2):
+        r, _ = ctx.align_long(q, s, sc)
+    torch.cuda.synchronize()
+    print(json.dumps({"profile_long": n, "cells": b.cells(), "score": int(r["score"][0])}))
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -373,8 +388,14 @@ def main():
     ap.add_argument("--pairs", type=int, default=262144, help="pairs per GPU (profiling runs use fewer)")
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--profile-long", type=int, default=0, metavar="N",
+                    help="profiling case: only the wavefront score of one N-letter long pair, twice")
     args = ap.parse_args()
     ws, rank, local = dist_env()
+
+    if args.profile_long:
+        profile_long(args.profile_long)
+        return
 
     if args.impl == "reference":
         run_reference(args, ws, rank)
