@@ -230,6 +230,18 @@ const char *anyseq_last_error(void);
 /* Library version string. */
 const char *anyseq_version(void);
 
+/* Gapped strings of one alignment (the output form of the paper's one-pair
+ * interface, Sec. III-C listing): from the letter codes q[0..n), s[0..m), the
+ * start cell (beg_q, beg_s) and cigar_len CIGAR words of a result, write the
+ * aligned letters to q_out and s_out (host buffers of cap characters),
+ * '-' against a gap, code c printed as letters[c] (e.g. "ACGT"), each string
+ * NUL-terminated; *len = columns. Host-only. Errors: ERR_ARG (a CIGAR op other
+ * than M/I/D or running past a sequence), ERR_ALPHABET, ERR_CAPACITY (*len set). */
+anyseq_status_t anyseq_gapped(const uint8_t *q, int64_t n, const uint8_t *s, int64_t m,
+                              int32_t beg_q, int32_t beg_s, const uint32_t *cigar, uint32_t cigar_len,
+                              const char *letters, int32_t alphabet, char *q_out, char *s_out,
+                              int64_t cap, int64_t *len);
+
 /* ------------------------------------------------------------------------
  * Graph plans (batching, not in the paper): one batch shape of
  * anyseq_align_batch (offsets, scoring, mode; score and optimum cell) whose

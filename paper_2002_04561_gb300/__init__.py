@@ -70,7 +70,7 @@ EXPORTS = ["anyseq_create", "anyseq_destroy", "anyseq_align_batch", "anyseq_alig
            "anyseq_band_gradient", "anyseq_band_train", "anyseq_align_long_noalloc",
            "anyseq_server_create", "anyseq_server_submit", "anyseq_server_wait", "anyseq_server_stat",
            "anyseq_server_destroy", "anyseq_plan_create", "anyseq_plan_buffers", "anyseq_plan_run",
-           "anyseq_plan_wait", "anyseq_plan_destroy"]
+           "anyseq_plan_wait", "anyseq_plan_destroy", "anyseq_gapped"]
 NOALLOC_MAX_LEN = 1048576
 BAND_FEATURES = 64
 BAND_PARAMS = 25090
@@ -121,6 +121,8 @@ def load(build_if_missing: bool = False):
     lib.anyseq_plan_run.argtypes = [P, P]
     lib.anyseq_plan_wait.argtypes = [P, P]
     lib.anyseq_plan_destroy.argtypes = [P]
+    lib.anyseq_gapped.argtypes = [P, I64, P, I64, I32, I32, P, U32, ctypes.c_char_p, I32, P, P, I64,
+                                  ctypes.POINTER(I64)]
     lib.anyseq_last_error.restype = ctypes.c_char_p
     lib.anyseq_last_error.argtypes = []
     lib.anyseq_version.restype = ctypes.c_char_p
@@ -130,7 +132,8 @@ def load(build_if_missing: bool = False):
                  "anyseq_band_model_load", "anyseq_band_forward", "anyseq_band_gradient", "anyseq_band_train",
                  "anyseq_align_long_noalloc", "anyseq_server_create", "anyseq_server_submit",
                  "anyseq_server_wait", "anyseq_server_stat", "anyseq_server_destroy", "anyseq_plan_create",
-                 "anyseq_plan_buffers", "anyseq_plan_run", "anyseq_plan_wait", "anyseq_plan_destroy"]:
+                 "anyseq_plan_buffers", "anyseq_plan_run", "anyseq_plan_wait", "anyseq_plan_destroy",
+                 "anyseq_gapped"]:
         getattr(lib, name).restype = ctypes.c_int
     _lib = lib
     return lib
@@ -277,6 +280,19 @@ def align_long_noalloc(q, s, scoring: Scoring, score, stream=None):
     m = s.numel() if hasattr(s, "numel") else len(s)
     _check(load().anyseq_align_long_noalloc(_ptr(q), n, _ptr(s), m, ctypes.byref(scoring), _ptr(score),
                                             _stream_handle(stream)))
+
+
+def gapped(q, s, beg_q: int, beg_s: int, cigar, letters: str = "ACGT"):
+    """anyseq_gapped: the two aligned strings ('-' against gaps) of one result."""
+    q = np.ascontiguousarray(q, dtype=np.uint8)
+    s = np.ascontiguousarray(s, dtype=np.uint8)
+    cigar = np.ascontiguousarray(cigar, dtype=np.uint32)
+    n = ctypes.c_int64(0)
+    cap = q.size + s.size + 1
+    qo, so = ctypes.create_string_buffer(cap), ctypes.create_string_buffer(cap)
+    _check(load().anyseq_gapped(_ptr(q), q.size, _ptr(s), s.size, beg_q, beg_s, _ptr(cigar), cigar.size,
+                                letters.encode(), len(letters), qo, so, cap, ctypes.byref(n)))
+    return qo.value.decode(), so.value.decode()
 
 
 def encode_dna(text: str) -> np.ndarray:

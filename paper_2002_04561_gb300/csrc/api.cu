@@ -508,10 +508,13 @@ extern "C" anyseq_status_t anyseq_align_batch(anyseq_ctx *ctx, const uint8_t *q,
     if (s2 != ANYSEQ_OK) return s2;
     const bool want_cigar = (want & ANYSEQ_WANT_CIGAR) != 0;
     TbOut tbo;
+    bool on_wave = false;
     if ((want & ANYSEQ_BAND_LEARNED) && !want_cigar && mode == ANYSEQ_GLOBAL && sc->alphabet <= 4) {
         TRY(band_scores(ctx, in, sc, score, eq, es, flags, st));
     } else {
-        TRY(batch_scores(ctx, in, sc, mode, score, eq, es, flags, st, want_cigar ? &tbo : nullptr));
+        if (mode == ANYSEQ_GLOBAL && !ctx->force32)
+            TRY(wave_batch(ctx, in, sc, score, eq, es, flags, st, want_cigar ? &tbo : nullptr, &on_wave));
+        if (!on_wave) TRY(batch_scores(ctx, in, sc, mode, score, eq, es, flags, st, want_cigar ? &tbo : nullptr));
     }
 
     int32_t *bq = nullptr, *bs = nullptr;
@@ -523,6 +526,8 @@ extern "C" anyseq_status_t anyseq_align_batch(anyseq_ctx *ctx, const uint8_t *q,
         W.n_pairs = n_pairs; W.mode = mode; W.q_off = in.q_off; W.s_off = in.s_off;
         W.end_q = eq; W.end_s = es;
         W.dirs = tbo.dirs; W.dir_base = tbo.dir_base; W.lay_pad = tbo.lay_pad; W.lay_ch0 = tbo.lay_ch0;
+        W.lanes_per_chunk = tbo.lanes_per_chunk;
+        W.rows_per_lane = tbo.rows_per_lane;
         W.tmp = arena<uint32_t>(ctx, "tb_tmp", (size_t)(in.q_len + in.s_len + n_pairs + 1), &s2);
         clen = W.cig_len = arena<int64_t>(ctx, "tb_clen", n_pairs + 1, &s2);
         coff = arena<int64_t>(ctx, "tb_coff", n_pairs + 1, &s2);
@@ -580,6 +585,107 @@ bool anyseq::long_range_ok(const anyseq_scoring_t *sc, int64_t n, int64_t m) {
         }
     const int64_t bound = 3 * (int64_t)(-sc->gap_open) + (n + m + 2) * (int64_t)(-sc->gap_extend) + smax * (n < m ? n : m + 1);
     return bound < (1ll << 28);
+}
+
+// A batch of a few large global pairs leaves most of the GPU idle in the
+// batched kernel (one 16-lane group per pair, its row chunks in sequence); the
+// wavefront runs each pair's stripes side by side instead. Qualifies: at most
+// WAVE_BATCH_PAIRS pairs, alphabet <= 4, every pair inside the wavefront's
+// 32-bit range, and the largest pair of at least WAVE_BATCH_CELLS cells.
+constexpr int64_t WAVE_BATCH_PAIRS = 8;
+constexpr double WAVE_BATCH_CELLS = 262144.0;
+
+anyseq_status_t anyseq::wave_batch(anyseq_ctx *ctx, const BatchInput &in, const anyseq_scoring_t *sc, int32_t *score,
+                                   int32_t *eq, int32_t *es, uint32_t *flags, cudaStream_t st, TbOut *tb,
+                                   bool *used) {
+    *used = false;
+    const int64_t n = in.n_pairs;
+    if (n > WAVE_BATCH_PAIRS || sc->alphabet > 4) return ANYSEQ_OK;
+    if ((double)in.max_n * (double)in.max_m < WAVE_BATCH_CELLS) return ANYSEQ_OK;
+    std::vector<int64_t> hq((size_t)n + 1), hs((size_t)n + 1);
+    CUDA_TRY(cudaMemcpyAsync(hq.data(), in.q_off, ((size_t)n + 1) * sizeof(int64_t), cudaMemcpyDeviceToHost, st));
+    CUDA_TRY(cudaMemcpyAsync(hs.data(), in.s_off, ((size_t)n + 1) * sizeof(int64_t), cudaMemcpyDeviceToHost, st));
+    CUDA_TRY(cudaStreamSynchronize(st));
+    for (int64_t p = 0; p < n; p++)
+        if (!long_range_ok(sc, hq[p + 1] - hq[p], hs[p + 1] - hs[p])) return ANYSEQ_OK;
+    *used = true;
+    anyseq_status_t s2 = ANYSEQ_OK;
+    uint32_t *q2 = arena<uint32_t>(ctx, "wb_q2", (size_t)(in.q_len + 15) / 16 + 2, &s2);
+    uint32_t *s2p = arena<uint32_t>(ctx, "wb_s2", (size_t)(in.s_len + 15) / 16 + 2, &s2);
+    int32_t *bad = arena<int32_t>(ctx, "wb_bad", 4, &s2);
+    if (s2 != ANYSEQ_OK) return s2;
+    CUDA_TRY(cudaMemsetAsync(bad, 0, sizeof(int32_t), st));
+    CUDA_TRY(launch_pack2bit(in.q, in.q_len, q2, sc->alphabet, bad, st));
+    CUDA_TRY(launch_pack2bit(in.s, in.s_len, s2p, sc->alphabet, bad, st));
+    ctx->launches += 2;
+    // one pass per non-empty pair; empty pairs take the closed forms of the recurrences
+    std::vector<WavePass> passes;
+    std::vector<int64_t> pass_of((size_t)n, -1);
+    int64_t out = 0;
+    for (int64_t p = 0; p < n; p++) {
+        const int64_t qn = hq[p + 1] - hq[p], sm = hs[p + 1] - hs[p];
+        if (qn == 0 || sm == 0) continue;
+        WavePass w;
+        memset(&w, 0, sizeof(w));
+        w.q0 = hq[p];
+        w.s0 = hs[p];
+        w.n = (int32_t)qn;
+        w.m = (int32_t)sm;
+        w.tb = sc->gap_open;
+        w.out_off = out;
+        out += sm + 1;
+        pass_of[(size_t)p] = (int64_t)passes.size();
+        passes.push_back(w);
+    }
+    std::vector<int32_t> hscore((size_t)n), heq((size_t)n), hes((size_t)n), hpad((size_t)n, 0), hch0((size_t)n, 0);
+    std::vector<uint32_t> hflags((size_t)n, ANYSEQ_FLAG_INT32);
+    std::vector<int64_t> hbase((size_t)n, 0);
+    WaveTb wtb;
+    if (!passes.empty()) {
+        int32_t *H = arena<int32_t>(ctx, "wb_H", (size_t)out + 2, &s2);
+        if (s2 != ANYSEQ_OK) return s2;
+        TRY(run_wave_passes(ctx, q2, s2p, passes, sc, H, nullptr, st, tb ? &wtb : nullptr));
+        for (int64_t p = 0; p < n; p++) {
+            const int64_t k = pass_of[(size_t)p];
+            if (k < 0) continue;
+            const WavePass &w = passes[(size_t)k];
+            CUDA_TRY(cudaMemcpyAsync(&hscore[(size_t)p], H + w.out_off + w.m, sizeof(int32_t), cudaMemcpyDeviceToHost, st));
+            hbase[(size_t)p] = w.dir_off;
+            const int32_t rows = WAVE_LANES * (tb ? wtb.rows_per_lane : 8);
+            hpad[(size_t)p] = ((w.n + rows - 1) / rows) * rows - w.n;
+        }
+    }
+    int32_t hb = 0;
+    CUDA_TRY(cudaMemcpyAsync(&hb, bad, sizeof(int32_t), cudaMemcpyDeviceToHost, st));
+    CUDA_TRY(cudaStreamSynchronize(st));
+    if (hb) return fail(ANYSEQ_ERR_ALPHABET, "a letter code is >= alphabet (%d)", sc->alphabet);
+    for (int64_t p = 0; p < n; p++) {
+        const int64_t qn = hq[p + 1] - hq[p], sm = hs[p + 1] - hs[p];
+        if (qn == 0 || sm == 0) hscore[(size_t)p] = (qn + sm == 0) ? 0 : sc->gap_open + (int32_t)(qn + sm) * sc->gap_extend;
+        heq[(size_t)p] = (int32_t)qn;
+        hes[(size_t)p] = (int32_t)sm;
+    }
+    CUDA_TRY(cudaMemcpyAsync(score, hscore.data(), (size_t)n * sizeof(int32_t), cudaMemcpyHostToDevice, st));
+    CUDA_TRY(cudaMemcpyAsync(eq, heq.data(), (size_t)n * sizeof(int32_t), cudaMemcpyHostToDevice, st));
+    CUDA_TRY(cudaMemcpyAsync(es, hes.data(), (size_t)n * sizeof(int32_t), cudaMemcpyHostToDevice, st));
+    CUDA_TRY(cudaMemcpyAsync(flags, hflags.data(), (size_t)n * sizeof(uint32_t), cudaMemcpyHostToDevice, st));
+    if (tb) {
+        tb->dirs = wtb.dirs;
+        tb->dir_base = arena<int64_t>(ctx, "wb_base", (size_t)n + 1, &s2);
+        tb->lay_pad = arena<int32_t>(ctx, "wb_pad", (size_t)n + 1, &s2);
+        tb->lay_ch0 = arena<int32_t>(ctx, "wb_ch0", (size_t)n + 1, &s2);
+        if (s2 != ANYSEQ_OK) return s2;
+        CUDA_TRY(cudaMemcpyAsync(tb->dir_base, hbase.data(), (size_t)n * sizeof(int64_t), cudaMemcpyHostToDevice, st));
+        CUDA_TRY(cudaMemcpyAsync(tb->lay_pad, hpad.data(), (size_t)n * sizeof(int32_t), cudaMemcpyHostToDevice, st));
+        CUDA_TRY(cudaMemcpyAsync(tb->lay_ch0, hch0.data(), (size_t)n * sizeof(int32_t), cudaMemcpyHostToDevice, st));
+        tb->lanes_per_chunk = WAVE_LANES;
+        tb->rows_per_lane = wtb.rows_per_lane;
+    }
+    // the host vectors must outlive the copies
+    CUDA_TRY(cudaStreamSynchronize(st));
+    ctx->pairs16 = 0;
+    ctx->pairs32 = n;
+    return ANYSEQ_OK;
 }
 
 // Global scores of several long pairs in one wavefront launch (one pass per

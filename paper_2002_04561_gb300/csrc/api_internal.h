@@ -69,8 +69,13 @@ struct TbOut {
     int64_t *dir_base = nullptr;
     int32_t *lay_pad = nullptr, *lay_ch0 = nullptr;
     int64_t dir_words = 0;
+    int32_t lanes_per_chunk = 16, rows_per_lane = 8;  // layout (batched kernel: 16 x TB_R)
 };
 
+// Small global batches on the wavefront: scores, end cells and (with tb) the
+// direction words of every pair; false in *used when the batch does not qualify.
+anyseq_status_t wave_batch(anyseq_ctx *ctx, const BatchInput &in, const anyseq_scoring_t *sc, int32_t *score,
+                           int32_t *eq, int32_t *es, uint32_t *flags, cudaStream_t st, TbOut *tb, bool *used);
 anyseq_status_t stage_batch(anyseq_ctx *ctx, const uint8_t *q, const int64_t *q_off, const uint8_t *s,
                             const int64_t *s_off, int64_t n_pairs, BatchInput &in, cudaStream_t st);
 anyseq_status_t band_scores(anyseq_ctx *ctx, const BatchInput &in, const anyseq_scoring_t *sc, int32_t *score,
@@ -82,9 +87,16 @@ anyseq_status_t long_scores(anyseq_ctx *ctx, const uint8_t *q, const int64_t *q_
 anyseq_status_t long_last_row(anyseq_ctx *ctx, const uint32_t *q2, int64_t q0, int32_t n, const uint32_t *s2,
                               int64_t s0, int32_t m, bool rev, int32_t tb, const anyseq_scoring_t *sc, int32_t *H,
                               int32_t *E, cudaStream_t st);
+// Traceback output of a wavefront launch: direction words in the layout of the
+// batched traceback with 32 lanes x rows_per_lane rows per chunk (see tb.h);
+// each pass's first word is its dir_off.
+struct WaveTb {
+    uint32_t *dirs = nullptr;
+    int32_t rows_per_lane = 0;
+};
 anyseq_status_t run_wave_passes(anyseq_ctx *ctx, const uint32_t *q2, const uint32_t *s2,
                                 std::vector<WavePass> &passes, const anyseq_scoring_t *sc, int32_t *H, int32_t *E,
-                                cudaStream_t st);
+                                cudaStream_t st, WaveTb *tb = nullptr);
 anyseq_status_t hirschberg_cigar(anyseq_ctx *ctx, const uint32_t *q2, int32_t n, const uint32_t *s2, int32_t m,
                                  const anyseq_scoring_t *sc, std::vector<uint32_t> &cigar, cudaStream_t st);
 

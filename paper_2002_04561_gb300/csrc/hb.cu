@@ -222,15 +222,22 @@ static T *arena_t(anyseq_ctx *ctx, const char *name, size_t count, anyseq_status
 
 anyseq_status_t run_wave_passes(anyseq_ctx *ctx, const uint32_t *q2, const uint32_t *s2,
                                 std::vector<WavePass> &passes, const anyseq_scoring_t *sc, int32_t *H, int32_t *E,
-                                cudaStream_t st) {
+                                cudaStream_t st, WaveTb *tb) {
     anyseq_status_t s2st = ANYSEQ_OK;
-    int64_t border = 0;
+    int64_t border = 0, rows = 0;
+    for (const auto &p : passes) rows += p.n;
+    const int wr = wave_rows_per_lane(rows, ctx->num_sms, (int64_t)passes.size());
+    const int stripe_rows = WAVE_LANES * wr;
     int32_t stripes = 0;
+    int64_t dir_words = 0;
     for (auto &p : passes) {
         p.border_off = border;
         border += 2 * (int64_t)p.m + 2;
         p.stripe0 = stripes;
-        stripes += (p.n + WAVE_ROWS - 1) / WAVE_ROWS;
+        const int32_t ns = (p.n + stripe_rows - 1) / stripe_rows;
+        stripes += ns;
+        p.dir_off = dir_words;
+        if (tb) dir_words += (int64_t)ns * (p.m + WAVE_LANES - 1) * WAVE_LANES * (wr / 8);
     }
     WaveArgs W;
     memset(&W, 0, sizeof(W));
@@ -252,9 +259,17 @@ anyseq_status_t run_wave_passes(anyseq_ctx *ctx, const uint32_t *q2, const uint3
     W.last_H = H;
     W.last_E = E;
     W.spin_limit = ctx->spin_limit;
+    W.rows_per_lane = wr;
+    W.dirs = nullptr;
+    if (tb) {
+        tb->rows_per_lane = wr;
+        tb->dirs = arena_t<uint32_t>(ctx, "w_dirs", (size_t)dir_words + 1, &s2st);
+        if (s2st != ANYSEQ_OK) return s2st;
+        W.dirs = tb->dirs;
+    }
     HB_CUDA(cudaMemcpyAsync(dpass, passes.data(), passes.size() * sizeof(WavePass), cudaMemcpyHostToDevice, st));
     HB_CUDA(cudaMemsetAsync(ctl, 0, ((size_t)stripes + 2) * sizeof(int32_t), st));
-    HB_CUDA(launch_wave(W, ctx->num_sms * wave_blocks_per_sm(), st));
+    HB_CUDA(launch_wave(W, ctx->num_sms, st));
     ctx->launches += 1;
     int32_t err = 0;
     HB_CUDA(cudaMemcpyAsync(&err, W.err, sizeof(int32_t), cudaMemcpyDeviceToHost, st));

@@ -24,7 +24,7 @@ namespace anyseq {
 
 constexpr int64_t NA_MAX = ANYSEQ_NOALLOC_MAX_LEN;
 constexpr int64_t NA_PACKED = NA_MAX / 16 + 4;                   // uint32 words per packed sequence
-constexpr int64_t NA_STRIPES = (NA_MAX + WAVE_ROWS - 1) / WAVE_ROWS;
+constexpr int64_t NA_STRIPES = (NA_MAX + WAVE_MIN_ROWS - 1) / WAVE_MIN_ROWS;  // the shortest stripes
 constexpr int64_t NA_CTL = NA_STRIPES + 8;                       // counter, error flag, progress counters
 // byte offsets inside the array (each 256-byte aligned)
 constexpr int64_t al(int64_t x) { return (x + 255) / 256 * 256; }
@@ -115,7 +115,11 @@ extern "C" anyseq_status_t anyseq_align_long_noalloc(const uint8_t *q, int64_t n
     ps.n = (int32_t)n;
     ps.m = (int32_t)m;
     ps.tb = sc->gap_open;
-    const int64_t stripes = (n + WAVE_ROWS - 1) / WAVE_ROWS;
+    int dev = 0, sms = 1;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    const int wr = wave_rows_per_lane(n, sms, 1);
+    const int64_t stripes = (n + WAVE_LANES * wr - 1) / (WAVE_LANES * wr);
     noalloc_init_kernel<<<8, 256, 0, st>>>(pass, ps, ctl, stripes + 2, bad);
     cudaError_t e = cudaGetLastError();
     if (e == cudaSuccess) e = launch_pack2bit(q, n, q2, sc->alphabet, bad, st);
@@ -138,10 +142,8 @@ extern "C" anyseq_status_t anyseq_align_long_noalloc(const uint8_t *q, int64_t n
     W.last_H = H;
     W.last_E = nullptr;
     W.spin_limit = 1ll << 24;
-    int dev = 0, sms = 1;
-    cudaGetDevice(&dev);
-    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-    if (e == cudaSuccess) e = launch_wave(W, sms * wave_blocks_per_sm(), st);
+    W.rows_per_lane = wr;
+    if (e == cudaSuccess) e = launch_wave(W, sms, st);
     if (e == cudaSuccess) {
         noalloc_finish_kernel<<<1, 1, 0, st>>>(H, (int32_t)m, score);
         e = cudaGetLastError();

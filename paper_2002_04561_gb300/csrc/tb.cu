@@ -87,7 +87,9 @@ __global__ void __launch_bounds__(TB_WARPS * 32) tb_walk_kernel(TbWalkArgs W) {
         } else {
             const uint32_t *dw = W.dirs + W.dir_base[p];
             const int32_t pad = W.lay_pad[p], ch0 = W.lay_ch0[p];
-            const int64_t S = m + GROUP - 1;
+            const int32_t lpc = W.lanes_per_chunk, wpl = W.rows_per_lane / 8;  // words per lane and step
+            const int32_t gpc = lpc * wpl;                                      // row groups of 8 per chunk
+            const int64_t S = m + lpc - 1;
             int state = 0;  // 0: H, 1: E, 2: F
             bool done = false;
             // every step moves up or left within two iterations; the bound and the
@@ -102,9 +104,9 @@ __global__ void __launch_bounds__(TB_WARPS * 32) tb_walk_kernel(TbWalkArgs W) {
                     const int32_t jj = j - lane;
                     if (jj >= j_lo) {
                         for (int32_t rg = rg_lo; rg <= rg_hi; rg++) {
-                            const int32_t ch = rg / GROUP, gl = rg % GROUP;
+                            const int32_t ch = rg / gpc, gl = (rg % gpc) / wpl, sub = rg % wpl;
                             const int64_t s = (int64_t)(jj - 1) + gl;
-                            wn[rg - rg_lo][lane] = dw[((int64_t)(ch - ch0) * S + s) * GROUP + gl];
+                            wn[rg - rg_lo][lane] = dw[(((int64_t)(ch - ch0) * S + s) * lpc + gl) * wpl + sub];
                         }
                     }
                 }

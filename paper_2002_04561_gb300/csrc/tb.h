@@ -16,6 +16,10 @@ struct TbWalkArgs {
     uint32_t *tmp;        // per pair n + m + 1 words at q_off[p] + s_off[p] + p
     int64_t *cig_len;
     int32_t *beg_q, *beg_s;
+    // layout of the direction words: chunks of lanes_per_chunk lanes x rows_per_lane
+    // rows (rows_per_lane a multiple of 8), steps = m + lanes_per_chunk - 1 per chunk,
+    // rows_per_lane / 8 words per lane and step (byte planes of 8 rows each)
+    int32_t lanes_per_chunk, rows_per_lane;
 };
 
 cudaError_t launch_tb_plan(const int32_t *list, const int64_t *n_list, int per_item, int64_t max_items,

@@ -22,9 +22,7 @@
 
 namespace anyseq {
 
-constexpr int WG = 32;   // lanes per stripe
-constexpr int WR = 16;   // rows per lane
-constexpr int WCH = WG * WR;
+constexpr int WG = WAVE_LANES;
 constexpr int WRING = 128;
 
 __device__ __forceinline__ uint32_t wletter(const uint32_t *packed, int64_t base, int32_t len, int32_t idx, bool rev) {
@@ -46,7 +44,12 @@ struct __align__(16) WaveSmem {
     int32_t bot[2 * WRING];
 };
 
-__global__ void __launch_bounds__(256, 2) wave_kernel(WaveArgs A) {
+// TB: also write the traceback direction words of every cell (the layout of the
+// batched traceback with 32 lanes x WR rows per chunk, see tb.h).
+template <int WR, bool TB>
+__global__ void __launch_bounds__(256, WR <= 8 ? 4 : 2) wave_kernel(WaveArgs A) {
+    constexpr int WCH = WG * WR;  // rows per stripe
+    static_assert(!TB || WR % 8 == 0, "direction words hold 8 rows");
     __shared__ WaveSmem smem[8];
     const int warp = threadIdx.x >> 5, g = threadIdx.x & 31;
     WaveSmem *sm = &smem[warp];
@@ -91,6 +94,8 @@ __global__ void __launch_bounds__(256, 2) wave_kernel(WaveArgs A) {
         int32_t *prog_prev = A.prog + ps.stripe0 + (k > 0 ? k - 1 : 0);
         int32_t *prog_mine = A.prog + t;
         bool failed = false;
+        // this stripe's direction words: [step][lane][WR / 8]
+        uint32_t *dw = TB ? A.dirs + ps.dir_off + (int64_t)k * S * WG * (WR / 8) + g * (WR / 8) : nullptr;
 
         // wait until the previous stripe published border block blk (bounded)
         auto wait_for = [&](int blk) {
@@ -172,15 +177,37 @@ __global__ void __launch_bounds__(256, 2) wave_kernel(WaveArgs A) {
                 T Ad = C::addc(prev_up, (uint32_t)C::sigma(prof[0], prof[0], sel));
                 prev_up = up_hoe;
                 T E = up_e, Ein = up_e;
+                T hup = up_hoe;  // Hoe of the row above, this column (traceback)
+                uint32_t pl_s0 = 0, pl_s1 = 0, pl_eo = 0, pl_fo = 0;
 #pragma unroll
                 for (int r = 0; r < WR; r++) {
                     F[r] = C::addmax(F[r], e_raw, Hoe[r]);
                     const T M = C::vmax(Ad, F[r]);
                     const T X = C::addc(M, oe_c);
+                    const T Adr = Ad;
                     if (r + 1 < WR) Ad = C::addc(Hoe[r], (uint32_t)C::sigma(prof[r + 1], prof[r + 1], sel));
+                    uint32_t fFo = 0;
+                    if (TB) fFo = C::ge(Hoe[r], F[r]);                 // F(i,j) opened from H(i,j-1)
                     Ein = E;
                     Hoe[r] = C::addmax(E, oe_raw, X);
                     E = C::addmax(E, e_raw, X);
+                    if (TB) {
+                        // the predecessor planes of the batched traceback (global mode)
+                        const uint32_t fD = C::ge(C::addc(Adr, oe_c), Hoe[r]);  // diagonal reaches H
+                        const uint32_t fE = C::ge(C::addc(Ein, oe_c), Hoe[r]);  // E reaches H
+                        const uint32_t fEo = C::ge(hup, Ein);                  // E(i,j) opened from H(i-1,j)
+                        const uint32_t FM = C::flag_mask();
+                        pl_s0 = (pl_s0 >> 1) | (fD & FM);
+                        pl_s1 = (pl_s1 >> 1) | (fE & FM);
+                        pl_eo = (pl_eo >> 1) | (fEo & FM);
+                        pl_fo = (pl_fo >> 1) | (fFo & FM);
+                        hup = Hoe[r];
+                        if ((r & 7) == 7) {
+                            // rows r-7..r: bytes s0, s1, E opened, F opened (bit k = row r-7+k)
+                            dw[(int64_t)s * WG * (WR / 8) + (r >> 3)] =
+                                prmt(prmt(pl_s0, pl_s1, 0x7351u), prmt(pl_eo, pl_fo, 0x7351u), 0x7632u);
+                        }
+                    }
                 }
                 last_hoe = Hoe[WR - 1];
                 last_e = E;
@@ -202,18 +229,34 @@ __global__ void __launch_bounds__(256, 2) wave_kernel(WaveArgs A) {
     }
 }
 
-cudaError_t launch_wave(const WaveArgs &A, int grid, cudaStream_t st) {
-    wave_kernel<<<grid, 256, 0, st>>>(A);
-    return cudaGetLastError();
-}
-
-int wave_blocks_per_sm() {
+template <int WR, bool TB>
+static int blocks_per_sm() {
     int nb = 0;
-    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, wave_kernel, 256, 0) != cudaSuccess) {
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, wave_kernel<WR, TB>, 256, 0) != cudaSuccess) {
         cudaGetLastError();
         nb = 1;
     }
     return nb < 1 ? 1 : nb;
+}
+
+int wave_rows_per_lane(int64_t total_rows, int num_sms, int64_t n_passes) {
+    // 16-row stripes that fill less than half of their resident warps leave the
+    // GPU idle; 8-row stripes double the stripes (and the pipeline's skew, which
+    // costs more than it gains once the 16-row stripes fill half the warps)
+    const int64_t stripes16 = total_rows / (WG * 16) + n_passes;  // upper bound of sum(ceil(n / 512))
+    return 2 * stripes16 <= (int64_t)num_sms * blocks_per_sm<16, false>() * 8 ? 8 : 16;
+}
+
+cudaError_t launch_wave(const WaveArgs &A, int num_sms, cudaStream_t st) {
+    const bool tb = A.dirs != nullptr;
+    if (A.rows_per_lane == 8) {
+        if (tb) wave_kernel<8, true><<<num_sms * blocks_per_sm<8, true>(), 256, 0, st>>>(A);
+        else wave_kernel<8, false><<<num_sms * blocks_per_sm<8, false>(), 256, 0, st>>>(A);
+    } else {
+        if (tb) wave_kernel<16, true><<<num_sms * blocks_per_sm<16, true>(), 256, 0, st>>>(A);
+        else wave_kernel<16, false><<<num_sms * blocks_per_sm<16, false>(), 256, 0, st>>>(A);
+    }
+    return cudaGetLastError();
 }
 
 }  // namespace anyseq

@@ -16,6 +16,7 @@ struct WavePass {
     int64_t border_off;
     int64_t out_off;
     int32_t stripe0, pad_;
+    int64_t dir_off;              // traceback: first direction word of the pass
 };
 
 struct WaveArgs {
@@ -30,10 +31,16 @@ struct WaveArgs {
     int32_t *err;                 // zeroed; 1 after a wait gave up
     int32_t *last_H, *last_E;     // optional outputs
     int64_t spin_limit;           // iterations of one wait
+    int32_t rows_per_lane;        // 8 or 16 (stripes of 32 lanes x rows_per_lane rows)
+    uint32_t *dirs;               // optional: traceback direction words (global mode)
 };
 
-cudaError_t launch_wave(const WaveArgs &A, int grid, cudaStream_t st);
-int wave_blocks_per_sm();
-constexpr int WAVE_ROWS = 512;    // rows per stripe
+// Rows per lane of a launch: 8 when 16-row stripes would fill less than half
+// of the resident warps (twice the stripes, half the per-step chain each),
+// otherwise 16. total_rows = sum of the passes' row counts.
+int wave_rows_per_lane(int64_t total_rows, int num_sms, int64_t n_passes);
+cudaError_t launch_wave(const WaveArgs &A, int num_sms, cudaStream_t st);
+constexpr int WAVE_LANES = 32;    // lanes per stripe
+constexpr int WAVE_MIN_ROWS = 256;  // rows of the shortest stripe (8 rows per lane)
 
 }  // namespace anyseq

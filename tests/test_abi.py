@@ -1,9 +1,11 @@
 """The C-ABI library builds for sm_103a, loads, and exports every function that
-include/anyseq.h declares (no compute call: this runs without a GPU)."""
+include/anyseq.h declares; its host-only calls work (no GPU call: this runs
+without a GPU)."""
 import ctypes
 import os
 import re
 
+import numpy as np
 import pytest
 
 ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
@@ -74,3 +76,36 @@ int main(void) {{
     assert sizes == [ctypes.sizeof(pkg.Scoring), pkg.RESULT_DTYPE.itemsize, ctypes.sizeof(pkg.ServerConfig)]
     assert offs == [pkg.Scoring.matrix.offset, pkg.RESULT_DTYPE.fields["cigar_off"][1],
                     pkg.ServerConfig.scoring.offset, pkg.ServerConfig.mem_budget_bytes.offset]
+
+
+def test_gapped_strings_from_oracle_cigars():
+    """anyseq_gapped (host only): the gapped strings of oracle CIGARs give back
+    the aligned substrings when the gaps are removed, and their columns score
+    to the alignment's score."""
+    import oracle
+    import synth
+    import paper_2002_04561_gb300 as pkg
+    pkg.load()
+    sc = oracle.Scoring(2, -3, -5, -2)
+    b = synth.random_pairs(40, 0, 60, seed=9500, related=0.7)
+    for mode in (0, 1, 2):
+        want, cigs = oracle.align_batch(b, sc, mode)
+        for p in range(b.n_pairs):
+            q, s = b.pair(p)
+            score, bq, bs, eq, es = (int(x) for x in want[p])
+            gq, gs = pkg.gapped(q, s, bq, bs, cigs[p])
+            assert gq.replace("-", "") == "".join("ACGT"[c] for c in q[bq:eq])
+            assert gs.replace("-", "") == "".join("ACGT"[c] for c in s[bs:es])
+            total, gap = 0, None
+            for a, c in zip(gq, gs):
+                if a != "-" and c != "-":
+                    total += 2 if a == c else -3
+                    gap = None
+                else:
+                    kind = "I" if c == "-" else "D"
+                    total += (-5 if gap != kind else 0) - 2
+                    gap = kind
+            assert total == score, (mode, p, gq, gs)
+    with pytest.raises(pkg.AnyseqError) as ei:
+        pkg.gapped(np.zeros(3, np.uint8), np.zeros(3, np.uint8), 0, 0, np.array([(5 << 4) | 0], np.uint32))
+    assert ei.value.status == 1

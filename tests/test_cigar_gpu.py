@@ -158,3 +158,23 @@ def test_protein_workload_cigar_sampled(pkg, ctx):
     idx = np.unique(st.integers(0, b.n_pairs - 1, 1500))
     sub = b.subset(idx)
     assert_cigar_parity(sub, res[idx], [cigars[int(p)] for p in idx], args, 1)
+
+
+@pytest.mark.parametrize("sc_args", [(2, -1, 0, -2), (2, -3, -5, -2), (1, -1, -2, -1)])
+def test_small_global_batches_on_the_wavefront(pkg, ctx, sc_args):
+    """A few large global pairs run on the wavefront (stripes side by side, its
+    own direction-word layout read by the same walk): score, cells and CIGAR
+    equal the oracle's full traceback, for the 1,000 x 1,100 pair, related and
+    unrelated pairs over several stripes, and a batch holding an empty pair."""
+    st = synth.Stream(9400, 1)
+    single = synth.single_pair()
+    related = []
+    for n, extra in ((700, 40), (1300, -25), (2600, 3)):
+        q = synth.random_codes(st, n, 4)
+        s, _ = synth.mutate(q, np.array([0, n], np.int64), 0.06, 0.02, 0.3, 4, st)
+        related.append((q, s[: max(1, len(s) + extra)]))
+    unrelated = (synth.random_codes(st, 900, 4), synth.random_codes(st, 1500, 4))
+    empty = (synth.random_codes(st, 600, 4), np.zeros(0, np.uint8))
+    for b in (single, synth.from_pairs(related), synth.from_pairs([unrelated, empty, related[0]])):
+        res, cigars, _ = gpu_align(pkg, ctx, b, sc_args, 0)
+        assert_cigar_parity(b, res, cigars, sc_args, 0)
