@@ -116,16 +116,51 @@ __global__ void __launch_bounds__(256, WR <= 8 ? 4 : 2) wave_kernel(WaveArgs A) 
             failed = !ok;
             __syncwarp();
         };
-        auto fill = [&](int blk) {
-            int c = blk * BLOCK + g;
+        // ring refill in two halves: fetch issues this lane's global loads of a block
+        // (packed subject word, border of the previous stripe) into registers, put
+        // writes them to the rings; in between, the warp computes, so the loads'
+        // latency overlaps half a block of cells
+        auto fetch = [&](int blk, uint32_t &fw, int32_t &fsh, int2 &ft) {
+            const int c = blk * BLOCK + g;
             if (c < m) {
-                sm->sel[c & (WRING - 1)] = C::selector(wletter(A.s2, ps.s0, m, c, rev), 0);
+                const int64_t pos = ps.s0 + (rev ? (int64_t)(m - 1 - c) : (int64_t)c);
+                fw = A.s2[pos >> 4];
+                fsh = 2 * (int32_t)(pos & 15);
                 if (k == 0) {
                     // row 0: H(0, c+1); E below row 0 comes from H only (E(0, .) = -inf)
                     const int32_t v = o + (c + 1) * e + oe;
-                    reinterpret_cast<int2 *>(sm->top)[c & (WRING - 1)] = make_int2(v, v);
+                    ft = make_int2(v, v);
                 } else if (!failed) {
-                    reinterpret_cast<int2 *>(sm->top)[c & (WRING - 1)] = bin[c];
+                    ft = bin[c];
+                }
+            }
+        };
+        auto put = [&](int blk, uint32_t fw, int32_t fsh, int2 ft) {
+            const int c = blk * BLOCK + g;
+            if (c < m) {
+                sm->sel[c & (WRING - 1)] = C::selector((fw >> fsh) & 3u, 0);
+                reinterpret_cast<int2 *>(sm->top)[c & (WRING - 1)] = ft;
+            }
+        };
+        auto fill = [&](int blk) {
+            uint32_t fw = 0;
+            int32_t fsh = 0;
+            int2 ft = make_int2(C::NEG, C::NEG);
+            fetch(blk, fw, fsh, ft);
+            put(blk, fw, fsh, ft);
+        };
+        // drain in two halves too: the stores of a finished bottom block, and (after a
+        // warp barrier) the release of the progress counter
+        auto drain_stores = [&](int blk) {
+            int c = blk * BLOCK + g;
+            if (blk >= 0 && c < m) {
+                const int2 b2 = reinterpret_cast<const int2 *>(sm->bot)[c & (WRING - 1)];
+                const int32_t hv = b2.x, ev = b2.y;
+                if (!last) {
+                    bout[c] = make_int2(hv, ev);
+                } else {
+                    if (outH) outH[c + 1] = hv - oe;
+                    if (outE) outE[c + 1] = ev;
                 }
             }
         };
@@ -150,16 +185,8 @@ __global__ void __launch_bounds__(256, WR <= 8 ? 4 : 2) wave_kernel(WaveArgs A) 
         __syncwarp();
         int drained = 0;
         T last_hoe = C::NEG, last_e = C::NEG, prev_up = diag0;
-        for (int s0 = 0; s0 < S && !failed; s0 += BLOCK) {
-          {
-            const int kb = s0 / BLOCK;
-            if ((kb + 1) * BLOCK < m) wait_for(kb + 1);
-            fill(kb + 1);
-            if (kb - 2 >= drained) { drain(kb - 2); drained = kb - 1; }
-            __syncwarp();
-          }
-          const int s1 = min(S, s0 + BLOCK);
-          for (int s = s0; s < s1; s++) {
+        // one step: column s - g of this lane's rows
+        auto step = [&](const int s) {
             const int c = s - g;
             T up_hoe = (T)__shfl_up_sync(0xffffffffu, (uint32_t)last_hoe, 1);
             T up_e = (T)__shfl_up_sync(0xffffffffu, (uint32_t)last_e, 1);
@@ -217,7 +244,26 @@ __global__ void __launch_bounds__(256, WR <= 8 ? 4 : 2) wave_kernel(WaveArgs A) 
                     reinterpret_cast<int2 *>(sm->bot)[c & (WRING - 1)] = make_int2(last_hoe, last ? Ein : E);
                 }
             }
-          }
+        };
+        for (int s0 = 0; s0 < S && !failed; s0 += BLOCK) {
+            const int kb = s0 / BLOCK;
+            if ((kb + 1) * BLOCK < m) wait_for(kb + 1);
+            uint32_t fw = 0;
+            int32_t fsh = 0;
+            int2 ft = make_int2(C::NEG, C::NEG);
+            fetch(kb + 1, fw, fsh, ft);
+            int released = -1;
+            if (kb - 2 >= drained) {
+                drain_stores(kb - 2);
+                released = kb - 2;
+                drained = kb - 1;
+            }
+            const int s1 = min(S, s0 + BLOCK), sm_ = min(s1, s0 + BLOCK / 2);
+            for (int s = s0; s < sm_; s++) step(s);
+            put(kb + 1, fw, fsh, ft);
+            __syncwarp();
+            if (released >= 0 && !last && g == 0) st_release(prog_mine, released + 1);
+            for (int s = sm_; s < s1; s++) step(s);
         }
         __syncwarp();
         for (int b = drained; b <= (m - 1) / BLOCK; b++) drain(b);
