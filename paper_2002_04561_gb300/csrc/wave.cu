@@ -286,11 +286,11 @@ static int blocks_per_sm() {
 }
 
 int wave_rows_per_lane(int64_t total_rows, int num_sms, int64_t n_passes) {
-    // 16-row stripes that fill less than half of their resident warps leave the
-    // GPU idle; 8-row stripes double the stripes (and the pipeline's skew, which
-    // costs more than it gains once the 16-row stripes fill half the warps)
+    // 8-row stripes double the stripes (and the pipeline's skew) and run at 64
+    // registers; measured on 100 kbp to 1 Mbp pairs, 16-row stripes win unless
+    // the problem is tiny (a few stripes, as a single pair of a thousand rows)
     const int64_t stripes16 = total_rows / (WG * 16) + n_passes;  // upper bound of sum(ceil(n / 512))
-    return 2 * stripes16 <= (int64_t)num_sms * blocks_per_sm<16, false>() * 8 ? 8 : 16;
+    return 16 * stripes16 <= (int64_t)num_sms * blocks_per_sm<16, false>() * 8 ? 8 : 16;
 }
 
 cudaError_t launch_wave(const WaveArgs &A, int num_sms, cudaStream_t st) {

@@ -35,9 +35,9 @@ struct WaveArgs {
     uint32_t *dirs;               // optional: traceback direction words (global mode)
 };
 
-// Rows per lane of a launch: 8 when 16-row stripes would fill less than half
-// of the resident warps (twice the stripes, half the per-step chain each),
-// otherwise 16. total_rows = sum of the passes' row counts.
+// Rows per lane of a launch: 8 when 16-row stripes would fill less than a
+// sixteenth of the resident warps (twice the stripes, half the per-step chain
+// each), otherwise 16. total_rows = sum of the passes' row counts.
 int wave_rows_per_lane(int64_t total_rows, int num_sms, int64_t n_passes);
 cudaError_t launch_wave(const WaveArgs &A, int num_sms, cudaStream_t st);
 constexpr int WAVE_LANES = 32;    // lanes per stripe
