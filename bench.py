@@ -196,6 +196,26 @@ def cpu_baseline(batch, budget_s: float = 12.0):
             "sample": f"first {n} of {batch.n_pairs} pairs ({sub.cells():.3e} cells), {dt:.1f} s"}
 
 
+def oracle_sample(batch, sc_args, mode, want_cigar=False, budget_s: float = 3.0, matrix=None):
+    """The CPU oracle on a bounded prefix of a secondary workload (all host
+    cores over pairs), as GCUPS with the sample it ran."""
+    import oracle
+    sc = oracle.Scoring(*sc_args, matrix=matrix)
+    threads = oracle.default_threads()
+    fn = oracle.align_batch if want_cigar else oracle.score_batch
+    n = 1
+    while True:
+        sub = batch.subset(np.arange(min(n, batch.n_pairs)))
+        t0 = time.perf_counter()
+        fn(sub, sc, mode, threads=threads)
+        dt = time.perf_counter() - t0
+        if dt > budget_s / 4 or n >= batch.n_pairs:
+            break
+        n *= 4
+    return {"GCUPS": sub.cells() / dt / 1e9, "cores": threads, "kind": "oracle",
+            "sample": f"first {sub.n_pairs} of {batch.n_pairs} pairs ({sub.cells():.3e} cells), {dt:.2f} s"}
+
+
 def run_reference(args, ws, rank):
     if rank != 0:
         return
@@ -313,7 +333,8 @@ def secondary_workloads(pkg, ctx, device):
     res = torch.zeros(40, dtype=torch.uint8, device=device)
     args = (dev(b.q), dev(b.q_off), dev(b.s), dev(b.s_off))
     ms = timed_events(lambda: ctx.align_batch(*args, sc, pkg.GLOBAL, want=7, out=res, cigar=cig), 20, stream)
-    out["single_pair_1000x1100_cigar"] = {"us": 1e3 * ms, "GCUPS": b.cells() / ms / 1e6}
+    out["single_pair_1000x1100_cigar"] = {"us": 1e3 * ms, "GCUPS": b.cells() / ms / 1e6,
+                                          "cpu_oracle": oracle_sample(b, (2, -1, 0, -2), 0, want_cigar=True)}
     # protein, local affine, score and CIGAR
     b = synth.protein_pairs()
     sc = pkg.Scoring.make(0, 0, -11, -1, matrix=synth.protein_matrix(3))
@@ -324,7 +345,9 @@ def secondary_workloads(pkg, ctx, device):
     cig = torch.zeros(cap, dtype=torch.int32, device=device)
     ms2 = timed_events(lambda: ctx.align_batch(*args, sc, pkg.LOCAL, want=7, out=res, cigar=cig), 3, stream)
     out["protein_65536_local_affine"] = {"score_ms": ms, "score_GCUPS": b.cells() / ms / 1e6,
-                                         "cigar_ms": ms2, "cigar_GCUPS": b.cells() / ms2 / 1e6}
+                                         "cigar_ms": ms2, "cigar_GCUPS": b.cells() / ms2 / 1e6,
+                                         "cpu_oracle": oracle_sample(b, (0, 0, -11, -1), 1,
+                                                                     matrix=synth.protein_matrix(3))}
     # 1 Mbp x 1 Mbp global affine: wavefront score, divide-and-conquer CIGAR
     b = synth.long_pair()
     qd, sd = dev(b.q), dev(b.s)
@@ -334,9 +357,12 @@ def secondary_workloads(pkg, ctx, device):
     t0 = time.perf_counter()
     r, used = ctx.align_long(qd, sd, sc, want=7, cigar=hcig)
     hb_s = time.perf_counter() - t0
+    # the oracle on a 20 kbp pair of the same generator (a 1 Mbp pair is 1e12 cells)
     out["long_pair_1Mbp_global_affine"] = {"score_s": ms / 1e3, "score_GCUPS": b.cells() / ms / 1e6,
                                            "cigar_total_s": hb_s, "cigar_words": int(used),
-                                           "score": int(r["score"][0])}
+                                           "score": int(r["score"][0]),
+                                           "cpu_oracle": oracle_sample(synth.long_pair(n=20_000, inversion=400),
+                                                                       (2, -3, -5, -2), 0)}
     del qd, sd
     # learned band vs full DP on 65,536 pairs of 1-10 kbp (scores must be equal)
     train = synth.band_pairs(n_pairs=2048, seed=105)
@@ -358,7 +384,8 @@ def secondary_workloads(pkg, ctx, device):
         "speedup": ms_full / ms_band, "scores_equal": bool(np.array_equal(fr["score"], br["score"])),
         "band_accepted": int(((br["flags"] & pkg.FLAG_BAND_ACCEPTED) != 0).sum()),
         "full_dp_fallback": int(((br["flags"] & pkg.FLAG_FULL_FALLBACK) != 0).sum()),
-        "full_dp_GCUPS": b.cells() / ms_full / 1e6, "train_s": train_s, "train_loss": loss}
+        "full_dp_GCUPS": b.cells() / ms_full / 1e6, "train_s": train_s, "train_loss": loss,
+        "cpu_oracle_full_dp": oracle_sample(b, (2, -3, -5, -2), 0)}
     # serving: Poisson arrivals through the native request queue
     out["serving_mix_3000_global_affine"] = serving_workload(pkg)
     return out
@@ -368,6 +395,7 @@ def profile_long(n: int):
     """One global long pair of the long-pair generator's shape, scored twice by
     the wavefront (a small case for ncu captures of the wavefront kernel)."""
     import torch
+    import paper_2002_04561_gb300 as pkg
     pkg.load(build_if_missing=True)
     ctx = pkg.Context(0)
     b = synth.long_pair(n=n, inversion=max(1, n // 50))

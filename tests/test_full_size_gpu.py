@@ -1,0 +1,79 @@
+"""Parity at the full sizes the benchmark times, on GPU:
+
+* the 1 Mbp x 1 Mbp global affine pair (1e12 cells, beyond the oracle): the
+  divide-and-conquer CIGAR consumes both sequences and re-scores exactly to the
+  wavefront's score, which equals the allocation-free entry point's score; a
+  20 kbp pair of the same generator matches the oracle bit for bit;
+* the 65,536 learned-band pairs of 1-10 kbp: the banded route's scores equal
+  the full DP's on every pair (the certificate is exact), and a sample of the
+  full DP equals the oracle.
+"""
+import numpy as np
+import pytest
+
+import oracle
+import synth
+from brute import rescore_cigar
+
+pytestmark = pytest.mark.gpu
+torch = pytest.importorskip("torch")
+
+C4 = (2, -3, -5, -2)
+
+
+@pytest.fixture(scope="module")
+def pkg():
+    if not torch.cuda.is_available():
+        pytest.skip("no GPU")
+    import paper_2002_04561_gb300 as p
+    p.load(build_if_missing=True)
+    return p
+
+
+@pytest.fixture(scope="module")
+def ctx(pkg):
+    c = pkg.Context(0)
+    yield c
+    c.close()
+
+
+def test_long_pair_1mbp_cigar_rescores_to_wavefront_score(pkg, ctx):
+    b = synth.long_pair()
+    q, s = b.pair(0)
+    sc = pkg.Scoring.make(*C4)
+    qd, sd = torch.from_numpy(q).cuda(), torch.from_numpy(s).cuda()
+    res, _ = ctx.align_long(qd, sd, sc)
+    score = int(res["score"][0])
+    cig = np.zeros(len(q) + len(s) + 4, np.uint32)
+    r2, used = ctx.align_long(qd, sd, sc, want=pkg.WANT_SCORE | pkg.WANT_CIGAR, cigar=cig)
+    assert int(r2["score"][0]) == score
+    got, eq, es = rescore_cigar(cig[:used], q, s, (0, 0), oracle.Scoring(*C4))
+    assert (got, eq, es) == (score, len(q), len(s))
+    out = torch.zeros(1, dtype=torch.int32, device="cuda")
+    pkg.align_long_noalloc(qd, sd, sc, out)
+    torch.cuda.synchronize()
+    assert int(out.item()) == score
+    small = synth.long_pair(n=20_000, inversion=400)
+    qs, ss = small.pair(0)
+    r3, _ = ctx.align_long(qs, ss, sc)
+    assert int(r3["score"][0]) == oracle.score(qs, ss, oracle.Scoring(*C4))[0]
+
+
+def test_band_workload_full_size_scores_equal_full_dp(pkg, ctx):
+    sc = pkg.Scoring.make(*C4)
+    train = synth.band_pairs(n_pairs=2048, seed=105)
+    ctx.band_train(train.q, train.q_off, train.s, train.s_off, sc, epochs=40, lr=1e-3)
+    b = synth.band_pairs()
+    dev = lambda a: torch.from_numpy(np.ascontiguousarray(a)).cuda()
+    args = (dev(b.q), dev(b.q_off), dev(b.s), dev(b.s_off))
+    full = torch.zeros(b.n_pairs * 40, dtype=torch.uint8, device="cuda")
+    band = torch.zeros_like(full)
+    ctx.align_batch(*args, sc, pkg.GLOBAL, out=full)
+    ctx.align_batch(*args, sc, pkg.GLOBAL, want=pkg.WANT_SCORE | pkg.BAND_LEARNED, out=band)
+    fr = full.cpu().numpy().view(pkg.RESULT_DTYPE)
+    br = band.cpu().numpy().view(pkg.RESULT_DTYPE)
+    assert np.array_equal(fr["score"], br["score"])
+    assert ((br["flags"] & pkg.FLAG_BAND_ACCEPTED) != 0).sum() > 1000
+    idx = np.arange(0, b.n_pairs, 1024)
+    want = oracle.score_batch(b.subset(idx), oracle.Scoring(*C4), 0)
+    assert np.array_equal(fr["score"][idx], want[0])
