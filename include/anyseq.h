@@ -128,8 +128,9 @@ anyseq_status_t anyseq_align_batch(anyseq_ctx *ctx,
  * Align one long pair (intra-sequence parallelism: anti-diagonal wavefront of
  * row stripes, Sec. IV-C), score in linear space, and with ANYSEQ_WANT_CIGAR
  * the divide-and-conquer traceback of Sec. III-A (Myers-Miller for affine
- * gaps). Only ANYSEQ_GLOBAL supports ANYSEQ_WANT_CIGAR. Arguments as for
- * anyseq_align_batch with one pair of lengths n and m.
+ * gaps). Only ANYSEQ_GLOBAL supports ANYSEQ_WANT_CIGAR; ANYSEQ_LOCAL and
+ * ANYSEQ_SEMIGLOBAL give score and optimum cell (lengths below 2^21). Arguments
+ * as for anyseq_align_batch with one pair of lengths n and m.
  */
 anyseq_status_t anyseq_align_long(anyseq_ctx *ctx,
                                   const uint8_t *q, int64_t n,
@@ -277,8 +278,8 @@ anyseq_status_t anyseq_plan_destroy(anyseq_plan *plan);
  * stream. Pairs are submitted one at a time from any thread and aligned in
  * micro-batches: the worker waits at most max_wait_us after the oldest queued
  * request (or until max_batch_pairs are queued), then aligns the batch's small
- * pairs with one anyseq_align_batch call and, in global mode, every pair of at
- * least long_cells cells with the wavefront of anyseq_align_long, all of them in
+ * pairs with one anyseq_align_batch call and every pair of at least long_cells
+ * cells with the wavefront of anyseq_align_long, all of them in
  * one launch (their stripes run side by side). Results carry score and optimum
  * cell.
  * Admission: the letters of queued and running requests never exceed

@@ -512,8 +512,8 @@ extern "C" anyseq_status_t anyseq_align_batch(anyseq_ctx *ctx, const uint8_t *q,
     if ((want & ANYSEQ_BAND_LEARNED) && !want_cigar && mode == ANYSEQ_GLOBAL && sc->alphabet <= 4) {
         TRY(band_scores(ctx, in, sc, score, eq, es, flags, st));
     } else {
-        if (mode == ANYSEQ_GLOBAL && !ctx->force32)
-            TRY(wave_batch(ctx, in, sc, score, eq, es, flags, st, want_cigar ? &tbo : nullptr, &on_wave));
+        if (!ctx->force32 && (mode == ANYSEQ_GLOBAL || !want_cigar))
+            TRY(wave_batch(ctx, in, sc, mode, score, eq, es, flags, st, want_cigar ? &tbo : nullptr, &on_wave));
         if (!on_wave) TRY(batch_scores(ctx, in, sc, mode, score, eq, es, flags, st, want_cigar ? &tbo : nullptr));
     }
 
@@ -595,12 +595,12 @@ bool anyseq::long_range_ok(const anyseq_scoring_t *sc, int64_t n, int64_t m) {
 constexpr int64_t WAVE_BATCH_PAIRS = 8;
 constexpr double WAVE_BATCH_CELLS = 262144.0;
 
-anyseq_status_t anyseq::wave_batch(anyseq_ctx *ctx, const BatchInput &in, const anyseq_scoring_t *sc, int32_t *score,
-                                   int32_t *eq, int32_t *es, uint32_t *flags, cudaStream_t st, TbOut *tb,
-                                   bool *used) {
+anyseq_status_t anyseq::wave_batch(anyseq_ctx *ctx, const BatchInput &in, const anyseq_scoring_t *sc,
+                                   int32_t mode, int32_t *score, int32_t *eq, int32_t *es, uint32_t *flags,
+                                   cudaStream_t st, TbOut *tb, bool *used) {
     *used = false;
     const int64_t n = in.n_pairs;
-    if (n > WAVE_BATCH_PAIRS || sc->alphabet > 4) return ANYSEQ_OK;
+    if (n > WAVE_BATCH_PAIRS || sc->alphabet > 4 || (tb && mode != ANYSEQ_GLOBAL)) return ANYSEQ_OK;
     if ((double)in.max_n * (double)in.max_m < WAVE_BATCH_CELLS) return ANYSEQ_OK;
     std::vector<int64_t> hq((size_t)n + 1), hs((size_t)n + 1);
     CUDA_TRY(cudaMemcpyAsync(hq.data(), in.q_off, ((size_t)n + 1) * sizeof(int64_t), cudaMemcpyDeviceToHost, st));
@@ -608,6 +608,7 @@ anyseq_status_t anyseq::wave_batch(anyseq_ctx *ctx, const BatchInput &in, const 
     CUDA_TRY(cudaStreamSynchronize(st));
     for (int64_t p = 0; p < n; p++)
         if (!long_range_ok(sc, hq[p + 1] - hq[p], hs[p + 1] - hs[p])) return ANYSEQ_OK;
+    std::vector<uint64_t> keys;
     *used = true;
     anyseq_status_t s2 = ANYSEQ_OK;
     uint32_t *q2 = arena<uint32_t>(ctx, "wb_q2", (size_t)(in.q_len + 15) / 16 + 2, &s2);
@@ -644,12 +645,13 @@ anyseq_status_t anyseq::wave_batch(anyseq_ctx *ctx, const BatchInput &in, const 
     if (!passes.empty()) {
         int32_t *H = arena<int32_t>(ctx, "wb_H", (size_t)out + 2, &s2);
         if (s2 != ANYSEQ_OK) return s2;
-        TRY(run_wave_passes(ctx, q2, s2p, passes, sc, H, nullptr, st, tb ? &wtb : nullptr));
+        TRY(run_wave_passes(ctx, q2, s2p, passes, sc, H, nullptr, st, tb ? &wtb : nullptr, mode, &keys));
         for (int64_t p = 0; p < n; p++) {
             const int64_t k = pass_of[(size_t)p];
             if (k < 0) continue;
             const WavePass &w = passes[(size_t)k];
-            CUDA_TRY(cudaMemcpyAsync(&hscore[(size_t)p], H + w.out_off + w.m, sizeof(int32_t), cudaMemcpyDeviceToHost, st));
+            if (mode == ANYSEQ_GLOBAL)
+                CUDA_TRY(cudaMemcpyAsync(&hscore[(size_t)p], H + w.out_off + w.m, sizeof(int32_t), cudaMemcpyDeviceToHost, st));
             hbase[(size_t)p] = w.dir_off;
             const int32_t rows = WAVE_LANES * (tb ? wtb.rows_per_lane : 8);
             hpad[(size_t)p] = ((w.n + rows - 1) / rows) * rows - w.n;
@@ -661,9 +663,19 @@ anyseq_status_t anyseq::wave_batch(anyseq_ctx *ctx, const BatchInput &in, const 
     if (hb) return fail(ANYSEQ_ERR_ALPHABET, "a letter code is >= alphabet (%d)", sc->alphabet);
     for (int64_t p = 0; p < n; p++) {
         const int64_t qn = hq[p + 1] - hq[p], sm = hs[p + 1] - hs[p];
-        if (qn == 0 || sm == 0) hscore[(size_t)p] = (qn + sm == 0) ? 0 : sc->gap_open + (int32_t)(qn + sm) * sc->gap_extend;
-        heq[(size_t)p] = (int32_t)qn;
-        hes[(size_t)p] = (int32_t)sm;
+        const int64_t k = pass_of[(size_t)p];
+        if (mode == ANYSEQ_GLOBAL) {
+            if (qn == 0 || sm == 0) hscore[(size_t)p] = (qn + sm == 0) ? 0 : sc->gap_open + (int32_t)(qn + sm) * sc->gap_extend;
+            heq[(size_t)p] = (int32_t)qn;
+            hes[(size_t)p] = (int32_t)sm;
+        } else if (k < 0) {
+            // an empty sequence: the empty alignment at (0, 0)
+            hscore[(size_t)p] = heq[(size_t)p] = hes[(size_t)p] = 0;
+        } else {
+            hscore[(size_t)p] = key_score(keys[(size_t)k]);
+            heq[(size_t)p] = key_i(keys[(size_t)k]);
+            hes[(size_t)p] = key_j(keys[(size_t)k]);
+        }
     }
     CUDA_TRY(cudaMemcpyAsync(score, hscore.data(), (size_t)n * sizeof(int32_t), cudaMemcpyHostToDevice, st));
     CUDA_TRY(cudaMemcpyAsync(eq, heq.data(), (size_t)n * sizeof(int32_t), cudaMemcpyHostToDevice, st));
@@ -693,7 +705,7 @@ anyseq_status_t anyseq::wave_batch(anyseq_ctx *ctx, const BatchInput &in, const 
 // non-empty and inside the 32-bit range test of anyseq_align_long.
 anyseq_status_t anyseq::long_scores(anyseq_ctx *ctx, const uint8_t *q, const int64_t *q_off, const uint8_t *s,
                                     const int64_t *s_off, int64_t count, const anyseq_scoring_t *sc, int32_t *scores,
-                                    cudaStream_t st) {
+                                    cudaStream_t st, int32_t mode, int32_t *end_q, int32_t *end_s) {
     if (count <= 0) return ANYSEQ_OK;
     anyseq_status_t s2 = ANYSEQ_OK;
     const int64_t nq = q_off[count], ns = s_off[count];
@@ -723,15 +735,24 @@ anyseq_status_t anyseq::long_scores(anyseq_ctx *ctx, const uint8_t *q, const int
     CUDA_TRY(launch_pack2bit((const uint8_t *)dq, nq, q2, sc->alphabet, bad, st));
     CUDA_TRY(launch_pack2bit((const uint8_t *)ds, ns, s2p, sc->alphabet, bad, st));
     ctx->launches += 2;
-    TRY(run_wave_passes(ctx, q2, s2p, passes, sc, H, nullptr, st));
+    std::vector<uint64_t> keys;
+    TRY(run_wave_passes(ctx, q2, s2p, passes, sc, H, nullptr, st, nullptr, mode, &keys));
     int32_t hb = 0;
     CUDA_TRY(cudaMemcpyAsync(&hb, bad, sizeof(int32_t), cudaMemcpyDeviceToHost, st));
-    for (int64_t k = 0; k < count; k++) {
-        const WavePass &p = passes[(size_t)k];
-        CUDA_TRY(cudaMemcpyAsync(&scores[k], H + p.out_off + p.m, sizeof(int32_t), cudaMemcpyDeviceToHost, st));
+    if (mode == ANYSEQ_GLOBAL) {
+        for (int64_t k = 0; k < count; k++) {
+            const WavePass &p = passes[(size_t)k];
+            CUDA_TRY(cudaMemcpyAsync(&scores[k], H + p.out_off + p.m, sizeof(int32_t), cudaMemcpyDeviceToHost, st));
+        }
     }
     CUDA_TRY(cudaStreamSynchronize(st));
     if (hb) return fail(ANYSEQ_ERR_ALPHABET, "a letter code is >= alphabet (%d)", sc->alphabet);
+    for (int64_t k = 0; k < count; k++) {
+        const WavePass &p = passes[(size_t)k];
+        if (mode != ANYSEQ_GLOBAL) scores[k] = key_score(keys[(size_t)k]);
+        if (end_q) end_q[k] = mode == ANYSEQ_GLOBAL ? p.n : key_i(keys[(size_t)k]);
+        if (end_s) end_s[k] = mode == ANYSEQ_GLOBAL ? p.m : key_j(keys[(size_t)k]);
+    }
     return ANYSEQ_OK;
 }
 
@@ -756,7 +777,10 @@ extern "C" anyseq_status_t anyseq_align_long(anyseq_ctx *ctx, const uint8_t *q, 
     if (!out) return fail(ANYSEQ_ERR_ARG, "out is NULL");
     if ((n > 0 && !q) || (m > 0 && !s)) return fail(ANYSEQ_ERR_ARG, "q or s is NULL");
     TRY(check_scoring(sc, mode));
-    if (mode != ANYSEQ_GLOBAL) return fail(ANYSEQ_ERR_ARG, "the long-pair path is global only");
+    if (mode != ANYSEQ_GLOBAL && (want & ANYSEQ_WANT_CIGAR))
+        return fail(ANYSEQ_ERR_ARG, "the long-pair traceback is global only (local and semi-global: score and end cell)");
+    if (mode != ANYSEQ_GLOBAL && (n >= (1ll << 21) || m >= (1ll << 21)))
+        return fail(ANYSEQ_ERR_ARG, "local and semi-global long pairs below 2^21 letters");
     if (sc->alphabet > 4) return fail(ANYSEQ_ERR_ARG, "the long-pair path takes alphabets of at most 4 letters");
     if (!long_range_ok(sc, n, m)) return fail(ANYSEQ_ERR_ARG, "scores of this pair may leave the 32-bit range");
     cudaStream_t st = (cudaStream_t)cuda_stream;
@@ -772,9 +796,13 @@ extern "C" anyseq_status_t anyseq_align_long(anyseq_ctx *ctx, const uint8_t *q, 
     const bool want_cigar = (want & ANYSEQ_WANT_CIGAR) != 0;
     std::vector<uint32_t> hcig;
     if (n == 0 || m == 0) {
-        r.score = (n + m == 0) ? 0 : sc->gap_open + (int32_t)(n + m) * sc->gap_extend;
-        if (m) hcig.push_back(((uint32_t)m << 4) | 2u);
-        if (n) hcig.push_back(((uint32_t)n << 4) | 1u);
+        if (mode == ANYSEQ_GLOBAL) {
+            r.score = (n + m == 0) ? 0 : sc->gap_open + (int32_t)(n + m) * sc->gap_extend;
+            if (m) hcig.push_back(((uint32_t)m << 4) | 2u);
+            if (n) hcig.push_back(((uint32_t)n << 4) | 1u);
+        } else {
+            r.score = r.end_q = r.end_s = 0;  // the empty alignment at (0, 0)
+        }
     } else {
         const void *dq, *ds;
         TRY(stage_input(ctx, "l_q", q, (size_t)n, st, &dq));
@@ -788,11 +816,28 @@ extern "C" anyseq_status_t anyseq_align_long(anyseq_ctx *ctx, const uint8_t *q, 
         CUDA_TRY(launch_pack2bit((const uint8_t *)dq, n, q2, sc->alphabet, bad, st));
         CUDA_TRY(launch_pack2bit((const uint8_t *)ds, m, s2p, sc->alphabet, bad, st));
         ctx->launches += 2;
-        TRY(long_last_row(ctx, q2, 0, (int32_t)n, s2p, 0, (int32_t)m, false, sc->gap_open, sc, H, nullptr, st));
+        if (mode == ANYSEQ_GLOBAL) {
+            TRY(long_last_row(ctx, q2, 0, (int32_t)n, s2p, 0, (int32_t)m, false, sc->gap_open, sc, H, nullptr, st));
+        } else {
+            std::vector<WavePass> passes(1);
+            memset(passes.data(), 0, sizeof(WavePass));
+            passes[0].n = (int32_t)n;
+            passes[0].m = (int32_t)m;
+            passes[0].tb = sc->gap_open;
+            std::vector<uint64_t> keys;
+            TRY(run_wave_passes(ctx, q2, s2p, passes, sc, H, nullptr, st, nullptr, mode, &keys));
+            r.score = key_score(keys[0]);
+            r.end_q = key_i(keys[0]);
+            r.end_s = key_j(keys[0]);
+        }
         int32_t hb = 0;
-        CUDA_TRY(cudaMemcpy(&hb, bad, sizeof(int32_t), cudaMemcpyDeviceToHost));
+        CUDA_TRY(cudaMemcpyAsync(&hb, bad, sizeof(int32_t), cudaMemcpyDeviceToHost, st));
+        CUDA_TRY(cudaStreamSynchronize(st));
         if (hb) return fail(ANYSEQ_ERR_ALPHABET, "a letter code is >= alphabet (%d)", sc->alphabet);
-        CUDA_TRY(cudaMemcpy(&r.score, H + m, sizeof(int32_t), cudaMemcpyDeviceToHost));
+        if (mode == ANYSEQ_GLOBAL) {
+            CUDA_TRY(cudaMemcpyAsync(&r.score, H + m, sizeof(int32_t), cudaMemcpyDeviceToHost, st));
+            CUDA_TRY(cudaStreamSynchronize(st));
+        }
         if (want_cigar) TRY(hirschberg_cigar(ctx, q2, (int32_t)n, s2p, (int32_t)m, sc, hcig, st));
     }
     if (want_cigar) {

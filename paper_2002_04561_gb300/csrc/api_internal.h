@@ -72,18 +72,22 @@ struct TbOut {
     int32_t lanes_per_chunk = 16, rows_per_lane = 8;  // layout (batched kernel: 16 x TB_R)
 };
 
-// Small global batches on the wavefront: scores, end cells and (with tb) the
+// Small batches on the wavefront: scores, end cells and (global, with tb) the
 // direction words of every pair; false in *used when the batch does not qualify.
-anyseq_status_t wave_batch(anyseq_ctx *ctx, const BatchInput &in, const anyseq_scoring_t *sc, int32_t *score,
-                           int32_t *eq, int32_t *es, uint32_t *flags, cudaStream_t st, TbOut *tb, bool *used);
+anyseq_status_t wave_batch(anyseq_ctx *ctx, const BatchInput &in, const anyseq_scoring_t *sc, int32_t mode,
+                           int32_t *score, int32_t *eq, int32_t *es, uint32_t *flags, cudaStream_t st, TbOut *tb,
+                           bool *used);
 anyseq_status_t stage_batch(anyseq_ctx *ctx, const uint8_t *q, const int64_t *q_off, const uint8_t *s,
                             const int64_t *s_off, int64_t n_pairs, BatchInput &in, cudaStream_t st);
 anyseq_status_t band_scores(anyseq_ctx *ctx, const BatchInput &in, const anyseq_scoring_t *sc, int32_t *score,
                             int32_t *eq, int32_t *es, uint32_t *flags, cudaStream_t st);
 bool long_range_ok(const anyseq_scoring_t *sc, int64_t n, int64_t m);
+// Scores (and, with end_q/end_s, optimum cells) of several long pairs in one
+// wavefront launch, in the given mode (host arrays).
 anyseq_status_t long_scores(anyseq_ctx *ctx, const uint8_t *q, const int64_t *q_off, const uint8_t *s,
                             const int64_t *s_off, int64_t count, const anyseq_scoring_t *sc, int32_t *scores,
-                            cudaStream_t st);
+                            cudaStream_t st, int32_t mode = ANYSEQ_GLOBAL, int32_t *end_q = nullptr,
+                            int32_t *end_s = nullptr);
 anyseq_status_t long_last_row(anyseq_ctx *ctx, const uint32_t *q2, int64_t q0, int32_t n, const uint32_t *s2,
                               int64_t s0, int32_t m, bool rev, int32_t tb, const anyseq_scoring_t *sc, int32_t *H,
                               int32_t *E, cudaStream_t st);
@@ -96,7 +100,8 @@ struct WaveTb {
 };
 anyseq_status_t run_wave_passes(anyseq_ctx *ctx, const uint32_t *q2, const uint32_t *s2,
                                 std::vector<WavePass> &passes, const anyseq_scoring_t *sc, int32_t *H, int32_t *E,
-                                cudaStream_t st, WaveTb *tb = nullptr);
+                                cudaStream_t st, WaveTb *tb = nullptr, int32_t mode = ANYSEQ_GLOBAL,
+                                std::vector<uint64_t> *keys = nullptr);
 anyseq_status_t hirschberg_cigar(anyseq_ctx *ctx, const uint32_t *q2, int32_t n, const uint32_t *s2, int32_t m,
                                  const anyseq_scoring_t *sc, std::vector<uint32_t> &cigar, cudaStream_t st);
 

@@ -132,13 +132,13 @@ __device__ __forceinline__ uint32_t codes16(const uint32_t *packed, int64_t k, i
 
 // Lexicographic key of an optimum candidate: larger score, then smaller i,
 // then smaller j wins (the tie rule of the optimum cell).
-__device__ __forceinline__ uint64_t end_key(int32_t score, int32_t i, int32_t j) {
+__host__ __device__ __forceinline__ uint64_t end_key(int32_t score, int32_t i, int32_t j) {
     return ((uint64_t)(uint32_t)(score + (1 << 21)) << 42) |
            ((uint64_t)(uint32_t)((1 << 21) - 1 - i) << 21) |
            (uint64_t)(uint32_t)((1 << 21) - 1 - j);
 }
-__device__ __forceinline__ int32_t key_score(uint64_t k) { return (int32_t)(k >> 42) - (1 << 21); }
-__device__ __forceinline__ int32_t key_i(uint64_t k) { return (1 << 21) - 1 - (int32_t)((k >> 21) & 0x1FFFFF); }
-__device__ __forceinline__ int32_t key_j(uint64_t k) { return (1 << 21) - 1 - (int32_t)(k & 0x1FFFFF); }
+__host__ __device__ __forceinline__ int32_t key_score(uint64_t k) { return (int32_t)(k >> 42) - (1 << 21); }
+__host__ __device__ __forceinline__ int32_t key_i(uint64_t k) { return (1 << 21) - 1 - (int32_t)((k >> 21) & 0x1FFFFF); }
+__host__ __device__ __forceinline__ int32_t key_j(uint64_t k) { return (1 << 21) - 1 - (int32_t)(k & 0x1FFFFF); }
 
 }  // namespace anyseq

@@ -222,11 +222,11 @@ static T *arena_t(anyseq_ctx *ctx, const char *name, size_t count, anyseq_status
 
 anyseq_status_t run_wave_passes(anyseq_ctx *ctx, const uint32_t *q2, const uint32_t *s2,
                                 std::vector<WavePass> &passes, const anyseq_scoring_t *sc, int32_t *H, int32_t *E,
-                                cudaStream_t st, WaveTb *tb) {
+                                cudaStream_t st, WaveTb *tb, int32_t mode, std::vector<uint64_t> *keys) {
     anyseq_status_t s2st = ANYSEQ_OK;
     int64_t border = 0, rows = 0;
     for (const auto &p : passes) rows += p.n;
-    const int wr = wave_rows_per_lane(rows, ctx->num_sms, (int64_t)passes.size());
+    const int wr = wave_rows_per_lane(rows, ctx->num_sms, (int64_t)passes.size(), mode);
     const int stripe_rows = WAVE_LANES * wr;
     int32_t stripes = 0;
     int64_t dir_words = 0;
@@ -247,7 +247,18 @@ anyseq_status_t run_wave_passes(anyseq_ctx *ctx, const uint32_t *q2, const uint3
     W.n_stripes = stripes;
     W.o = sc->gap_open;
     W.e = sc->gap_extend;
-    HB_TRY(make_rowprof(sc, ANYSEQ_GLOBAL, W.rowprof));
+    HB_TRY(make_rowprof(sc, mode, W.rowprof));
+    W.mode = mode;
+    W.best = nullptr;
+    std::vector<uint64_t> hkeys;
+    if (mode != ANYSEQ_GLOBAL) {
+        // best cell per pass, starting from the empty alignment's cell
+        hkeys.resize(passes.size());
+        for (size_t k = 0; k < passes.size(); k++) hkeys[k] = end_key(0, 0, mode == ANYSEQ_SEMIGLOBAL ? passes[k].m : 0);
+        W.best = arena_t<uint64_t>(ctx, "w_best", passes.size() + 1, &s2st);
+        if (s2st != ANYSEQ_OK) return s2st;
+        HB_CUDA(cudaMemcpyAsync(W.best, hkeys.data(), hkeys.size() * sizeof(uint64_t), cudaMemcpyHostToDevice, st));
+    }
     WavePass *dpass = arena_t<WavePass>(ctx, "w_pass", passes.size() + 1, &s2st);
     W.border = arena_t<int2>(ctx, "w_border", (size_t)border + 2, &s2st);
     int32_t *ctl = arena_t<int32_t>(ctx, "w_ctl", (size_t)stripes + 8, &s2st);
@@ -273,7 +284,9 @@ anyseq_status_t run_wave_passes(anyseq_ctx *ctx, const uint32_t *q2, const uint3
     ctx->launches += 1;
     int32_t err = 0;
     HB_CUDA(cudaMemcpyAsync(&err, W.err, sizeof(int32_t), cudaMemcpyDeviceToHost, st));
+    if (W.best) HB_CUDA(cudaMemcpyAsync(hkeys.data(), W.best, hkeys.size() * sizeof(uint64_t), cudaMemcpyDeviceToHost, st));
     HB_CUDA(cudaStreamSynchronize(st));
+    if (keys) *keys = hkeys;
     if (err) return fail(ANYSEQ_ERR_TIMEOUT, "a stripe of the wavefront waited past its limit");
     return ANYSEQ_OK;
 }

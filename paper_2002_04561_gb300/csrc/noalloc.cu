@@ -118,7 +118,7 @@ extern "C" anyseq_status_t anyseq_align_long_noalloc(const uint8_t *q, int64_t n
     int dev = 0, sms = 1;
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-    const int wr = wave_rows_per_lane(n, sms, 1);
+    const int wr = wave_rows_per_lane(n, sms, 1, GLOBAL);
     const int64_t stripes = (n + WAVE_LANES * wr - 1) / (WAVE_LANES * wr);
     noalloc_init_kernel<<<8, 256, 0, st>>>(pass, ps, ctl, stripes + 2, bad);
     cudaError_t e = cudaGetLastError();

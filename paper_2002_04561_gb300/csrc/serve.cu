@@ -7,7 +7,7 @@
 // are queued), then aligns every small pair of the batch with one
 // anyseq_align_batch call (inter-sequence parallelism) and every pair of at
 // least long_cells cells with the wavefront of anyseq_align_long (intra-sequence
-// parallelism, global mode), all of them in one launch. Admission: the
+// parallelism), all of them in one launch. Admission: the
 // letters of queued and running requests may not exceed mem_budget_bytes; a
 // submit that would exceed it is refused with ANYSEQ_ERR_BUDGET.
 #include <chrono>
@@ -70,8 +70,8 @@ void run_batch(anyseq_server *S, std::vector<Request *> &reqs) {
     std::vector<Request *> small, big;
     for (Request *r : reqs) {
         const double cells = (double)r->q.size() * (double)r->s.size();
-        const bool is_long = S->cfg.mode == ANYSEQ_GLOBAL && cells >= (double)S->cfg.long_cells && !r->q.empty() &&
-                             !r->s.empty() && S->sc.alphabet <= 4 &&
+        const bool is_long = cells >= (double)S->cfg.long_cells && !r->q.empty() && !r->s.empty() &&
+                             S->sc.alphabet <= 4 && r->q.size() < (1u << 21) && r->s.size() < (1u << 21) &&
                              anyseq::long_range_ok(&S->sc, (int64_t)r->q.size(), (int64_t)r->s.size());
         (is_long ? big : small).push_back(r);
     }
@@ -112,9 +112,10 @@ void run_batch(anyseq_server *S, std::vector<Request *> &reqs) {
             memcpy(q.data() + qo[k], big[k]->q.data(), big[k]->q.size());
             memcpy(s.data() + so[k], big[k]->s.data(), big[k]->s.size());
         }
-        std::vector<int32_t> scores(big.size(), 0);
+        std::vector<int32_t> scores(big.size(), 0), eq(big.size(), 0), es(big.size(), 0);
         const anyseq_status_t st = anyseq::long_scores(S->ctx, q.data(), qo.data(), s.data(), so.data(),
-                                                       (int64_t)big.size(), &S->sc, scores.data(), S->stream);
+                                                       (int64_t)big.size(), &S->sc, scores.data(), S->stream,
+                                                       S->cfg.mode, eq.data(), es.data());
         const std::string msg = st != ANYSEQ_OK ? anyseq_last_error() : "";
         const int64_t t = now_ns();
         for (size_t k = 0; k < big.size(); k++) {
@@ -122,8 +123,8 @@ void run_batch(anyseq_server *S, std::vector<Request *> &reqs) {
             memset(&r->res, 0, sizeof(r->res));
             r->res.score = scores[k];
             r->res.beg_q = r->res.beg_s = -1;
-            r->res.end_q = (int32_t)r->q.size();
-            r->res.end_s = (int32_t)r->s.size();
+            r->res.end_q = eq[k];
+            r->res.end_s = es[k];
             r->res.flags = ANYSEQ_FLAG_INT32;
             r->status = st;
             r->error = msg;

@@ -45,11 +45,18 @@ struct __align__(16) WaveSmem {
 };
 
 // TB: also write the traceback direction words of every cell (the layout of the
-// batched traceback with 32 lanes x WR rows per chunk, see tb.h).
-template <int WR, bool TB>
-__global__ void __launch_bounds__(256, WR <= 8 ? 4 : 2) wave_kernel(WaveArgs A) {
+// batched traceback with 32 lanes x WR rows per chunk, see tb.h), global only.
+// MODE: the initialisation and optimum of Sec. III-A. Local and semi-global
+// passes keep their best cell as a key (score, then smaller i, then smaller j)
+// merged per pass by a 64-bit atomic maximum: local from every row's running
+// maximum and its first column (rows per lane 8 there, the extra registers),
+// semi-global from the last column (at each lane's last-column step) and the
+// last row (the last stripe's bottom row).
+template <int WR, bool TB, int MODE>
+__global__ void __launch_bounds__(256, (WR <= 8 && MODE != LOCAL) ? 4 : 2) wave_kernel(WaveArgs A) {
     constexpr int WCH = WG * WR;  // rows per stripe
     static_assert(!TB || WR % 8 == 0, "direction words hold 8 rows");
+    static_assert(!TB || MODE == GLOBAL, "traceback on the wavefront is global");
     __shared__ WaveSmem smem[8];
     const int warp = threadIdx.x >> 5, g = threadIdx.x & 31;
     WaveSmem *sm = &smem[warp];
@@ -85,10 +92,22 @@ __global__ void __launch_bounds__(256, WR <= 8 ? 4 : 2) wave_kernel(WaveArgs A) 
         for (int r = 0; r < WR; r++) {
             int32_t i = rb + r - pad;
             prof[r] = (i >= 1) ? A.rowprof[wletter(A.q2, ps.q0, n, i - 1, rev)] : A.rowprof[4];
-            Hoe[r] = col0(GLOBAL, i, o, e, ps.tb) + oe;
+            Hoe[r] = col0(MODE, i, o, e, ps.tb) + oe;
             F[r] = C::NEG;
         }
-        const T diag0 = col0(GLOBAL, rb - 1 - pad, o, e, ps.tb) + oe;
+        const T diag0 = col0(MODE, rb - 1 - pad, o, e, ps.tb) + oe;
+        // local / semi-global: this lane's best cell as a key; local rows' running
+        // maxima (Hoe) and their first columns
+        uint64_t best = end_key(0, 0, MODE == SEMIGLOBAL ? m : 0);
+        T rowmax[MODE == LOCAL ? WR : 1];
+        int32_t rowj[MODE == LOCAL ? WR : 1];
+        if (MODE == LOCAL) {
+#pragma unroll
+            for (int r = 0; r < WR; r++) {
+                rowmax[r] = oe;  // Hoe of H = 0
+                rowj[r] = 0;
+            }
+        }
         const int2 *bin = A.border + ps.border_off + (int64_t)((k - 1) & 1) * m;
         int2 *bout = A.border + ps.border_off + (int64_t)(k & 1) * m;
         int32_t *prog_prev = A.prog + ps.stripe0 + (k > 0 ? k - 1 : 0);
@@ -128,7 +147,7 @@ __global__ void __launch_bounds__(256, WR <= 8 ? 4 : 2) wave_kernel(WaveArgs A) 
                 fsh = 2 * (int32_t)(pos & 15);
                 if (k == 0) {
                     // row 0: H(0, c+1); E below row 0 comes from H only (E(0, .) = -inf)
-                    const int32_t v = o + (c + 1) * e + oe;
+                    const int32_t v = (MODE == GLOBAL ? o + (c + 1) * e : 0) + oe;
                     ft = make_int2(v, v);
                 } else if (!failed) {
                     ft = bin[c];
@@ -161,6 +180,10 @@ __global__ void __launch_bounds__(256, WR <= 8 ? 4 : 2) wave_kernel(WaveArgs A) 
                 } else {
                     if (outH) outH[c + 1] = hv - oe;
                     if (outE) outE[c + 1] = ev;
+                    if (MODE == SEMIGLOBAL) {
+                        const uint64_t key = end_key(hv - oe, n, c + 1);
+                        best = key > best ? key : best;
+                    }
                 }
             }
         };
@@ -174,6 +197,10 @@ __global__ void __launch_bounds__(256, WR <= 8 ? 4 : 2) wave_kernel(WaveArgs A) 
                 } else {
                     if (outH) outH[c + 1] = hv - oe;
                     if (outE) outE[c + 1] = ev;
+                    if (MODE == SEMIGLOBAL) {
+                        const uint64_t key = end_key(hv - oe, n, c + 1);
+                        best = key > best ? key : best;
+                    }
                 }
             }
             __syncwarp();
@@ -209,7 +236,7 @@ __global__ void __launch_bounds__(256, WR <= 8 ? 4 : 2) wave_kernel(WaveArgs A) 
 #pragma unroll
                 for (int r = 0; r < WR; r++) {
                     F[r] = C::addmax(F[r], e_raw, Hoe[r]);
-                    const T M = C::vmax(Ad, F[r]);
+                    const T M = (MODE == LOCAL) ? C::maxrelu(Ad, F[r]) : C::vmax(Ad, F[r]);
                     const T X = C::addc(M, oe_c);
                     const T Adr = Ad;
                     if (r + 1 < WR) Ad = C::addc(Hoe[r], (uint32_t)C::sigma(prof[r + 1], prof[r + 1], sel));
@@ -218,6 +245,13 @@ __global__ void __launch_bounds__(256, WR <= 8 ? 4 : 2) wave_kernel(WaveArgs A) 
                     Ein = E;
                     Hoe[r] = C::addmax(E, oe_raw, X);
                     E = C::addmax(E, e_raw, X);
+                    if (MODE == LOCAL) {
+                        // strict improvement of the row maximum: the column of its first occurrence
+                        if (Hoe[r] > rowmax[r]) {
+                            rowmax[r] = Hoe[r];
+                            rowj[r] = c + 1;
+                        }
+                    }
                     if (TB) {
                         // the predecessor planes of the batched traceback (global mode)
                         const uint32_t fD = C::ge(C::addc(Adr, oe_c), Hoe[r]);  // diagonal reaches H
@@ -233,6 +267,16 @@ __global__ void __launch_bounds__(256, WR <= 8 ? 4 : 2) wave_kernel(WaveArgs A) 
                             // rows r-7..r: bytes s0, s1, E opened, F opened (bit k = row r-7+k)
                             dw[(int64_t)s * WG * (WR / 8) + (r >> 3)] =
                                 prmt(prmt(pl_s0, pl_s1, 0x7351u), prmt(pl_eo, pl_fo, 0x7351u), 0x7632u);
+                        }
+                    }
+                }
+                if (MODE == SEMIGLOBAL && c == m - 1) {
+#pragma unroll
+                    for (int r = 0; r < WR; r++) {
+                        const int32_t i = rb + r - pad;
+                        if (i >= 1) {
+                            const uint64_t key = end_key(Hoe[r] - oe, i, m);
+                            best = key > best ? key : best;
                         }
                     }
                 }
@@ -269,38 +313,71 @@ __global__ void __launch_bounds__(256, WR <= 8 ? 4 : 2) wave_kernel(WaveArgs A) 
         for (int b = drained; b <= (m - 1) / BLOCK; b++) drain(b);
         if (!last && g == 0) st_release(prog_mine, (m + BLOCK - 1) / BLOCK + 1);
         if (last && g == 0) {
-            if (outH) outH[0] = col0(GLOBAL, n, o, e, ps.tb);
-            if (outE) outE[0] = col0(GLOBAL, n, o, e, ps.tb);
+            if (outH) outH[0] = col0(MODE, n, o, e, ps.tb);
+            if (outE) outE[0] = col0(MODE, n, o, e, ps.tb);
+        }
+        if (MODE != GLOBAL) {
+            if (MODE == LOCAL) {
+#pragma unroll
+                for (int r = 0; r < WR; r++) {
+                    const int32_t i = rb + r - pad, v = rowmax[r] - oe;
+                    if (i >= 1 && v > 0) {
+                        const uint64_t key = end_key(v, i, rowj[r]);
+                        best = key > best ? key : best;
+                    }
+                }
+            }
+#pragma unroll
+            for (int off = 16; off >= 1; off >>= 1) {
+                const uint64_t ox = __shfl_xor_sync(0xffffffffu, best, off);
+                best = ox > best ? ox : best;
+            }
+            if (g == 0) atomicMax(reinterpret_cast<unsigned long long *>(A.best) + lo,
+                                  (unsigned long long)best);
         }
     }
 }
 
-template <int WR, bool TB>
+template <int WR, bool TB, int MODE>
 static int blocks_per_sm() {
     int nb = 0;
-    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, wave_kernel<WR, TB>, 256, 0) != cudaSuccess) {
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, wave_kernel<WR, TB, MODE>, 256, 0) != cudaSuccess) {
         cudaGetLastError();
         nb = 1;
     }
     return nb < 1 ? 1 : nb;
 }
 
-int wave_rows_per_lane(int64_t total_rows, int num_sms, int64_t n_passes) {
+int wave_rows_per_lane(int64_t total_rows, int num_sms, int64_t n_passes, int mode) {
+    if (mode == LOCAL) return 8;        // the rows' maxima and columns take registers
+    if (mode == SEMIGLOBAL) return 16;  // its 8-row variant would spill
     // 8-row stripes double the stripes (and the pipeline's skew) and run at 64
     // registers; measured on 100 kbp to 1 Mbp pairs, 16-row stripes win unless
     // the problem is tiny (a few stripes, as a single pair of a thousand rows)
     const int64_t stripes16 = total_rows / (WG * 16) + n_passes;  // upper bound of sum(ceil(n / 512))
-    return 16 * stripes16 <= (int64_t)num_sms * blocks_per_sm<16, false>() * 8 ? 8 : 16;
+    return 16 * stripes16 <= (int64_t)num_sms * blocks_per_sm<16, false, GLOBAL>() * 8 ? 8 : 16;
+}
+
+template <int WR, bool TB, int MODE>
+static void launch_one(const WaveArgs &A, int num_sms, cudaStream_t st) {
+    wave_kernel<WR, TB, MODE><<<num_sms * blocks_per_sm<WR, TB, MODE>(), 256, 0, st>>>(A);
 }
 
 cudaError_t launch_wave(const WaveArgs &A, int num_sms, cudaStream_t st) {
     const bool tb = A.dirs != nullptr;
-    if (A.rows_per_lane == 8) {
-        if (tb) wave_kernel<8, true><<<num_sms * blocks_per_sm<8, true>(), 256, 0, st>>>(A);
-        else wave_kernel<8, false><<<num_sms * blocks_per_sm<8, false>(), 256, 0, st>>>(A);
+    // the stripe table was built for A.rows_per_lane (from wave_rows_per_lane)
+    if (A.mode == LOCAL) {
+        if (A.rows_per_lane != 8 || tb) return cudaErrorInvalidValue;
+        launch_one<8, false, LOCAL>(A, num_sms, st);
+    } else if (A.mode == SEMIGLOBAL) {
+        if (A.rows_per_lane != 16 || tb) return cudaErrorInvalidValue;
+        launch_one<16, false, SEMIGLOBAL>(A, num_sms, st);
+    } else if (A.rows_per_lane == 8) {
+        if (tb) launch_one<8, true, GLOBAL>(A, num_sms, st);
+        else launch_one<8, false, GLOBAL>(A, num_sms, st);
     } else {
-        if (tb) wave_kernel<16, true><<<num_sms * blocks_per_sm<16, true>(), 256, 0, st>>>(A);
-        else wave_kernel<16, false><<<num_sms * blocks_per_sm<16, false>(), 256, 0, st>>>(A);
+        if (tb) launch_one<16, true, GLOBAL>(A, num_sms, st);
+        else launch_one<16, false, GLOBAL>(A, num_sms, st);
     }
     return cudaGetLastError();
 }

@@ -33,12 +33,16 @@ struct WaveArgs {
     int64_t spin_limit;           // iterations of one wait
     int32_t rows_per_lane;        // 8 or 16 (stripes of 32 lanes x rows_per_lane rows)
     uint32_t *dirs;               // optional: traceback direction words (global mode)
+    int32_t mode;                 // GLOBAL, LOCAL or SEMIGLOBAL (every pass of the launch)
+    uint64_t *best;               // local / semi-global: per pass the best cell's key (initialised)
 };
 
 // Rows per lane of a launch: 8 when 16-row stripes would fill less than a
 // sixteenth of the resident warps (twice the stripes, half the per-step chain
 // each), otherwise 16. total_rows = sum of the passes' row counts.
-int wave_rows_per_lane(int64_t total_rows, int num_sms, int64_t n_passes);
+// (Local mode: always 8; semi-global: always 16.) The stripe table of a launch
+// must be built with this value, and WaveArgs.rows_per_lane set to it.
+int wave_rows_per_lane(int64_t total_rows, int num_sms, int64_t n_passes, int mode);
 cudaError_t launch_wave(const WaveArgs &A, int num_sms, cudaStream_t st);
 constexpr int WAVE_LANES = 32;    // lanes per stripe
 constexpr int WAVE_MIN_ROWS = 256;  // rows of the shortest stripe (8 rows per lane)

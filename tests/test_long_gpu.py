@@ -121,3 +121,46 @@ def test_wavefront_wait_limit_reports_timeout(pkg, ctx):
         ctx.set_option("spin_limit", 1 << 24)
     out, _ = ctx.align_long(q, s, pkg.Scoring.make(*C4))
     assert out["score"][0] == oracle.score(q, s, oracle.Scoring(*C4))[0]
+
+
+def tied_long_pairs(seed):
+    """Long pairs whose local / semi-global optimum sits where ties are likely:
+    a repeated block (two equal local alignments at different rows), a query
+    longer than its subject (semi-global last column), and motif repeats."""
+    st = synth.Stream(seed, 1)
+    X = synth.random_codes(st, 700, 4)
+    junk = synth.random_codes(st, 900, 4)
+    tail = synth.random_codes(st, 1200, 4)
+    motif = synth.random_codes(st, 5, 4)
+    return [(np.concatenate([X, junk, X]), X), (X, np.concatenate([X, junk, X])),
+            (np.concatenate([X, tail]), X), (np.concatenate([tail, X]), X),
+            (np.tile(motif, 300), np.tile(motif, 320))]
+
+
+@pytest.mark.parametrize("mode", [1, 2])
+def test_long_local_and_semiglobal_scores(pkg, ctx, mode):
+    """Local and semi-global long pairs on the wavefront: score and optimum cell
+    equal the oracle's under the tie rule (larger score, smaller i, smaller j)."""
+    st = synth.Stream(2500 + mode, 1)
+    pairs = [related(n, extra, seed=2600 + n + mode) for n, extra in ((1, 0), (513, 7), (1800, -40), (3000, 11))]
+    pairs += [(synth.random_codes(st, 2000, 4), synth.random_codes(st, 700, 4)),
+              (synth.random_codes(st, 600, 4), synth.random_codes(st, 2100, 4))]
+    pairs += tied_long_pairs(2700 + mode)
+    for args in (C4, (1, -4, -6, -1), (2, -1, 0, -1)):
+        for q, s in pairs:
+            out, _ = ctx.align_long(q, s, pkg.Scoring.make(*args), mode=mode)
+            want = oracle.score(q, s, oracle.Scoring(*args), mode)
+            got = (int(out["score"][0]), int(out["end_q"][0]), int(out["end_s"][0]))
+            assert got == tuple(int(x) for x in want), (len(q), len(s), args, got, want)
+
+
+@pytest.mark.parametrize("mode", [1, 2])
+def test_small_batches_on_the_wavefront_all_modes(pkg, ctx, mode):
+    """A batch of a few large pairs (score and optimum cell) takes the wavefront
+    in every mode; an empty pair in the batch gets the empty alignment."""
+    pairs = tied_long_pairs(2800 + mode)[:3] + [(related(900, 5, seed=2900)[0], np.zeros(0, np.uint8))]
+    b = synth.from_pairs(pairs)
+    out, _ = ctx.align_batch(b.q, b.q_off, b.s, b.s_off, pkg.Scoring.make(*C4), mode)
+    want = oracle.score_batch(b, oracle.Scoring(*C4), mode)
+    assert np.array_equal(out["score"], want[0])
+    assert np.array_equal(out["end_q"], want[1]) and np.array_equal(out["end_s"], want[2])

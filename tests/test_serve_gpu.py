@@ -2,8 +2,8 @@
 
 * pairs submitted from several threads, of sizes on both sides of the
   long-pair threshold, come back with the oracle's score and optimum cell;
-* small pairs are batched (fewer batches than requests), long global pairs
-  take the wavefront path (long_pairs statistic);
+* small pairs are batched (fewer batches than requests), long pairs take the
+  wavefront path in every mode (long_pairs statistic);
 * admission: a submit beyond the letter budget is refused with ERR_BUDGET and
   queues nothing, and a refused caller can submit again once the server drains;
 * a wait with a short limit on an unfinished ticket reports ERR_TIMEOUT and
@@ -69,7 +69,7 @@ def test_server_results_match_oracle(pkg, mode):
         assert srv.stat("completed") == len(pairs)
         assert srv.stat("batches") < len(pairs)
         n_long = sum(1 for q, s in pairs if len(q) * len(s) >= 4_000_000)
-        assert srv.stat("long_pairs") == (n_long if mode == 0 else 0)
+        assert srv.stat("long_pairs") == n_long
         assert srv.stat("held_bytes") == 0
     finally:
         srv.close()
