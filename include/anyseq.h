@@ -198,7 +198,10 @@ anyseq_status_t anyseq_set_option(anyseq_ctx *ctx, const char *key, int64_t valu
  * (cells relaxed by banded passes), "band_accepted", "band_fallback" (pairs),
  * "band_rounds", and the host time of its phases "band_plan_ms" (packing,
  * features, network, band plan), "band_pass_ms" (banded passes with the
- * certificate), "band_full_ms" (full DP of the rest). Unknown keys: ANYSEQ_ERR_ARG. */
+ * certificate), "band_full_ms" (full DP of the rest). Of the context, not the
+ * call: "tuned_bins" (length bins with a tuned cap), "autotune_gain" (default
+ * time / tuned time on the tuning sample; 1 when untuned). Unknown keys:
+ * ANYSEQ_ERR_ARG. */
 anyseq_status_t anyseq_get_stat(anyseq_ctx *ctx, const char *key, double *value);
 
 /*
@@ -230,6 +233,26 @@ const char *anyseq_last_error(void);
 
 /* Library version string. */
 const char *anyseq_version(void);
+
+/* Autotuner of the batched path (not in the paper). The sample (arguments as
+ * for anyseq_align_batch, score only; synchronous) is aligned once per
+ * candidate tile shape (rows per lane capped at 4, 8, 12 or 16) while the
+ * kernel counts SM cycles and cells per length bin (the 8-bit logarithmic
+ * bucket of a work item's longest query); each bin takes the cap with the
+ * fewest cycles per cell. Then the whole sample is timed (CUDA events, median
+ * of five) under the default shape, each smaller uniform cap and the per-bin
+ * table; the fastest is kept if it beats the default by 1 %, else the context
+ * stays untuned. Later calls of the context use the table for the kernels
+ * without traceback and substitution matrix; results do not change.
+ * anyseq_set_option(ctx, "autotune_reset", 0) drops it; anyseq_autotune_table
+ * copies the 256 caps (0 = default) to the host, and anyseq_autotune_set_table
+ * installs a saved table (host array of 256 caps, each 0, 4, 8, 12 or 16,
+ * else ERR_ARG; synchronous). */
+anyseq_status_t anyseq_autotune(anyseq_ctx *ctx, const uint8_t *q, const int64_t *q_off,
+                                const uint8_t *s, const int64_t *s_off, int64_t n_pairs,
+                                const anyseq_scoring_t *sc, int32_t mode, void *cuda_stream);
+anyseq_status_t anyseq_autotune_table(anyseq_ctx *ctx, uint8_t *caps);
+anyseq_status_t anyseq_autotune_set_table(anyseq_ctx *ctx, const uint8_t *caps);
 
 /* Gapped strings of one alignment (the output form of the paper's one-pair
  * interface, Sec. III-C listing): from the letter codes q[0..n), s[0..m), the

@@ -70,7 +70,8 @@ EXPORTS = ["anyseq_create", "anyseq_destroy", "anyseq_align_batch", "anyseq_alig
            "anyseq_band_gradient", "anyseq_band_train", "anyseq_align_long_noalloc",
            "anyseq_server_create", "anyseq_server_submit", "anyseq_server_wait", "anyseq_server_stat",
            "anyseq_server_destroy", "anyseq_plan_create", "anyseq_plan_buffers", "anyseq_plan_run",
-           "anyseq_plan_wait", "anyseq_plan_destroy", "anyseq_gapped"]
+           "anyseq_plan_wait", "anyseq_plan_destroy", "anyseq_gapped", "anyseq_autotune",
+           "anyseq_autotune_table", "anyseq_autotune_set_table"]
 NOALLOC_MAX_LEN = 1048576
 BAND_FEATURES = 64
 BAND_PARAMS = 25090
@@ -121,6 +122,9 @@ def load(build_if_missing: bool = False):
     lib.anyseq_plan_run.argtypes = [P, P]
     lib.anyseq_plan_wait.argtypes = [P, P]
     lib.anyseq_plan_destroy.argtypes = [P]
+    lib.anyseq_autotune.argtypes = [P, P, P, P, P, I64, P, I32, P]
+    lib.anyseq_autotune_table.argtypes = [P, P]
+    lib.anyseq_autotune_set_table.argtypes = [P, P]
     lib.anyseq_gapped.argtypes = [P, I64, P, I64, I32, I32, P, U32, ctypes.c_char_p, I32, P, P, I64,
                                   ctypes.POINTER(I64)]
     lib.anyseq_last_error.restype = ctypes.c_char_p
@@ -133,7 +137,8 @@ def load(build_if_missing: bool = False):
                  "anyseq_align_long_noalloc", "anyseq_server_create", "anyseq_server_submit",
                  "anyseq_server_wait", "anyseq_server_stat", "anyseq_server_destroy", "anyseq_plan_create",
                  "anyseq_plan_buffers", "anyseq_plan_run", "anyseq_plan_wait", "anyseq_plan_destroy",
-                 "anyseq_gapped"]:
+                 "anyseq_gapped", "anyseq_autotune", "anyseq_autotune_table",
+                 "anyseq_autotune_set_table"]:
         getattr(lib, name).restype = ctypes.c_int
     _lib = lib
     return lib
@@ -226,6 +231,21 @@ class Context:
 
 
     # ---------------------------------------------------------------- learned band
+    def autotune(self, q, q_off, s, s_off, scoring: Scoring, mode: int = GLOBAL, stream=None):
+        """anyseq_autotune on a sample; returns the 256 per-bin caps (0 = default)."""
+        _check(load().anyseq_autotune(self.h, _ptr(q), _ptr(q_off), _ptr(s), _ptr(s_off), len(q_off) - 1,
+                                      ctypes.byref(scoring), mode, _stream_handle(stream)))
+        caps = np.zeros(256, dtype=np.uint8)
+        _check(load().anyseq_autotune_table(self.h, _ptr(caps)))
+        return caps
+
+    def autotune_set_table(self, caps):
+        """anyseq_autotune_set_table: install a saved table of 256 caps."""
+        caps = np.ascontiguousarray(caps, dtype=np.uint8)
+        if caps.shape != (256,):
+            raise ValueError("the table holds 256 caps")
+        _check(load().anyseq_autotune_set_table(self.h, _ptr(caps)))
+
     def band_features(self, q, q_off, s, s_off, out=None, stream=None):
         n_pairs = len(q_off) - 1
         if out is None:

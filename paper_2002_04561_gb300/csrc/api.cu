@@ -114,6 +114,12 @@ extern "C" anyseq_status_t anyseq_set_option(anyseq_ctx *ctx, const char *key, i
         ctx->band_area16_pct = (int32_t)value;
         return ANYSEQ_OK;
     }
+    if (!strcmp(key, "autotune_reset")) {
+        ctx->tuned = false;
+        ctx->tune_gain = 1.0;
+        memset(ctx->tune_tab, 0, sizeof(ctx->tune_tab));
+        return ANYSEQ_OK;
+    }
     if (!strcmp(key, "spin_limit")) {
         if (value < 1) return fail(ANYSEQ_ERR_ARG, "spin_limit must be >= 1");
         ctx->spin_limit = value;
@@ -139,6 +145,12 @@ extern "C" anyseq_status_t anyseq_get_stat(anyseq_ctx *ctx, const char *key, dou
     else if (!strcmp(key, "band_accepted")) *value = (double)ctx->band_accepted;
     else if (!strcmp(key, "band_fallback")) *value = (double)ctx->band_fallback;
     else if (!strcmp(key, "band_rounds")) *value = (double)ctx->band_rounds;
+    else if (!strcmp(key, "tuned_bins")) {
+        int64_t k = 0;
+        for (int b = 0; b < 256; b++) k += ctx->tuned && ctx->tune_tab[b] != 0;
+        *value = (double)k;
+    }
+    else if (!strcmp(key, "autotune_gain")) *value = ctx->tune_gain;
     else if (!strcmp(key, "band_plan_ms")) *value = ctx->band_plan_ms;
     else if (!strcmp(key, "band_pass_ms")) *value = ctx->band_pass_ms;
     else if (!strcmp(key, "band_full_ms")) *value = ctx->band_full_ms;
@@ -372,6 +384,8 @@ anyseq_status_t anyseq::batch_scores(anyseq_ctx *ctx, const BatchInput &in, cons
     }
     A.o = sc->gap_open; A.e = sc->gap_extend;
     A.score = score; A.end_q = eq; A.end_s = es; A.flags = flags;
+    A.rmax_tab = ctx->tuned ? ctx->d_tune_tab : nullptr;
+    A.bin_stats = ctx->d_bin_stats;
     A.counter = arena<int32_t>(ctx, "counter", 4, &s2);
     if (s2 != ANYSEQ_OK) return s2;
     if (tb) {
@@ -405,9 +419,11 @@ anyseq_status_t anyseq::batch_scores(anyseq_ctx *ctx, const BatchInput &in, cons
         A.n_list = P.counts + cell32;
         A.scratch = nullptr;
         A.scratch_cols = 0;
-        // border rows between row chunks: the smallest chunk of any variant is
-        // GROUP * TB_R = 128 rows (traceback), so longer queries need scratch
-        if (in.max_n > GROUP * TB_R) {
+        // border rows between row chunks: the smallest chunk of any untuned
+        // variant is GROUP * TB_R = 128 rows (traceback); a tuned table can
+        // cap a chunk at GROUP * 4 rows. Longer queries need scratch.
+        const int32_t min_chunk = GROUP * (A.rmax_tab ? TUNE_MIN_R : TB_R);
+        if (in.max_n > min_chunk) {
             A.scratch_cols = in.max_m + 1;
             A.scratch = arena<int32_t>(ctx, "border", (size_t)grid * (sigp ? 8 : 16) * 2 * (size_t)A.scratch_cols, &s2);
             if (s2 != ANYSEQ_OK) return s2;

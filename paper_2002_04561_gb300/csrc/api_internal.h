@@ -38,6 +38,13 @@ struct anyseq_ctx {
     double dp_ms = 0, dp32_ms = 0;
     int64_t pairs16 = 0, pairs32 = 0;
     int32_t *bad_code = nullptr;  // letter-check flag of the last captured batch (graph plans)
+    // autotuning: rows-per-lane cap per length bin (0 = the kernel's own), its
+    // device copy (when tuned), and the per-bin statistics buffer of a tuning run
+    uint8_t tune_tab[256] = {0};
+    uint8_t *d_tune_tab = nullptr;
+    unsigned long long *d_bin_stats = nullptr;
+    bool tuned = false;
+    double tune_gain = 1.0;  // default time / tuned time on the tuning sample
     std::vector<Buf> bufs;        // device scratch, grown on demand, reused across calls
     std::vector<Buf> pinned;      // pinned host staging
     // Named device buffer of at least 'bytes'; contents are not preserved on growth.

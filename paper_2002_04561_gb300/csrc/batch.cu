@@ -393,6 +393,18 @@ __global__ void __launch_bounds__(SIGP ? 128 : 256, SIGP ? 4 : 2) batch_kernel(B
         if (item >= n_items) break;
         ItemPlan P = plan_item(A.list, n_list, item, per_item, A.q_off, A.s_off, RMAX, !(TB || SIGP));
         if (TB || SIGP) P.R = TB_R;
+        uint32_t tbin = 0;
+        if (!(TB || SIGP) && (A.rmax_tab || A.bin_stats)) {
+            // the tuned tile shape of this item's length bin (rows per lane cap)
+            int32_t nmax = 0;
+            for (int kk = 0; kk < per_item; kk++) nmax = max(nmax, P.n[kk]);
+            tbin = lbucket(nmax);
+            const int cap = A.rmax_tab ? (int)A.rmax_tab[tbin] : 0;
+            if (cap > 0 && cap < RMAX)
+                P = plan_item(A.list, n_list, item, per_item, A.q_off, A.s_off, cap, true);
+        }
+        long long t_item = 0;
+        if (A.bin_stats && lane == 0) t_item = clock64();
         Slot sl;
         int32_t pid[2] = {-1, -1};
 #pragma unroll
@@ -426,6 +438,13 @@ __global__ void __launch_bounds__(SIGP ? 128 : 256, SIGP ? 4 : 2) batch_kernel(B
                 case 14: run_slot<C, MODE, (RMAX < 14 ? RMAX : 14), TB, SIGP>(A, sm, sl, P.nch, P.Mit, g, gslot, res, pid, qp, tab, lc); break;
                 default: run_slot<C, MODE, RMAX, TB, SIGP>(A, sm, sl, P.nch, P.Mit, g, gslot, res, pid, qp, tab, lc); break;
             }
+        }
+        if (A.bin_stats && lane == 0) {
+            // SM cycles of the item and its cells, per length bin (autotuning)
+            unsigned long long cells = 0;
+            for (int kk = 0; kk < per_item; kk++) cells += (unsigned long long)P.n[kk] * (unsigned long long)P.m[kk];
+            atomicAdd(&A.bin_stats[2 * tbin], (unsigned long long)(clock64() - t_item));
+            atomicAdd(&A.bin_stats[2 * tbin + 1], cells);
         }
         if (g == 0) {
 #pragma unroll

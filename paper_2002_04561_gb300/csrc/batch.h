@@ -24,6 +24,18 @@ __host__ __device__ __forceinline__ bool fits_int16(int64_t n, int64_t m, int32_
     return hi <= 16000 && lo >= -16000 && (mode != LOCAL || m < 65535);
 }
 
+// 8-bit logarithmic length bucket, 8 sub-steps per octave.
+__host__ __device__ __forceinline__ uint32_t lbucket(int64_t x) {
+    if (x < 16) return (uint32_t)x;
+#ifdef __CUDA_ARCH__
+    const int lg = 63 - __clzll(x);
+#else
+    const int lg = 63 - __builtin_clzll((unsigned long long)x);
+#endif
+    uint32_t q = 16u + (uint32_t)(lg - 4) * 8u + (uint32_t)((x >> (lg - 3)) & 7);
+    return q > 255u ? 255u : q;
+}
+
 struct BatchArgs {
     const uint32_t *q2, *s2;        // 2-bit packed letters, 16 per word, global positions
     const int64_t *q_off, *s_off;   // n_pairs + 1 offsets
@@ -46,6 +58,11 @@ struct BatchArgs {
     uint32_t *dirs;
     const int64_t *dir_base;
     int32_t *lay_pad, *lay_ch0;
+    // autotuning (row-profile kernels without traceback): the rows-per-lane cap
+    // per length bin of a work item's longest query (0: the kernel's own), and
+    // optional per-bin statistics (SM cycles, cells) of the items
+    const uint8_t *rmax_tab;
+    unsigned long long *bin_stats;
 };
 
 // Work item of the persistent batched kernels: per_item consecutive pairs of a
@@ -95,6 +112,8 @@ int batch_blocks_per_sm(int cell32, int mode, int tb, int sigp, int alphabet);
 constexpr int QP_ROWS = 128;        // rows of the shared-memory query profile (chunk of 16 lanes x 8 rows)
 // Rows per lane of the traceback kernels (one 32-bit direction word per lane, step and pair).
 constexpr int TB_R = 8;
+// Smallest rows-per-lane cap a tuned table may set (a chunk of GROUP * 4 rows).
+constexpr int TUNE_MIN_R = 4;
 
 // Packing, range tests and length binning (pack.cu).
 struct PrepArgs {

@@ -43,13 +43,6 @@ __global__ void validate_kernel(const uint8_t *codes, int64_t len, int32_t alpha
         if (codes[k] >= alphabet) *bad = 1;
 }
 
-// 8-bit logarithmic length bucket, 8 sub-steps per octave.
-__device__ __forceinline__ uint32_t lbucket(int64_t x) {
-    if (x < 16) return (uint32_t)x;
-    int lg = 63 - __clzll(x);
-    uint32_t q = 16u + (uint32_t)(lg - 4) * 8u + (uint32_t)((x >> (lg - 3)) & 7);
-    return q > 255u ? 255u : q;
-}
 
 
 __global__ void bin_kernel(PrepArgs P) {

@@ -253,3 +253,50 @@ def test_designed_optimum_cells(pkg, ctx, mode, force32):
     b = designed_optimum_pairs()
     for sc_args in SCHEMES + [(1, -1, 0, 0)]:
         assert_parity(run(pkg, ctx, b, sc_args, mode, force32=force32), oracle_of(b, sc_args, mode), b)
+
+
+@pytest.mark.parametrize("mode", [0, 2])
+def test_autotuned_tile_shapes_keep_results(pkg, ctx, mode):
+    """The autotuner picks a rows-per-lane cap per length bin from measured SM
+    cycles per cell; results with the tuned table equal the untuned ones and the
+    oracle's (sampled), and every cap is one of the candidates."""
+    b = synth.random_pairs(3000, 10, 600, seed=9600, related=0.7, p_sub=0.05, p_indel=0.02)
+    sc_args = (1, -4, -6, -1)
+    before = run(pkg, ctx, b, sc_args, mode)
+    try:
+        caps = ctx.autotune(dev(b.q), dev(b.q_off), dev(b.s), dev(b.s_off), pkg.Scoring.make(*sc_args), mode)
+        assert set(np.unique(caps)) <= {0, 4, 8, 12}
+        assert ctx.stat("autotune_gain") >= 1.0
+        assert ctx.stat("tuned_bins") == int(np.count_nonzero(caps))
+        after = run(pkg, ctx, b, sc_args, mode)
+        assert np.array_equal(before, after)
+        idx = np.arange(0, b.n_pairs, 23)
+        assert_parity(after[idx], oracle_of(b.subset(idx), sc_args, mode), b.subset(idx))
+    finally:
+        ctx.set_option("autotune_reset", 0)
+
+
+@pytest.mark.parametrize("mode", [0, 1, 2])
+@pytest.mark.parametrize("cap", [4, 8, 12])
+def test_forced_tile_caps_match_oracle(pkg, ctx, mode, cap):
+    """Every bin forced to one rows-per-lane cap: queries of 65-128 letters then
+    span two or more row chunks of 16 x cap rows (the border scratch must exist
+    even though no query is longer than 128), and longer ones many."""
+    sc_args = (1, -4, -6, -1)
+    try:
+        ctx.autotune_set_table(np.full(256, cap, np.uint8))
+        for lo, hi, seed in ((65, 128, 9700), (1, 700, 9701)):
+            b = synth.random_pairs(700, lo, hi, seed=seed + cap, related=0.7, p_sub=0.05, p_indel=0.02)
+            got = run(pkg, ctx, b, sc_args, mode)
+            assert_parity(got, oracle_of(b, sc_args, mode), b)
+    finally:
+        ctx.set_option("autotune_reset", 0)
+
+
+def test_set_table_rejects_bad_caps(pkg, ctx):
+    bad = np.zeros(256, np.uint8)
+    bad[17] = 5
+    with pytest.raises(pkg.AnyseqError) as ei:
+        ctx.autotune_set_table(bad)
+    assert ei.value.status == 1
+    assert ctx.stat("tuned_bins") == 0
