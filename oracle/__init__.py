@@ -65,9 +65,10 @@ def _load():
             lib.orc_align.argtypes = [P, I64, P, I64, P, ctypes.c_int, P, P, I64, P]
             lib.orc_last_row.argtypes = [P, I64, P, I64, P, I64, ctypes.c_int, P, P]
             lib.orc_hirschberg.argtypes = [P, I64, P, I64, P, I64, P, I64, P, P]
+            lib.orc_start_cell.argtypes = [P, I64, P, I64, P, ctypes.c_int, P, P, P]
             lib.orc_score_batch.argtypes = [P, P, P, P, I64, I64, P, ctypes.c_int, P]
             lib.orc_align_batch.argtypes = [P, P, P, P, I64, I64, P, ctypes.c_int, P, P, P, P]
-            for f in (lib.orc_score, lib.orc_align, lib.orc_last_row, lib.orc_hirschberg,
+            for f in (lib.orc_score, lib.orc_align, lib.orc_last_row, lib.orc_hirschberg, lib.orc_start_cell,
                       lib.orc_score_batch, lib.orc_align_batch):
                 f.restype = ctypes.c_int
             _lib = lib
@@ -167,6 +168,42 @@ def hirschberg(q, s, sc: Scoring, base_cells: int = BASE_CELLS):
     _check(lib.orc_hirschberg(_ptr(q), len(q), _ptr(s), len(s), ctypes.byref(st), base_cells,
                               _ptr(cig), cap, ctypes.byref(n_c), ctypes.byref(cells)), "hirschberg")
     return cig[:n_c.value].copy(), int(cells.value)
+
+
+def start_cell(q, s, sc: Scoring, mode: int):
+    """(G, i, j): the start of largest G(i, j) = global score of q[i:] against
+    s[j:] (local: any start; semi-global: i == 0 or j == 0), ties: largest i,
+    then largest j (anyseq_oracle.c, orc_start_cell)."""
+    lib = _load()
+    q, s = _u8(q), _u8(s)
+    st, keep = sc._c()
+    g, i, j = ctypes.c_int64(0), ctypes.c_int64(0), ctypes.c_int64(0)
+    _check(lib.orc_start_cell(_ptr(q), len(q), _ptr(s), len(s), ctypes.byref(st), mode,
+                              ctypes.byref(g), ctypes.byref(i), ctypes.byref(j)), "start_cell")
+    return int(g.value), int(i.value), int(j.value)
+
+
+def long_alignment(q, s, sc: Scoring, mode: int = GLOBAL, base_cells: int = BASE_CELLS):
+    """The linear-space alignment of one long pair, in every mode:
+    (score, (beg_q, beg_s), (end_q, end_s), cigar).
+
+    Global: the divide-and-conquer CIGAR of the whole pair. Local and
+    semi-global: the optimum cell (score()), the start cell (start_cell() over
+    the prefixes ending there), and the divide-and-conquer CIGAR of the two
+    substrings between them; an empty optimum (score 0) begins at its end."""
+    q, s = _u8(q), _u8(s)
+    if mode == GLOBAL:
+        S, _, _ = score(q, s, sc, GLOBAL)
+        cig, _ = hirschberg(q, s, sc, base_cells)
+        return S, (0, 0), (len(q), len(s)), cig
+    S, ei, ej = score(q, s, sc, mode)
+    if S <= 0 or ei == 0 or ej == 0:
+        return S, (ei, ej), (ei, ej), np.zeros(0, dtype=np.uint32)
+    G, bi, bj = start_cell(q[:ei], s[:ej], sc, mode)
+    if G != S:
+        raise RuntimeError(f"oracle start cell: G = {G}, optimum {S}")
+    cig, _ = hirschberg(q[bi:ei], s[bj:ej], sc, base_cells)
+    return S, (bi, bj), (ei, ej), cig
 
 
 def _chunks(n: int, threads: int):

@@ -432,6 +432,62 @@ int orc_hirschberg(const uint8_t *q, int64_t n, const uint8_t *s, int64_t m,
     return rc;
 }
 
+/* ------------------------------------------- start of a long-pair traceback */
+
+/*
+ * Local and semi-global long pairs are traced back in linear space: the
+ * alignment ends at the optimum cell (ei, ej) of score S (orc_score), and
+ * between its start and that cell it is a global alignment (Eq. 1 with global
+ * initialisation) of the two substrings. For every start (i, j), i <= ei and
+ * j <= ej, G(i, j) = global score of q[i..ei) against s[j..ej); the optimal
+ * alignments ending at (ei, ej) are those whose start has G = S, among the
+ * starts the mode allows (local: any cell; semi-global: row 0 or column 0,
+ * where its free leading gaps end). The start taken is the allowed cell of
+ * largest G, ties: largest i, then largest j.
+ *
+ * G over all starts is one DP over the reversed prefixes (the recurrences of
+ * orc_last_row, reading q and s from ei and ej backwards): cell (r, c) is the
+ * start (ei - r, ej - c). Scanning r and then c upwards and keeping strict
+ * improvements gives the tie rule.
+ */
+int orc_start_cell(const uint8_t *q, int64_t ei, const uint8_t *s, int64_t ej,
+                   const orc_scoring *sc, int mode, int64_t *best, int64_t *bi, int64_t *bj) {
+    const sc_t o = sc->gap_open, e = sc->gap_extend;
+    sc_t *CC = (sc_t *)malloc((size_t)(ej + 1) * sizeof(sc_t));
+    sc_t *DD = (sc_t *)malloc((size_t)(ej + 1) * sizeof(sc_t));
+    if (!CC || !DD) { free(CC); free(DD); return ORC_ERR_MEM; }
+    sc_t bv = NEG_INF; int64_t br = 0, bc = 0;
+#define ORC_START_CAND(r, c, v)                                                        \
+    do {                                                                               \
+        int ok = mode == ORC_LOCAL || (r) == ei || (c) == ej;                          \
+        if (ok && (v) > bv) { bv = (v); br = (r); bc = (c); }                           \
+    } while (0)
+    CC[0] = 0; DD[0] = NEG_INF;
+    for (int64_t c = 1; c <= ej; c++) { CC[c] = o + c * e; DD[c] = NEG_INF; }
+    for (int64_t c = 0; c <= ej; c++) ORC_START_CAND(0, c, CC[c]);
+    for (int64_t r = 1; r <= ei; r++) {
+        uint8_t qi = q[ei - r];
+        sc_t diag = CC[0];
+        CC[0] = o + r * e;
+        DD[0] = CC[0];
+        ORC_START_CAND(r, 0, CC[0]);
+        sc_t Fv = NEG_INF;
+        for (int64_t c = 1; c <= ej; c++) {
+            uint8_t sj = s[ej - c];
+            sc_t Ev = max2(DD[c] + e, CC[c] + o + e);
+            Fv = max2(Fv + e, CC[c - 1] + o + e);
+            sc_t Hv = max2(max2(diag + sigma(sc, qi, sj), Ev), Fv);
+            diag = CC[c];
+            CC[c] = Hv; DD[c] = Ev;
+            ORC_START_CAND(r, c, Hv);
+        }
+    }
+#undef ORC_START_CAND
+    free(CC); free(DD);
+    *best = bv; *bi = ei - br; *bj = ej - bc;
+    return ORC_OK;
+}
+
 /* --------------------------------------------------------------- batches */
 
 /* Score-only over pairs [p0, p1) of a batch (offsets index the code arrays). */

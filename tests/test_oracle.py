@@ -247,3 +247,74 @@ def test_last_row_E_is_best_gap_ending():
         for j in range(1, len(s) + 1):
             cands = [score_ops(o, q, s[:j], sc) for o in op_strings(len(q), j) if o.endswith("I")]
             assert DD[j] == max(cands)
+
+
+# ---------------------------------------------------------------- start cell of a long-pair traceback
+# schemes for the start cell: mismatch 0 makes tied starts common (a mismatch
+# before the core costs nothing), and the others make an interior start beat
+# every start on the edge of a semi-global matrix
+START_SCHEMES = [oracle.Scoring(1, 0, -2, -1), oracle.Scoring(2, -3, -5, -2), oracle.Scoring(1, -4, -6, -1),
+                 oracle.Scoring(0, 0, -3, -1, matrix=asym_matrix())]
+
+
+@pytest.mark.parametrize("mode", [oracle.LOCAL, oracle.SEMIGLOBAL])
+@pytest.mark.parametrize("sc", START_SCHEMES)
+def test_start_cell_against_brute_force(sc, mode):
+    """For every allowed start (i, j) up to the optimum cell, the best global
+    score of q[i:ei] against s[j:ej] by enumeration of explicit alignments: its
+    maximum is the optimum, and the oracle's start is the largest i, then the
+    largest j, reaching it. The CIGAR then re-scores to the optimum from the
+    start to the optimum cell."""
+    for q, s in tiny_pairs(16, 2, 6, 1200 + mode, alphabet=3):
+        S, (bi, bj), (ei, ej), cig = oracle.long_alignment(q, s, sc, mode)
+        assert S == (best_local(q, s, sc) if mode == oracle.LOCAL else best_semiglobal(q, s, sc))
+        if S == 0:
+            assert (bi, bj) == (ei, ej) and len(cig) == 0
+            continue
+        starts = [(i, j) for i in range(ei + 1) for j in range(ej + 1)
+                  if (i, j) != (ei, ej) and (mode == oracle.LOCAL or i == 0 or j == 0)]
+        g = {st: best_global(q[st[0]:ei], s[st[1]:ej], sc) for st in starts}
+        assert max(g.values()) == S
+        assert (bi, bj) == max(st for st in starts if g[st] == S)
+        assert rescore_cigar(cig, q, s, (bi, bj), sc) == (S, ei, ej)
+
+
+def test_start_cell_planted_cases():
+    sc = oracle.Scoring(2, -3, -5, -2)
+    st = synth.Stream(1300, 1)
+    core = synth.random_codes(st, 40, 4)
+    # semi-global: q inside s, so the alignment starts in row 0 at the insertion point
+    s = np.concatenate([synth.random_codes(st, 17, 4), core, synth.random_codes(st, 9, 4)])
+    S, beg, end, cig = oracle.long_alignment(core, s, sc, oracle.SEMIGLOBAL)
+    assert (S, beg, end, cigar_ops(cig)) == (80, (0, 17), (40, 57), "M" * 40)
+    # local: the planted core between unrelated flanks of A against flanks of C
+    q = np.concatenate([np.zeros(12, np.uint8), core, np.zeros(5, np.uint8)])
+    s = np.concatenate([np.full(30, 1, np.uint8), core, np.full(7, 1, np.uint8)])
+    S, beg, end, cig = oracle.long_alignment(q, s, sc, oracle.LOCAL)
+    assert S >= 80 and rescore_cigar(cig, q, s, beg, sc) == (S, end[0], end[1])
+    assert beg[0] <= 12 and end[0] >= 52 and beg[1] <= 30 and end[1] >= 70
+    # tied local starts (mismatch 0): the later start, without the free mismatch
+    sc0 = oracle.Scoring(1, 0, -2, -1)
+    S, beg, end, cig = oracle.long_alignment(np.array([0, 1], np.uint8), np.array([2, 1], np.uint8), sc0, oracle.LOCAL)
+    assert (S, beg, end, cigar_ops(cig)) == (1, (1, 1), (2, 2), "M")
+    # semi-global: the interior start (1, 1) would score 4 (AC against AC), but a
+    # start must lie in row 0 or column 0; from (0, 0): T/G mismatch, then AC
+    q3, s3 = np.array([3, 0, 1], np.uint8), np.array([2, 0, 1], np.uint8)
+    S, beg, end, cig = oracle.long_alignment(q3, s3, sc, oracle.SEMIGLOBAL)
+    assert (S, beg, end, cigar_ops(cig)) == (1, (0, 0), (3, 3), "MMM")
+    # no positive cell: the empty local alignment at (0, 0)
+    S, beg, end, cig = oracle.long_alignment(np.zeros(9, np.uint8), np.full(7, 2, np.uint8), sc, oracle.LOCAL)
+    assert (S, beg, end, len(cig)) == (0, (0, 0), (0, 0), 0)
+
+
+@pytest.mark.parametrize("mode", [oracle.LOCAL, oracle.SEMIGLOBAL])
+def test_long_alignment_agrees_with_full_traceback(mode):
+    """Same score and optimum cell as the full-matrix traceback, and both CIGARs
+    re-score to that score (ties may give different paths)."""
+    sc = oracle.Scoring(2, -3, -5, -2)
+    for q, s in tiny_pairs(20, 30, 120, 1400 + mode):
+        S, beg, end, cig = oracle.long_alignment(q, s, sc, mode, base_cells=64)
+        S2, beg2, end2, cig2 = oracle.align(q, s, sc, mode)
+        assert (S, end) == (S2, end2)
+        assert rescore_cigar(cig, q, s, beg, sc) == (S, end[0], end[1])
+        assert rescore_cigar(cig2, q, s, beg2, sc) == (S2, end2[0], end2[1])
