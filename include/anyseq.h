@@ -113,7 +113,10 @@ anyseq_status_t anyseq_destroy(anyseq_ctx *ctx);
  *                 returns ANYSEQ_ERR_CAPACITY with *cigar_used = words needed; NULL/0 allowed otherwise.
  *   cuda_stream   cudaStream_t (NULL = legacy default stream)
  * Errors: ERR_ARG (null pointers, decreasing offsets, open/extend > 0, alphabet out of
- * range, mode unknown), ERR_ALPHABET (a code >= alphabet), ERR_BUDGET, ERR_CUDA.
+ * range, mode unknown, a pair of 2^21 letters or more, and in local and
+ * semi-global mode a pair whose score could reach 2^21: largest positive
+ * substitution score times min(n, m)), ERR_ALPHABET (a code >= alphabet),
+ * ERR_BUDGET, ERR_CUDA.
  */
 anyseq_status_t anyseq_align_batch(anyseq_ctx *ctx,
                                    const uint8_t *q, const int64_t *q_off,
@@ -128,9 +131,17 @@ anyseq_status_t anyseq_align_batch(anyseq_ctx *ctx,
  * Align one long pair (intra-sequence parallelism: anti-diagonal wavefront of
  * row stripes, Sec. IV-C), score in linear space, and with ANYSEQ_WANT_CIGAR
  * the divide-and-conquer traceback of Sec. III-A (Myers-Miller for affine
- * gaps). Only ANYSEQ_GLOBAL supports ANYSEQ_WANT_CIGAR; ANYSEQ_LOCAL and
- * ANYSEQ_SEMIGLOBAL give score and optimum cell (lengths below 2^21). Arguments
- * as for anyseq_align_batch with one pair of lengths n and m.
+ * gaps). Global: the CIGAR of the whole pair. ANYSEQ_LOCAL and
+ * ANYSEQ_SEMIGLOBAL (lengths below 2^21): the alignment ends at the optimum
+ * cell; its start (beg_q, beg_s) is the start of largest beg_q, then largest
+ * beg_s, among the optimal alignments ending there (any cell for local, row 0
+ * or column 0 for semi-global), found by one more wavefront pass over the
+ * reversed prefixes; the CIGAR is the global divide-and-conquer CIGAR of
+ * q[beg_q .. end_q) against s[beg_s .. end_s). An empty optimum (score 0) has
+ * no CIGAR words and begins at its end. Arguments as for anyseq_align_batch
+ * with one pair of lengths n and m. Errors as there, and ERR_ARG for local and
+ * semi-global pairs whose score could reach 2^21 (largest positive
+ * substitution score times min(n, m)).
  */
 anyseq_status_t anyseq_align_long(anyseq_ctx *ctx,
                                   const uint8_t *q, int64_t n,

@@ -230,7 +230,7 @@ class Context:
         return out, used.value
 
 
-    # ---------------------------------------------------------------- learned band
+    # ---------------------------------------------------------------- autotuner
     def autotune(self, q, q_off, s, s_off, scoring: Scoring, mode: int = GLOBAL, stream=None):
         """anyseq_autotune on a sample; returns the 256 per-bin caps (0 = default)."""
         _check(load().anyseq_autotune(self.h, _ptr(q), _ptr(q_off), _ptr(s), _ptr(s_off), len(q_off) - 1,
@@ -246,6 +246,7 @@ class Context:
             raise ValueError("the table holds 256 caps")
         _check(load().anyseq_autotune_set_table(self.h, _ptr(caps)))
 
+    # ---------------------------------------------------------------- learned band
     def band_features(self, q, q_off, s, s_off, out=None, stream=None):
         n_pairs = len(q_off) - 1
         if out is None:

@@ -220,29 +220,36 @@ anyseq_status_t anyseq::make_rowprof(const anyseq_scoring_t *sc, int32_t mode, u
 }
 
 __global__ void len_stats_kernel(const int64_t *q_off, const int64_t *s_off, int64_t n_pairs, int64_t *stats) {
-    // stats: [0] max n, [1] max m, [2] bad-offset flag; one atomic per block
-    __shared__ unsigned long long red[3][32];
+    // stats: [0] max n, [1] max m, [2] bad-offset flag, [3] max of min(n, m);
+    // one atomic per block and value
+    __shared__ unsigned long long red[4][32];
     int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    unsigned long long mn = 0, mm = 0, bad = 0;
+    unsigned long long mn = 0, mm = 0, bad = 0, mmin = 0;
     for (; p < n_pairs; p += (int64_t)gridDim.x * blockDim.x) {
         int64_t n = q_off[p + 1] - q_off[p], m = s_off[p + 1] - s_off[p];
         if (n < 0 || m < 0 || n >= (1 << 21) || m >= (1 << 21)) bad = 1;
         if (n > (int64_t)mn) mn = (unsigned long long)n;
         if (m > (int64_t)mm) mm = (unsigned long long)m;
+        const int64_t lo = n < m ? n : m;
+        if (lo > (int64_t)mmin) mmin = (unsigned long long)lo;
     }
     for (int off = 16; off; off >>= 1) {
         mn = max(mn, __shfl_xor_sync(0xffffffffu, mn, off));
         mm = max(mm, __shfl_xor_sync(0xffffffffu, mm, off));
+        mmin = max(mmin, __shfl_xor_sync(0xffffffffu, mmin, off));
         bad |= __shfl_xor_sync(0xffffffffu, bad, off);
     }
     const int lane = threadIdx.x & 31, w = threadIdx.x >> 5, nw = blockDim.x >> 5;
-    if (lane == 0) { red[0][w] = mn; red[1][w] = mm; red[2][w] = bad; }
+    if (lane == 0) { red[0][w] = mn; red[1][w] = mm; red[2][w] = bad; red[3][w] = mmin; }
     __syncthreads();
     if (threadIdx.x == 0) {
-        for (int k = 1; k < nw; k++) { mn = max(mn, red[0][k]); mm = max(mm, red[1][k]); bad |= red[2][k]; }
+        for (int k = 1; k < nw; k++) {
+            mn = max(mn, red[0][k]); mm = max(mm, red[1][k]); bad |= red[2][k]; mmin = max(mmin, red[3][k]);
+        }
         if (bad) atomicOr(reinterpret_cast<unsigned long long *>(&stats[2]), 1ull);
         atomicMax(reinterpret_cast<unsigned long long *>(&stats[0]), mn);
         atomicMax(reinterpret_cast<unsigned long long *>(&stats[1]), mm);
+        atomicMax(reinterpret_cast<unsigned long long *>(&stats[3]), mmin);
     }
 }
 
@@ -319,6 +326,8 @@ anyseq_status_t anyseq::batch_scores(anyseq_ctx *ctx, const BatchInput &in, cons
                                      TbOut *tb, bool capture) {
     anyseq_status_t s2 = ANYSEQ_OK;
     const int64_t n = in.n_pairs;
+    if (mode != ANYSEQ_GLOBAL && !key_range_ok(sc, in.max_min))
+        return fail(ANYSEQ_ERR_ARG, "local / semi-global scores of a pair may reach 2^21 (the optimum key's range)");
     const int sigp = (sc->alphabet > 4 || ctx->force_matrix) ? 1 : 0;
     PrepArgs P;
     memset(&P, 0, sizeof(P));
@@ -469,14 +478,14 @@ anyseq_status_t anyseq::stage_batch(anyseq_ctx *ctx, const uint8_t *q, const int
     in.s_off = (const int64_t *)ds_off;
     int64_t *stats = arena<int64_t>(ctx, "stats", 8, &s2);
     if (s2 != ANYSEQ_OK) return s2;
-    int64_t hstats[5];
-    CUDA_TRY(cudaMemsetAsync(stats, 0, 3 * sizeof(int64_t), st));
+    int64_t hstats[6];
+    CUDA_TRY(cudaMemsetAsync(stats, 0, 4 * sizeof(int64_t), st));
     len_stats_kernel<<<grid_for(n_pairs) > 304 ? 304 : grid_for(n_pairs), 256, 0, st>>>(in.q_off, in.s_off, n_pairs, stats);
     CUDA_TRY(cudaGetLastError());
     ctx->launches += 1;
-    CUDA_TRY(cudaMemcpyAsync(hstats, stats, 3 * sizeof(int64_t), cudaMemcpyDeviceToHost, st));
-    CUDA_TRY(cudaMemcpyAsync(&hstats[3], in.q_off + n_pairs, sizeof(int64_t), cudaMemcpyDeviceToHost, st));
-    CUDA_TRY(cudaMemcpyAsync(&hstats[4], in.s_off + n_pairs, sizeof(int64_t), cudaMemcpyDeviceToHost, st));
+    CUDA_TRY(cudaMemcpyAsync(hstats, stats, 4 * sizeof(int64_t), cudaMemcpyDeviceToHost, st));
+    CUDA_TRY(cudaMemcpyAsync(&hstats[4], in.q_off + n_pairs, sizeof(int64_t), cudaMemcpyDeviceToHost, st));
+    CUDA_TRY(cudaMemcpyAsync(&hstats[5], in.s_off + n_pairs, sizeof(int64_t), cudaMemcpyDeviceToHost, st));
     int64_t q0 = 0, s0 = 0;
     CUDA_TRY(cudaMemcpyAsync(&q0, in.q_off, sizeof(int64_t), cudaMemcpyDeviceToHost, st));
     CUDA_TRY(cudaMemcpyAsync(&s0, in.s_off, sizeof(int64_t), cudaMemcpyDeviceToHost, st));
@@ -485,8 +494,9 @@ anyseq_status_t anyseq::stage_batch(anyseq_ctx *ctx, const uint8_t *q, const int
         return fail(ANYSEQ_ERR_ARG, "offsets must start at 0, be non-decreasing and give lengths below 2^21");
     in.max_n = hstats[0];
     in.max_m = hstats[1];
-    in.q_len = hstats[3];
-    in.s_len = hstats[4];
+    in.max_min = hstats[3];
+    in.q_len = hstats[4];
+    in.s_len = hstats[5];
     if ((in.q_len > 0 && !q) || (in.s_len > 0 && !s)) return fail(ANYSEQ_ERR_ARG, "q or s is NULL");
     const void *dq, *ds;
     TRY(stage_input(ctx, "in_q", q, (size_t)in.q_len, st, &dq));
@@ -516,6 +526,8 @@ extern "C" anyseq_status_t anyseq_align_batch(anyseq_ctx *ctx, const uint8_t *q,
     ctx->launches = 0;
     BatchInput in;
     TRY(stage_batch(ctx, q, q_off, s, s_off, n_pairs, in, st));
+    if (mode != ANYSEQ_GLOBAL && !key_range_ok(sc, in.max_min))
+        return fail(ANYSEQ_ERR_ARG, "local / semi-global scores of a pair may reach 2^21 (the optimum key's range)");
 
     int32_t *score = arena<int32_t>(ctx, "r_score", n_pairs, &s2);
     int32_t *eq = arena<int32_t>(ctx, "r_eq", n_pairs, &s2);
@@ -592,6 +604,19 @@ extern "C" anyseq_status_t anyseq_align_batch(anyseq_ctx *ctx, const uint8_t *q,
 }
 
 // 32-bit range of the wavefront: every |value| of the pair stays below 2^28.
+// Local and semi-global optima are searched by 64-bit keys whose score field
+// holds values below 2^21 (end_key): the best score of a pair is at most the
+// largest positive substitution score times min(n, m).
+bool anyseq::key_range_ok(const anyseq_scoring_t *sc, int64_t min_nm) {
+    int64_t pmax = 0;
+    for (int a = 0; a < sc->alphabet; a++)
+        for (int b = 0; b < sc->alphabet; b++) {
+            const int64_t v = sigma_host(sc, a, b);
+            pmax = v > pmax ? v : pmax;
+        }
+    return pmax * min_nm < (1ll << 21) - 1;
+}
+
 bool anyseq::long_range_ok(const anyseq_scoring_t *sc, int64_t n, int64_t m) {
     int64_t smax = 0;
     for (int a = 0; a < sc->alphabet; a++)
@@ -624,6 +649,7 @@ anyseq_status_t anyseq::wave_batch(anyseq_ctx *ctx, const BatchInput &in, const 
     CUDA_TRY(cudaStreamSynchronize(st));
     for (int64_t p = 0; p < n; p++)
         if (!long_range_ok(sc, hq[p + 1] - hq[p], hs[p + 1] - hs[p])) return ANYSEQ_OK;
+    if (mode != ANYSEQ_GLOBAL && !key_range_ok(sc, in.max_min)) return ANYSEQ_OK;
     std::vector<uint64_t> keys;
     *used = true;
     anyseq_status_t s2 = ANYSEQ_OK;
@@ -735,6 +761,8 @@ anyseq_status_t anyseq::long_scores(anyseq_ctx *ctx, const uint8_t *q, const int
         p.n = (int32_t)(q_off[k + 1] - q_off[k]);
         p.m = (int32_t)(s_off[k + 1] - s_off[k]);
         if (p.n <= 0 || p.m <= 0) return fail(ANYSEQ_ERR_ARG, "long_scores: empty pair %lld", (long long)k);
+        if (mode != ANYSEQ_GLOBAL && !key_range_ok(sc, p.n < p.m ? p.n : p.m))
+            return fail(ANYSEQ_ERR_ARG, "long_scores: scores of pair %lld may reach 2^21", (long long)k);
         p.tb = sc->gap_open;
         p.out_off = out;
         out += p.m + 1;
@@ -784,6 +812,40 @@ anyseq_status_t anyseq::long_last_row(anyseq_ctx *ctx, const uint32_t *q2, int64
     return run_wave_passes(ctx, q2, s2, passes, sc, H, E, st);
 }
 
+// Start cell of a local or semi-global long-pair traceback (r holds the score
+// and the optimum cell). The alignment ends at the optimum cell (ei, ej); its
+// score S is the largest global score of q[i .. ei) against s[j .. ej) over the
+// starts (i, j) the mode allows: any cell (local), row 0 or column 0
+// (semi-global). One anchored wavefront pass over the reversed prefixes gives
+// those global scores; its best cell, largest score and then smallest reversed
+// row and column, is the start with the largest i and then the largest j. An
+// empty optimum (S = 0) starts where it ends.
+anyseq_status_t anyseq::long_start_cell(anyseq_ctx *ctx, const uint32_t *q2, const uint32_t *s2p,
+                                        const anyseq_scoring_t *sc, int32_t mode, anyseq_result_t &r,
+                                        cudaStream_t st) {
+    r.beg_q = r.end_q;
+    r.beg_s = r.end_s;
+    if (r.score <= 0 || r.end_q == 0 || r.end_s == 0) return ANYSEQ_OK;
+    anyseq_status_t s2 = ANYSEQ_OK;
+    int32_t *H = arena<int32_t>(ctx, "ls_start_H", (size_t)r.end_s + 2, &s2);
+    if (s2 != ANYSEQ_OK) return s2;
+    std::vector<WavePass> passes(1);
+    memset(passes.data(), 0, sizeof(WavePass));
+    passes[0].n = r.end_q;
+    passes[0].m = r.end_s;
+    passes[0].tb = sc->gap_open;
+    passes[0].rev = 1;
+    std::vector<uint64_t> keys;
+    TRY(run_wave_passes(ctx, q2, s2p, passes, sc, H, nullptr, st, nullptr,
+                        mode == ANYSEQ_LOCAL ? ANCHORED_LOCAL : ANCHORED_SEMIGLOBAL, &keys));
+    if (keys[0] == 0 || key_score(keys[0]) != r.score)
+        return fail(ANYSEQ_ERR_CUDA, "start-cell pass found score %d, the optimum is %d",
+                    keys[0] ? key_score(keys[0]) : -1, r.score);
+    r.beg_q = r.end_q - key_i(keys[0]);
+    r.beg_s = r.end_s - key_j(keys[0]);
+    return ANYSEQ_OK;
+}
+
 extern "C" anyseq_status_t anyseq_align_long(anyseq_ctx *ctx, const uint8_t *q, int64_t n, const uint8_t *s,
                                              int64_t m, const anyseq_scoring_t *sc, int32_t mode, uint32_t want,
                                              anyseq_result_t *out, uint32_t *cigar, uint64_t cigar_cap,
@@ -793,10 +855,10 @@ extern "C" anyseq_status_t anyseq_align_long(anyseq_ctx *ctx, const uint8_t *q, 
     if (!out) return fail(ANYSEQ_ERR_ARG, "out is NULL");
     if ((n > 0 && !q) || (m > 0 && !s)) return fail(ANYSEQ_ERR_ARG, "q or s is NULL");
     TRY(check_scoring(sc, mode));
-    if (mode != ANYSEQ_GLOBAL && (want & ANYSEQ_WANT_CIGAR))
-        return fail(ANYSEQ_ERR_ARG, "the long-pair traceback is global only (local and semi-global: score and end cell)");
     if (mode != ANYSEQ_GLOBAL && (n >= (1ll << 21) || m >= (1ll << 21)))
         return fail(ANYSEQ_ERR_ARG, "local and semi-global long pairs below 2^21 letters");
+    if (mode != ANYSEQ_GLOBAL && !key_range_ok(sc, n < m ? n : m))
+        return fail(ANYSEQ_ERR_ARG, "local / semi-global scores of this pair may reach 2^21 (the optimum key's range)");
     if (sc->alphabet > 4) return fail(ANYSEQ_ERR_ARG, "the long-pair path takes alphabets of at most 4 letters");
     if (!long_range_ok(sc, n, m)) return fail(ANYSEQ_ERR_ARG, "scores of this pair may leave the 32-bit range");
     cudaStream_t st = (cudaStream_t)cuda_stream;
@@ -854,11 +916,20 @@ extern "C" anyseq_status_t anyseq_align_long(anyseq_ctx *ctx, const uint8_t *q, 
             CUDA_TRY(cudaMemcpyAsync(&r.score, H + m, sizeof(int32_t), cudaMemcpyDeviceToHost, st));
             CUDA_TRY(cudaStreamSynchronize(st));
         }
-        if (want_cigar) TRY(hirschberg_cigar(ctx, q2, (int32_t)n, s2p, (int32_t)m, sc, hcig, st));
+        if (want_cigar && mode == ANYSEQ_GLOBAL) {
+            TRY(hirschberg_cigar(ctx, q2, 0, (int32_t)n, s2p, 0, (int32_t)m, sc, hcig, st));
+            r.beg_q = r.beg_s = 0;
+        } else if (want_cigar) {
+            TRY(long_start_cell(ctx, q2, s2p, sc, mode, r, st));
+            if (r.end_q > r.beg_q || r.end_s > r.beg_s)
+                TRY(hirschberg_cigar(ctx, q2, r.beg_q, r.end_q, s2p, r.beg_s, r.end_s, sc, hcig, st));
+        }
     }
     if (want_cigar) {
-        r.beg_q = 0;
-        r.beg_s = 0;
+        if (n == 0 || m == 0) {
+            r.beg_q = mode == ANYSEQ_GLOBAL ? 0 : r.end_q;
+            r.beg_s = mode == ANYSEQ_GLOBAL ? 0 : r.end_s;
+        }
         r.cigar_off = 0;
         r.cigar_len = (uint32_t)hcig.size();
         if (cigar_used) *cigar_used = hcig.size();

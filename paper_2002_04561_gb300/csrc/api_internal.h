@@ -57,6 +57,7 @@ struct BatchInput {
     const uint8_t *q = nullptr, *s = nullptr;          // device
     const int64_t *q_off = nullptr, *s_off = nullptr;  // device
     int64_t n_pairs = 0, q_len = 0, s_len = 0, max_n = 0, max_m = 0;
+    int64_t max_min = 0;  // largest min(n, m) of a pair
     const uint8_t *select = nullptr;                   // optional subset of pairs (device)
 };
 
@@ -89,6 +90,8 @@ anyseq_status_t stage_batch(anyseq_ctx *ctx, const uint8_t *q, const int64_t *q_
 anyseq_status_t band_scores(anyseq_ctx *ctx, const BatchInput &in, const anyseq_scoring_t *sc, int32_t *score,
                             int32_t *eq, int32_t *es, uint32_t *flags, cudaStream_t st);
 bool long_range_ok(const anyseq_scoring_t *sc, int64_t n, int64_t m);
+// local / semi-global: the best score of a pair with min(n, m) <= min_nm fits the optimum key
+bool key_range_ok(const anyseq_scoring_t *sc, int64_t min_nm);
 // Scores (and, with end_q/end_s, optimum cells) of several long pairs in one
 // wavefront launch, in the given mode (host arrays).
 anyseq_status_t long_scores(anyseq_ctx *ctx, const uint8_t *q, const int64_t *q_off, const uint8_t *s,
@@ -109,8 +112,15 @@ anyseq_status_t run_wave_passes(anyseq_ctx *ctx, const uint32_t *q2, const uint3
                                 std::vector<WavePass> &passes, const anyseq_scoring_t *sc, int32_t *H, int32_t *E,
                                 cudaStream_t st, WaveTb *tb = nullptr, int32_t mode = ANYSEQ_GLOBAL,
                                 std::vector<uint64_t> *keys = nullptr);
-anyseq_status_t hirschberg_cigar(anyseq_ctx *ctx, const uint32_t *q2, int32_t n, const uint32_t *s2, int32_t m,
-                                 const anyseq_scoring_t *sc, std::vector<uint32_t> &cigar, cudaStream_t st);
+// Start cell of a local / semi-global long-pair traceback from r's score and
+// optimum cell (sets r.beg_q, r.beg_s).
+anyseq_status_t long_start_cell(anyseq_ctx *ctx, const uint32_t *q2, const uint32_t *s2, const anyseq_scoring_t *sc,
+                                int32_t mode, anyseq_result_t &r, cudaStream_t st);
+// Global divide-and-conquer CIGAR of q[i0 .. i1) against s[j0 .. j1) (positions
+// in the packed arrays q2, s2).
+anyseq_status_t hirschberg_cigar(anyseq_ctx *ctx, const uint32_t *q2, int32_t i0, int32_t i1, const uint32_t *s2,
+                                 int32_t j0, int32_t j1, const anyseq_scoring_t *sc, std::vector<uint32_t> &cigar,
+                                 cudaStream_t st);
 
 // Scores and optimum cells of a batch; with tb != null also the direction words.
 anyseq_status_t batch_scores(anyseq_ctx *ctx, const BatchInput &in, const anyseq_scoring_t *sc, int32_t mode,

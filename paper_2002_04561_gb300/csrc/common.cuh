@@ -131,8 +131,14 @@ __device__ __forceinline__ uint32_t codes16(const uint32_t *packed, int64_t k, i
 }
 
 // Lexicographic key of an optimum candidate: larger score, then smaller i,
-// then smaller j wins (the tie rule of the optimum cell).
+// then smaller j wins (the tie rule of the optimum cell). Fields: score + 2^21
+// in 22 bits, 2^21 - 1 - i and 2^21 - 1 - j in 21 bits each. A score below -1
+// is stored as -1: every search starts from a candidate of score 0 (the empty
+// alignment) or looks for a positive optimum, so such a candidate never wins,
+// and the clamp keeps it inside its field. Callers keep scores below 2^21
+// (key_range_ok on the host).
 __host__ __device__ __forceinline__ uint64_t end_key(int32_t score, int32_t i, int32_t j) {
+    score = score < -1 ? -1 : score;
     return ((uint64_t)(uint32_t)(score + (1 << 21)) << 42) |
            ((uint64_t)(uint32_t)((1 << 21) - 1 - i) << 21) |
            (uint64_t)(uint32_t)((1 << 21) - 1 - j);

@@ -247,14 +247,19 @@ anyseq_status_t run_wave_passes(anyseq_ctx *ctx, const uint32_t *q2, const uint3
     W.n_stripes = stripes;
     W.o = sc->gap_open;
     W.e = sc->gap_extend;
-    HB_TRY(make_rowprof(sc, mode, W.rowprof));
+    HB_TRY(make_rowprof(sc, wave_init_mode(mode), W.rowprof));
     W.mode = mode;
     W.best = nullptr;
     std::vector<uint64_t> hkeys;
     if (mode != ANYSEQ_GLOBAL) {
-        // best cell per pass, starting from the empty alignment's cell
+        // best cell per pass, starting from the empty alignment's cell (local,
+        // semi-global) or from no candidate (anchored passes look for a
+        // positive optimum)
         hkeys.resize(passes.size());
-        for (size_t k = 0; k < passes.size(); k++) hkeys[k] = end_key(0, 0, mode == ANYSEQ_SEMIGLOBAL ? passes[k].m : 0);
+        for (size_t k = 0; k < passes.size(); k++)
+            hkeys[k] = mode == ANYSEQ_LOCAL        ? end_key(0, 0, 0)
+                       : mode == ANYSEQ_SEMIGLOBAL ? end_key(0, 0, passes[k].m)
+                                                   : 0;
         W.best = arena_t<uint64_t>(ctx, "w_best", passes.size() + 1, &s2st);
         if (s2st != ANYSEQ_OK) return s2st;
         HB_CUDA(cudaMemcpyAsync(W.best, hkeys.data(), hkeys.size() * sizeof(uint64_t), cudaMemcpyHostToDevice, st));
@@ -291,12 +296,13 @@ anyseq_status_t run_wave_passes(anyseq_ctx *ctx, const uint32_t *q2, const uint3
     return ANYSEQ_OK;
 }
 
-anyseq_status_t hirschberg_cigar(anyseq_ctx *ctx, const uint32_t *q2, int32_t n, const uint32_t *s2, int32_t m,
-                                 const anyseq_scoring_t *sc, std::vector<uint32_t> &cigar, cudaStream_t st) {
+anyseq_status_t hirschberg_cigar(anyseq_ctx *ctx, const uint32_t *q2, int32_t i0, int32_t i1, const uint32_t *s2,
+                                 int32_t j0, int32_t j1, const anyseq_scoring_t *sc, std::vector<uint32_t> &cigar,
+                                 cudaStream_t st) {
     anyseq_status_t s2st = ANYSEQ_OK;
     const int32_t o = sc->gap_open;
     std::vector<Node> nodes;
-    nodes.push_back(Node{Sub{0, n, 0, m, o, o}});
+    nodes.push_back(Node{Sub{i0, i1, j0, j1, o, o}});
     std::vector<int> level{0}, bases;
     while (!level.empty()) {
         std::vector<int> splits;

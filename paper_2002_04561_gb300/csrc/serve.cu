@@ -219,6 +219,9 @@ extern "C" anyseq_status_t anyseq_server_submit(anyseq_server *S, const uint8_t 
                                                 int64_t m, uint64_t *ticket) {
     if (!S || !ticket) return anyseq::fail(ANYSEQ_ERR_ARG, "server and ticket must not be NULL");
     if (n < 0 || m < 0 || (n > 0 && !q) || (m > 0 && !s)) return anyseq::fail(ANYSEQ_ERR_ARG, "bad pair");
+    if (n >= (1ll << 21) || m >= (1ll << 21)) return anyseq::fail(ANYSEQ_ERR_ARG, "pairs below 2^21 letters");
+    if (S->cfg.mode != ANYSEQ_GLOBAL && !anyseq::key_range_ok(&S->sc, n < m ? n : m))
+        return anyseq::fail(ANYSEQ_ERR_ARG, "local / semi-global scores of this pair may reach 2^21");
     Request *r = new Request();
     r->q.assign(q, q + n);
     r->s.assign(s, s + m);

@@ -44,16 +44,23 @@ struct __align__(16) WaveSmem {
     int32_t bot[2 * WRING];
 };
 
+// Best-cell searches of a mode: over every cell, or over the last row and column.
+__host__ __device__ constexpr bool best_all(int mode) { return mode == LOCAL || mode == ANCHORED_LOCAL; }
+__host__ __device__ constexpr bool best_edge(int mode) { return mode == SEMIGLOBAL || mode == ANCHORED_SEMIGLOBAL; }
+
 // TB: also write the traceback direction words of every cell (the layout of the
 // batched traceback with 32 lanes x WR rows per chunk, see tb.h), global only.
-// MODE: the initialisation and optimum of Sec. III-A. Local and semi-global
-// passes keep their best cell as a key (score, then smaller i, then smaller j)
-// merged per pass by a 64-bit atomic maximum: local from every row's running
-// maximum and its first column (rows per lane 8 there, the extra registers),
-// semi-global from the last column (at each lane's last-column step) and the
-// last row (the last stripe's bottom row).
+// MODE: the initialisation and optimum of Sec. III-A, or an anchored mode of
+// the start-cell pass (wave.h). Passes with a best-cell search keep their best
+// cell as a key (score, then smaller i, then smaller j) merged per pass by a
+// 64-bit atomic maximum: over every cell from each row's running maximum and
+// its first column (rows per lane 8 there, the extra registers), over the edge
+// from the last column (at each lane's last-column step) and the last row (the
+// last stripe's bottom row).
 template <int WR, bool TB, int MODE>
-__global__ void __launch_bounds__(256, (WR <= 8 && MODE != LOCAL) ? 4 : 2) wave_kernel(WaveArgs A) {
+__global__ void __launch_bounds__(256, (WR <= 8 && !best_all(MODE)) ? 4 : 2) wave_kernel(WaveArgs A) {
+    constexpr int INIT = wave_init_mode(MODE);
+    constexpr bool ALL = best_all(MODE), EDGE = best_edge(MODE);
     constexpr int WCH = WG * WR;  // rows per stripe
     static_assert(!TB || WR % 8 == 0, "direction words hold 8 rows");
     static_assert(!TB || MODE == GLOBAL, "traceback on the wavefront is global");
@@ -92,16 +99,16 @@ __global__ void __launch_bounds__(256, (WR <= 8 && MODE != LOCAL) ? 4 : 2) wave_
         for (int r = 0; r < WR; r++) {
             int32_t i = rb + r - pad;
             prof[r] = (i >= 1) ? A.rowprof[wletter(A.q2, ps.q0, n, i - 1, rev)] : A.rowprof[4];
-            Hoe[r] = col0(MODE, i, o, e, ps.tb) + oe;
+            Hoe[r] = col0(INIT, i, o, e, ps.tb) + oe;
             F[r] = C::NEG;
         }
-        const T diag0 = col0(MODE, rb - 1 - pad, o, e, ps.tb) + oe;
-        // local / semi-global: this lane's best cell as a key; local rows' running
-        // maxima (Hoe) and their first columns
-        uint64_t best = end_key(0, 0, MODE == SEMIGLOBAL ? m : 0);
-        T rowmax[MODE == LOCAL ? WR : 1];
-        int32_t rowj[MODE == LOCAL ? WR : 1];
-        if (MODE == LOCAL) {
+        const T diag0 = col0(INIT, rb - 1 - pad, o, e, ps.tb) + oe;
+        // best-cell searches: this lane's best cell as a key (the pass's floor is
+        // set by the host); rows' running maxima (Hoe) and their first columns
+        uint64_t best = 0;
+        T rowmax[ALL ? WR : 1];
+        int32_t rowj[ALL ? WR : 1];
+        if (ALL) {
 #pragma unroll
             for (int r = 0; r < WR; r++) {
                 rowmax[r] = oe;  // Hoe of H = 0
@@ -147,7 +154,7 @@ __global__ void __launch_bounds__(256, (WR <= 8 && MODE != LOCAL) ? 4 : 2) wave_
                 fsh = 2 * (int32_t)(pos & 15);
                 if (k == 0) {
                     // row 0: H(0, c+1); E below row 0 comes from H only (E(0, .) = -inf)
-                    const int32_t v = (MODE == GLOBAL ? o + (c + 1) * e : 0) + oe;
+                    const int32_t v = (INIT == GLOBAL ? o + (c + 1) * e : 0) + oe;
                     ft = make_int2(v, v);
                 } else if (!failed) {
                     ft = bin[c];
@@ -180,7 +187,7 @@ __global__ void __launch_bounds__(256, (WR <= 8 && MODE != LOCAL) ? 4 : 2) wave_
                 } else {
                     if (outH) outH[c + 1] = hv - oe;
                     if (outE) outE[c + 1] = ev;
-                    if (MODE == SEMIGLOBAL) {
+                    if (EDGE) {
                         const uint64_t key = end_key(hv - oe, n, c + 1);
                         best = key > best ? key : best;
                     }
@@ -197,7 +204,7 @@ __global__ void __launch_bounds__(256, (WR <= 8 && MODE != LOCAL) ? 4 : 2) wave_
                 } else {
                     if (outH) outH[c + 1] = hv - oe;
                     if (outE) outE[c + 1] = ev;
-                    if (MODE == SEMIGLOBAL) {
+                    if (EDGE) {
                         const uint64_t key = end_key(hv - oe, n, c + 1);
                         best = key > best ? key : best;
                     }
@@ -236,7 +243,7 @@ __global__ void __launch_bounds__(256, (WR <= 8 && MODE != LOCAL) ? 4 : 2) wave_
 #pragma unroll
                 for (int r = 0; r < WR; r++) {
                     F[r] = C::addmax(F[r], e_raw, Hoe[r]);
-                    const T M = (MODE == LOCAL) ? C::maxrelu(Ad, F[r]) : C::vmax(Ad, F[r]);
+                    const T M = (MODE == LOCAL) ? C::maxrelu(Ad, F[r]) : C::vmax(Ad, F[r]);  // the clamp at 0
                     const T X = C::addc(M, oe_c);
                     const T Adr = Ad;
                     if (r + 1 < WR) Ad = C::addc(Hoe[r], (uint32_t)C::sigma(prof[r + 1], prof[r + 1], sel));
@@ -245,7 +252,7 @@ __global__ void __launch_bounds__(256, (WR <= 8 && MODE != LOCAL) ? 4 : 2) wave_
                     Ein = E;
                     Hoe[r] = C::addmax(E, oe_raw, X);
                     E = C::addmax(E, e_raw, X);
-                    if (MODE == LOCAL) {
+                    if (ALL) {
                         // strict improvement of the row maximum: the column of its first occurrence
                         if (Hoe[r] > rowmax[r]) {
                             rowmax[r] = Hoe[r];
@@ -270,7 +277,7 @@ __global__ void __launch_bounds__(256, (WR <= 8 && MODE != LOCAL) ? 4 : 2) wave_
                         }
                     }
                 }
-                if (MODE == SEMIGLOBAL && c == m - 1) {
+                if (EDGE && c == m - 1) {
 #pragma unroll
                     for (int r = 0; r < WR; r++) {
                         const int32_t i = rb + r - pad;
@@ -313,11 +320,11 @@ __global__ void __launch_bounds__(256, (WR <= 8 && MODE != LOCAL) ? 4 : 2) wave_
         for (int b = drained; b <= (m - 1) / BLOCK; b++) drain(b);
         if (!last && g == 0) st_release(prog_mine, (m + BLOCK - 1) / BLOCK + 1);
         if (last && g == 0) {
-            if (outH) outH[0] = col0(MODE, n, o, e, ps.tb);
-            if (outE) outE[0] = col0(MODE, n, o, e, ps.tb);
+            if (outH) outH[0] = col0(INIT, n, o, e, ps.tb);
+            if (outE) outE[0] = col0(INIT, n, o, e, ps.tb);
         }
-        if (MODE != GLOBAL) {
-            if (MODE == LOCAL) {
+        if (ALL || EDGE) {
+            if (ALL) {
 #pragma unroll
                 for (int r = 0; r < WR; r++) {
                     const int32_t i = rb + r - pad, v = rowmax[r] - oe;
@@ -349,8 +356,8 @@ static int blocks_per_sm() {
 }
 
 int wave_rows_per_lane(int64_t total_rows, int num_sms, int64_t n_passes, int mode) {
-    if (mode == LOCAL) return 8;        // the rows' maxima and columns take registers
-    if (mode == SEMIGLOBAL) return 16;  // its 8-row variant would spill
+    if (best_all(mode)) return 8;    // the rows' maxima and columns take registers
+    if (best_edge(mode)) return 16;  // its 8-row variant would spill
     // 8-row stripes double the stripes (and the pipeline's skew) and run at 64
     // registers; measured on 100 kbp to 1 Mbp pairs, 16-row stripes win unless
     // the problem is tiny (a few stripes, as a single pair of a thousand rows)
@@ -366,12 +373,17 @@ static void launch_one(const WaveArgs &A, int num_sms, cudaStream_t st) {
 cudaError_t launch_wave(const WaveArgs &A, int num_sms, cudaStream_t st) {
     const bool tb = A.dirs != nullptr;
     // the stripe table was built for A.rows_per_lane (from wave_rows_per_lane)
+    if (A.mode != GLOBAL && (tb || A.rows_per_lane != (best_all(A.mode) ? 8 : 16))) return cudaErrorInvalidValue;
     if (A.mode == LOCAL) {
-        if (A.rows_per_lane != 8 || tb) return cudaErrorInvalidValue;
         launch_one<8, false, LOCAL>(A, num_sms, st);
+    } else if (A.mode == ANCHORED_LOCAL) {
+        launch_one<8, false, ANCHORED_LOCAL>(A, num_sms, st);
     } else if (A.mode == SEMIGLOBAL) {
-        if (A.rows_per_lane != 16 || tb) return cudaErrorInvalidValue;
         launch_one<16, false, SEMIGLOBAL>(A, num_sms, st);
+    } else if (A.mode == ANCHORED_SEMIGLOBAL) {
+        launch_one<16, false, ANCHORED_SEMIGLOBAL>(A, num_sms, st);
+    } else if (A.mode != GLOBAL) {
+        return cudaErrorInvalidValue;
     } else if (A.rows_per_lane == 8) {
         if (tb) launch_one<8, true, GLOBAL>(A, num_sms, st);
         else launch_one<8, false, GLOBAL>(A, num_sms, st);

@@ -3,6 +3,8 @@
 #include <cstdint>
 #include <cuda_runtime.h>
 
+#include "common.cuh"
+
 namespace anyseq {
 
 // One global pass over q[q0 .. q0+n) x s[s0 .. s0+m) (read reversed when rev),
@@ -33,14 +35,27 @@ struct WaveArgs {
     int64_t spin_limit;           // iterations of one wait
     int32_t rows_per_lane;        // 8 or 16 (stripes of 32 lanes x rows_per_lane rows)
     uint32_t *dirs;               // optional: traceback direction words (global mode)
-    int32_t mode;                 // GLOBAL, LOCAL or SEMIGLOBAL (every pass of the launch)
+    int32_t mode;                 // GLOBAL, LOCAL, SEMIGLOBAL or an anchored mode (every pass)
     uint64_t *best;               // local / semi-global: per pass the best cell's key (initialised)
 };
+
+// Wavefront-only modes of the start-cell pass of a local or semi-global
+// long-pair traceback. The pass runs over the reversed prefixes that end at
+// the optimum cell, so its values are the global scores of the substrings
+// ending there: global initialisation, no clamp at 0, and the best cell
+// (largest score, then smallest reversed row, then smallest reversed column)
+// over every cell (ANCHORED_LOCAL) or over the last row and column
+// (ANCHORED_SEMIGLOBAL, whose cells are the starts in row 0 or column 0).
+constexpr int32_t ANCHORED_LOCAL = 3, ANCHORED_SEMIGLOBAL = 4;
+// The initialisation (column 0, row 0, padding rows) of a mode.
+__host__ __device__ constexpr int32_t wave_init_mode(int32_t mode) {
+    return (mode == LOCAL || mode == SEMIGLOBAL) ? mode : GLOBAL;
+}
 
 // Rows per lane of a launch: 8 when 16-row stripes would fill less than a
 // sixteenth of the resident warps (twice the stripes, half the per-step chain
 // each), otherwise 16. total_rows = sum of the passes' row counts.
-// (Local mode: always 8; semi-global: always 16.) The stripe table of a launch
+// (Local modes: always 8; semi-global modes: always 16.) The stripe table of a launch
 // must be built with this value, and WaveArgs.rows_per_lane set to it.
 int wave_rows_per_lane(int64_t total_rows, int num_sms, int64_t n_passes, int mode);
 cudaError_t launch_wave(const WaveArgs &A, int num_sms, cudaStream_t st);

@@ -6,7 +6,11 @@ stripe wavefront (score) and the divide-and-conquer traceback (CIGAR).
 * the CIGAR equals the oracle's Hirschberg (Myers-Miller) CIGAR under the same
   midpoint rule, for small and large base sizes;
 * every CIGAR re-scores to the reported score (a property that holds at any
-  size), including a 200 kbp pair shaped like the long-genome workload.
+  size), including a 200 kbp pair shaped like the long-genome workload;
+* local and semi-global long pairs: score, optimum cell, start cell and CIGAR
+  equal the oracle's linear-space alignment word for word;
+* local and semi-global inputs whose score could leave the optimum key's
+  range are refused.
 """
 import numpy as np
 import pytest
@@ -152,6 +156,82 @@ def test_long_local_and_semiglobal_scores(pkg, ctx, mode):
             want = oracle.score(q, s, oracle.Scoring(*args), mode)
             got = (int(out["score"][0]), int(out["end_q"][0]), int(out["end_s"][0]))
             assert got == tuple(int(x) for x in want), (len(q), len(s), args, got, want)
+
+
+def long_cigar_mode(pkg, ctx, q, s, args, mode):
+    cap = len(q) + len(s) + 4
+    cig = np.zeros(cap, dtype=np.uint32)
+    out, used = ctx.align_long(q, s, pkg.Scoring.make(*args), mode=mode, want=pkg.WANT_SCORE | pkg.WANT_CIGAR,
+                               cigar=cig)
+    r = out[0]
+    return int(r["score"]), (int(r["beg_q"]), int(r["beg_s"])), (int(r["end_q"]), int(r["end_s"])), cig[:used]
+
+
+@pytest.mark.parametrize("base", [256, 1 << 16])
+@pytest.mark.parametrize("mode", [1, 2])
+def test_long_local_and_semiglobal_cigars(pkg, ctx, mode, base):
+    """Traceback of local and semi-global long pairs: the optimum cell, the
+    start cell of the anchored reverse wavefront pass (largest start row, then
+    column, among the optimal alignments ending there) and the divide-and-
+    conquer CIGAR between them equal the oracle's, word for word; the pairs
+    include repeated blocks and a mismatch-0 scheme, where starts tie."""
+    st = synth.Stream(3100 + mode, 1)
+    core = synth.random_codes(st, 1500, 4)
+    planted = (np.concatenate([synth.random_codes(st, 700, 4), core, synth.random_codes(st, 300, 4)]),
+               np.concatenate([synth.random_codes(st, 1100, 4), core[::-1].copy(), core, synth.random_codes(st, 90, 4)]))
+    pairs = [related(n, extra, seed=3200 + n + mode) for n, extra in ((1, 0), (513, 7), (1800, -40), (3000, 11))]
+    pairs += [(synth.random_codes(st, 1900, 4), synth.random_codes(st, 600, 4)), planted]
+    pairs += tied_long_pairs(3300 + mode)
+    ctx.set_option("hirschberg_base_cells", base)
+    try:
+        for args in (C4, (1, 0, -2, -1), (2, -1, 0, -1)):
+            for q, s in pairs:
+                got = long_cigar_mode(pkg, ctx, q, s, args, mode)
+                S, beg, end, cig = oracle.long_alignment(q, s, oracle.Scoring(*args), mode, base)
+                assert got[:3] == (S, beg, end), (len(q), len(s), args, got[:3], (S, beg, end))
+                assert np.array_equal(got[3], cig), (len(q), len(s), args)
+                if S > 0:
+                    assert rescore_cigar(got[3], q, s, beg, oracle.Scoring(*args)) == (S, end[0], end[1])
+    finally:
+        ctx.set_option("hirschberg_base_cells", 1 << 16)
+
+
+@pytest.mark.parametrize("mode", [1, 2])
+def test_long_local_and_semiglobal_cigar_60kbp(pkg, ctx, mode):
+    """A 60 kbp pair of the long-genome shape embedded in unrelated flanks: the
+    CIGAR re-scores to the optimum between the reported start and end cells,
+    the start satisfies the mode's rule, and score and end equal the oracle's
+    linear-space score."""
+    b = synth.long_pair(seed=5, n=60_000, inversion=10_000, n_inversions=1)
+    q, s = b.pair(0)
+    st = synth.Stream(3400, 1)
+    q = np.concatenate([synth.random_codes(st, 3000, 4), q])
+    s = np.concatenate([s, synth.random_codes(st, 5000, 4)])
+    S, beg, end, cig = long_cigar_mode(pkg, ctx, q, s, C4, mode)
+    assert (S,) + end == oracle.score(q, s, oracle.Scoring(*C4), mode)
+    assert rescore_cigar(cig, q, s, beg, oracle.Scoring(*C4)) == (S, end[0], end[1])
+    if mode == 2:
+        assert beg[0] == 0 or beg[1] == 0
+
+
+def test_key_range_is_checked(pkg, ctx):
+    """Local and semi-global optima are searched by keys whose score field holds
+    values below 2^21: a pair whose best score could reach that (largest match
+    score times min(n, m)) is refused with ERR_ARG before any launch; global
+    mode has no such limit."""
+    st = synth.Stream(3500, 1)
+    q = synth.random_codes(st, 21_000, 4)
+    big = (100, -100, -5, -2)
+    for mode in (1, 2):
+        with pytest.raises(pkg.AnyseqError) as ei:
+            ctx.align_long(q, q, pkg.Scoring.make(*big), mode=mode)
+        assert ei.value.status == 1
+        qo = np.array([0, len(q)], np.int64)
+        with pytest.raises(pkg.AnyseqError) as ei:
+            ctx.align_batch(q, qo, q, qo, pkg.Scoring.make(*big), mode)
+        assert ei.value.status == 1
+    out, _ = ctx.align_long(q, q, pkg.Scoring.make(*big))
+    assert out["score"][0] == 100 * len(q)
 
 
 @pytest.mark.parametrize("mode", [1, 2])
