@@ -407,6 +407,27 @@ def profile_long(n: int):
     print(json.dumps({"profile_long": n, "cells": b.cells(), "score": int(r["score"][0])}))
 
 
+def profile_protein(n_pairs: int):
+    """The protein workload's first n_pairs pairs (local affine, 20x20 matrix),
+    score only, aligned twice (a small case for ncu captures of the batched
+    kernel's shared-memory-profile variant)."""
+    import torch
+    import paper_2002_04561_gb300 as pkg
+    pkg.load(build_if_missing=True)
+    ctx = pkg.Context(0)
+    ctx.set_option("profile", 1)
+    b = synth.protein_pairs(n_pairs=n_pairs)
+    dev = lambda a: torch.from_numpy(np.ascontiguousarray(a)).cuda()
+    args = (dev(b.q), dev(b.q_off), dev(b.s), dev(b.s_off))
+    sc = pkg.Scoring.make(0, 0, -11, -1, matrix=synth.protein_matrix(3))
+    res = torch.zeros(b.n_pairs * 40, dtype=torch.uint8, device="cuda")
+    for _ in range(2):
+        ctx.align_batch(*args, sc, pkg.LOCAL, out=res)
+    torch.cuda.synchronize()
+    print(json.dumps({"profile_protein": n_pairs, "cells": b.cells(), "dp_ms": ctx.stat("dp_ms"),
+                      "dp32_ms": ctx.stat("dp32_ms"), "pairs16": ctx.stat("pairs16"), "pairs32": ctx.stat("pairs32")}))
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -418,11 +439,16 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--profile-long", type=int, default=0, metavar="N",
                     help="profiling case: only the wavefront score of one N-letter long pair, twice")
+    ap.add_argument("--profile-protein", type=int, default=0, metavar="N",
+                    help="profiling case: only the protein local scores of the first N pairs, twice")
     args = ap.parse_args()
     ws, rank, local = dist_env()
 
     if args.profile_long:
         profile_long(args.profile_long)
+        return
+    if args.profile_protein:
+        profile_protein(args.profile_protein)
         return
 
     if args.impl == "reference":

@@ -51,8 +51,8 @@ __device__ __forceinline__ void build_qprofile(const BatchArgs &A, const Slot &s
 // row words there; the candidates H(i, m_h) are ranked after the chunk, so
 // the step loop carries no per-row work for them.
 // Local mode keeps, per row, the running maximum and the first column where it
-// occurs (four instructions per cell pair); the optimum is ranked after each
-// chunk.
+// occurs (a DPX maximum whose predicates flag a strict improvement per half,
+// and a select per half); the optimum is ranked after each chunk.
 template <class C, int MODE, int R, bool TB, int SIGP>
 __device__ __noinline__ void run_slot(const BatchArgs &A, GroupSmem *sm, const Slot &sl,
                                       int nch, int Mit, int g, int64_t gslot, int32_t *res, const int32_t *pid,
@@ -60,7 +60,8 @@ __device__ __noinline__ void run_slot(const BatchArgs &A, GroupSmem *sm, const S
     typedef typename C::T T;
     const int32_t o = A.o, e = A.e, oe = A.o + A.e;
     const uint32_t e_raw = C::raw(e), oe_raw = C::raw(oe);   // per-half constants of DPX add-max
-    const uint32_t oe_c = C::cst(oe);                        // packed constant of IADD
+    const uint32_t oe_c = C::cst(oe), e_c = C::cst(e), moe_c = C::cst(-oe);  // packed constants of IADD
+    const T zero = C::make(0, 0);                            // H = 0 in both halves
     const T NEGv = C::make(C::NEG, C::NEG);
     const int CH = GROUP * R;
     const int S = Mit + GROUP - 1;
@@ -77,8 +78,8 @@ __device__ __noinline__ void run_slot(const BatchArgs &A, GroupSmem *sm, const S
         const int32_t rb = ch * CH + g * R + 1;  // padded row of register 0
         uint32_t profA[R], profB[R];
         T Hoe[R], F[R];
-        T rowmax[MODE == LOCAL ? R : 1];   // Hoe of the row maximum so far
-        uint32_t rowj[MODE == LOCAL ? R : 1];  // its first column (int16x2: one per half)
+        T rowmax[MODE == LOCAL ? R : 1];   // the row maximum of H so far
+        uint32_t rowj0[MODE == LOCAL ? R : 1], rowj1[MODE == LOCAL ? R : 1];  // its first column per half
 #pragma unroll
         for (int r = 0; r < R; r++) {
             int32_t h0[2] = {0, 0};
@@ -94,8 +95,8 @@ __device__ __noinline__ void run_slot(const BatchArgs &A, GroupSmem *sm, const S
             Hoe[r] = C::make(h0[0], h0[1]);
             F[r] = NEGv;
             if (MODE == LOCAL) {
-                rowmax[r] = C::make(oe, oe);  // Hoe of H = 0
-                rowj[r] = 0;
+                rowmax[r] = zero;
+                rowj0[r] = rowj1[r] = 0;
             }
         }
         T diag0;
@@ -232,25 +233,35 @@ __device__ __noinline__ void run_slot(const BatchArgs &A, GroupSmem *sm, const S
                 T Ad = C::addc(prev_up, sigma_r(0));
                 prev_up = up_hoe;
                 T E = up_e;
-                const uint32_t jj = C::PAIRS == 2 ? (uint32_t)(c + 1) * 65537u : (uint32_t)(c + 1);
+                const uint32_t jj = (uint32_t)(c + 1);
                 // direction bit planes (traceback): bit 8+r / 24+r of each accumulator
                 uint32_t pl_s0 = 0, pl_s1 = 0, pl_eo = 0, pl_fo = 0;
                 T hup = up_hoe;  // Hoe of the row above, this column
 #pragma unroll
                 for (int r = 0; r < R; r++) {
                     // H(i,j) = max(H(i-1,j-1)+sigma, E(i,j), F(i,j) [,0]) kept as Hoe = H + o + e
-                    F[r] = C::addmax(F[r], e_raw, Hoe[r]);             // Eq. 5 (Hoe[r]: the left neighbour)
-                    const T M = (MODE == LOCAL) ? C::maxrelu(Ad, F[r]) : C::vmax(Ad, F[r]);
-                    const T X = C::addc(M, oe_c);                     // max(diag, F) + o + e
                     T Adn = Ad;
-                    if (r + 1 < R) Adn = C::addc(Hoe[r], sigma_r(r + 1));
-                    uint32_t fFo = 0;
-                    if (TB) fFo = C::ge(Hoe[r], F[r]);                // F(i,j) opened from H(i,j-1)
-                    const T Ein = E;
-                    Hoe[r] = C::addmax(E, oe_raw, X);                  // H + o + e
-                    E = C::addmax(E, e_raw, X);                        // Eq. 4 for row i+1
-                    if (TB) {
-                        // a >= b  <=>  sign bit (bit 15 / 31 per lane) of b - a - 1 ... expressed per cell type
+                    if (r + 1 < R) Adn = C::addc(Hoe[r], sigma_r(r + 1));  // old Hoe[r]: next row's diagonal
+                    if (!TB) {
+                        // one 3-input maximum for H; local mode keeps F >= 0 (exact for H:
+                        // max(F, 0) follows the same recurrence), which makes H >= 0 without
+                        // a separate clamp
+                        if (MODE == LOCAL) F[r] = C::vmax3(C::addc(F[r], e_c), Hoe[r], zero);  // Eq. 5
+                        else F[r] = C::addmax(F[r], e_raw, Hoe[r]);                            // Eq. 5
+                        const T Hn = C::vmax3(Ad, F[r], E);                                    // Eq. 1
+                        Hoe[r] = C::addc(Hn, oe_c);
+                        E = C::addmax(E, e_raw, Hoe[r]);                                       // Eq. 4, row i+1
+                        // strict improvement of the row maximum: the column of its first occurrence
+                        if (MODE == LOCAL) C::track(rowmax[r], rowj0[r], rowj1[r], Hn, jj);
+                    } else {
+                        F[r] = C::addmax(F[r], e_raw, Hoe[r]);             // Eq. 5 (Hoe[r]: the left neighbour)
+                        const T M = (MODE == LOCAL) ? C::maxrelu(Ad, F[r]) : C::vmax(Ad, F[r]);
+                        const T X = C::addc(M, oe_c);                     // max(diag, F) + o + e
+                        const uint32_t fFo = C::ge(Hoe[r], F[r]);          // F(i,j) opened from H(i,j-1)
+                        const T Ein = E;
+                        Hoe[r] = C::addmax(E, oe_raw, X);                  // H + o + e
+                        E = C::addmax(E, e_raw, X);                        // Eq. 4 for row i+1
+                        // predecessor flags: a >= b is the sign bit (bit 15 / 31 per lane) of C::ge
                         uint32_t fD = C::ge(C::addc(Ad, oe_c), Hoe[r]);   // diagonal reaches H
                         uint32_t fE = C::ge(C::addc(Ein, oe_c), Hoe[r]);  // E reaches H
                         uint32_t fEo = C::ge(hup, Ein);                    // E(i,j) opened from H(i-1,j)
@@ -266,12 +277,7 @@ __device__ __noinline__ void run_slot(const BatchArgs &A, GroupSmem *sm, const S
                         pl_eo = (pl_eo >> 1) | (fEo & FM);
                         pl_fo = (pl_fo >> 1) | (fFo & FM);
                         hup = Hoe[r];
-                    }
-                    if (MODE == LOCAL) {
-                        // strict improvement of the row maximum: the column of its first occurrence
-                        const uint32_t gm = C::gt_mask(Hoe[r], rowmax[r]);
-                        rowj[r] = (jj & gm) | (rowj[r] & ~gm);
-                        rowmax[r] = C::vmax(rowmax[r], Hoe[r]);
+                        if (MODE == LOCAL) C::track(rowmax[r], rowj0[r], rowj1[r], C::addc(Hoe[r], moe_c), jj);
                     }
                     Ad = Adn;
                 }
@@ -323,8 +329,8 @@ __device__ __noinline__ void run_slot(const BatchArgs &A, GroupSmem *sm, const S
             for (int h = 0; h < C::PAIRS; h++) {
 #pragma unroll
                 for (int r = 0; r < R; r++) {
-                    const int32_t i = rb + r - sl.pad[h], v = C::get(rowmax[r], h) - oe;
-                    const int32_t j = C::PAIRS == 2 ? (int32_t)((rowj[r] >> (16 * h)) & 0xFFFFu) : (int32_t)rowj[r];
+                    const int32_t i = rb + r - sl.pad[h], v = C::get(rowmax[r], h);
+                    const int32_t j = (int32_t)(h == 0 ? rowj0[r] : rowj1[r]);
                     if (i >= 1 && v > 0) {
                         const uint64_t k = end_key(v, i, j);
                         best[h] = k > best[h] ? k : best[h];

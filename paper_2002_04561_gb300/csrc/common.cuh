@@ -46,7 +46,17 @@ struct CellI32 {
     __device__ __forceinline__ static uint32_t raw(int32_t c) { return (uint32_t)c; }
     __device__ __forceinline__ static T addmax(T a, uint32_t b, T c) { return __viaddmax_s32(a, (int32_t)b, c); }
     __device__ __forceinline__ static T vmax(T a, T b) { return max(a, b); }
+    // row maximum with the first column of a strict improvement (j0: the column):
+    // keep the column unless v > mx
+    __device__ __forceinline__ static void track(T &mx, uint32_t &j0, uint32_t &, T v, uint32_t j) {
+        asm("{ .reg .pred k;\n\t"
+            "setp.ge.s32 k, %0, %2;\n\t"
+            "max.s32 %0, %0, %2;\n\t"
+            "selp.b32 %1, %1, %3, k; }"
+            : "+r"(mx), "+r"(j0) : "r"(v), "r"(j));
+    }
     __device__ __forceinline__ static T maxrelu(T a, T b) { return __vimax_s32_relu(a, b); }
+    __device__ __forceinline__ static T vmax3(T a, T b, T c) { return __vimax3_s32(a, b, c); }
     // sigma' >= 0 from a row profile word (4 bytes indexed by subject letter)
     __device__ __forceinline__ static T sigma(uint32_t pa, uint32_t pb, uint32_t sel) {
         (void)pb; return (int32_t)prmt(pa, pa, sel);
@@ -62,7 +72,6 @@ struct CellI32 {
     __device__ __forceinline__ static uint32_t ge(T a, T b) { return (uint32_t)(b - a - 1); }
     __device__ __forceinline__ static uint32_t flag_mask() { return 0x80000000u; }
     // all ones where a > b
-    __device__ __forceinline__ static uint32_t gt_mask(T a, T b) { return a > b ? 0xFFFFFFFFu : 0u; }
     __device__ __forceinline__ static uint32_t zero_hoe(int32_t oe) { return (uint32_t)oe; }
     // selector of a column past the end of the pair: the sign byte of profile byte 0
     // in all four bytes (sigma' = 0 or -1)
@@ -89,7 +98,26 @@ struct CellI16x2 {
     __device__ __forceinline__ static uint32_t raw(int32_t c) { return ((uint32_t)c & 0xFFFFu) * 65537u; }
     __device__ __forceinline__ static T addmax(T a, uint32_t b, T c) { return __viaddmax_u16x2(a, b, c); }
     __device__ __forceinline__ static T vmax(T a, T b) { return __vmaxu2(a, b); }
+    // row maxima of both halves with the first column of a strict improvement
+    // (j0: low half, j1: high half): a packed maximum, a per-half test that it
+    // kept the old value, and a select per half. Written out in PTX with the
+    // old maximum unpacked before it is overwritten (a read-write operand), so
+    // no register assignment can make the test compare the new maximum with
+    // itself.
+    __device__ __forceinline__ static void track(T &mx, uint32_t &j0, uint32_t &j1, T v, uint32_t j) {
+        asm("{ .reg .pred kl, kh;\n\t"
+            ".reg .u16 a0, a1, m0, m1;\n\t"
+            "mov.b32 {a0, a1}, %0;\n\t"
+            "max.u16x2 %0, %0, %3;\n\t"
+            "mov.b32 {m0, m1}, %0;\n\t"
+            "setp.eq.u16 kl, m0, a0;\n\t"
+            "setp.eq.u16 kh, m1, a1;\n\t"
+            "selp.b32 %1, %1, %4, kl;\n\t"
+            "selp.b32 %2, %2, %4, kh; }"
+            : "+r"(mx), "+r"(j0), "+r"(j1) : "r"(v), "r"(j));
+    }
     __device__ __forceinline__ static T maxrelu(T a, T b) { return __vimax3_u16x2(a, b, 0x80008000u); }
+    __device__ __forceinline__ static T vmax3(T a, T b, T c) { return __vimax3_u16x2(a, b, c); }
     __device__ __forceinline__ static T sigma(uint32_t pa, uint32_t pb, uint32_t sel) { return prmt(pa, pb, sel); }
     // low half: byte ca of pa, high half: byte cb of pb; bytes are >= 0 so the
     // sign replication fills zeros
@@ -103,9 +131,6 @@ struct CellI16x2 {
     // add because a - b + 2^15 stays inside [0, 2^16) when |a - b| < 2^15
     __device__ __forceinline__ static uint32_t ge(T a, T b) { return a + 0x80008000u - b; }
     __device__ __forceinline__ static uint32_t flag_mask() { return 0x80008000u; }
-    // all ones in each half where a > b: a - b - 1 + 2^15 has bit 15 set (no borrow
-    // across halves while |a - b| < 2^15), and prmt replicates the sign of bytes 1 and 3
-    __device__ __forceinline__ static uint32_t gt_mask(T a, T b) { return prmt(a + 0x7FFF7FFFu - b, 0u, 0xBB99u); }
     // selector nibbles 8 of a half past the end of its pair: the sign of profile
     // byte 0, which is >= 0, in both bytes (sigma' = 0)
     __device__ __forceinline__ static uint32_t null_past_end(uint32_t sel, bool va, bool vb) {

@@ -254,10 +254,9 @@ __global__ void __launch_bounds__(256, (WR <= 8 && !best_all(MODE)) ? 4 : 2) wav
                     E = C::addmax(E, e_raw, X);
                     if (ALL) {
                         // strict improvement of the row maximum: the column of its first occurrence
-                        if (Hoe[r] > rowmax[r]) {
-                            rowmax[r] = Hoe[r];
-                            rowj[r] = c + 1;
-                        }
+                        uint32_t unused = 0, jr = (uint32_t)rowj[r];
+                        C::track(rowmax[r], jr, unused, Hoe[r], (uint32_t)(c + 1));
+                        rowj[r] = (int32_t)jr;
                     }
                     if (TB) {
                         // the predecessor planes of the batched traceback (global mode)
