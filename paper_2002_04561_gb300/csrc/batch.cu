@@ -53,11 +53,17 @@ __device__ __forceinline__ void build_qprofile(const BatchArgs &A, const Slot &s
 // Local mode keeps, per row, the running maximum and the first column where it
 // occurs (a DPX maximum whose predicates flag a strict improvement per half,
 // and a select per half); the optimum is ranked after each chunk.
+// Refill block (columns) of a variant: 32, or 16 for the matrix path, whose
+// query profile leaves less shared memory for the rings (16-column blocks
+// halve them, so four 4-warp CTAs fit on an SM instead of three).
+__host__ __device__ constexpr int block_cols(int sigp) { return sigp ? 16 : 32; }
+
 template <class C, int MODE, int R, bool TB, int SIGP>
-__device__ __noinline__ void run_slot(const BatchArgs &A, GroupSmem *sm, const Slot &sl,
+__device__ __noinline__ void run_slot(const BatchArgs &A, GroupSmemT<4 * block_cols(SIGP)> *sm, const Slot &sl,
                                       int nch, int Mit, int g, int64_t gslot, int32_t *res, const int32_t *pid,
                                       uint32_t *qp, const int8_t *tab, uint32_t *lc) {
     typedef typename C::T T;
+    constexpr int BLOCK = block_cols(SIGP), RING = 4 * BLOCK;
     const int32_t o = A.o, e = A.e, oe = A.o + A.e;
     const uint32_t e_raw = C::raw(e), oe_raw = C::raw(oe);   // per-half constants of DPX add-max
     const uint32_t oe_c = C::cst(oe), e_c = C::cst(e), moe_c = C::cst(-oe);  // packed constants of IADD
@@ -111,7 +117,7 @@ __device__ __noinline__ void run_slot(const BatchArgs &A, GroupSmem *sm, const S
         //     the bottom ring (border of this chunk, or the query's last row)
         auto fill = [&](int blk) {
 #pragma unroll
-            for (int k = 0; k < 2; k++) {
+            for (int k = 0; k < BLOCK / 16; k++) {
                 int c = blk * BLOCK + g + 16 * k;
                 if (c < Mit) {
                     // columns past the end of a pair read a zero sigma' (sigma = open + extend):
@@ -143,7 +149,7 @@ __device__ __noinline__ void run_slot(const BatchArgs &A, GroupSmem *sm, const S
         };
         auto drain = [&](int blk) {
 #pragma unroll
-            for (int k = 0; k < 2; k++) {
+            for (int k = 0; k < BLOCK / 16; k++) {
                 int c = blk * BLOCK + g + 16 * k;
                 if (blk >= 0 && c < Mit) {
                     int32_t hv = sm->bot[2 * (c & (RING - 1))];
@@ -369,11 +375,11 @@ __device__ __noinline__ void run_slot(const BatchArgs &A, GroupSmem *sm, const S
 template <class C, int MODE, bool TB, int SIGP>
 __global__ void __launch_bounds__(SIGP ? 128 : 256, SIGP ? 4 : 2) batch_kernel(BatchArgs A) {
     constexpr int THREADS = SIGP ? 128 : 256;
-    __shared__ GroupSmem smem[THREADS / 16];
+    __shared__ GroupSmemT<4 * block_cols(SIGP)> smem[THREADS / 16];
     extern __shared__ __align__(16) uint8_t dyn_smem[];
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int grp = lane >> 4, g = lane & 15;
-    GroupSmem *sm = &smem[warp * 2 + grp];
+    GroupSmemT<4 * block_cols(SIGP)> *sm = &smem[warp * 2 + grp];
     int8_t *tab = nullptr;
     uint32_t *qp = nullptr;
     if (SIGP) {

@@ -29,11 +29,14 @@
 
 namespace anyseq {
 
-// Per-group shared memory: subject selectors, top and bottom border rings.
-struct __align__(16) GroupSmem {
-    uint32_t sel[RING];
-    int32_t top[2 * RING];  // (Hoe, E) of the row above the chunk
-    int32_t bot[2 * RING];  // (Hoe, E) of the chunk's last row
+// Per-group shared memory: subject selectors, top and bottom border rings of
+// RG columns (four refill blocks: the one being filled, the one being
+// computed, the one the last lanes still finish, the one being drained).
+template <int RG>
+struct __align__(16) GroupSmemT {
+    uint32_t sel[RG];
+    int32_t top[2 * RG];  // (Hoe, E) of the row above the chunk
+    int32_t bot[2 * RG];  // (Hoe, E) of the chunk's last row
 };
 
 // Column-0 value H(i, 0) of padded row with real index i (i <= 0: padding).
