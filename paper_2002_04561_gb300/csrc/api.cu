@@ -434,7 +434,7 @@ anyseq_status_t anyseq::batch_scores(anyseq_ctx *ctx, const BatchInput &in, cons
         const int32_t min_chunk = GROUP * (A.rmax_tab ? TUNE_MIN_R : TB_R);
         if (in.max_n > min_chunk) {
             A.scratch_cols = in.max_m + 1;
-            A.scratch = arena<int32_t>(ctx, "border", (size_t)grid * (sigp ? 8 : 16) * 2 * (size_t)A.scratch_cols, &s2);
+            A.scratch = arena<int32_t>(ctx, "border", (size_t)grid * (batch_threads(sigp) / GROUP) * 2 * (size_t)A.scratch_cols, &s2);
             if (s2 != ANYSEQ_OK) return s2;
         }
         CUDA_TRY(cudaMemsetAsync(A.counter, 0, sizeof(int32_t), st));

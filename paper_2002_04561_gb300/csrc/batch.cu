@@ -369,12 +369,12 @@ __device__ __noinline__ void run_slot(const BatchArgs &A, GroupSmemT<4 * block_c
 }
 
 // Persistent kernel: each warp pulls work items (2 slots of 16 lanes) from the
-// sorted list until it is empty. THREADS = 256 for the row-profile path, 128
-// for the matrix path (whose per-group query profile lives in dynamic shared
-// memory after a copy of the sigma' table).
+// sorted list until it is empty. THREADS = batch_threads (batch.h); the matrix
+// path's per-group query profile lives in dynamic shared memory after a copy
+// of the sigma' table.
 template <class C, int MODE, bool TB, int SIGP>
-__global__ void __launch_bounds__(SIGP ? 128 : 256, SIGP ? 4 : 2) batch_kernel(BatchArgs A) {
-    constexpr int THREADS = SIGP ? 128 : 256;
+__global__ void __launch_bounds__(batch_threads(SIGP), batch_min_ctas(SIGP)) batch_kernel(BatchArgs A) {
+    constexpr int THREADS = batch_threads(SIGP);
     __shared__ GroupSmemT<4 * block_cols(SIGP)> smem[THREADS / 16];
     extern __shared__ __align__(16) uint8_t dyn_smem[];
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
@@ -475,7 +475,7 @@ __global__ void __launch_bounds__(SIGP ? 128 : 256, SIGP ? 4 : 2) batch_kernel(B
 // Dynamic shared memory: [sigma table (1 KB) + per-group query profiles] for the
 // matrix path, then the per-group last-column buffers of the semi-global kernels.
 static size_t dyn_smem_bytes(int sigp, int alphabet, int mode, bool tb) {
-    const int groups = (sigp ? 128 : 256) / GROUP;
+    const int groups = batch_threads(sigp) / GROUP;
     const int rmax = (tb || sigp) ? TB_R : 16;
     return lc_offset(sigp, alphabet) + (mode == SEMIGLOBAL ? (size_t)groups * 2 * GROUP * rmax * 4 : 0);
 }
@@ -489,13 +489,13 @@ static int run_one(const BatchArgs *A, int alphabet, int grid, cudaStream_t st, 
     if (dyn) cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)dyn);
     if (occupancy) {
         int nb = 0;
-        if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, kern, SIGP ? 128 : 256, dyn) != cudaSuccess) {
+        if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, kern, batch_threads(SIGP), dyn) != cudaSuccess) {
             cudaGetLastError();
             nb = 1;
         }
         return nb < 1 ? 1 : nb;
     }
-    kern<<<grid, SIGP ? 128 : 256, dyn, st>>>(*A);
+    kern<<<grid, batch_threads(SIGP), dyn, st>>>(*A);
     *err = cudaGetLastError();
     return 0;
 }

@@ -110,6 +110,12 @@ __device__ __forceinline__ ItemPlan plan_item(const int32_t *list, int64_t n_lis
 cudaError_t launch_batch(const BatchArgs &A, int cell32, int mode, int tb, int sigp, int grid, cudaStream_t st);
 int batch_blocks_per_sm(int cell32, int mode, int tb, int sigp, int alphabet);
 constexpr int QP_ROWS = 128;        // rows of the shared-memory query profile (chunk of 16 lanes x 8 rows)
+// Threads per CTA of the batched kernel and the CTAs per SM its register
+// budget is compiled for: 4-warp CTAs, four per SM (16 warps at 128
+// registers). Measured on short reads: 2 % faster than 8-warp CTAs at the same
+// occupancy; 20 or 24 warps at 12 rows per lane (80-96 registers) were slower.
+__host__ __device__ constexpr int batch_threads(int sigp) { return sigp ? 128 : 128; }
+__host__ __device__ constexpr int batch_min_ctas(int sigp) { return sigp ? 4 : 4; }
 // Rows per lane of the traceback kernels (one 32-bit direction word per lane, step and pair).
 constexpr int TB_R = 8;
 // Smallest rows-per-lane cap a tuned table may set (a chunk of GROUP * 4 rows).
