@@ -354,12 +354,11 @@ __device__ __noinline__ void band_slot(const BandArgs &A, BandSmem *sm, int32_t 
                     T E = up_e;
 #pragma unroll
                     for (int r = 0; r < BR; r++) {
-                        F[r] = C::addmax(F[r], e_raw, Hoe[r]);
-                        const T M = C::vmax(Ad, F[r]);
-                        const T X = C::addc(M, oe_c);
+                        F[r] = C::addmax(F[r], e_raw, Hoe[r]);                 // Eq. 5
+                        const T Hn = C::vmax3(Ad, F[r], E);                    // Eq. 1, one 3-input maximum
                         if (r + 1 < BR) Ad = C::addc(Hoe[r], (uint32_t)C::sigma(prof[r + 1], prof[r + 1], sel));
-                        Hoe[r] = C::addmax(E, oe_raw, X);
-                        E = C::addmax(E, e_raw, X);
+                        Hoe[r] = C::addc(Hn, oe_c);
+                        E = C::addmax(E, e_raw, Hoe[r]);                       // Eq. 4, row i+1
                     }
                     last_hoe = Hoe[BR - 1];
                     last_e = E;

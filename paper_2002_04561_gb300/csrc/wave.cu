@@ -57,7 +57,7 @@ __host__ __device__ constexpr bool best_edge(int mode) { return mode == SEMIGLOB
 // its first column (rows per lane 8 there, the extra registers), over the edge
 // from the last column (at each lane's last-column step) and the last row (the
 // last stripe's bottom row).
-template <int WR, bool TB, int MODE>
+template <int WR, bool TB, int MODE, bool TRI>
 __global__ void __launch_bounds__(256, (WR <= 8 && !best_all(MODE)) ? 4 : 2) wave_kernel(WaveArgs A) {
     constexpr int INIT = wave_init_mode(MODE);
     constexpr bool ALL = best_all(MODE), EDGE = best_edge(MODE);
@@ -70,7 +70,7 @@ __global__ void __launch_bounds__(256, (WR <= 8 && !best_all(MODE)) ? 4 : 2) wav
     typedef CellI32 C;
     typedef int32_t T;
     const int32_t o = A.o, e = A.e, oe = A.o + A.e;
-    const uint32_t e_raw = C::raw(e), oe_raw = C::raw(oe), oe_c = C::cst(oe);
+    const uint32_t e_raw = C::raw(e), oe_raw = C::raw(oe), oe_c = C::cst(oe), e_c = C::cst(e);
     for (;;) {
         int32_t t = 0;
         if (g == 0) t = atomicAdd(A.stripe_counter, 1);
@@ -242,16 +242,28 @@ __global__ void __launch_bounds__(256, (WR <= 8 && !best_all(MODE)) ? 4 : 2) wav
                 uint32_t pl_s0 = 0, pl_s1 = 0, pl_eo = 0, pl_fo = 0;
 #pragma unroll
                 for (int r = 0; r < WR; r++) {
-                    F[r] = C::addmax(F[r], e_raw, Hoe[r]);
-                    const T M = (MODE == LOCAL) ? C::maxrelu(Ad, F[r]) : C::vmax(Ad, F[r]);  // the clamp at 0
-                    const T X = C::addc(M, oe_c);
                     const T Adr = Ad;
                     if (r + 1 < WR) Ad = C::addc(Hoe[r], (uint32_t)C::sigma(prof[r + 1], prof[r + 1], sel));
                     uint32_t fFo = 0;
-                    if (TB) fFo = C::ge(Hoe[r], F[r]);                 // F(i,j) opened from H(i,j-1)
                     Ein = E;
-                    Hoe[r] = C::addmax(E, oe_raw, X);
-                    E = C::addmax(E, e_raw, X);
+                    if (TRI) {
+                        // H by one 3-input maximum: fewer instructions, but a chain of three
+                        // through the rows instead of one, so the launch picks it only when
+                        // enough stripes run side by side to hide the latency. Local mode
+                        // keeps F >= 0 instead of clamping H (exact for H: max(F, 0)
+                        // follows the same recurrence)
+                        if (MODE == LOCAL) F[r] = C::vmax3(C::addc(F[r], e_c), Hoe[r], 0);  // Eq. 5
+                        else F[r] = C::addmax(F[r], e_raw, Hoe[r]);                        // Eq. 5
+                        Hoe[r] = C::addc(C::vmax3(Adr, F[r], E), oe_c);                    // Eq. 1
+                        E = C::addmax(E, e_raw, Hoe[r]);                                   // Eq. 4, row i+1
+                    } else {
+                        F[r] = C::addmax(F[r], e_raw, Hoe[r]);                             // Eq. 5
+                        const T M = (MODE == LOCAL) ? C::maxrelu(Adr, F[r]) : C::vmax(Adr, F[r]);  // the clamp at 0
+                        const T X = C::addc(M, oe_c);
+                        if (TB) fFo = C::ge(Hoe[r], F[r]);         // F(i,j) opened from H(i,j-1)
+                        Hoe[r] = C::addmax(E, oe_raw, X);                                  // Eq. 1
+                        E = C::addmax(E, e_raw, X);                                        // Eq. 4, row i+1
+                    }
                     if (ALL) {
                         // strict improvement of the row maximum: the column of its first occurrence
                         uint32_t unused = 0, jr = (uint32_t)rowj[r];
@@ -344,10 +356,10 @@ __global__ void __launch_bounds__(256, (WR <= 8 && !best_all(MODE)) ? 4 : 2) wav
     }
 }
 
-template <int WR, bool TB, int MODE>
+template <int WR, bool TB, int MODE, bool TRI = false>
 static int blocks_per_sm() {
     int nb = 0;
-    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, wave_kernel<WR, TB, MODE>, 256, 0) != cudaSuccess) {
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, wave_kernel<WR, TB, MODE, TRI>, 256, 0) != cudaSuccess) {
         cudaGetLastError();
         nb = 1;
     }
@@ -364,13 +376,21 @@ int wave_rows_per_lane(int64_t total_rows, int num_sms, int64_t n_passes, int mo
     return 16 * stripes16 <= (int64_t)num_sms * blocks_per_sm<16, false, GLOBAL>() * 8 ? 8 : 16;
 }
 
-template <int WR, bool TB, int MODE>
+template <int WR, bool TB, int MODE, bool TRI = false>
 static void launch_one(const WaveArgs &A, int num_sms, cudaStream_t st) {
-    wave_kernel<WR, TB, MODE><<<num_sms * blocks_per_sm<WR, TB, MODE>(), 256, 0, st>>>(A);
+    wave_kernel<WR, TB, MODE, TRI><<<num_sms * blocks_per_sm<WR, TB, MODE, TRI>(), 256, 0, st>>>(A);
 }
+
+// 16-row stripes side by side per SM from which the 3-input-maximum cell wins
+// in global passes (measured on single pairs: up to 6.4 stripes per SM it was
+// up to 4 % slower, from 9 per SM 12 % faster; in semi-global passes, where it
+// spills, slower at every size).
+constexpr int WAVE_TRI_STRIPES_PER_SM = 8;
 
 cudaError_t launch_wave(const WaveArgs &A, int num_sms, cudaStream_t st) {
     const bool tb = A.dirs != nullptr;
+    const bool tri = A.mode == GLOBAL && A.rows_per_lane >= 16 &&
+                     (int64_t)A.n_stripes >= (int64_t)WAVE_TRI_STRIPES_PER_SM * num_sms;
     // the stripe table was built for A.rows_per_lane (from wave_rows_per_lane)
     if (A.mode != GLOBAL && (tb || A.rows_per_lane != (best_all(A.mode) ? 8 : 16))) return cudaErrorInvalidValue;
     if (A.mode == LOCAL) {
@@ -388,6 +408,7 @@ cudaError_t launch_wave(const WaveArgs &A, int num_sms, cudaStream_t st) {
         else launch_one<8, false, GLOBAL>(A, num_sms, st);
     } else {
         if (tb) launch_one<16, true, GLOBAL>(A, num_sms, st);
+        else if (tri) launch_one<16, false, GLOBAL, true>(A, num_sms, st);
         else launch_one<16, false, GLOBAL>(A, num_sms, st);
     }
     return cudaGetLastError();
