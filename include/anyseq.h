@@ -198,8 +198,10 @@ anyseq_status_t anyseq_band_train(anyseq_ctx *ctx, const uint8_t *q, const int64
  * band that fails its certificate before the full DP; "band_area_pct" (default
  * 60) sends a pair whose band would exceed that share of its matrix to the full
  * DP, "band_area16_pct" (default 15) the same for pairs that pass the int16
- * range test (the full DP runs those two per 32-bit lane). Unknown keys:
- * ANYSEQ_ERR_ARG. */
+ * range test (the full DP runs those two per 32-bit lane); "wave_cell"
+ * (default 0) picks the wavefront's cell update in global passes: 0 by the
+ * number of stripes side by side, 1 always the three-input maximum, 2 always
+ * the two-step form (results are the same). Unknown keys: ANYSEQ_ERR_ARG. */
 anyseq_status_t anyseq_set_option(anyseq_ctx *ctx, const char *key, int64_t value);
 
 /* Statistics of the context's last call (host values, valid after the call's

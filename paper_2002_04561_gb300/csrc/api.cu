@@ -114,6 +114,11 @@ extern "C" anyseq_status_t anyseq_set_option(anyseq_ctx *ctx, const char *key, i
         ctx->band_area16_pct = (int32_t)value;
         return ANYSEQ_OK;
     }
+    if (!strcmp(key, "wave_cell")) {
+        if (value < 0 || value > 2) return fail(ANYSEQ_ERR_ARG, "wave_cell must be 0, 1 or 2");
+        ctx->wave_cell = (int32_t)value;
+        return ANYSEQ_OK;
+    }
     if (!strcmp(key, "autotune_reset")) {
         ctx->tuned = false;
         ctx->tune_gain = 1.0;

@@ -44,7 +44,8 @@ struct anyseq_ctx {
     uint8_t *d_tune_tab = nullptr;
     unsigned long long *d_bin_stats = nullptr;
     bool tuned = false;
-    double tune_gain = 1.0;  // default time / tuned time on the tuning sample
+    double tune_gain = 1.0;
+    int32_t wave_cell = 0;  // wavefront cell of global passes: 0 by stripe count, 1 three-input max, 2 two-step  // default time / tuned time on the tuning sample
     std::vector<Buf> bufs;        // device scratch, grown on demand, reused across calls
     std::vector<Buf> pinned;      // pinned host staging
     // Named device buffer of at least 'bytes'; contents are not preserved on growth.

@@ -275,6 +275,7 @@ anyseq_status_t run_wave_passes(anyseq_ctx *ctx, const uint32_t *q2, const uint3
     W.last_H = H;
     W.last_E = E;
     W.spin_limit = ctx->spin_limit;
+    W.cell = ctx->wave_cell;
     W.rows_per_lane = wr;
     W.dirs = nullptr;
     if (tb) {

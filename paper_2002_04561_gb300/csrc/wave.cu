@@ -390,7 +390,7 @@ constexpr int WAVE_TRI_STRIPES_PER_SM = 8;
 cudaError_t launch_wave(const WaveArgs &A, int num_sms, cudaStream_t st) {
     const bool tb = A.dirs != nullptr;
     const bool tri = A.mode == GLOBAL && A.rows_per_lane >= 16 &&
-                     (int64_t)A.n_stripes >= (int64_t)WAVE_TRI_STRIPES_PER_SM * num_sms;
+                     (A.cell == 1 || (A.cell == 0 && (int64_t)A.n_stripes >= (int64_t)WAVE_TRI_STRIPES_PER_SM * num_sms));
     // the stripe table was built for A.rows_per_lane (from wave_rows_per_lane)
     if (A.mode != GLOBAL && (tb || A.rows_per_lane != (best_all(A.mode) ? 8 : 16))) return cudaErrorInvalidValue;
     if (A.mode == LOCAL) {

@@ -37,6 +37,7 @@ struct WaveArgs {
     uint32_t *dirs;               // optional: traceback direction words (global mode)
     int32_t mode;                 // GLOBAL, LOCAL, SEMIGLOBAL or an anchored mode (every pass)
     uint64_t *best;               // local / semi-global: per pass the best cell's key (initialised)
+    int32_t cell;                 // global passes: 0 = by stripe count, 1 = 3-input maximum, 2 = two-step
 };
 
 // Wavefront-only modes of the start-cell pass of a local or semi-global

@@ -244,3 +244,22 @@ def test_small_batches_on_the_wavefront_all_modes(pkg, ctx, mode):
     want = oracle.score_batch(b, oracle.Scoring(*C4), mode)
     assert np.array_equal(out["score"], want[0])
     assert np.array_equal(out["end_q"], want[1]) and np.array_equal(out["end_s"], want[2])
+
+
+@pytest.mark.parametrize("cell", [1, 2])
+def test_wavefront_cell_forms_match_oracle(pkg, ctx, cell):
+    """Both cell updates of the wavefront's global passes (the three-input
+    maximum, picked for launches with many stripes, and the two-step form)
+    give the oracle's scores and divide-and-conquer CIGARs on pairs that span
+    several stripes."""
+    ctx.set_option("wave_cell", cell)
+    try:
+        for k, (n, extra) in enumerate([(513, 7), (1800, -40), (3000, 11)]):
+            q, s = related(n, extra, seed=3600 + k)
+            out, _ = ctx.align_long(q, s, pkg.Scoring.make(*C4))
+            assert out["score"][0] == oracle.score(q, s, oracle.Scoring(*C4))[0]
+            res, cig = long_cigar(pkg, ctx, q, s, C4)
+            want, _ = oracle.hirschberg(q, s, oracle.Scoring(*C4))
+            assert np.array_equal(cig, want)
+    finally:
+        ctx.set_option("wave_cell", 0)
