@@ -439,6 +439,26 @@ def profile_protein(n_pairs: int):
                       "dp32_ms": ctx.stat("dp32_ms"), "pairs16": ctx.stat("pairs16"), "pairs32": ctx.stat("pairs32")}))
 
 
+def profile_cigar(n_pairs: int):
+    """The first n_pairs short reads, semi-global, score + optimum cell + CIGAR,
+    aligned twice (a small case for ncu captures of the traceback path)."""
+    import torch
+    import paper_2002_04561_gb300 as pkg
+    pkg.load(build_if_missing=True)
+    ctx = pkg.Context(0)
+    ctx.set_option("profile", 1)
+    b = synth.short_reads(n_pairs=n_pairs)
+    dev = lambda a: torch.from_numpy(np.ascontiguousarray(a)).cuda()
+    args = (dev(b.q), dev(b.q_off), dev(b.s), dev(b.s_off))
+    sc = pkg.Scoring.make(*SCORING)
+    res = torch.zeros(b.n_pairs * 40, dtype=torch.uint8, device="cuda")
+    cig = torch.zeros(int(b.q_len().sum() + b.s_len().sum() + b.n_pairs), dtype=torch.int32, device="cuda")
+    for _ in range(2):
+        _, used = ctx.align_batch(*args, sc, MODE, want=7, out=res, cigar=cig)
+    torch.cuda.synchronize()
+    print(json.dumps({"profile_cigar": n_pairs, "cells": b.cells(), "dp_ms": ctx.stat("dp_ms"), "cigar_words": used}))
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -452,6 +472,8 @@ def main():
                     help="profiling case: only the wavefront score of one N-letter long pair, twice")
     ap.add_argument("--profile-protein", type=int, default=0, metavar="N",
                     help="profiling case: only the protein local scores of the first N pairs, twice")
+    ap.add_argument("--profile-cigar", type=int, default=0, metavar="N",
+                    help="profiling case: only the first N short reads with CIGAR, twice")
     args = ap.parse_args()
     ws, rank, local = dist_env()
 
@@ -460,6 +482,9 @@ def main():
         return
     if args.profile_protein:
         profile_protein(args.profile_protein)
+        return
+    if args.profile_cigar:
+        profile_cigar(args.profile_cigar)
         return
 
     if args.impl == "reference":
