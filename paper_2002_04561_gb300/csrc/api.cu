@@ -114,6 +114,11 @@ extern "C" anyseq_status_t anyseq_set_option(anyseq_ctx *ctx, const char *key, i
         ctx->band_area16_pct = (int32_t)value;
         return ANYSEQ_OK;
     }
+    if (!strcmp(key, "tb_walker")) {
+        if (value < 0 || value > 2) return fail(ANYSEQ_ERR_ARG, "tb_walker must be 0, 1 or 2");
+        ctx->tb_walker = (int32_t)value;
+        return ANYSEQ_OK;
+    }
     if (!strcmp(key, "wave_cell")) {
         if (value < 0 || value > 2) return fail(ANYSEQ_ERR_ARG, "wave_cell must be 0, 1 or 2");
         ctx->wave_cell = (int32_t)value;
@@ -561,6 +566,7 @@ extern "C" anyseq_status_t anyseq_align_batch(anyseq_ctx *ctx, const uint8_t *q,
         W.dirs = tbo.dirs; W.dir_base = tbo.dir_base; W.lay_pad = tbo.lay_pad; W.lay_ch0 = tbo.lay_ch0;
         W.lanes_per_chunk = tbo.lanes_per_chunk;
         W.rows_per_lane = tbo.rows_per_lane;
+        W.walker = ctx->tb_walker;
         W.tmp = arena<uint32_t>(ctx, "tb_tmp", (size_t)(in.q_len + in.s_len + n_pairs + 1), &s2);
         clen = W.cig_len = arena<int64_t>(ctx, "tb_clen", n_pairs + 1, &s2);
         coff = arena<int64_t>(ctx, "tb_coff", n_pairs + 1, &s2);

@@ -171,6 +171,88 @@ __global__ void __launch_bounds__(TB_WARPS * 32) tb_walk_kernel(TbWalkArgs W) {
     }
 }
 
+// One thread per pair: the same walk, reading each direction word from global
+// memory (the last word stays in a register, so vertical steps inside a lane's
+// 8 rows reuse it). A walk is a chain of dependent loads; with one walker per
+// thread a whole batch keeps tens of thousands of them in flight, where the
+// warp walk keeps one per warp. Used for large batches (launch_tb_walk).
+__global__ void __launch_bounds__(256) tb_walk_thread_kernel(TbWalkArgs W) {
+    for (int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; p < W.n_pairs;
+         p += (int64_t)gridDim.x * blockDim.x) {
+        const int32_t n = (int32_t)(W.q_off[p + 1] - W.q_off[p]);
+        const int32_t m = (int32_t)(W.s_off[p + 1] - W.s_off[p]);
+        Runs rl;
+        rl.out = W.tmp + W.q_off[p] + W.s_off[p] + p;
+        rl.k = 0;
+        rl.op = 0;
+        rl.len = 0;
+        int32_t i = W.end_q[p], j = W.end_s[p];
+        if (n == 0 || m == 0) {
+            if (W.mode == GLOBAL) {
+                rl.push(2u, (uint32_t)m);
+                rl.push(1u, (uint32_t)n);
+                i = 0;
+                j = 0;
+            }
+        } else {
+            const uint32_t *dw = W.dirs + W.dir_base[p];
+            const int32_t pad = W.lay_pad[p], ch0 = W.lay_ch0[p];
+            const int32_t lpc = W.lanes_per_chunk, wpl = W.rows_per_lane / 8;
+            const int32_t gpc = lpc * wpl;
+            const int64_t S = m + lpc - 1;
+            int64_t cached = -1;
+            uint32_t w = 0;
+            // the word of cell (ii, jj) and its row bit r
+            auto word = [&](int32_t ii, int32_t jj, int32_t &r) -> uint32_t {
+                const int32_t ip = ii + pad - 1, rg = ip / TB_R;
+                r = ip % TB_R;
+                const int32_t ch = rg / gpc, gl = (rg % gpc) / wpl, sub = rg % wpl;
+                const int64_t idx = (((int64_t)(ch - ch0) * S + (jj - 1) + gl) * lpc + gl) * wpl + sub;
+                if (idx != cached) {
+                    cached = idx;
+                    w = dw[idx];
+                }
+                return w;
+            };
+            int state = 0;  // 0: H, 1: E, 2: F
+            for (int64_t guard = 2 * ((int64_t)n + m) + 4; guard > 0; guard--) {
+                if (state != 0 && (i <= 0 || j <= 0)) break;
+                if (state == 0) {
+                    if (i == 0 && j == 0) break;
+                    if (W.mode != GLOBAL) {
+                        if (i == 0 || j == 0) break;
+                    } else {
+                        if (j == 0) { rl.push(1u, (uint32_t)i); i = 0; break; }
+                        if (i == 0) { rl.push(2u, (uint32_t)j); j = 0; break; }
+                    }
+                    int32_t r;
+                    const uint32_t x = word(i, j, r);
+                    const uint32_t s0 = (x >> r) & 1u, s1 = (x >> (8 + r)) & 1u;
+                    if (W.mode == LOCAL && s0 && s1) break;  // H = 0: the alignment starts here
+                    if (s0) { rl.push(0u, 1u); i--; j--; }
+                    else state = s1 ? 1 : 2;
+                } else {
+                    int32_t r;
+                    const uint32_t x = word(i, j, r);
+                    if (state == 1) {
+                        rl.push(1u, 1u);
+                        if ((x >> (16 + r)) & 1u) state = 0;
+                        i--;
+                    } else {
+                        rl.push(2u, 1u);
+                        if ((x >> (24 + r)) & 1u) state = 0;
+                        j--;
+                    }
+                }
+            }
+        }
+        rl.flush();
+        W.cig_len[p] = rl.k;
+        W.beg_q[p] = i;
+        W.beg_s[p] = j;
+    }
+}
+
 // Reverse each pair's runs into the output buffer at its offset.
 __global__ void tb_compact_kernel(int64_t n_pairs, const int64_t *q_off, const int64_t *s_off, const uint32_t *tmp,
                                   const int64_t *cig_len, const int64_t *cig_off, uint32_t *out) {
@@ -193,7 +275,17 @@ cudaError_t launch_tb_plan(const int32_t *list, const int64_t *n_list, int per_i
     return cudaGetLastError();
 }
 
+// Pairs from which a batch walks one thread per pair. Below it, the warp walk's
+// staged windows keep a single long walk short; above it, there are enough
+// walks to keep memory busy with one dependent load each.
+constexpr int64_t TB_THREAD_WALK_PAIRS = 4096;
+
 cudaError_t launch_tb_walk(const TbWalkArgs &W, cudaStream_t st) {
+    const bool per_thread = W.walker == 2 || (W.walker == 0 && W.n_pairs >= TB_THREAD_WALK_PAIRS);
+    if (per_thread) {
+        tb_walk_thread_kernel<<<grid_of(W.n_pairs), 256, 0, st>>>(W);
+        return cudaGetLastError();
+    }
     int64_t blocks = (W.n_pairs + TB_WARPS - 1) / TB_WARPS;
     blocks = blocks < 1 ? 1 : (blocks > 65535 ? 65535 : blocks);
     tb_walk_kernel<<<(int)blocks, TB_WARPS * 32, 0, st>>>(W);

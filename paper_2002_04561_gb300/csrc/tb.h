@@ -20,6 +20,7 @@ struct TbWalkArgs {
     // rows (rows_per_lane a multiple of 8), steps = m + lanes_per_chunk - 1 per chunk,
     // rows_per_lane / 8 words per lane and step (byte planes of 8 rows each)
     int32_t lanes_per_chunk, rows_per_lane;
+    int32_t walker;       // 0: by batch size, 1: a warp per pair, 2: a thread per pair
 };
 
 cudaError_t launch_tb_plan(const int32_t *list, const int64_t *n_list, int per_item, int64_t max_items,

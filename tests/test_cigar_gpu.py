@@ -178,3 +178,18 @@ def test_small_global_batches_on_the_wavefront(pkg, ctx, sc_args):
     for b in (single, synth.from_pairs(related), synth.from_pairs([unrelated, empty, related[0]])):
         res, cigars, _ = gpu_align(pkg, ctx, b, sc_args, 0)
         assert_cigar_parity(b, res, cigars, sc_args, 0)
+
+
+@pytest.mark.parametrize("walker", [1, 2])
+@pytest.mark.parametrize("mode", [0, 1, 2])
+def test_both_walkers_match_oracle(pkg, ctx, mode, walker):
+    """The traceback walk as a warp per pair (staged windows) and as a thread
+    per pair give the oracle's start cells and CIGARs."""
+    b = synth.random_pairs(300, 0, 400, seed=4800 + mode, related=0.7, p_sub=0.05, p_indel=0.02)
+    ctx.set_option("tb_walker", walker)
+    try:
+        res, cigars, used = gpu_align(pkg, ctx, b, (2, -3, -5, -2), mode)
+        assert used == sum(len(c) for c in cigars)
+        assert_cigar_parity(b, res, cigars, (2, -3, -5, -2), mode)
+    finally:
+        ctx.set_option("tb_walker", 0)
