@@ -66,7 +66,7 @@ __device__ __noinline__ void run_slot(const BatchArgs &A, GroupSmemT<4 * block_c
     constexpr int BLOCK = block_cols(SIGP), RING = 4 * BLOCK;
     const int32_t o = A.o, e = A.e, oe = A.o + A.e;
     const uint32_t e_raw = C::raw(e), oe_raw = C::raw(oe);   // per-half constants of DPX add-max
-    const uint32_t oe_c = C::cst(oe), e_c = C::cst(e), moe_c = C::cst(-oe);  // packed constants of IADD
+    const uint32_t oe_c = C::cst(oe), e_c = C::cst(e);       // packed constants of IADD
     const T zero = C::make(0, 0);                            // H = 0 in both halves
     const T NEGv = C::make(C::NEG, C::NEG);
     const int CH = GROUP * R;
@@ -260,20 +260,21 @@ __device__ __noinline__ void run_slot(const BatchArgs &A, GroupSmemT<4 * block_c
                         // strict improvement of the row maximum: the column of its first occurrence
                         if (MODE == LOCAL) C::track(rowmax[r], rowj0[r], rowj1[r], Hn, jj);
                     } else {
-                        F[r] = C::addmax(F[r], e_raw, Hoe[r]);             // Eq. 5 (Hoe[r]: the left neighbour)
-                        const T M = (MODE == LOCAL) ? C::maxrelu(Ad, F[r]) : C::vmax(Ad, F[r]);
-                        const T X = C::addc(M, oe_c);                     // max(diag, F) + o + e
+                        // the same cell, and the predecessor flags of the traceback: each
+                        // is the sign bit (bit 15 / 31 per lane) of a biased difference
+                        if (MODE == LOCAL) F[r] = C::vmax3(C::addc(F[r], e_c), Hoe[r], zero);  // Eq. 5
+                        else F[r] = C::addmax(F[r], e_raw, Hoe[r]);                            // Eq. 5
                         const uint32_t fFo = C::ge(Hoe[r], F[r]);          // F(i,j) opened from H(i,j-1)
-                        const T Ein = E;
-                        Hoe[r] = C::addmax(E, oe_raw, X);                  // H + o + e
-                        E = C::addmax(E, e_raw, X);                        // Eq. 4 for row i+1
-                        // predecessor flags: a >= b is the sign bit (bit 15 / 31 per lane) of C::ge
-                        uint32_t fD = C::ge(C::addc(Ad, oe_c), Hoe[r]);   // diagonal reaches H
-                        uint32_t fE = C::ge(C::addc(Ein, oe_c), Hoe[r]);  // E reaches H
-                        uint32_t fEo = C::ge(hup, Ein);                    // E(i,j) opened from H(i-1,j)
+                        const T Ein = E;                                   // E(i,j)
+                        const T Hn = C::vmax3(Ad, F[r], E);                // Eq. 1
+                        Hoe[r] = C::addc(Hn, oe_c);
+                        E = C::addmax(E, e_raw, Hoe[r]);                   // Eq. 4, row i+1
+                        const uint32_t fD = C::ge(Ad, Hn);                 // diagonal reaches H
+                        const uint32_t fE = C::ge(Ein, Hn);                // E reaches H
+                        const uint32_t fEo = C::ge(hup, Ein);              // E(i,j) opened from H(i-1,j)
                         uint32_t s0 = fD, s1 = fE;
                         if (MODE == LOCAL) {
-                            uint32_t fZ = C::ge(C::from_u(C::zero_hoe(oe)), Hoe[r]);  // H == 0
+                            const uint32_t fZ = C::ge(zero, Hn);           // H == 0 (H >= 0 here)
                             s0 = fZ | fD;
                             s1 = fZ | (fE & ~fD);
                         }
@@ -283,7 +284,7 @@ __device__ __noinline__ void run_slot(const BatchArgs &A, GroupSmemT<4 * block_c
                         pl_eo = (pl_eo >> 1) | (fEo & FM);
                         pl_fo = (pl_fo >> 1) | (fFo & FM);
                         hup = Hoe[r];
-                        if (MODE == LOCAL) C::track(rowmax[r], rowj0[r], rowj1[r], C::addc(Hoe[r], moe_c), jj);
+                        if (MODE == LOCAL) C::track(rowmax[r], rowj0[r], rowj1[r], Hn, jj);
                     }
                     Ad = Adn;
                 }

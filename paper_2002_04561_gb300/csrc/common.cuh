@@ -71,8 +71,6 @@ struct CellI32 {
     // flag word: bit 31 set iff a >= b (sign of b - a - 1; |a - b| < 2^31)
     __device__ __forceinline__ static uint32_t ge(T a, T b) { return (uint32_t)(b - a - 1); }
     __device__ __forceinline__ static uint32_t flag_mask() { return 0x80000000u; }
-    // all ones where a > b
-    __device__ __forceinline__ static uint32_t zero_hoe(int32_t oe) { return (uint32_t)oe; }
     // selector of a column past the end of the pair: the sign byte of profile byte 0
     // in all four bytes (sigma' = 0 or -1)
     __device__ __forceinline__ static uint32_t null_past_end(uint32_t sel, bool va, bool vb) {
@@ -135,9 +133,6 @@ struct CellI16x2 {
     // byte 0, which is >= 0, in both bytes (sigma' = 0)
     __device__ __forceinline__ static uint32_t null_past_end(uint32_t sel, bool va, bool vb) {
         return (va ? (sel & 0x00FFu) : 0x0088u) | (vb ? (sel & 0xFF00u) : 0x8800u);
-    }
-    __device__ __forceinline__ static uint32_t zero_hoe(int32_t oe) {
-        return ((uint32_t)(oe + 32768) & 0xFFFFu) * 65537u;
     }
 };
 
