@@ -414,10 +414,15 @@ anyseq_status_t anyseq::batch_scores(anyseq_ctx *ctx, const BatchInput &in, cons
         int64_t *stmp = arena<int64_t>(ctx, "scan_tmp", scan_tmp_words(n) + 2, &s2);
         A.lay_pad = arena<int32_t>(ctx, "tb_pad", n + 1, &s2);
         A.lay_ch0 = arena<int32_t>(ctx, "tb_ch0", n + 1, &s2);
+        int32_t *lay_r = arena<int32_t>(ctx, "tb_rows", n + 1, &s2);
         if (s2 != ANYSEQ_OK) return s2;
         CUDA_TRY(cudaMemsetAsync(words, 0, n * sizeof(int64_t), st));
-        CUDA_TRY(launch_tb_plan(P.list16, P.counts + 0, 4, (n + 3) / 4 + 1, in.q_off, in.s_off, words, A.lay_pad, A.lay_ch0, st));
-        CUDA_TRY(launch_tb_plan(P.list32, P.counts + 1, 2, (n + 1) / 2 + 1, in.q_off, in.s_off, words, A.lay_pad, A.lay_ch0, st));
+        // the DP kernels' row caps: TB_R fixed on the matrix path, else an even R up to row_rmax
+        CUDA_TRY(launch_tb_plan(P.list16, P.counts + 0, 4, (n + 3) / 4 + 1, in.q_off, in.s_off, words, A.lay_pad,
+                                A.lay_ch0, lay_r, sigp ? TB_R : row_rmax(mode, 2, true), sigp ? TB_R : 0, st));
+        CUDA_TRY(launch_tb_plan(P.list32, P.counts + 1, 2, (n + 1) / 2 + 1, in.q_off, in.s_off, words, A.lay_pad,
+                                A.lay_ch0, lay_r, sigp ? TB_R : row_rmax(mode, 1, true), sigp ? TB_R : 0, st));
+        tb->lay_r = lay_r;
         CUDA_TRY(scan_exclusive_i64(words, base, n, stmp, stmp + scan_tmp_words(n), st));
         int64_t total = 0;
         CUDA_TRY(cudaMemcpyAsync(&total, stmp + scan_tmp_words(n), sizeof(int64_t), cudaMemcpyDeviceToHost, st));
@@ -566,6 +571,7 @@ extern "C" anyseq_status_t anyseq_align_batch(anyseq_ctx *ctx, const uint8_t *q,
         W.dirs = tbo.dirs; W.dir_base = tbo.dir_base; W.lay_pad = tbo.lay_pad; W.lay_ch0 = tbo.lay_ch0;
         W.lanes_per_chunk = tbo.lanes_per_chunk;
         W.rows_per_lane = tbo.rows_per_lane;
+        W.lay_r = tbo.lay_r;
         W.walker = ctx->tb_walker;
         W.tmp = arena<uint32_t>(ctx, "tb_tmp", (size_t)(in.q_len + in.s_len + n_pairs + 1), &s2);
         clen = W.cig_len = arena<int64_t>(ctx, "tb_clen", n_pairs + 1, &s2);

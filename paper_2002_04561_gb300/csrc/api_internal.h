@@ -78,8 +78,9 @@ struct TbOut {
     uint32_t *dirs = nullptr;
     int64_t *dir_base = nullptr;
     int32_t *lay_pad = nullptr, *lay_ch0 = nullptr;
+    int32_t *lay_r = nullptr;                         // rows per lane of each pair (batched kernel)
     int64_t dir_words = 0;
-    int32_t lanes_per_chunk = 16, rows_per_lane = 8;  // layout (batched kernel: 16 x TB_R)
+    int32_t lanes_per_chunk = 16, rows_per_lane = 8;  // layout when lay_r is null (wavefront: 32 x 8 or 16)
 };
 
 // Small batches on the wavefront: scores, end cells and (global, with tb) the

@@ -178,8 +178,10 @@ __device__ __noinline__ void run_slot(const BatchArgs &A, GroupSmemT<4 * block_c
         __syncwarp();
         int drained = 0;  // next bottom block to drain
 
-        // traceback: this chunk's direction words of each half (row chunks before
-        // the pair's first real row are not stored)
+        // traceback: this chunk's direction words of each half, WPL words per lane
+        // and step (rows 8k..8k+7 of the lane in word k; row chunks before the
+        // pair's first real row are not stored)
+        constexpr int WPL = (R + 7) / 8;
         uint32_t *dptr[2] = {nullptr, nullptr};
         int32_t Sh[2] = {0, 0};
         if (TB) {
@@ -188,7 +190,7 @@ __device__ __noinline__ void run_slot(const BatchArgs &A, GroupSmemT<4 * block_c
                 int32_t ch0 = sl.pad[h] / CH;
                 Sh[h] = sl.m[h] + GROUP - 1;
                 if (pid[h] >= 0 && ch >= ch0)
-                    dptr[h] = A.dirs + A.dir_base[pid[h]] + (int64_t)(ch - ch0) * Sh[h] * GROUP + g;
+                    dptr[h] = A.dirs + A.dir_base[pid[h]] + ((int64_t)(ch - ch0) * Sh[h] * GROUP + g) * WPL;
             }
         }
         // diag starts as H(i0-1, 0) and afterwards is the Hoe that came down at the
@@ -291,10 +293,22 @@ __device__ __noinline__ void run_slot(const BatchArgs &A, GroupSmemT<4 * block_c
                 last_hoe = Hoe[R - 1];
                 last_e = E;
                 if (TB) {
-                    uint32_t w01 = prmt(pl_s0, pl_s1, 0x7351u);   // s0.b1 s1.b1 s0.b3 s1.b3
-                    uint32_t w23 = prmt(pl_eo, pl_fo, 0x7351u);
-                    if (dptr[0] && s < Sh[0]) dptr[0][(int64_t)s * GROUP] = C::PAIRS == 2 ? prmt(w01, w23, 0x5410u) : prmt(w01, w23, 0x7632u);
-                    if (C::PAIRS == 2 && dptr[1] && s < Sh[1]) dptr[1][(int64_t)s * GROUP] = prmt(w01, w23, 0x7632u);
+                    // each plane holds R rows per half, the last row in the half's top bit:
+                    // one shift brings rows 0..7 / 8..15 of the low half to bytes 0 / 1 and
+                    // those of the high half (int16x2) to bytes 2 / 3; the bits between
+                    // are zero. Word k of a half: bytes s0, s1, E opened, F opened of rows
+                    // 8k..8k+7.
+                    constexpr int SH = C::PAIRS == 2 ? 16 - R : 32 - R;
+                    const uint32_t x0 = pl_s0 >> SH, x1 = pl_s1 >> SH, x2 = pl_eo >> SH, x3 = pl_fo >> SH;
+#pragma unroll
+                    for (int k = 0; k < WPL; k++) {
+                        const uint32_t a = prmt(x0, x1, (uint32_t)(k | ((4 + k) << 4) | ((2 + k) << 8) | ((6 + k) << 12)));
+                        const uint32_t b = prmt(x2, x3, (uint32_t)(k | ((4 + k) << 4) | ((2 + k) << 8) | ((6 + k) << 12)));
+                        // a: s0/s1 bytes of the low half, then of the high half; b likewise
+                        if (dptr[0] && s < Sh[0]) dptr[0][(int64_t)s * GROUP * WPL + k] = prmt(a, b, 0x5410u);
+                        if (C::PAIRS == 2 && dptr[1] && s < Sh[1])
+                            dptr[1][(int64_t)s * GROUP * WPL + k] = prmt(a, b, 0x7632u);
+                    }
                 }
                 if (g == GROUP - 1)
                     reinterpret_cast<int2 *>(sm->bot)[c & (RING - 1)] =
@@ -391,8 +405,9 @@ __global__ void __launch_bounds__(batch_threads(SIGP), batch_min_ctas(SIGP)) bat
     }
     const int64_t gslot = ((int64_t)blockIdx.x * (THREADS >> 5) + warp) * 2 + grp;
     // rows per lane: at most 16 (12 for local int16x2, which also keeps per-row
-    // maxima and columns); exactly TB_R for the traceback and matrix kernels
-    constexpr int RMAX = (TB || SIGP) ? TB_R : ((MODE == LOCAL && C::PAIRS == 2) ? 12 : 16);
+    // maxima and columns); exactly TB_R for the matrix kernels, whose query
+    // profile covers 16 x TB_R rows
+    constexpr int RMAX = SIGP ? TB_R : row_rmax(MODE, C::PAIRS, TB);
     uint32_t *lc = nullptr;
     if (MODE == SEMIGLOBAL)
         lc = reinterpret_cast<uint32_t *>(dyn_smem + lc_offset(SIGP, A.alphabet)) + (warp * 2 + grp) * 2 * GROUP * RMAX;
@@ -404,8 +419,8 @@ __global__ void __launch_bounds__(batch_threads(SIGP), batch_min_ctas(SIGP)) bat
         if (lane == 0) item = atomicAdd(A.counter, 1);
         item = __shfl_sync(0xffffffffu, item, 0);
         if (item >= n_items) break;
-        ItemPlan P = plan_item(A.list, n_list, item, per_item, A.q_off, A.s_off, RMAX, !(TB || SIGP));
-        if (TB || SIGP) P.R = TB_R;
+        ItemPlan P = plan_item(A.list, n_list, item, per_item, A.q_off, A.s_off, RMAX, !SIGP);
+        if (SIGP) P.R = TB_R;
         uint32_t tbin = 0;
         if (!(TB || SIGP) && (A.rmax_tab || A.bin_stats)) {
             // the tuned tile shape of this item's length bin (rows per lane cap)
@@ -438,7 +453,7 @@ __global__ void __launch_bounds__(batch_threads(SIGP), batch_min_ctas(SIGP)) bat
             // the host sizes the border scratch for every multi-chunk query; never reached
             continue;
         }
-        if (TB || SIGP) {
+        if (SIGP) {
             run_slot<C, MODE, TB_R, TB, SIGP>(A, sm, sl, P.nch, P.Mit, g, gslot, res, pid, qp, tab, lc);
         } else {
             switch (P.R) {
@@ -447,7 +462,7 @@ __global__ void __launch_bounds__(batch_threads(SIGP), batch_min_ctas(SIGP)) bat
                 case 6: run_slot<C, MODE, 6, TB, SIGP>(A, sm, sl, P.nch, P.Mit, g, gslot, res, pid, qp, tab, lc); break;
                 case 8: run_slot<C, MODE, 8, TB, SIGP>(A, sm, sl, P.nch, P.Mit, g, gslot, res, pid, qp, tab, lc); break;
                 case 10: run_slot<C, MODE, 10, TB, SIGP>(A, sm, sl, P.nch, P.Mit, g, gslot, res, pid, qp, tab, lc); break;
-                case 12: run_slot<C, MODE, 12, TB, SIGP>(A, sm, sl, P.nch, P.Mit, g, gslot, res, pid, qp, tab, lc); break;
+                case 12: run_slot<C, MODE, (RMAX < 12 ? RMAX : 12), TB, SIGP>(A, sm, sl, P.nch, P.Mit, g, gslot, res, pid, qp, tab, lc); break;
                 case 14: run_slot<C, MODE, (RMAX < 14 ? RMAX : 14), TB, SIGP>(A, sm, sl, P.nch, P.Mit, g, gslot, res, pid, qp, tab, lc); break;
                 default: run_slot<C, MODE, RMAX, TB, SIGP>(A, sm, sl, P.nch, P.Mit, g, gslot, res, pid, qp, tab, lc); break;
             }
@@ -477,7 +492,7 @@ __global__ void __launch_bounds__(batch_threads(SIGP), batch_min_ctas(SIGP)) bat
 // matrix path, then the per-group last-column buffers of the semi-global kernels.
 static size_t dyn_smem_bytes(int sigp, int alphabet, int mode, bool tb) {
     const int groups = batch_threads(sigp) / GROUP;
-    const int rmax = (tb || sigp) ? TB_R : 16;
+    const int rmax = sigp ? TB_R : 16;
     return lc_offset(sigp, alphabet) + (mode == SEMIGLOBAL ? (size_t)groups * 2 * GROUP * rmax * 4 : 0);
 }
 

@@ -4,8 +4,9 @@
 // buffer.
 //
 // Direction words: for every pair, row chunk (from the first chunk holding a
-// real row), step s and lane g, one 32-bit word for the lane's 8 rows:
-//   byte 0: s0, byte 1: s1, byte 2: E opened, byte 3: F opened  (bit r = row r)
+// real row), step s, lane g and k < ceil(R / 8), one 32-bit word for rows
+// 8k..8k+7 of the lane's R rows:
+//   byte 0: s0, byte 1: s1, byte 2: E opened, byte 3: F opened  (bit t = row 8k+t)
 // H-source from (s0, s1): global/semi-global (1,x) DIAG, (0,1) E, (0,0) F;
 // local (1,0) DIAG, (0,1) E, (0,0) F, (1,1) ZERO (H = 0 ends the alignment).
 #include "batch.h"
@@ -14,22 +15,61 @@
 
 namespace anyseq {
 
+// Direction-word layout of one pair: lpc lanes of R rows per chunk, S steps
+// per chunk, wpl = ceil(R / 8) words per lane and step.
+struct TbLayout {
+    int32_t pad, ch0, R, wpl, lpc;
+    int64_t S;
+};
+
+__device__ __forceinline__ TbLayout tb_layout(const TbWalkArgs &W, int64_t p, int32_t m) {
+    TbLayout L;
+    L.pad = W.lay_pad[p];
+    L.ch0 = W.lay_ch0[p];
+    L.R = W.lay_r ? W.lay_r[p] : W.rows_per_lane;
+    L.wpl = (L.R + 7) / 8;
+    L.lpc = W.lanes_per_chunk;
+    L.S = (int64_t)m + L.lpc - 1;
+    return L;
+}
+
+// The word unit (chunk, lane, word of the lane) of DP row ii, numbered in
+// increasing row order, and the row's bit in it.
+__device__ __forceinline__ int64_t tb_unit(const TbLayout &L, int32_t ii, int32_t &bit) {
+    const int32_t ip = ii + L.pad - 1, chr = L.lpc * L.R;
+    const int32_t ch = ip / chr, within = ip % chr, gl = within / L.R, rr = within % L.R;
+    bit = rr & 7;
+    return ((int64_t)ch * L.lpc + gl) * L.wpl + (rr >> 3);
+}
+
+// Index of the word of unit u at column jj (step jj - 1 + lane).
+__device__ __forceinline__ int64_t tb_word_index(const TbLayout &L, int64_t u, int32_t jj) {
+    const int64_t per_chunk = (int64_t)L.lpc * L.wpl;
+    const int64_t ch = u / per_chunk, rem = u % per_chunk;
+    const int32_t gl = (int32_t)(rem / L.wpl), sub = (int32_t)(rem % L.wpl);
+    return (((ch - L.ch0) * L.S + (jj - 1) + gl) * L.lpc + gl) * L.wpl + sub;
+}
+
 __global__ void tb_plan_kernel(const int32_t *list, const int64_t *n_list_p, int per_item, const int64_t *q_off,
-                               const int64_t *s_off, int64_t *words, int32_t *lay_pad, int32_t *lay_ch0) {
+                               const int64_t *s_off, int64_t *words, int32_t *lay_pad, int32_t *lay_ch0,
+                               int32_t *lay_r, int rmax, int fixed_r) {
     const int64_t n_list = *n_list_p;
     const int64_t n_items = (n_list + per_item - 1) / per_item;
     for (int64_t item = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; item < n_items;
          item += (int64_t)gridDim.x * blockDim.x) {
-        ItemPlan P = plan_item(list, n_list, item, per_item, q_off, s_off, TB_R, false);
-        const int32_t CH = GROUP * TB_R;
+        // the DP kernel's own plan of the item
+        ItemPlan P = plan_item(list, n_list, item, per_item, q_off, s_off, rmax, fixed_r == 0);
+        if (fixed_r) P.R = fixed_r;
+        const int32_t CH = GROUP * P.R;
         for (int k = 0; k < per_item; k++) {
             int32_t p = P.pid[k];
             if (p < 0) continue;
             int32_t pad = P.nch * CH - P.n[k];
             int32_t ch0 = pad / CH;
-            words[p] = (int64_t)(P.nch - ch0) * (P.m[k] + GROUP - 1) * GROUP;
+            words[p] = (int64_t)(P.nch - ch0) * (P.m[k] + GROUP - 1) * GROUP * ((P.R + 7) / 8);
             lay_pad[p] = pad;
             lay_ch0[p] = ch0;
+            lay_r[p] = P.R;
         }
     }
 }
@@ -60,7 +100,7 @@ struct Runs {
 // leaving the window triggers the next load. This turns one dependent global
 // load per step into one per window.
 constexpr int TBW = 32;                  // window height and width (cells)
-constexpr int TBG = TBW / TB_R + 1;      // row groups a window can touch
+constexpr int TBG = TBW / 2 + 1;         // word units a window can touch (lanes of 2 rows at least)
 constexpr int TB_WARPS = 8;              // warps per block of the walk
 
 __global__ void __launch_bounds__(TB_WARPS * 32) tb_walk_kernel(TbWalkArgs W) {
@@ -86,10 +126,7 @@ __global__ void __launch_bounds__(TB_WARPS * 32) tb_walk_kernel(TbWalkArgs W) {
             }
         } else {
             const uint32_t *dw = W.dirs + W.dir_base[p];
-            const int32_t pad = W.lay_pad[p], ch0 = W.lay_ch0[p];
-            const int32_t lpc = W.lanes_per_chunk, wpl = W.rows_per_lane / 8;  // words per lane and step
-            const int32_t gpc = lpc * wpl;                                      // row groups of 8 per chunk
-            const int64_t S = m + lpc - 1;
+            const TbLayout L = tb_layout(W, p, m);
             int state = 0;  // 0: H, 1: E, 2: F
             bool done = false;
             // every step moves up or left within two iterations; the bound and the
@@ -98,16 +135,13 @@ __global__ void __launch_bounds__(TB_WARPS * 32) tb_walk_kernel(TbWalkArgs W) {
             while (!done) {
                 // stage the window below-right of (i, j): rows i_lo..i, columns j_lo..j
                 const int32_t i_lo = max(1, i - TBW + 1), j_lo = max(1, j - TBW + 1);
-                const int32_t rg_lo = (i_lo + pad - 1) / TB_R;  // row group of the window's top row
+                int32_t unused;
+                const int64_t rg_lo = tb_unit(L, i_lo, unused);  // word unit of the window's top row
                 if (i >= 1 && j >= 1) {
-                    const int32_t rg_hi = (i + pad - 1) / TB_R;
+                    const int64_t rg_hi = tb_unit(L, i, unused);
                     const int32_t jj = j - lane;
                     if (jj >= j_lo) {
-                        for (int32_t rg = rg_lo; rg <= rg_hi; rg++) {
-                            const int32_t ch = rg / gpc, gl = (rg % gpc) / wpl, sub = rg % wpl;
-                            const int64_t s = (int64_t)(jj - 1) + gl;
-                            wn[rg - rg_lo][lane] = dw[(((int64_t)(ch - ch0) * S + s) * lpc + gl) * wpl + sub];
-                        }
+                        for (int64_t rg = rg_lo; rg <= rg_hi; rg++) wn[rg - rg_lo][lane] = dw[tb_word_index(L, rg, jj)];
                     }
                 }
                 __syncwarp();
@@ -115,9 +149,7 @@ __global__ void __launch_bounds__(TB_WARPS * 32) tb_walk_kernel(TbWalkArgs W) {
                     const int32_t jtop = j;  // the window's right column (j moves while walking)
                     // the word of (ii, jj) inside the window, r = its row bit
                     auto word = [&](int32_t ii, int32_t jj, int32_t &r) -> uint32_t {
-                        const int32_t ip = ii + pad - 1;
-                        r = ip % TB_R;
-                        return wn[ip / TB_R - rg_lo][jtop - jj];
+                        return wn[tb_unit(L, ii, r) - rg_lo][jtop - jj];
                     };
                     auto inside = [&](int32_t ii, int32_t jj) { return ii >= i_lo && jj >= j_lo && jj <= jtop; };
                     for (; guard > 0; guard--) {
@@ -196,18 +228,12 @@ __global__ void __launch_bounds__(256) tb_walk_thread_kernel(TbWalkArgs W) {
             }
         } else {
             const uint32_t *dw = W.dirs + W.dir_base[p];
-            const int32_t pad = W.lay_pad[p], ch0 = W.lay_ch0[p];
-            const int32_t lpc = W.lanes_per_chunk, wpl = W.rows_per_lane / 8;
-            const int32_t gpc = lpc * wpl;
-            const int64_t S = m + lpc - 1;
+            const TbLayout L = tb_layout(W, p, m);
             int64_t cached = -1;
             uint32_t w = 0;
             // the word of cell (ii, jj) and its row bit r
             auto word = [&](int32_t ii, int32_t jj, int32_t &r) -> uint32_t {
-                const int32_t ip = ii + pad - 1, rg = ip / TB_R;
-                r = ip % TB_R;
-                const int32_t ch = rg / gpc, gl = (rg % gpc) / wpl, sub = rg % wpl;
-                const int64_t idx = (((int64_t)(ch - ch0) * S + (jj - 1) + gl) * lpc + gl) * wpl + sub;
+                const int64_t idx = tb_word_index(L, tb_unit(L, ii, r), jj);
                 if (idx != cached) {
                     cached = idx;
                     w = dw[idx];
@@ -270,8 +296,9 @@ static int grid_of(int64_t work) {
 
 cudaError_t launch_tb_plan(const int32_t *list, const int64_t *n_list, int per_item, int64_t max_items,
                            const int64_t *q_off, const int64_t *s_off, int64_t *words, int32_t *lay_pad,
-                           int32_t *lay_ch0, cudaStream_t st) {
-    tb_plan_kernel<<<grid_of(max_items), 256, 0, st>>>(list, n_list, per_item, q_off, s_off, words, lay_pad, lay_ch0);
+                           int32_t *lay_ch0, int32_t *lay_r, int rmax, int fixed_r, cudaStream_t st) {
+    tb_plan_kernel<<<grid_of(max_items), 256, 0, st>>>(list, n_list, per_item, q_off, s_off, words, lay_pad, lay_ch0,
+                                                        lay_r, rmax, fixed_r);
     return cudaGetLastError();
 }
 
