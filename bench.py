@@ -335,6 +335,21 @@ def secondary_workloads(pkg, ctx, device):
     ms = timed_events(lambda: ctx.align_batch(*args, sc, pkg.GLOBAL, want=7, out=res, cigar=cig), 20, stream)
     out["single_pair_1000x1100_cigar"] = {"us": 1e3 * ms, "GCUPS": b.cells() / ms / 1e6,
                                           "cpu_oracle": oracle_sample(b, (2, -1, 0, -2), 0, want_cigar=True)}
+    # the headline short reads with CIGAR (traceback DP, walk, compaction)
+    b = synth.short_reads()
+    sc = pkg.Scoring.make(*SCORING)
+    args = (dev(b.q), dev(b.q_off), dev(b.s), dev(b.s_off))
+    res = torch.zeros(b.n_pairs * 40, dtype=torch.uint8, device=device)
+    cig = torch.zeros(int(b.q_len().sum() + b.s_len().sum() + b.n_pairs), dtype=torch.int32, device=device)
+    ms = timed_events(lambda: ctx.align_batch(*args, sc, MODE, want=7, out=res, cigar=cig), 5, stream)
+    dp = []
+    for _ in range(3):
+        ctx.align_batch(*args, sc, MODE, want=7, out=res, cigar=cig)
+        dp.append(ctx.stat("dp_ms") + ctx.stat("dp32_ms"))
+    out["short_reads_262144_semiglobal_cigar"] = {
+        "ms": ms, "GCUPS": b.cells() / ms / 1e6, "dp_kernel_ms": statistics.median(dp),
+        "cpu_oracle": oracle_sample(b, SCORING, MODE, want_cigar=True)}
+    del res, cig
     # protein, local affine, score and CIGAR
     b = synth.protein_pairs()
     sc = pkg.Scoring.make(0, 0, -11, -1, matrix=synth.protein_matrix(3))
