@@ -33,21 +33,38 @@ __device__ __forceinline__ TbLayout tb_layout(const TbWalkArgs &W, int64_t p, in
     return L;
 }
 
-// The word unit (chunk, lane, word of the lane) of DP row ii, numbered in
-// increasing row order, and the row's bit in it.
-__device__ __forceinline__ int64_t tb_unit(const TbLayout &L, int32_t ii, int32_t &bit) {
+// Position of a DP row in the layout: chunk, lane, row of the lane. The walks
+// move up one row at a time, so after one division the position follows by
+// decrements (tb_up).
+struct TbCursor {
+    int32_t ch, gl, rr;
+};
+
+__device__ __forceinline__ TbCursor tb_cursor(const TbLayout &L, int32_t ii) {
     const int32_t ip = ii + L.pad - 1, chr = L.lpc * L.R;
-    const int32_t ch = ip / chr, within = ip % chr, gl = within / L.R, rr = within % L.R;
-    bit = rr & 7;
-    return ((int64_t)ch * L.lpc + gl) * L.wpl + (rr >> 3);
+    const int32_t within = ip % chr;
+    return TbCursor{ip / chr, within / L.R, within % L.R};
 }
 
-// Index of the word of unit u at column jj (step jj - 1 + lane).
-__device__ __forceinline__ int64_t tb_word_index(const TbLayout &L, int64_t u, int32_t jj) {
-    const int64_t per_chunk = (int64_t)L.lpc * L.wpl;
-    const int64_t ch = u / per_chunk, rem = u % per_chunk;
-    const int32_t gl = (int32_t)(rem / L.wpl), sub = (int32_t)(rem % L.wpl);
-    return (((ch - L.ch0) * L.S + (jj - 1) + gl) * L.lpc + gl) * L.wpl + sub;
+__device__ __forceinline__ void tb_up(const TbLayout &L, TbCursor &c) {
+    if (--c.rr < 0) {
+        c.rr = L.R - 1;
+        if (--c.gl < 0) {
+            c.gl = L.lpc - 1;
+            c.ch--;
+        }
+    }
+}
+
+// The word unit (chunk, lane, word of the lane) of a position, numbered in
+// increasing row order; the row's bit in the word is rr & 7.
+__device__ __forceinline__ int32_t tb_unit(const TbLayout &L, const TbCursor &c) {
+    return (c.ch * L.lpc + c.gl) * L.wpl + (c.rr >> 3);
+}
+
+// Index of the word of a position at column jj (step jj - 1 + lane).
+__device__ __forceinline__ int64_t tb_word_index(const TbLayout &L, int32_t ch, int32_t gl, int32_t sub, int32_t jj) {
+    return (((int64_t)(ch - L.ch0) * L.S + (jj - 1) + gl) * L.lpc + gl) * L.wpl + sub;
 }
 
 __global__ void tb_plan_kernel(const int32_t *list, const int64_t *n_list_p, int per_item, const int64_t *q_off,
@@ -135,21 +152,25 @@ __global__ void __launch_bounds__(TB_WARPS * 32) tb_walk_kernel(TbWalkArgs W) {
             while (!done) {
                 // stage the window below-right of (i, j): rows i_lo..i, columns j_lo..j
                 const int32_t i_lo = max(1, i - TBW + 1), j_lo = max(1, j - TBW + 1);
-                int32_t unused;
-                const int64_t rg_lo = tb_unit(L, i_lo, unused);  // word unit of the window's top row
+                const int32_t rg_lo = tb_unit(L, tb_cursor(L, i_lo));  // word unit of the window's top row
                 if (i >= 1 && j >= 1) {
-                    const int64_t rg_hi = tb_unit(L, i, unused);
-                    const int32_t jj = j - lane;
+                    const int32_t rg_hi = tb_unit(L, tb_cursor(L, i));
+                    const int32_t jj = j - lane, per_chunk = L.lpc * L.wpl;
                     if (jj >= j_lo) {
-                        for (int64_t rg = rg_lo; rg <= rg_hi; rg++) wn[rg - rg_lo][lane] = dw[tb_word_index(L, rg, jj)];
+                        for (int32_t rg = rg_lo; rg <= rg_hi; rg++) {
+                            const int32_t rem = rg % per_chunk;
+                            wn[rg - rg_lo][lane] = dw[tb_word_index(L, rg / per_chunk, rem / L.wpl, rem % L.wpl, jj)];
+                        }
                     }
                 }
                 __syncwarp();
                 if (lane == 0) {
                     const int32_t jtop = j;  // the window's right column (j moves while walking)
-                    // the word of (ii, jj) inside the window, r = its row bit
-                    auto word = [&](int32_t ii, int32_t jj, int32_t &r) -> uint32_t {
-                        return wn[tb_unit(L, ii, r) - rg_lo][jtop - jj];
+                    TbCursor cur = tb_cursor(L, i);  // row i; follows i downwards
+                    // the word of (i, jj) inside the window, r = its row bit
+                    auto word = [&](int32_t jj, int32_t &r) -> uint32_t {
+                        r = cur.rr & 7;
+                        return wn[tb_unit(L, cur) - rg_lo][jtop - jj];
                     };
                     auto inside = [&](int32_t ii, int32_t jj) { return ii >= i_lo && jj >= j_lo && jj <= jtop; };
                     for (; guard > 0; guard--) {
@@ -164,19 +185,20 @@ __global__ void __launch_bounds__(TB_WARPS * 32) tb_walk_kernel(TbWalkArgs W) {
                             }
                             if (!inside(i, j)) break;  // next window
                             int32_t r;
-                            const uint32_t w = word(i, j, r);
+                            const uint32_t w = word(j, r);
                             const uint32_t s0 = (w >> r) & 1u, s1 = (w >> (8 + r)) & 1u;
                             if (W.mode == LOCAL && s0 && s1) { done = true; break; }  // H = 0: the alignment starts here
-                            if (s0) { rl.push(0u, 1u); i--; j--; }
+                            if (s0) { rl.push(0u, 1u); i--; j--; tb_up(L, cur); }
                             else state = s1 ? 1 : 2;
                         } else {
                             if (!inside(i, j)) break;
                             int32_t r;
-                            const uint32_t w = word(i, j, r);
+                            const uint32_t w = word(j, r);
                             if (state == 1) {
                                 rl.push(1u, 1u);
                                 if ((w >> (16 + r)) & 1u) state = 0;
                                 i--;
+                                tb_up(L, cur);
                             } else {
                                 rl.push(2u, 1u);
                                 if ((w >> (24 + r)) & 1u) state = 0;
@@ -231,9 +253,11 @@ __global__ void __launch_bounds__(256) tb_walk_thread_kernel(TbWalkArgs W) {
             const TbLayout L = tb_layout(W, p, m);
             int64_t cached = -1;
             uint32_t w = 0;
-            // the word of cell (ii, jj) and its row bit r
-            auto word = [&](int32_t ii, int32_t jj, int32_t &r) -> uint32_t {
-                const int64_t idx = tb_word_index(L, tb_unit(L, ii, r), jj);
+            TbCursor cur = tb_cursor(L, i > 0 ? i : 1);  // row i; follows i downwards
+            // the word of cell (i, jj) and its row bit r
+            auto word = [&](int32_t jj, int32_t &r) -> uint32_t {
+                r = cur.rr & 7;
+                const int64_t idx = tb_word_index(L, cur.ch, cur.gl, cur.rr >> 3, jj);
                 if (idx != cached) {
                     cached = idx;
                     w = dw[idx];
@@ -252,18 +276,19 @@ __global__ void __launch_bounds__(256) tb_walk_thread_kernel(TbWalkArgs W) {
                         if (i == 0) { rl.push(2u, (uint32_t)j); j = 0; break; }
                     }
                     int32_t r;
-                    const uint32_t x = word(i, j, r);
+                    const uint32_t x = word(j, r);
                     const uint32_t s0 = (x >> r) & 1u, s1 = (x >> (8 + r)) & 1u;
                     if (W.mode == LOCAL && s0 && s1) break;  // H = 0: the alignment starts here
-                    if (s0) { rl.push(0u, 1u); i--; j--; }
+                    if (s0) { rl.push(0u, 1u); i--; j--; tb_up(L, cur); }
                     else state = s1 ? 1 : 2;
                 } else {
                     int32_t r;
-                    const uint32_t x = word(i, j, r);
+                    const uint32_t x = word(j, r);
                     if (state == 1) {
                         rl.push(1u, 1u);
                         if ((x >> (16 + r)) & 1u) state = 0;
                         i--;
+                        tb_up(L, cur);
                     } else {
                         rl.push(2u, 1u);
                         if ((x >> (24 + r)) & 1u) state = 0;
