@@ -138,10 +138,14 @@ anyseq_status_t anyseq_align_batch(anyseq_ctx *ctx,
  * or column 0 for semi-global), found by one more wavefront pass over the
  * reversed prefixes; the CIGAR is the global divide-and-conquer CIGAR of
  * q[beg_q .. end_q) against s[beg_s .. end_s). An empty optimum (score 0) has
- * no CIGAR words and begins at its end. Arguments as for anyseq_align_batch
- * with one pair of lengths n and m. Errors as there, and ERR_ARG for local and
- * semi-global pairs whose score could reach 2^21 (largest positive
- * substitution score times min(n, m)).
+ * no CIGAR words and begins at its end. Alphabets of up to 4 letters use 2-bit
+ * letters and row profiles; larger alphabets (a substitution matrix, up to 32
+ * letters) use byte letters and per-stripe query profiles in shared memory.
+ * Arguments as for anyseq_align_batch with one pair of lengths n and m. Errors
+ * as there, and ERR_ARG for local and semi-global pairs whose score could
+ * reach 2^21 (largest positive substitution score times min(n, m)), and for a
+ * scoring with sigma - open - extend (or extend - open - extend) outside
+ * [-128, 127].
  */
 anyseq_status_t anyseq_align_long(anyseq_ctx *ctx,
                                   const uint8_t *q, int64_t n,

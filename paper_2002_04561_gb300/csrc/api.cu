@@ -821,12 +821,12 @@ anyseq_status_t anyseq::long_scores(anyseq_ctx *ctx, const uint8_t *q, const int
 // multi-pass form used by the divide-and-conquer traceback).
 anyseq_status_t anyseq::long_last_row(anyseq_ctx *ctx, const uint32_t *q2, int64_t q0, int32_t n, const uint32_t *s2,
                                       int64_t s0, int32_t m, bool rev, int32_t tb, const anyseq_scoring_t *sc,
-                                      int32_t *H, int32_t *E, cudaStream_t st) {
+                                      int32_t *H, int32_t *E, cudaStream_t st, const MatLetters *mat) {
     std::vector<WavePass> passes(1);
     memset(passes.data(), 0, sizeof(WavePass));
     passes[0].q0 = q0; passes[0].s0 = s0; passes[0].n = n; passes[0].m = m;
     passes[0].tb = tb; passes[0].rev = rev ? 1 : 0; passes[0].out_off = 0;
-    return run_wave_passes(ctx, q2, s2, passes, sc, H, E, st);
+    return run_wave_passes(ctx, q2, s2, passes, sc, H, E, st, nullptr, ANYSEQ_GLOBAL, nullptr, mat);
 }
 
 // Start cell of a local or semi-global long-pair traceback (r holds the score
@@ -839,7 +839,7 @@ anyseq_status_t anyseq::long_last_row(anyseq_ctx *ctx, const uint32_t *q2, int64
 // empty optimum (S = 0) starts where it ends.
 anyseq_status_t anyseq::long_start_cell(anyseq_ctx *ctx, const uint32_t *q2, const uint32_t *s2p,
                                         const anyseq_scoring_t *sc, int32_t mode, anyseq_result_t &r,
-                                        cudaStream_t st) {
+                                        cudaStream_t st, const MatLetters *mat) {
     r.beg_q = r.end_q;
     r.beg_s = r.end_s;
     if (r.score <= 0 || r.end_q == 0 || r.end_s == 0) return ANYSEQ_OK;
@@ -854,7 +854,7 @@ anyseq_status_t anyseq::long_start_cell(anyseq_ctx *ctx, const uint32_t *q2, con
     passes[0].rev = 1;
     std::vector<uint64_t> keys;
     TRY(run_wave_passes(ctx, q2, s2p, passes, sc, H, nullptr, st, nullptr,
-                        mode == ANYSEQ_LOCAL ? ANCHORED_LOCAL : ANCHORED_SEMIGLOBAL, &keys));
+                        mode == ANYSEQ_LOCAL ? ANCHORED_LOCAL : ANCHORED_SEMIGLOBAL, &keys, mat));
     if (keys[0] == 0 || key_score(keys[0]) != r.score)
         return fail(ANYSEQ_ERR_CUDA, "start-cell pass found score %d, the optimum is %d",
                     keys[0] ? key_score(keys[0]) : -1, r.score);
@@ -876,8 +876,18 @@ extern "C" anyseq_status_t anyseq_align_long(anyseq_ctx *ctx, const uint8_t *q, 
         return fail(ANYSEQ_ERR_ARG, "local and semi-global long pairs below 2^21 letters");
     if (mode != ANYSEQ_GLOBAL && !key_range_ok(sc, n < m ? n : m))
         return fail(ANYSEQ_ERR_ARG, "local / semi-global scores of this pair may reach 2^21 (the optimum key's range)");
-    if (sc->alphabet > 4) return fail(ANYSEQ_ERR_ARG, "the long-pair path takes alphabets of at most 4 letters");
     if (!long_range_ok(sc, n, m)) return fail(ANYSEQ_ERR_ARG, "scores of this pair may leave the 32-bit range");
+    {
+        // the profiles hold sigma - open - extend (and the padding rows' value) in signed bytes
+        const int32_t oe = sc->gap_open + sc->gap_extend;
+        bool ok = sc->gap_extend - oe <= 127 && -oe <= 127;
+        for (int a = 0; a < sc->alphabet; a++)
+            for (int b = 0; b < sc->alphabet; b++) {
+                const int32_t v = sigma_host(sc, a, b) - oe;
+                ok = ok && v >= -128 && v <= 127;
+            }
+        if (!ok) return fail(ANYSEQ_ERR_ARG, "sigma - open - extend leaves the signed byte range on the long-pair path");
+    }
     cudaStream_t st = (cudaStream_t)cuda_stream;
     if (cudaSetDevice(ctx->device) != cudaSuccess) return fail(ANYSEQ_ERR_CUDA, "cudaSetDevice failed");
     ctx->launches = 0;
@@ -908,11 +918,17 @@ extern "C" anyseq_status_t anyseq_align_long(anyseq_ctx *ctx, const uint8_t *q, 
         int32_t *H = arena<int32_t>(ctx, "l_H", (size_t)m + 2, &s2);
         if (s2 != ANYSEQ_OK) return s2;
         CUDA_TRY(cudaMemsetAsync(bad, 0, sizeof(int32_t), st));
+        // letter check (and the 2-bit letters of alphabets up to 4)
         CUDA_TRY(launch_pack2bit((const uint8_t *)dq, n, q2, sc->alphabet, bad, st));
         CUDA_TRY(launch_pack2bit((const uint8_t *)ds, m, s2p, sc->alphabet, bad, st));
         ctx->launches += 2;
+        // alphabets above 4 letters (or the forced matrix path): byte letters and a sigma table
+        MatLetters ml;
+        ml.q8 = (const uint8_t *)dq;
+        ml.s8 = (const uint8_t *)ds;
+        const MatLetters *mat = (sc->alphabet > 4 || ctx->force_matrix) ? &ml : nullptr;
         if (mode == ANYSEQ_GLOBAL) {
-            TRY(long_last_row(ctx, q2, 0, (int32_t)n, s2p, 0, (int32_t)m, false, sc->gap_open, sc, H, nullptr, st));
+            TRY(long_last_row(ctx, q2, 0, (int32_t)n, s2p, 0, (int32_t)m, false, sc->gap_open, sc, H, nullptr, st, mat));
         } else {
             std::vector<WavePass> passes(1);
             memset(passes.data(), 0, sizeof(WavePass));
@@ -920,7 +936,7 @@ extern "C" anyseq_status_t anyseq_align_long(anyseq_ctx *ctx, const uint8_t *q, 
             passes[0].m = (int32_t)m;
             passes[0].tb = sc->gap_open;
             std::vector<uint64_t> keys;
-            TRY(run_wave_passes(ctx, q2, s2p, passes, sc, H, nullptr, st, nullptr, mode, &keys));
+            TRY(run_wave_passes(ctx, q2, s2p, passes, sc, H, nullptr, st, nullptr, mode, &keys, mat));
             r.score = key_score(keys[0]);
             r.end_q = key_i(keys[0]);
             r.end_s = key_j(keys[0]);
@@ -934,12 +950,12 @@ extern "C" anyseq_status_t anyseq_align_long(anyseq_ctx *ctx, const uint8_t *q, 
             CUDA_TRY(cudaStreamSynchronize(st));
         }
         if (want_cigar && mode == ANYSEQ_GLOBAL) {
-            TRY(hirschberg_cigar(ctx, q2, 0, (int32_t)n, s2p, 0, (int32_t)m, sc, hcig, st));
+            TRY(hirschberg_cigar(ctx, q2, 0, (int32_t)n, s2p, 0, (int32_t)m, sc, hcig, st, mat));
             r.beg_q = r.beg_s = 0;
         } else if (want_cigar) {
-            TRY(long_start_cell(ctx, q2, s2p, sc, mode, r, st));
+            TRY(long_start_cell(ctx, q2, s2p, sc, mode, r, st, mat));
             if (r.end_q > r.beg_q || r.end_s > r.beg_s)
-                TRY(hirschberg_cigar(ctx, q2, r.beg_q, r.end_q, s2p, r.beg_s, r.end_s, sc, hcig, st));
+                TRY(hirschberg_cigar(ctx, q2, r.beg_q, r.end_q, s2p, r.beg_s, r.end_s, sc, hcig, st, mat));
         }
     }
     if (want_cigar) {

@@ -83,6 +83,11 @@ struct TbOut {
     int32_t lanes_per_chunk = 16, rows_per_lane = 8;  // layout when lay_r is null (wavefront: 32 x 8 or 16)
 };
 
+// Letters of the long-pair path with a substitution matrix (alphabets above 4):
+// device codes one byte each, at the same positions as the 2-bit arrays.
+struct MatLetters {
+    const uint8_t *q8 = nullptr, *s8 = nullptr;
+};
 // Small batches on the wavefront: scores, end cells and (global, with tb) the
 // direction words of every pair; false in *used when the batch does not qualify.
 anyseq_status_t wave_batch(anyseq_ctx *ctx, const BatchInput &in, const anyseq_scoring_t *sc, int32_t mode,
@@ -103,7 +108,7 @@ anyseq_status_t long_scores(anyseq_ctx *ctx, const uint8_t *q, const int64_t *q_
                             int32_t *end_s = nullptr);
 anyseq_status_t long_last_row(anyseq_ctx *ctx, const uint32_t *q2, int64_t q0, int32_t n, const uint32_t *s2,
                               int64_t s0, int32_t m, bool rev, int32_t tb, const anyseq_scoring_t *sc, int32_t *H,
-                              int32_t *E, cudaStream_t st);
+                              int32_t *E, cudaStream_t st, const MatLetters *mat = nullptr);
 // Traceback output of a wavefront launch: direction words in the layout of the
 // batched traceback with 32 lanes x rows_per_lane rows per chunk (see tb.h);
 // each pass's first word is its dir_off.
@@ -114,16 +119,16 @@ struct WaveTb {
 anyseq_status_t run_wave_passes(anyseq_ctx *ctx, const uint32_t *q2, const uint32_t *s2,
                                 std::vector<WavePass> &passes, const anyseq_scoring_t *sc, int32_t *H, int32_t *E,
                                 cudaStream_t st, WaveTb *tb = nullptr, int32_t mode = ANYSEQ_GLOBAL,
-                                std::vector<uint64_t> *keys = nullptr);
+                                std::vector<uint64_t> *keys = nullptr, const MatLetters *mat = nullptr);
 // Start cell of a local / semi-global long-pair traceback from r's score and
 // optimum cell (sets r.beg_q, r.beg_s).
 anyseq_status_t long_start_cell(anyseq_ctx *ctx, const uint32_t *q2, const uint32_t *s2, const anyseq_scoring_t *sc,
-                                int32_t mode, anyseq_result_t &r, cudaStream_t st);
+                                int32_t mode, anyseq_result_t &r, cudaStream_t st, const MatLetters *mat = nullptr);
 // Global divide-and-conquer CIGAR of q[i0 .. i1) against s[j0 .. j1) (positions
 // in the packed arrays q2, s2).
 anyseq_status_t hirschberg_cigar(anyseq_ctx *ctx, const uint32_t *q2, int32_t i0, int32_t i1, const uint32_t *s2,
                                  int32_t j0, int32_t j1, const anyseq_scoring_t *sc, std::vector<uint32_t> &cigar,
-                                 cudaStream_t st);
+                                 cudaStream_t st, const MatLetters *mat = nullptr);
 
 // Scores and optimum cells of a batch; with tb != null also the direction words.
 anyseq_status_t batch_scores(anyseq_ctx *ctx, const BatchInput &in, const anyseq_scoring_t *sc, int32_t mode,

@@ -92,10 +92,18 @@ struct BaseArgs {
     int32_t *rows;
     uint32_t *pieces;
     int32_t *piece_len;
+    // substitution matrix: byte letter codes and sigma' per letter pair
+    const uint8_t *q8, *s8;
+    const int8_t *sig;
+    int32_t alphabet;
 };
 
 __device__ __forceinline__ int32_t sig(const BaseArgs &A, uint32_t a, uint32_t b, int32_t oe) {
+    if (A.sig) return (int32_t)A.sig[a * A.alphabet + b] + oe;
     return (int32_t)(int8_t)((A.rowprof[a] >> (8 * b)) & 0xFFu) + oe;
+}
+__device__ __forceinline__ uint32_t base_letter(const uint32_t *p2, const uint8_t *p8, int64_t k) {
+    return p8 ? (uint32_t)p8[k] : code2(p2, k);
 }
 
 // One thread per base case: the full-matrix global alignment with column-0
@@ -125,12 +133,12 @@ __global__ void hb_base_kernel(BaseArgs A) {
         for (int32_t j = 1; j <= m; j++) { Hrow[j] = o + j * e; Erow[j] = NEG32; }
         int32_t cornerD = 0, cornerE = 0, cornerF = 0;
         for (int32_t i = 1; i <= n; i++) {
-            const uint32_t qi = code2(A.q2, bc.q0 + i - 1);
+            const uint32_t qi = base_letter(A.q2, A.q8, bc.q0 + i - 1);
             int32_t diag = Hrow[0];
             Hrow[0] = bc.tb + i * e;
             int32_t F = NEG32, Hleft = Hrow[0];
             for (int32_t j = 1; j <= m; j++) {
-                const uint32_t sj = code2(A.s2, bc.s0 + j - 1);
+                const uint32_t sj = base_letter(A.s2, A.s8, bc.s0 + j - 1);
                 int32_t Eo = Hrow[j] + oe, Ee = Erow[j] + e;
                 int32_t Ev = Ee > Eo ? Ee : Eo;
                 int32_t Fo = Hleft + oe, Fe = F + e;
@@ -220,9 +228,28 @@ static T *arena_t(anyseq_ctx *ctx, const char *name, size_t count, anyseq_status
     return static_cast<T *>(ctx->get(name, count * sizeof(T) + 16, st));
 }
 
+// The sigma' table (sigma - open - extend per letter pair) of the matrix path on
+// the device; nullptr when the letters are 2-bit.
+static const int8_t *device_sig_table(anyseq_ctx *ctx, const anyseq_scoring_t *sc, const MatLetters *mat,
+                                      cudaStream_t st, anyseq_status_t *s) {
+    if (!mat) return nullptr;
+    const int32_t a = sc->alphabet, oe = sc->gap_open + sc->gap_extend;
+    int8_t h[WAVE_SIG_BYTES];
+    for (int x = 0; x < a; x++)
+        for (int y = 0; y < a; y++) h[x * a + y] = (int8_t)(sigma_host(sc, x, y) - oe);
+    int8_t *d = arena_t<int8_t>(ctx, "w_sig", WAVE_SIG_BYTES, s);
+    if (*s != ANYSEQ_OK) return nullptr;
+    if (cudaMemcpyAsync(d, h, (size_t)a * a, cudaMemcpyHostToDevice, st) != cudaSuccess) {
+        *s = fail(ANYSEQ_ERR_CUDA, "copying the sigma table failed");
+        return nullptr;
+    }
+    return d;
+}
+
 anyseq_status_t run_wave_passes(anyseq_ctx *ctx, const uint32_t *q2, const uint32_t *s2,
                                 std::vector<WavePass> &passes, const anyseq_scoring_t *sc, int32_t *H, int32_t *E,
-                                cudaStream_t st, WaveTb *tb, int32_t mode, std::vector<uint64_t> *keys) {
+                                cudaStream_t st, WaveTb *tb, int32_t mode, std::vector<uint64_t> *keys,
+                                const MatLetters *mat) {
     anyseq_status_t s2st = ANYSEQ_OK;
     int64_t border = 0, rows = 0;
     for (const auto &p : passes) rows += p.n;
@@ -276,6 +303,15 @@ anyseq_status_t run_wave_passes(anyseq_ctx *ctx, const uint32_t *q2, const uint3
     W.last_E = E;
     W.spin_limit = ctx->spin_limit;
     W.cell = ctx->wave_cell;
+    if (mat) {
+        W.mat = 1;
+        W.alphabet = sc->alphabet;
+        W.q8 = mat->q8;
+        W.s8 = mat->s8;
+        W.sig = device_sig_table(ctx, sc, mat, st, &s2st);
+        if (s2st != ANYSEQ_OK) return s2st;
+        W.sig_pad = (wave_init_mode(mode) == GLOBAL ? sc->gap_extend : 0) - (sc->gap_open + sc->gap_extend);
+    }
     W.rows_per_lane = wr;
     W.dirs = nullptr;
     if (tb) {
@@ -299,7 +335,7 @@ anyseq_status_t run_wave_passes(anyseq_ctx *ctx, const uint32_t *q2, const uint3
 
 anyseq_status_t hirschberg_cigar(anyseq_ctx *ctx, const uint32_t *q2, int32_t i0, int32_t i1, const uint32_t *s2,
                                  int32_t j0, int32_t j1, const anyseq_scoring_t *sc, std::vector<uint32_t> &cigar,
-                                 cudaStream_t st) {
+                                 cudaStream_t st, const MatLetters *mat) {
     anyseq_status_t s2st = ANYSEQ_OK;
     const int32_t o = sc->gap_open;
     std::vector<Node> nodes;
@@ -341,7 +377,7 @@ anyseq_status_t hirschberg_cigar(anyseq_ctx *ctx, const uint32_t *q2, int32_t i0
         int32_t *H = arena_t<int32_t>(ctx, "hb_H", (size_t)out + 1, &s2st);
         int32_t *E = arena_t<int32_t>(ctx, "hb_E", (size_t)out + 1, &s2st);
         if (s2st != ANYSEQ_OK) return s2st;
-        HB_TRY(run_wave_passes(ctx, q2, s2, passes, sc, H, E, st));
+        HB_TRY(run_wave_passes(ctx, q2, s2, passes, sc, H, E, st, nullptr, ANYSEQ_GLOBAL, nullptr, mat));
         // midpoints
         const size_t ns = splits.size();
         int64_t *dmeta = arena_t<int64_t>(ctx, "hb_meta", 2 * ns + 1, &s2st);
@@ -400,6 +436,13 @@ anyseq_status_t hirschberg_cigar(anyseq_ctx *ctx, const uint32_t *q2, int32_t i0
     memset(&B, 0, sizeof(B));
     B.q2 = q2; B.s2 = s2; B.n_cases = (int32_t)nb; B.o = o; B.e = sc->gap_extend;
     HB_TRY(make_rowprof(sc, ANYSEQ_GLOBAL, B.rowprof));  // bytes hold sigma - open - extend
+    if (mat) {
+        B.q8 = mat->q8;
+        B.s8 = mat->s8;
+        B.alphabet = sc->alphabet;
+        B.sig = device_sig_table(ctx, sc, mat, st, &s2st);
+        if (s2st != ANYSEQ_OK) return s2st;
+    }
     BaseCase *dbc = arena_t<BaseCase>(ctx, "hb_cases", nb + 1, &s2st);
     B.dirs = arena_t<uint8_t>(ctx, "hb_dirs", (size_t)dir_total + 16, &s2st);
     B.rows = arena_t<int32_t>(ctx, "hb_rows", (size_t)row_total + 16, &s2st);

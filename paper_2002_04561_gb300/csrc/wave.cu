@@ -57,16 +57,31 @@ __host__ __device__ constexpr bool best_edge(int mode) { return mode == SEMIGLOB
 // its first column (rows per lane 8 there, the extra registers), over the edge
 // from the last column (at each lane's last-column step) and the last row (the
 // last stripe's bottom row).
-template <int WR, bool TB, int MODE, bool TRI>
+//
+// MAT: the substitution-matrix path (alphabets above 4 letters). Each warp
+// builds the query profile of its stripe in shared memory, byte [a][row] =
+// sigma'(q_row, a) for the stripe's 32 x WR rows; the subject ring holds the
+// byte offset of the column letter's plane, and a lane reads its WR bytes of
+// that plane in one vector load. sigma' of row r is then one byte permute, as
+// on the row-profile path.
+template <int WR, bool TB, int MODE, bool TRI, bool MAT>
 __global__ void __launch_bounds__(256, (WR <= 8 && !best_all(MODE)) ? 4 : 2) wave_kernel(WaveArgs A) {
     constexpr int INIT = wave_init_mode(MODE);
     constexpr bool ALL = best_all(MODE), EDGE = best_edge(MODE);
     constexpr int WCH = WG * WR;  // rows per stripe
     static_assert(!TB || WR % 8 == 0, "direction words hold 8 rows");
     static_assert(!TB || MODE == GLOBAL, "traceback on the wavefront is global");
+    static_assert(!(TB && MAT), "the wavefront's traceback variant takes 2-bit letters");
     __shared__ WaveSmem smem[8];
+    extern __shared__ __align__(16) uint8_t wdyn[];
     const int warp = threadIdx.x >> 5, g = threadIdx.x & 31;
     WaveSmem *sm = &smem[warp];
+    int8_t *stab = reinterpret_cast<int8_t *>(wdyn);
+    uint8_t *qp = wdyn + WAVE_SIG_BYTES + (size_t)warp * A.alphabet * WCH;
+    if (MAT) {
+        for (int x = threadIdx.x; x < A.alphabet * A.alphabet; x += blockDim.x) stab[x] = A.sig[x];
+        __syncthreads();
+    }
     typedef CellI32 C;
     typedef int32_t T;
     const int32_t o = A.o, e = A.e, oe = A.o + A.e;
@@ -93,14 +108,39 @@ __global__ void __launch_bounds__(256, (WR <= 8 && !best_all(MODE)) ? 4 : 2) wav
         int32_t *outH = A.last_H ? A.last_H + ps.out_off : nullptr;
         int32_t *outE = A.last_E ? A.last_E + ps.out_off : nullptr;
         const int32_t rb = k * WCH + g * WR + 1;
-        uint32_t prof[WR];
+        uint32_t prof[MAT ? 1 : WR];
         T Hoe[WR], F[WR];
 #pragma unroll
         for (int r = 0; r < WR; r++) {
             int32_t i = rb + r - pad;
-            prof[r] = (i >= 1) ? A.rowprof[wletter(A.q2, ps.q0, n, i - 1, rev)] : A.rowprof[4];
+            if constexpr (!MAT) prof[r] = (i >= 1) ? A.rowprof[wletter(A.q2, ps.q0, n, i - 1, rev)] : A.rowprof[4];
             Hoe[r] = col0(INIT, i, o, e, ps.tb) + oe;
             F[r] = C::NEG;
+        }
+        if (MAT) {
+            // this lane's rows of the stripe's query profile (the warp's previous
+            // stripe is finished: its last step ended with a warp barrier)
+            __syncwarp();
+            int32_t qa[WR];
+#pragma unroll
+            for (int r = 0; r < WR; r++) {
+                const int32_t i = rb + r - pad;
+                qa[r] = i >= 1 ? (int32_t)A.q8[ps.q0 + (rev ? (int64_t)(n - i) : (int64_t)(i - 1))] : -1;
+            }
+            for (int a = 0; a < A.alphabet; a++) {
+#pragma unroll
+                for (int w4 = 0; w4 < WR / 4; w4++) {
+                    uint32_t word = 0;
+#pragma unroll
+                    for (int b = 0; b < 4; b++) {
+                        const int32_t q = qa[4 * w4 + b];
+                        const int32_t v = q >= 0 ? (int32_t)stab[q * A.alphabet + a] : A.sig_pad;
+                        word |= ((uint32_t)v & 0xFFu) << (8 * b);
+                    }
+                    *reinterpret_cast<uint32_t *>(qp + (size_t)a * WCH + g * WR + 4 * w4) = word;
+                }
+            }
+            __syncwarp();
         }
         const T diag0 = col0(INIT, rb - 1 - pad, o, e, ps.tb) + oe;
         // best-cell searches: this lane's best cell as a key (the pass's floor is
@@ -150,8 +190,12 @@ __global__ void __launch_bounds__(256, (WR <= 8 && !best_all(MODE)) ? 4 : 2) wav
             const int c = blk * BLOCK + g;
             if (c < m) {
                 const int64_t pos = ps.s0 + (rev ? (int64_t)(m - 1 - c) : (int64_t)c);
-                fw = A.s2[pos >> 4];
-                fsh = 2 * (int32_t)(pos & 15);
+                if (MAT) {
+                    fw = A.s8[pos];
+                } else {
+                    fw = A.s2[pos >> 4];
+                    fsh = 2 * (int32_t)(pos & 15);
+                }
                 if (k == 0) {
                     // row 0: H(0, c+1); E below row 0 comes from H only (E(0, .) = -inf)
                     const int32_t v = (INIT == GLOBAL ? o + (c + 1) * e : 0) + oe;
@@ -164,7 +208,7 @@ __global__ void __launch_bounds__(256, (WR <= 8 && !best_all(MODE)) ? 4 : 2) wav
         auto put = [&](int blk, uint32_t fw, int32_t fsh, int2 ft) {
             const int c = blk * BLOCK + g;
             if (c < m) {
-                sm->sel[c & (WRING - 1)] = C::selector((fw >> fsh) & 3u, 0);
+                sm->sel[c & (WRING - 1)] = MAT ? fw * (uint32_t)WCH : C::selector((fw >> fsh) & 3u, 0);
                 reinterpret_cast<int2 *>(sm->top)[c & (WRING - 1)] = ft;
             }
         };
@@ -233,9 +277,28 @@ __global__ void __launch_bounds__(256, (WR <= 8 && !best_all(MODE)) ? 4 : 2) wav
             }
             if ((unsigned)c < (unsigned)m) {
                 const uint32_t sel = sm->sel[c & (WRING - 1)];
+                // this lane's sigma' bytes of the column letter (matrix path)
+                uint32_t wq[MAT ? WR / 4 : 1];
+                if constexpr (MAT) {
+                    const uint8_t *src = qp + sel + g * WR;
+                    if constexpr (WR == 16) {
+                        const uint4 v = *reinterpret_cast<const uint4 *>(src);
+                        wq[0] = v.x; wq[1] = v.y; wq[2] = v.z; wq[3] = v.w;
+                    } else {
+                        const uint2 v = *reinterpret_cast<const uint2 *>(src);
+                        wq[0] = v.x; wq[1] = v.y;
+                    }
+                }
+                auto sigma_r = [&](int r) -> uint32_t {
+                    if constexpr (MAT) {
+                        const uint32_t b = (uint32_t)(r & 3);  // byte b, sign-extended
+                        return prmt(wq[r >> 2], 0u, b | ((b | 8u) << 4) | ((b | 8u) << 8) | ((b | 8u) << 12));
+                    }
+                    else return (uint32_t)C::sigma(prof[r], prof[r], sel);
+                };
                 // prev_up is diag0 until the first valid column; each later row takes the
                 // old Hoe of the row above before that register is overwritten
-                T Ad = C::addc(prev_up, (uint32_t)C::sigma(prof[0], prof[0], sel));
+                T Ad = C::addc(prev_up, sigma_r(0));
                 prev_up = up_hoe;
                 T E = up_e, Ein = up_e;
                 T hup = up_hoe;  // Hoe of the row above, this column (traceback)
@@ -243,7 +306,7 @@ __global__ void __launch_bounds__(256, (WR <= 8 && !best_all(MODE)) ? 4 : 2) wav
 #pragma unroll
                 for (int r = 0; r < WR; r++) {
                     const T Adr = Ad;
-                    if (r + 1 < WR) Ad = C::addc(Hoe[r], (uint32_t)C::sigma(prof[r + 1], prof[r + 1], sel));
+                    if (r + 1 < WR) Ad = C::addc(Hoe[r], sigma_r(r + 1));
                     uint32_t fFo = 0;
                     Ein = E;
                     if (TRI) {
@@ -356,10 +419,19 @@ __global__ void __launch_bounds__(256, (WR <= 8 && !best_all(MODE)) ? 4 : 2) wav
     }
 }
 
-template <int WR, bool TB, int MODE, bool TRI = false>
-static int blocks_per_sm() {
+// Dynamic shared memory of a launch: none on the row-profile path; the sigma'
+// table and one query profile per warp (alphabet x 32 x WR bytes) on the
+// matrix path.
+static size_t wave_dyn_smem(bool mat, int wr, int alphabet) {
+    return mat ? (size_t)WAVE_SIG_BYTES + 8 * (size_t)alphabet * WG * wr : 0;
+}
+
+template <int WR, bool TB, int MODE, bool TRI = false, bool MAT = false>
+static int blocks_per_sm(size_t dyn = 0) {
+    auto kern = wave_kernel<WR, TB, MODE, TRI, MAT>;
+    if (dyn) cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)dyn);
     int nb = 0;
-    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, wave_kernel<WR, TB, MODE, TRI>, 256, 0) != cudaSuccess) {
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, kern, 256, dyn) != cudaSuccess) {
         cudaGetLastError();
         nb = 1;
     }
@@ -376,9 +448,10 @@ int wave_rows_per_lane(int64_t total_rows, int num_sms, int64_t n_passes, int mo
     return 16 * stripes16 <= (int64_t)num_sms * blocks_per_sm<16, false, GLOBAL>() * 8 ? 8 : 16;
 }
 
-template <int WR, bool TB, int MODE, bool TRI = false>
+template <int WR, bool TB, int MODE, bool TRI = false, bool MAT = false>
 static void launch_one(const WaveArgs &A, int num_sms, cudaStream_t st) {
-    wave_kernel<WR, TB, MODE, TRI><<<num_sms * blocks_per_sm<WR, TB, MODE, TRI>(), 256, 0, st>>>(A);
+    const size_t dyn = wave_dyn_smem(MAT, WR, A.alphabet);
+    wave_kernel<WR, TB, MODE, TRI, MAT><<<num_sms * blocks_per_sm<WR, TB, MODE, TRI, MAT>(dyn), 256, dyn, st>>>(A);
 }
 
 // 16-row stripes side by side per SM from which the 3-input-maximum cell wins
@@ -389,10 +462,22 @@ constexpr int WAVE_TRI_STRIPES_PER_SM = 8;
 
 cudaError_t launch_wave(const WaveArgs &A, int num_sms, cudaStream_t st) {
     const bool tb = A.dirs != nullptr;
-    const bool tri = A.mode == GLOBAL && A.rows_per_lane >= 16 &&
+    const bool tri = A.mode == GLOBAL && A.rows_per_lane >= 16 && !A.mat &&
                      (A.cell == 1 || (A.cell == 0 && (int64_t)A.n_stripes >= (int64_t)WAVE_TRI_STRIPES_PER_SM * num_sms));
     // the stripe table was built for A.rows_per_lane (from wave_rows_per_lane)
     if (A.mode != GLOBAL && (tb || A.rows_per_lane != (best_all(A.mode) ? 8 : 16))) return cudaErrorInvalidValue;
+    if (A.mat) {
+        // the matrix path: letters one byte each, sigma' from shared query profiles
+        if (tb || A.alphabet < 1 || A.alphabet > 32 || !A.q8 || !A.s8 || !A.sig) return cudaErrorInvalidValue;
+        if (A.mode == LOCAL) launch_one<8, false, LOCAL, false, true>(A, num_sms, st);
+        else if (A.mode == ANCHORED_LOCAL) launch_one<8, false, ANCHORED_LOCAL, false, true>(A, num_sms, st);
+        else if (A.mode == SEMIGLOBAL) launch_one<16, false, SEMIGLOBAL, false, true>(A, num_sms, st);
+        else if (A.mode == ANCHORED_SEMIGLOBAL) launch_one<16, false, ANCHORED_SEMIGLOBAL, false, true>(A, num_sms, st);
+        else if (A.mode != GLOBAL) return cudaErrorInvalidValue;
+        else if (A.rows_per_lane == 8) launch_one<8, false, GLOBAL, false, true>(A, num_sms, st);
+        else launch_one<16, false, GLOBAL, false, true>(A, num_sms, st);
+        return cudaGetLastError();
+    }
     if (A.mode == LOCAL) {
         launch_one<8, false, LOCAL>(A, num_sms, st);
     } else if (A.mode == ANCHORED_LOCAL) {

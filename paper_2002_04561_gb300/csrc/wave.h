@@ -38,6 +38,13 @@ struct WaveArgs {
     int32_t mode;                 // GLOBAL, LOCAL, SEMIGLOBAL or an anchored mode (every pass)
     uint64_t *best;               // local / semi-global: per pass the best cell's key (initialised)
     int32_t cell;                 // global passes: 0 = by stripe count, 1 = 3-input maximum, 2 = two-step
+    // substitution matrix (alphabets above 4 letters): letter codes one byte
+    // each, and sigma - open - extend per (query, subject) letter pair
+    int32_t mat;                  // 0: 2-bit letters and row profiles; 1: the matrix path
+    int32_t alphabet;
+    const uint8_t *q8, *s8;
+    const int8_t *sig;            // alphabet x alphabet bytes (device)
+    int32_t sig_pad;              // sigma' of the padding rows above a pass
 };
 
 // Wavefront-only modes of the start-cell pass of a local or semi-global
@@ -61,6 +68,7 @@ __host__ __device__ constexpr int32_t wave_init_mode(int32_t mode) {
 int wave_rows_per_lane(int64_t total_rows, int num_sms, int64_t n_passes, int mode);
 cudaError_t launch_wave(const WaveArgs &A, int num_sms, cudaStream_t st);
 constexpr int WAVE_LANES = 32;    // lanes per stripe
+constexpr int WAVE_SIG_BYTES = 1024;  // shared copy of the sigma' table (alphabets up to 32)
 constexpr int WAVE_MIN_ROWS = 256;  // rows of the shortest stripe (8 rows per lane)
 
 }  // namespace anyseq

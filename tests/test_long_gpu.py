@@ -263,3 +263,55 @@ def test_wavefront_cell_forms_match_oracle(pkg, ctx, cell):
             assert np.array_equal(cig, want)
     finally:
         ctx.set_option("wave_cell", 0)
+
+
+PROTEIN = (0, 0, -11, -1)
+
+
+def protein_pair(n, extra, seed):
+    st = synth.Stream(seed, 1)
+    q = synth.random_codes(st, n, 20)
+    s, _ = synth.mutate(q, np.array([0, n], np.int64), 0.3, 0.03, 0.5, 20, st)
+    return q, s[: max(1, len(s) + extra)]
+
+
+@pytest.mark.parametrize("base", [256, 1 << 16])
+@pytest.mark.parametrize("mode", [0, 1, 2])
+def test_long_protein_pairs_with_matrix(pkg, ctx, mode, base):
+    """Long protein pairs (20 letters, a 20 x 20 matrix) on the wavefront's
+    matrix path: score, optimum cell, start cell and divide-and-conquer CIGAR
+    equal the oracle's linear-space alignment, for pairs of one to six
+    stripes; small base cases run the matrix through the base-case kernel."""
+    mat = synth.protein_matrix(3)
+    sc = pkg.Scoring.make(*PROTEIN, matrix=mat)
+    osc = oracle.Scoring(*PROTEIN, matrix=mat)
+    ctx.set_option("hirschberg_base_cells", base)
+    try:
+        for k, (n, extra) in enumerate([(1, 0), (700, 9), (1800, -30), (3000, 5)]):
+            q, s = protein_pair(n, extra, 3700 + 10 * mode + k)
+            cap = len(q) + len(s) + 4
+            cig = np.zeros(cap, dtype=np.uint32)
+            out, used = ctx.align_long(q, s, sc, mode=mode, want=pkg.WANT_SCORE | pkg.WANT_CIGAR, cigar=cig)
+            r = out[0]
+            got = (int(r["score"]), (int(r["beg_q"]), int(r["beg_s"])), (int(r["end_q"]), int(r["end_s"])))
+            S, beg, end, want = oracle.long_alignment(q, s, osc, mode, base)
+            assert got == (S, beg, end), (n, mode, got, (S, beg, end))
+            assert np.array_equal(cig[:used], want), (n, mode)
+    finally:
+        ctx.set_option("hirschberg_base_cells", 1 << 16)
+
+
+@pytest.mark.parametrize("mode", [0, 1, 2])
+def test_matrix_path_equals_row_profiles_on_dna(pkg, ctx, mode):
+    """DNA pairs forced through the matrix path (byte letters, shared query
+    profiles) give the same score, cells and CIGAR as the 2-bit row-profile
+    path."""
+    pairs = [related(n, extra, seed=3800 + n) for n, extra in ((513, 7), (2600, -11))] + tied_long_pairs(3810)[:2]
+    for q, s in pairs:
+        base = long_cigar_mode(pkg, ctx, q, s, C4, mode)
+        ctx.set_option("force_matrix_path", 1)
+        try:
+            forced = long_cigar_mode(pkg, ctx, q, s, C4, mode)
+        finally:
+            ctx.set_option("force_matrix_path", 0)
+        assert base[:3] == forced[:3] and np.array_equal(base[3], forced[3]), (len(q), len(s), mode)
