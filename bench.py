@@ -374,6 +374,24 @@ def secondary_workloads(pkg, ctx, device):
                                          "cigar_ms": ms2, "cigar_GCUPS": b.cells() / ms2 / 1e6,
                                          "cpu_oracle": oracle_sample(b, (0, 0, -11, -1), 1,
                                                                      matrix=synth.protein_matrix(3))}
+    # one long protein pair (titin-sized), local, 20 x 20 matrix: the wavefront's
+    # matrix path, score + optimum cell, then start cell and CIGAR
+    st = synth.Stream(3, 7)
+    pq = synth.random_codes(st, 35_000, 20)
+    ps, _ = synth.mutate(pq, np.array([0, len(pq)], np.int64), 0.3, 0.03, 0.5, 20, st)
+    psc = pkg.Scoring.make(0, 0, -11, -1, matrix=synth.protein_matrix(3))
+    dq, ds = dev(pq), dev(ps)
+    pcig = torch.zeros(len(pq) + len(ps) + 4, dtype=torch.int32, device=device)
+    ms = timed_events(lambda: ctx.align_long(dq, ds, psc, mode=pkg.LOCAL), 3, stream)
+    ms2 = timed_events(lambda: ctx.align_long(dq, ds, psc, mode=pkg.LOCAL, want=pkg.WANT_SCORE | pkg.WANT_CIGAR,
+                                              cigar=pcig), 2, stream)
+    r, used = ctx.align_long(dq, ds, psc, mode=pkg.LOCAL, want=pkg.WANT_SCORE | pkg.WANT_CIGAR, cigar=pcig)
+    cells = len(pq) * len(ps)
+    small = synth.from_pairs([(pq[:8000], ps[:8000])], alphabet=20)
+    out["long_protein_pair_35000_local_matrix"] = {
+        "score_ms": ms, "score_GCUPS": cells / ms / 1e6, "cigar_total_ms": ms2, "cigar_words": int(used),
+        "score": int(r["score"][0]),
+        "cpu_oracle": oracle_sample(small, (0, 0, -11, -1), 1, matrix=synth.protein_matrix(3))}
     # 1 Mbp x 1 Mbp global affine: wavefront score, divide-and-conquer CIGAR
     b = synth.long_pair()
     qd, sd = dev(b.q), dev(b.s)
