@@ -2,6 +2,7 @@
 // buffers, dispatch of the batched path. See include/anyseq.h.
 #include <cstdarg>
 #include <cstdio>
+#include <algorithm>
 #include <cstring>
 #include <string>
 #include <vector>
@@ -555,9 +556,12 @@ extern "C" anyseq_status_t anyseq_align_batch(anyseq_ctx *ctx, const uint8_t *q,
     if ((want & ANYSEQ_BAND_LEARNED) && !want_cigar && mode == ANYSEQ_GLOBAL && sc->alphabet <= 4) {
         TRY(band_scores(ctx, in, sc, score, eq, es, flags, st));
     } else {
-        if (!ctx->force32 && (mode == ANYSEQ_GLOBAL || !want_cigar))
-            TRY(wave_batch(ctx, in, sc, mode, score, eq, es, flags, st, want_cigar ? &tbo : nullptr, &on_wave));
-        if (!on_wave) TRY(batch_scores(ctx, in, sc, mode, score, eq, es, flags, st, want_cigar ? &tbo : nullptr));
+        BatchInput rest = in;
+        if (!ctx->force32 && want_cigar && mode == ANYSEQ_GLOBAL)
+            TRY(wave_batch(ctx, in, sc, mode, score, eq, es, flags, st, &tbo, &on_wave));
+        else if (!ctx->force32 && !want_cigar)
+            TRY(long_pairs_split(ctx, in, sc, mode, score, eq, es, flags, st, rest, &on_wave));
+        if (!on_wave) TRY(batch_scores(ctx, rest, sc, mode, score, eq, es, flags, st, want_cigar ? &tbo : nullptr));
     }
 
     int32_t *bq = nullptr, *bs = nullptr;
@@ -634,6 +638,19 @@ bool anyseq::key_range_ok(const anyseq_scoring_t *sc, int64_t min_nm) {
     return pmax * min_nm < (1ll << 21) - 1;
 }
 
+// The wavefront's profiles hold sigma - open - extend (and the padding rows'
+// value) in signed bytes.
+bool anyseq::long_profile_ok(const anyseq_scoring_t *sc) {
+    const int32_t oe = sc->gap_open + sc->gap_extend;
+    bool ok = sc->gap_extend - oe <= 127 && -oe <= 127;
+    for (int a = 0; a < sc->alphabet; a++)
+        for (int b = 0; b < sc->alphabet; b++) {
+            const int32_t v = sigma_host(sc, a, b) - oe;
+            ok = ok && v >= -128 && v <= 127;
+        }
+    return ok;
+}
+
 bool anyseq::long_range_ok(const anyseq_scoring_t *sc, int64_t n, int64_t m) {
     int64_t smax = 0;
     for (int a = 0; a < sc->alphabet; a++)
@@ -645,20 +662,149 @@ bool anyseq::long_range_ok(const anyseq_scoring_t *sc, int64_t n, int64_t m) {
     return bound < (1ll << 28);
 }
 
-// A batch of a few large global pairs leaves most of the GPU idle in the
-// batched kernel (one 16-lane group per pair, its row chunks in sequence); the
-// wavefront runs each pair's stripes side by side instead. Qualifies: at most
-// WAVE_BATCH_PAIRS pairs, alphabet <= 4, every pair inside the wavefront's
-// 32-bit range, and the largest pair of at least WAVE_BATCH_CELLS cells.
+// Batches of at most this many pairs, the largest of at least WAVE_BATCH_CELLS
+// cells, run on the wavefront (scores: long_pairs_split; CIGAR: wave_batch).
 constexpr int64_t WAVE_BATCH_PAIRS = 8;
 constexpr double WAVE_BATCH_CELLS = 262144.0;
+
+__global__ void scatter_results_kernel(int64_t k, const int64_t *idx, const int32_t *vals, int32_t *score,
+                                       int32_t *eq, int32_t *es, uint32_t *flags) {
+    for (int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; t < k; t += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t p = idx[t];
+        score[p] = vals[3 * t];
+        eq[p] = vals[3 * t + 1];
+        es[p] = vals[3 * t + 2];
+        flags[p] = ANYSEQ_FLAG_INT32;
+    }
+}
+
+// Pairs far larger than the rest of a batch leave the batched kernel waiting on
+// one 16-lane group per pair, each walking its row chunks in sequence (9
+// protein pairs of 20,000 residues: 521 ms, against 10 ms on the wavefront). So
+// the long pairs of a score-only batch run as one multi-pass wavefront launch,
+// their stripes side by side, and the batched kernel takes the rest through
+// its pair selection. A pair is long from 2^18 cells in a batch of at most
+// WAVE_BATCH_PAIRS pairs, otherwise from max(2^24, 4 x the batch's cells / the
+// resident 16-lane groups); it must also pass the wavefront's range tests.
+// *all_done: every pair ran on the wavefront; rest: the batch with the other
+// pairs selected.
+anyseq_status_t anyseq::long_pairs_split(anyseq_ctx *ctx, const BatchInput &in, const anyseq_scoring_t *sc,
+                                         int32_t mode, int32_t *score, int32_t *eq, int32_t *es, uint32_t *flags,
+                                         cudaStream_t st, BatchInput &rest, bool *all_done) {
+    *all_done = false;
+    rest = in;
+    const int64_t n = in.n_pairs;
+    if (n < 1 || !long_profile_ok(sc)) return ANYSEQ_OK;
+    const double small_batch_cells = WAVE_BATCH_CELLS, big_batch_cells = 16777216.0;
+    if ((double)in.max_n * (double)in.max_m < (n <= WAVE_BATCH_PAIRS ? small_batch_cells : big_batch_cells))
+        return ANYSEQ_OK;
+    std::vector<int64_t> hq((size_t)n + 1), hs((size_t)n + 1);
+    CUDA_TRY(cudaMemcpyAsync(hq.data(), in.q_off, ((size_t)n + 1) * sizeof(int64_t), cudaMemcpyDeviceToHost, st));
+    CUDA_TRY(cudaMemcpyAsync(hs.data(), in.s_off, ((size_t)n + 1) * sizeof(int64_t), cudaMemcpyDeviceToHost, st));
+    CUDA_TRY(cudaStreamSynchronize(st));
+    double total = 0;
+    for (int64_t p = 0; p < n; p++) total += (double)(hq[p + 1] - hq[p]) * (double)(hs[p + 1] - hs[p]);
+    const double groups = (double)ctx->num_sms * batch_min_ctas(0) * (batch_threads(0) / GROUP);
+    const double thr = n <= WAVE_BATCH_PAIRS ? small_batch_cells : std::max(big_batch_cells, 4.0 * total / groups);
+    std::vector<int64_t> idx;
+    for (int64_t p = 0; p < n; p++) {
+        const int64_t qn = hq[p + 1] - hq[p], sm = hs[p + 1] - hs[p];
+        if (qn == 0 || sm == 0 || (double)qn * (double)sm < thr) continue;
+        if (!long_range_ok(sc, qn, sm) || (mode != ANYSEQ_GLOBAL && !key_range_ok(sc, qn < sm ? qn : sm))) continue;
+        idx.push_back(p);
+    }
+    if (idx.empty()) return ANYSEQ_OK;
+    const int64_t k = (int64_t)idx.size();
+    anyseq_status_t s2 = ANYSEQ_OK;
+    uint32_t *q2 = arena<uint32_t>(ctx, "wb_q2", (size_t)(in.q_len + 15) / 16 + 2, &s2);
+    uint32_t *s2p = arena<uint32_t>(ctx, "wb_s2", (size_t)(in.s_len + 15) / 16 + 2, &s2);
+    int32_t *bad = arena<int32_t>(ctx, "wb_bad", 4, &s2);
+    int32_t *H = nullptr;
+    if (s2 != ANYSEQ_OK) return s2;
+    CUDA_TRY(cudaMemsetAsync(bad, 0, sizeof(int32_t), st));
+    CUDA_TRY(launch_pack2bit(in.q, in.q_len, q2, sc->alphabet, bad, st));
+    CUDA_TRY(launch_pack2bit(in.s, in.s_len, s2p, sc->alphabet, bad, st));
+    ctx->launches += 2;
+    std::vector<WavePass> passes((size_t)k);
+    int64_t out = 0;
+    for (int64_t t = 0; t < k; t++) {
+        const int64_t p = idx[(size_t)t];
+        WavePass &w = passes[(size_t)t];
+        memset(&w, 0, sizeof(w));
+        w.q0 = hq[p];
+        w.s0 = hs[p];
+        w.n = (int32_t)(hq[p + 1] - hq[p]);
+        w.m = (int32_t)(hs[p + 1] - hs[p]);
+        w.tb = sc->gap_open;
+        w.out_off = out;
+        out += w.m + 1;
+    }
+    H = arena<int32_t>(ctx, "wb_H", (size_t)out + 2, &s2);
+    if (s2 != ANYSEQ_OK) return s2;
+    MatLetters ml;
+    ml.q8 = in.q;
+    ml.s8 = in.s;
+    const bool use_mat = sc->alphabet > 4 || ctx->force_matrix;
+    std::vector<uint64_t> keys;
+    TRY(run_wave_passes(ctx, q2, s2p, passes, sc, H, nullptr, st, nullptr, mode, &keys, use_mat ? &ml : nullptr));
+    std::vector<int32_t> vals((size_t)(3 * k));
+    for (int64_t t = 0; t < k; t++) {
+        const WavePass &w = passes[(size_t)t];
+        if (mode == ANYSEQ_GLOBAL) {
+            CUDA_TRY(cudaMemcpyAsync(&vals[(size_t)(3 * t)], H + w.out_off + w.m, sizeof(int32_t), cudaMemcpyDeviceToHost, st));
+            vals[(size_t)(3 * t + 1)] = w.n;
+            vals[(size_t)(3 * t + 2)] = w.m;
+        } else {
+            vals[(size_t)(3 * t)] = key_score(keys[(size_t)t]);
+            vals[(size_t)(3 * t + 1)] = key_i(keys[(size_t)t]);
+            vals[(size_t)(3 * t + 2)] = key_j(keys[(size_t)t]);
+        }
+    }
+    int32_t hb = 0;
+    CUDA_TRY(cudaMemcpyAsync(&hb, bad, sizeof(int32_t), cudaMemcpyDeviceToHost, st));
+    CUDA_TRY(cudaStreamSynchronize(st));
+    if (hb) return fail(ANYSEQ_ERR_ALPHABET, "a letter code is >= alphabet (%d)", sc->alphabet);
+    int64_t *didx = arena<int64_t>(ctx, "wb_idx", (size_t)k + 1, &s2);
+    int32_t *dvals = arena<int32_t>(ctx, "wb_vals", (size_t)(3 * k) + 1, &s2);
+    if (s2 != ANYSEQ_OK) return s2;
+    CUDA_TRY(cudaMemcpyAsync(didx, idx.data(), (size_t)k * sizeof(int64_t), cudaMemcpyHostToDevice, st));
+    CUDA_TRY(cudaMemcpyAsync(dvals, vals.data(), (size_t)(3 * k) * sizeof(int32_t), cudaMemcpyHostToDevice, st));
+    scatter_results_kernel<<<(unsigned)std::min<int64_t>((k + 255) / 256, 1024), 256, 0, st>>>(k, didx, dvals, score, eq,
+                                                                                             es, flags);
+    CUDA_TRY(cudaGetLastError());
+    ctx->launches += 1;
+    if (k == n) {
+        *all_done = true;
+        ctx->pairs16 = 0;
+        ctx->pairs32 = n;
+    } else {
+        // the batched kernel takes the other pairs
+        std::vector<uint8_t> sel((size_t)n, 1);
+        for (int64_t p : idx) sel[(size_t)p] = 0;
+        uint8_t *dsel = arena<uint8_t>(ctx, "wb_sel", (size_t)n + 16, &s2);
+        if (s2 != ANYSEQ_OK) return s2;
+        CUDA_TRY(cudaMemcpyAsync(dsel, sel.data(), (size_t)n, cudaMemcpyHostToDevice, st));
+        rest.select = dsel;
+    }
+    // the host vectors must outlive the copies
+    CUDA_TRY(cudaStreamSynchronize(st));
+    return ANYSEQ_OK;
+}
+
+// CIGAR of a batch of a few large global pairs: the wavefront's traceback
+// variant runs each pair's stripes side by side, where the batched kernel would
+// give each pair one 16-lane group. Qualifies: at most WAVE_BATCH_PAIRS pairs,
+// 2-bit letters, every pair inside the wavefront's 32-bit range, and the
+// largest pair of at least WAVE_BATCH_CELLS cells.
 
 anyseq_status_t anyseq::wave_batch(anyseq_ctx *ctx, const BatchInput &in, const anyseq_scoring_t *sc,
                                    int32_t mode, int32_t *score, int32_t *eq, int32_t *es, uint32_t *flags,
                                    cudaStream_t st, TbOut *tb, bool *used) {
     *used = false;
     const int64_t n = in.n_pairs;
-    if (n > WAVE_BATCH_PAIRS || sc->alphabet > 4 || (tb && mode != ANYSEQ_GLOBAL)) return ANYSEQ_OK;
+    // the traceback variant reads 2-bit letters and row profiles
+    if (n > WAVE_BATCH_PAIRS || mode != ANYSEQ_GLOBAL || sc->alphabet > 4 || ctx->force_matrix || !long_profile_ok(sc))
+        return ANYSEQ_OK;
     if ((double)in.max_n * (double)in.max_m < WAVE_BATCH_CELLS) return ANYSEQ_OK;
     std::vector<int64_t> hq((size_t)n + 1), hs((size_t)n + 1);
     CUDA_TRY(cudaMemcpyAsync(hq.data(), in.q_off, ((size_t)n + 1) * sizeof(int64_t), cudaMemcpyDeviceToHost, st));
@@ -877,17 +1023,8 @@ extern "C" anyseq_status_t anyseq_align_long(anyseq_ctx *ctx, const uint8_t *q, 
     if (mode != ANYSEQ_GLOBAL && !key_range_ok(sc, n < m ? n : m))
         return fail(ANYSEQ_ERR_ARG, "local / semi-global scores of this pair may reach 2^21 (the optimum key's range)");
     if (!long_range_ok(sc, n, m)) return fail(ANYSEQ_ERR_ARG, "scores of this pair may leave the 32-bit range");
-    {
-        // the profiles hold sigma - open - extend (and the padding rows' value) in signed bytes
-        const int32_t oe = sc->gap_open + sc->gap_extend;
-        bool ok = sc->gap_extend - oe <= 127 && -oe <= 127;
-        for (int a = 0; a < sc->alphabet; a++)
-            for (int b = 0; b < sc->alphabet; b++) {
-                const int32_t v = sigma_host(sc, a, b) - oe;
-                ok = ok && v >= -128 && v <= 127;
-            }
-        if (!ok) return fail(ANYSEQ_ERR_ARG, "sigma - open - extend leaves the signed byte range on the long-pair path");
-    }
+    if (!long_profile_ok(sc))
+        return fail(ANYSEQ_ERR_ARG, "sigma - open - extend leaves the signed byte range on the long-pair path");
     cudaStream_t st = (cudaStream_t)cuda_stream;
     if (cudaSetDevice(ctx->device) != cudaSuccess) return fail(ANYSEQ_ERR_CUDA, "cudaSetDevice failed");
     ctx->launches = 0;

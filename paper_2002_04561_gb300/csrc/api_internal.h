@@ -88,16 +88,22 @@ struct TbOut {
 struct MatLetters {
     const uint8_t *q8 = nullptr, *s8 = nullptr;
 };
-// Small batches on the wavefront: scores, end cells and (global, with tb) the
+// Small global batches with CIGAR on the wavefront: scores, end cells and the
 // direction words of every pair; false in *used when the batch does not qualify.
 anyseq_status_t wave_batch(anyseq_ctx *ctx, const BatchInput &in, const anyseq_scoring_t *sc, int32_t mode,
                            int32_t *score, int32_t *eq, int32_t *es, uint32_t *flags, cudaStream_t st, TbOut *tb,
                            bool *used);
+// Long pairs of a score-only batch on the wavefront (see api.cu); rest: the
+// batch with the other pairs selected, *all_done when none is left.
+anyseq_status_t long_pairs_split(anyseq_ctx *ctx, const BatchInput &in, const anyseq_scoring_t *sc, int32_t mode,
+                                 int32_t *score, int32_t *eq, int32_t *es, uint32_t *flags, cudaStream_t st,
+                                 BatchInput &rest, bool *all_done);
 anyseq_status_t stage_batch(anyseq_ctx *ctx, const uint8_t *q, const int64_t *q_off, const uint8_t *s,
                             const int64_t *s_off, int64_t n_pairs, BatchInput &in, cudaStream_t st);
 anyseq_status_t band_scores(anyseq_ctx *ctx, const BatchInput &in, const anyseq_scoring_t *sc, int32_t *score,
                             int32_t *eq, int32_t *es, uint32_t *flags, cudaStream_t st);
 bool long_range_ok(const anyseq_scoring_t *sc, int64_t n, int64_t m);
+bool long_profile_ok(const anyseq_scoring_t *sc);
 // local / semi-global: the best score of a pair with min(n, m) <= min_nm fits the optimum key
 bool key_range_ok(const anyseq_scoring_t *sc, int64_t min_nm);
 // Scores (and, with end_q/end_s, optimum cells) of several long pairs in one

@@ -315,3 +315,50 @@ def test_matrix_path_equals_row_profiles_on_dna(pkg, ctx, mode):
         finally:
             ctx.set_option("force_matrix_path", 0)
         assert base[:3] == forced[:3] and np.array_equal(base[3], forced[3]), (len(q), len(s), mode)
+
+
+@pytest.mark.parametrize("mode", [0, 1, 2])
+def test_small_protein_batches_on_the_matrix_wavefront(pkg, ctx, mode):
+    """A batch of a few large protein pairs (scores) runs on the wavefront's
+    matrix path, one pass per pair side by side; scores and optimum cells
+    equal the oracle's, and an empty pair gets the empty alignment."""
+    mat = synth.protein_matrix(3)
+    pairs = [protein_pair(n, extra, 3900 + 10 * mode + k) for k, (n, extra) in enumerate([(1500, 7), (900, -20), (2100, 3)])]
+    pairs.append((pairs[0][0], np.zeros(0, np.uint8)))
+    b = synth.from_pairs(pairs, alphabet=20)
+    out = np.zeros(b.n_pairs, dtype=pkg.RESULT_DTYPE)
+    res, _ = ctx.align_batch(b.q, b.q_off, b.s, b.s_off, pkg.Scoring.make(*PROTEIN, matrix=mat), mode, out=out)
+    want = oracle.score_batch(b, oracle.Scoring(*PROTEIN, matrix=mat), mode)
+    assert np.array_equal(res["score"], want[0])
+    assert np.array_equal(res["end_q"], want[1]) and np.array_equal(res["end_s"], want[2])
+
+
+@pytest.mark.parametrize("alphabet", [4, 20])
+@pytest.mark.parametrize("mode", [0, 1, 2])
+def test_mixed_batches_split_long_pairs(pkg, ctx, mode, alphabet):
+    """A score-only batch of many short pairs and a few long ones: the long
+    pairs run on the wavefront, the rest on the batched kernel through its
+    pair selection; every score and optimum cell equals the oracle's."""
+    st = synth.Stream(4000 + mode + alphabet, 1)
+    pairs = []
+    for k in range(3000):
+        L = int(st.integers(60, 300, 1)[0])
+        q = synth.random_codes(st, L, alphabet)
+        s, _ = synth.mutate(q, np.array([0, L], np.int64), 0.1, 0.02, 0.5, alphabet, st)
+        pairs.append((q, s))
+    for k, L in enumerate((5200, 4300, 6100)):
+        q = synth.random_codes(st, L, alphabet)
+        s, _ = synth.mutate(q, np.array([0, L], np.int64), 0.1, 0.02, 0.5, alphabet, st)
+        pairs.insert(700 * k + 11, (q, s))
+    b = synth.from_pairs(pairs, alphabet=alphabet)
+    if alphabet == 4:
+        args, sco = C4, oracle.Scoring(*C4)
+        sc = pkg.Scoring.make(*C4)
+    else:
+        mat = synth.protein_matrix(3)
+        sc, sco = pkg.Scoring.make(*PROTEIN, matrix=mat), oracle.Scoring(*PROTEIN, matrix=mat)
+    out = np.zeros(b.n_pairs, dtype=pkg.RESULT_DTYPE)
+    res, _ = ctx.align_batch(b.q, b.q_off, b.s, b.s_off, sc, mode, out=out)
+    want = oracle.score_batch(b, sco, mode)
+    bad = np.nonzero((res["score"] != want[0]) | (res["end_q"] != want[1]) | (res["end_s"] != want[2]))[0]
+    assert len(bad) == 0, (len(bad), bad[:5])
