@@ -141,7 +141,7 @@ class ClockSampler:
 
 
 # sources that define the batched DP kernel: its DRAM counters stay valid while these are unchanged
-KERNEL_SOURCES = ("batch.cu", "batch.h", "common.cuh", "engine.cuh")
+KERNEL_SOURCES = ("batch_kernel.cuh", "batch.h", "common.cuh", "engine.cuh")
 
 
 def kernel_source_hash() -> str:
