@@ -116,10 +116,11 @@ constexpr int QP_ROWS = 128;        // rows of the shared-memory query profile (
 // occupancy; 20 or 24 warps at 12 rows per lane (80-96 registers) were slower.
 __host__ __device__ constexpr int batch_threads(int sigp) { return sigp ? 128 : 128; }
 __host__ __device__ constexpr int batch_min_ctas(int sigp) { return sigp ? 4 : 4; }
-// Rows per lane of the matrix-path kernels (their query profile covers 16 x TB_R
-// rows). The row-profile kernels pick R per work item (even with traceback) up
-// to row_rmax: 16, or for local int16x2, which also keeps per-row maxima and
-// columns, 12 (10 with traceback flags: at 12 that variant spills).
+// Rows per lane of the matrix-path kernels: at most TB_R (their query profile
+// has a TB_R-byte slot per lane), exactly TB_R with traceback. The row-profile
+// kernels pick R per work item (even with traceback) up to row_rmax: 16, or
+// for local int16x2, which also keeps per-row maxima and columns, 12 (10 with
+// traceback flags: at 12 that variant spills).
 constexpr int TB_R = 8;
 __host__ __device__ constexpr int row_rmax(int mode, int pairs, bool tb) {
     return (mode == LOCAL && pairs == 2) ? (tb ? 10 : 12) : 16;

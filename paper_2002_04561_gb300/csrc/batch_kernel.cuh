@@ -20,11 +20,13 @@ __device__ __forceinline__ uint32_t letter(const uint32_t *packed, int64_t base,
     return code2(packed, base + (rev ? (int64_t)(len - 1 - idx) : (int64_t)idx));
 }
 
-// Query profile of one group for the matrix path: byte [h][a][row] = sigma'(q_row, a)
-// for the chunk's 128 rows (padding rows: sig_pad), built by the 16 lanes together.
-// Letter a = alphabet is a null letter with sigma' = 0 (sigma = open + extend),
-// read by the columns past the end of a pair.
-template <class C>
+// Query profile of one group for the matrix path: byte [h][a][8 * lane + r] =
+// sigma'(q_row, a) for row r of the lane's R rows in the chunk (padding rows:
+// sig_pad). Each lane has an 8-byte slot whatever R is, so its profile words load
+// aligned. Built by the 16 lanes together. Letter a = alphabet is a null letter
+// with sigma' = 0 (sigma = open + extend), read by the columns past the end of a
+// pair.
+template <class C, int R>
 __device__ __forceinline__ void build_qprofile(const BatchArgs &A, const Slot &sl, int ch, int g, uint32_t *qp,
                                                const int8_t *tab) {
     const int alpha = A.alphabet;
@@ -34,8 +36,9 @@ __device__ __forceinline__ void build_qprofile(const BatchArgs &A, const Slot &s
         int32_t code[4];
 #pragma unroll
         for (int k = 0; k < 4; k++) {
-            int32_t i = ch * QP_ROWS + w * 4 + k + 1 - sl.pad[h];
-            code[k] = (h < C::PAIRS && i >= 1 && sl.n[h] > 0)
+            const int lane = (w * 4 + k) >> 3, r = (w * 4 + k) & 7;
+            int32_t i = ch * GROUP * R + lane * R + r + 1 - sl.pad[h];
+            code[k] = (h < C::PAIRS && r < R && i >= 1 && sl.n[h] > 0)
                           ? (int32_t)A.q8[sl.q0[h] + (sl.rev[h] ? sl.n[h] - i : i - 1)] : -1;
         }
         for (int a = 0; a <= alpha; a++) {
@@ -177,7 +180,7 @@ __device__ __noinline__ void run_slot(const BatchArgs &A, GroupSmemT<4 * block_c
         };
 
         __syncwarp();
-        if (SIGP) build_qprofile<C>(A, sl, ch, g, qp, tab);
+        if (SIGP) build_qprofile<C, R>(A, sl, ch, g, qp, tab);
         fill(0);
         __syncwarp();
         int drained = 0;  // next bottom block to drain
@@ -226,7 +229,7 @@ __device__ __noinline__ void run_slot(const BatchArgs &A, GroupSmemT<4 * block_c
                 const uint32_t sel = sm->sel[c & (RING - 1)];
                 uint2 qa = make_uint2(0, 0), qb = make_uint2(0, 0);
                 if (SIGP) {
-                    const uint8_t *qpb = reinterpret_cast<const uint8_t *>(qp) + g * R;
+                    const uint8_t *qpb = reinterpret_cast<const uint8_t *>(qp) + g * 8;  // the lane's slot
                     qa = *reinterpret_cast<const uint2 *>(qpb + (sel & 0xFFFFu));
                     if (C::PAIRS == 2) qb = *reinterpret_cast<const uint2 *>(qpb + (sel >> 16));
                 }
@@ -417,8 +420,9 @@ __global__ void __launch_bounds__(batch_threads(SIGP), batch_min_ctas(SIGP)) bat
     }
     const int64_t gslot = ((int64_t)blockIdx.x * (THREADS >> 5) + warp) * 2 + grp;
     // rows per lane: at most 16 (12 for local int16x2, which also keeps per-row
-    // maxima and columns); exactly TB_R for the matrix kernels, whose query
-    // profile covers 16 x TB_R rows
+    // maxima and columns); at most TB_R for the matrix kernels, whose query
+    // profile has an 8-byte slot per lane (exactly TB_R with traceback, the
+    // direction-word layout of tb.cu)
     constexpr int RMAX = SIGP ? TB_R : row_rmax(MODE, C::PAIRS, TB);
     uint32_t *lc = nullptr;
     if (MODE == SEMIGLOBAL)
@@ -434,7 +438,7 @@ __global__ void __launch_bounds__(batch_threads(SIGP), batch_min_ctas(SIGP)) bat
         // rows per lane: any R for the score kernels (the least top padding), an even R
         // with traceback (the direction-word layout of tb.cu plans the same even R)
         ItemPlan P = plan_item(A.list, n_list, item, per_item, A.q_off, A.s_off, RMAX, TB);
-        if (SIGP) P.R = TB_R;
+        if (SIGP && TB) P.R = TB_R;
         uint32_t tbin = 0;
         if (!(TB || SIGP) && (A.rmax_tab || A.bin_stats)) {
             // the tuned tile shape of this item's length bin (rows per lane cap)
@@ -467,7 +471,7 @@ __global__ void __launch_bounds__(batch_threads(SIGP), batch_min_ctas(SIGP)) bat
             // the host sizes the border scratch for every multi-chunk query; never reached
             continue;
         }
-        if (SIGP) {
+        if (SIGP && TB) {
             run_slot<C, MODE, TB_R, TB, SIGP>(A, sm, sl, P.nch, P.Mit, g, gslot, res, pid, qp, tab, lc);
         } else {
             switch (P.R) {

@@ -185,6 +185,35 @@ def test_protein_matrix_parity(pkg, ctx, mode, force32):
     assert_parity(run(pkg, ctx, b, args, mode, force32=force32), oracle_of(b, args, mode), b)
 
 
+# query lengths at the edges of a lane's rows and of a chunk: 16 lanes x R rows,
+# R up to 16 (row profiles) or 8 (matrix), several chunks above that
+BOUNDARY_LENGTHS = [1, 2, 15, 16, 17, 31, 32, 33, 47, 48, 49, 63, 64, 65, 79, 80, 81, 95, 96, 97, 111, 112, 113,
+                    127, 128, 129, 143, 144, 145, 175, 176, 177, 255, 256, 257, 383, 384, 385, 511, 512, 513]
+
+
+@pytest.mark.parametrize("mode", MODES)
+@pytest.mark.parametrize("alphabet", [4, 20])
+def test_row_counts_at_chunk_boundaries(pkg, ctx, mode, alphabet):
+    """Every rows-per-lane count and chunk count: 8 pairs per query length, so each
+    4-pair work item is planned from one length (odd and even R, one or several
+    chunks; row profiles for 4 letters, the shared-memory matrix profile for 20)."""
+    st = synth.Stream(1050 + mode, 1)
+    pairs = []
+    for n in BOUNDARY_LENGTHS:
+        for k in range(8):
+            q = synth.random_codes(st, n, alphabet)
+            m = int(st.integers(max(1, n - 20), n + 40, 1)[0])
+            s = synth.random_codes(st, m, alphabet)
+            if k % 2 == 0:   # related pairs: a mutated copy of the query
+                s, _ = synth.mutate(q, np.array([0, n], np.int64), 0.1, 0.02, 0.3, alphabet, st)
+            pairs.append((q, s))
+    b = synth.from_pairs(pairs, alphabet)
+    args = (0, 0, -11, -1, synth.protein_matrix(seed=3)) if alphabet == 20 else (2, -3, -5, -2)
+    res = run(pkg, ctx, b, args, mode)
+    assert_parity(res, oracle_of(b, args, mode), b)
+    assert not np.any(res["flags"][(b.q_len() > 0) & (b.s_len() > 0)] & 1)  # int16x2 lanes throughout
+
+
 def test_wide_alphabet_asymmetric_matrix(pkg, ctx):
     st = synth.Stream(1100, 1)
     mat = st.integers(-6, 9, 32 * 32).reshape(32, 32).astype(np.int8)
