@@ -418,7 +418,7 @@ anyseq_status_t anyseq::batch_scores(anyseq_ctx *ctx, const BatchInput &in, cons
         int32_t *lay_r = arena<int32_t>(ctx, "tb_rows", n + 1, &s2);
         if (s2 != ANYSEQ_OK) return s2;
         CUDA_TRY(cudaMemsetAsync(words, 0, n * sizeof(int64_t), st));
-        // the DP kernels' row caps: TB_R fixed on the matrix path, else an even R up to row_rmax
+        // the DP kernels' row caps: TB_R fixed on the matrix path, else any R up to row_rmax
         CUDA_TRY(launch_tb_plan(P.list16, P.counts + 0, 4, (n + 3) / 4 + 1, in.q_off, in.s_off, words, A.lay_pad,
                                 A.lay_ch0, lay_r, sigp ? TB_R : row_rmax(mode, 2, true), sigp ? TB_R : 0, st));
         CUDA_TRY(launch_tb_plan(P.list32, P.counts + 1, 2, (n + 1) / 2 + 1, in.q_off, in.s_off, words, A.lay_pad,

@@ -1,22 +1,34 @@
-// Launchers of the batched DP kernel: dispatch by alignment mode to the
-// per-mode instantiations (batch_global.cu, batch_local.cu, batch_semiglobal.cu).
+// Launchers of the batched DP kernel: dispatch by alignment mode and lane type
+// to the instantiations in batch_{global,local,semiglobal}_{i16,i32}.cu.
 #include "batch.h"
 
 namespace anyseq {
 
-int batch_run_global(const BatchArgs *A, int cell32, int tb, int sigp, int alphabet, int grid, cudaStream_t st,
-                     bool occ, cudaError_t *err);
-int batch_run_local(const BatchArgs *A, int cell32, int tb, int sigp, int alphabet, int grid, cudaStream_t st,
-                    bool occ, cudaError_t *err);
-int batch_run_semiglobal(const BatchArgs *A, int cell32, int tb, int sigp, int alphabet, int grid, cudaStream_t st,
-                         bool occ, cudaError_t *err);
+int batch_run_global_i16(const BatchArgs *A, int tb, int sigp, int alphabet, int grid, cudaStream_t st, bool occ,
+                         cudaError_t *err);
+int batch_run_global_i32(const BatchArgs *A, int tb, int sigp, int alphabet, int grid, cudaStream_t st, bool occ,
+                         cudaError_t *err);
+int batch_run_local_i16(const BatchArgs *A, int tb, int sigp, int alphabet, int grid, cudaStream_t st, bool occ,
+                        cudaError_t *err);
+int batch_run_local_i32(const BatchArgs *A, int tb, int sigp, int alphabet, int grid, cudaStream_t st, bool occ,
+                        cudaError_t *err);
+int batch_run_semiglobal_i16(const BatchArgs *A, int tb, int sigp, int alphabet, int grid, cudaStream_t st, bool occ,
+                             cudaError_t *err);
+int batch_run_semiglobal_i32(const BatchArgs *A, int tb, int sigp, int alphabet, int grid, cudaStream_t st, bool occ,
+                             cudaError_t *err);
 
 static int dispatch(const BatchArgs *A, int cell32, int mode, int tb, int sigp, int alphabet, int grid,
                     cudaStream_t st, bool occ, cudaError_t *err) {
     switch (mode) {
-        case GLOBAL: return batch_run_global(A, cell32, tb, sigp, alphabet, grid, st, occ, err);
-        case LOCAL: return batch_run_local(A, cell32, tb, sigp, alphabet, grid, st, occ, err);
-        default: return batch_run_semiglobal(A, cell32, tb, sigp, alphabet, grid, st, occ, err);
+        case GLOBAL:
+            return cell32 ? batch_run_global_i32(A, tb, sigp, alphabet, grid, st, occ, err)
+                          : batch_run_global_i16(A, tb, sigp, alphabet, grid, st, occ, err);
+        case LOCAL:
+            return cell32 ? batch_run_local_i32(A, tb, sigp, alphabet, grid, st, occ, err)
+                          : batch_run_local_i16(A, tb, sigp, alphabet, grid, st, occ, err);
+        default:
+            return cell32 ? batch_run_semiglobal_i32(A, tb, sigp, alphabet, grid, st, occ, err)
+                          : batch_run_semiglobal_i16(A, tb, sigp, alphabet, grid, st, occ, err);
     }
 }
 

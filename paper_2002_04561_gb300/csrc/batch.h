@@ -74,7 +74,7 @@ struct ItemPlan {
 };
 
 __device__ __forceinline__ ItemPlan plan_item(const int32_t *list, int64_t n_list, int64_t item, int per_item,
-                                              const int64_t *q_off, const int64_t *s_off, int rmax, bool r_even) {
+                                              const int64_t *q_off, const int64_t *s_off, int rmax) {
     ItemPlan P;
     int32_t nmax = 0;
     P.Mit = 0;
@@ -99,7 +99,6 @@ __device__ __forceinline__ ItemPlan plan_item(const int32_t *list, int64_t n_lis
     P.nch = (nmax + 16 * rmax - 1) / (16 * rmax);
     if (P.nch < 1) P.nch = 1;
     int R = (nmax + 16 * P.nch - 1) / (16 * P.nch);
-    if (r_even) R += R & 1;
     if (R < 2) R = 2;
     if (R > rmax) R = rmax;
     P.R = R;
@@ -118,9 +117,9 @@ __host__ __device__ constexpr int batch_threads(int sigp) { return sigp ? 128 : 
 __host__ __device__ constexpr int batch_min_ctas(int sigp) { return sigp ? 4 : 4; }
 // Rows per lane of the matrix-path kernels: at most TB_R (their query profile
 // has a TB_R-byte slot per lane), exactly TB_R with traceback. The row-profile
-// kernels pick R per work item (even with traceback) up to row_rmax: 16, or
-// for local int16x2, which also keeps per-row maxima and columns, 12 (10 with
-// traceback flags: at 12 that variant spills).
+// kernels pick R per work item up to row_rmax: 16, or for local int16x2, which
+// also keeps per-row maxima and columns, 12 (10 with traceback flags: at 12
+// that variant spills).
 constexpr int TB_R = 8;
 __host__ __device__ constexpr int row_rmax(int mode, int pairs, bool tb) {
     return (mode == LOCAL && pairs == 2) ? (tb ? 10 : 12) : 16;

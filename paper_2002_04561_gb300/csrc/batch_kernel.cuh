@@ -1,8 +1,8 @@
 // Batched inter-sequence DP kernel (Sec. VI: inter-sequence parallelism):
 // score and optimum cell of many independent pairs, one slot per 16-lane
 // group, persistent warps pulling work items from a length-sorted queue.
-// The templates are instantiated per alignment mode in batch_global.cu,
-// batch_local.cu and batch_semiglobal.cu (three translation units that
+// The templates are instantiated per alignment mode and lane type in
+// batch_{global,local,semiglobal}_{i16,i32}.cu (six translation units that
 // compile in parallel); batch.cu dispatches to them.
 #pragma once
 #include "engine.cuh"
@@ -394,13 +394,9 @@ __device__ __noinline__ void run_slot(const BatchArgs &A, GroupSmemT<4 * block_c
 // sorted list until it is empty. THREADS = batch_threads (batch.h); the matrix
 // path's per-group query profile lives in dynamic shared memory after a copy
 // of the sigma' table.
-// The run_slot instantiation of a planned R: R itself up to RMAX; the traceback
-// kernels only plan even R, so their odd cases reuse the even one below (never
-// reached) instead of compiling a variant.
-template <bool TB, int RMAX>
-__host__ __device__ constexpr int rsel(int r) {
-    return (TB ? (r & ~1) : r) < RMAX ? (TB ? (r & ~1) : r) : RMAX;
-}
+// The run_slot instantiation of a planned R: R itself, at most RMAX.
+template <int RMAX>
+__host__ __device__ constexpr int rsel(int r) { return r < RMAX ? r : RMAX; }
 
 template <class C, int MODE, bool TB, int SIGP>
 __global__ void __launch_bounds__(batch_threads(SIGP), batch_min_ctas(SIGP)) batch_kernel(BatchArgs A) {
@@ -435,9 +431,9 @@ __global__ void __launch_bounds__(batch_threads(SIGP), batch_min_ctas(SIGP)) bat
         if (lane == 0) item = atomicAdd(A.counter, 1);
         item = __shfl_sync(0xffffffffu, item, 0);
         if (item >= n_items) break;
-        // rows per lane: any R for the score kernels (the least top padding), an even R
-        // with traceback (the direction-word layout of tb.cu plans the same even R)
-        ItemPlan P = plan_item(A.list, n_list, item, per_item, A.q_off, A.s_off, RMAX, TB);
+        // rows per lane: the least R that covers the longest query in its chunks (the
+        // direction-word layout of tb.cu plans the same R)
+        ItemPlan P = plan_item(A.list, n_list, item, per_item, A.q_off, A.s_off, RMAX);
         if (SIGP && TB) P.R = TB_R;
         uint32_t tbin = 0;
         if (!(TB || SIGP) && (A.rmax_tab || A.bin_stats)) {
@@ -447,7 +443,7 @@ __global__ void __launch_bounds__(batch_threads(SIGP), batch_min_ctas(SIGP)) bat
             tbin = lbucket(nmax);
             const int cap = A.rmax_tab ? (int)A.rmax_tab[tbin] : 0;
             if (cap > 0 && cap < RMAX)
-                P = plan_item(A.list, n_list, item, per_item, A.q_off, A.s_off, cap, false);
+                P = plan_item(A.list, n_list, item, per_item, A.q_off, A.s_off, cap);
         }
         long long t_item = 0;
         if (A.bin_stats && lane == 0) t_item = clock64();
@@ -475,20 +471,20 @@ __global__ void __launch_bounds__(batch_threads(SIGP), batch_min_ctas(SIGP)) bat
             run_slot<C, MODE, TB_R, TB, SIGP>(A, sm, sl, P.nch, P.Mit, g, gslot, res, pid, qp, tab, lc);
         } else {
             switch (P.R) {
-                case 2: run_slot<C, MODE, rsel<TB, RMAX>(2), TB, SIGP>(A, sm, sl, P.nch, P.Mit, g, gslot, res, pid, qp, tab, lc); break;
-                case 3: run_slot<C, MODE, rsel<TB, RMAX>(3), TB, SIGP>(A, sm, sl, P.nch, P.Mit, g, gslot, res, pid, qp, tab, lc); break;
-                case 4: run_slot<C, MODE, rsel<TB, RMAX>(4), TB, SIGP>(A, sm, sl, P.nch, P.Mit, g, gslot, res, pid, qp, tab, lc); break;
-                case 5: run_slot<C, MODE, rsel<TB, RMAX>(5), TB, SIGP>(A, sm, sl, P.nch, P.Mit, g, gslot, res, pid, qp, tab, lc); break;
-                case 6: run_slot<C, MODE, rsel<TB, RMAX>(6), TB, SIGP>(A, sm, sl, P.nch, P.Mit, g, gslot, res, pid, qp, tab, lc); break;
-                case 7: run_slot<C, MODE, rsel<TB, RMAX>(7), TB, SIGP>(A, sm, sl, P.nch, P.Mit, g, gslot, res, pid, qp, tab, lc); break;
-                case 8: run_slot<C, MODE, rsel<TB, RMAX>(8), TB, SIGP>(A, sm, sl, P.nch, P.Mit, g, gslot, res, pid, qp, tab, lc); break;
-                case 9: run_slot<C, MODE, rsel<TB, RMAX>(9), TB, SIGP>(A, sm, sl, P.nch, P.Mit, g, gslot, res, pid, qp, tab, lc); break;
-                case 10: run_slot<C, MODE, rsel<TB, RMAX>(10), TB, SIGP>(A, sm, sl, P.nch, P.Mit, g, gslot, res, pid, qp, tab, lc); break;
-                case 11: run_slot<C, MODE, rsel<TB, RMAX>(11), TB, SIGP>(A, sm, sl, P.nch, P.Mit, g, gslot, res, pid, qp, tab, lc); break;
-                case 12: run_slot<C, MODE, rsel<TB, RMAX>(12), TB, SIGP>(A, sm, sl, P.nch, P.Mit, g, gslot, res, pid, qp, tab, lc); break;
-                case 13: run_slot<C, MODE, rsel<TB, RMAX>(13), TB, SIGP>(A, sm, sl, P.nch, P.Mit, g, gslot, res, pid, qp, tab, lc); break;
-                case 14: run_slot<C, MODE, rsel<TB, RMAX>(14), TB, SIGP>(A, sm, sl, P.nch, P.Mit, g, gslot, res, pid, qp, tab, lc); break;
-                case 15: run_slot<C, MODE, rsel<TB, RMAX>(15), TB, SIGP>(A, sm, sl, P.nch, P.Mit, g, gslot, res, pid, qp, tab, lc); break;
+                case 2: run_slot<C, MODE, rsel<RMAX>(2), TB, SIGP>(A, sm, sl, P.nch, P.Mit, g, gslot, res, pid, qp, tab, lc); break;
+                case 3: run_slot<C, MODE, rsel<RMAX>(3), TB, SIGP>(A, sm, sl, P.nch, P.Mit, g, gslot, res, pid, qp, tab, lc); break;
+                case 4: run_slot<C, MODE, rsel<RMAX>(4), TB, SIGP>(A, sm, sl, P.nch, P.Mit, g, gslot, res, pid, qp, tab, lc); break;
+                case 5: run_slot<C, MODE, rsel<RMAX>(5), TB, SIGP>(A, sm, sl, P.nch, P.Mit, g, gslot, res, pid, qp, tab, lc); break;
+                case 6: run_slot<C, MODE, rsel<RMAX>(6), TB, SIGP>(A, sm, sl, P.nch, P.Mit, g, gslot, res, pid, qp, tab, lc); break;
+                case 7: run_slot<C, MODE, rsel<RMAX>(7), TB, SIGP>(A, sm, sl, P.nch, P.Mit, g, gslot, res, pid, qp, tab, lc); break;
+                case 8: run_slot<C, MODE, rsel<RMAX>(8), TB, SIGP>(A, sm, sl, P.nch, P.Mit, g, gslot, res, pid, qp, tab, lc); break;
+                case 9: run_slot<C, MODE, rsel<RMAX>(9), TB, SIGP>(A, sm, sl, P.nch, P.Mit, g, gslot, res, pid, qp, tab, lc); break;
+                case 10: run_slot<C, MODE, rsel<RMAX>(10), TB, SIGP>(A, sm, sl, P.nch, P.Mit, g, gslot, res, pid, qp, tab, lc); break;
+                case 11: run_slot<C, MODE, rsel<RMAX>(11), TB, SIGP>(A, sm, sl, P.nch, P.Mit, g, gslot, res, pid, qp, tab, lc); break;
+                case 12: run_slot<C, MODE, rsel<RMAX>(12), TB, SIGP>(A, sm, sl, P.nch, P.Mit, g, gslot, res, pid, qp, tab, lc); break;
+                case 13: run_slot<C, MODE, rsel<RMAX>(13), TB, SIGP>(A, sm, sl, P.nch, P.Mit, g, gslot, res, pid, qp, tab, lc); break;
+                case 14: run_slot<C, MODE, rsel<RMAX>(14), TB, SIGP>(A, sm, sl, P.nch, P.Mit, g, gslot, res, pid, qp, tab, lc); break;
+                case 15: run_slot<C, MODE, rsel<RMAX>(15), TB, SIGP>(A, sm, sl, P.nch, P.Mit, g, gslot, res, pid, qp, tab, lc); break;
                 default: run_slot<C, MODE, RMAX, TB, SIGP>(A, sm, sl, P.nch, P.Mit, g, gslot, res, pid, qp, tab, lc); break;
             }
         }
@@ -541,20 +537,15 @@ static int run_one(const BatchArgs *A, int alphabet, int grid, cudaStream_t st, 
     return 0;
 }
 
-// Every variant of one mode: launch (occupancy == false) or blocks per SM.
-template <int MODE>
-int run_mode(const BatchArgs *A, int cell32, int tb, int sigp, int alphabet, int grid, cudaStream_t st, bool occ,
+// Every variant of one mode and lane type: launch (occupancy == false) or
+// blocks per SM.
+template <class C, int MODE>
+int run_mode(const BatchArgs *A, int tb, int sigp, int alphabet, int grid, cudaStream_t st, bool occ,
              cudaError_t *err) {
-    if (cell32) {
-        if (sigp) return tb ? run_one<CellI32, MODE, true, 1>(A, alphabet, grid, st, occ, err)
-                            : run_one<CellI32, MODE, false, 1>(A, alphabet, grid, st, occ, err);
-        return tb ? run_one<CellI32, MODE, true, 0>(A, alphabet, grid, st, occ, err)
-                  : run_one<CellI32, MODE, false, 0>(A, alphabet, grid, st, occ, err);
-    }
-    if (sigp) return tb ? run_one<CellI16x2, MODE, true, 1>(A, alphabet, grid, st, occ, err)
-                        : run_one<CellI16x2, MODE, false, 1>(A, alphabet, grid, st, occ, err);
-    return tb ? run_one<CellI16x2, MODE, true, 0>(A, alphabet, grid, st, occ, err)
-              : run_one<CellI16x2, MODE, false, 0>(A, alphabet, grid, st, occ, err);
+    if (sigp) return tb ? run_one<C, MODE, true, 1>(A, alphabet, grid, st, occ, err)
+                        : run_one<C, MODE, false, 1>(A, alphabet, grid, st, occ, err);
+    return tb ? run_one<C, MODE, true, 0>(A, alphabet, grid, st, occ, err)
+              : run_one<C, MODE, false, 0>(A, alphabet, grid, st, occ, err);
 }
 
 }  // namespace anyseq

@@ -75,7 +75,7 @@ __global__ void tb_plan_kernel(const int32_t *list, const int64_t *n_list_p, int
     for (int64_t item = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; item < n_items;
          item += (int64_t)gridDim.x * blockDim.x) {
         // the DP kernel's own plan of the item
-        ItemPlan P = plan_item(list, n_list, item, per_item, q_off, s_off, rmax, fixed_r == 0);
+        ItemPlan P = plan_item(list, n_list, item, per_item, q_off, s_off, rmax);
         if (fixed_r) P.R = fixed_r;
         const int32_t CH = GROUP * P.R;
         for (int k = 0; k < per_item; k++) {

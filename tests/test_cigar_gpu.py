@@ -193,3 +193,29 @@ def test_both_walkers_match_oracle(pkg, ctx, mode, walker):
         assert_cigar_parity(b, res, cigars, (2, -3, -5, -2), mode)
     finally:
         ctx.set_option("tb_walker", 0)
+
+
+# query lengths at the edges of a lane's rows and of a chunk (16 lanes x R rows,
+# any R up to 16, or 10 for local int16x2 with traceback)
+BOUNDARY_LENGTHS = [1, 2, 15, 16, 17, 31, 32, 33, 47, 48, 49, 63, 64, 65, 95, 96, 97, 127, 128, 129, 143, 144,
+                    145, 159, 160, 161, 175, 176, 177, 255, 256, 257, 319, 320, 321]
+
+
+@pytest.mark.parametrize("mode", [0, 1, 2])
+@pytest.mark.parametrize("force32", [False, True])
+def test_cigar_row_counts_at_chunk_boundaries(pkg, ctx, mode, force32):
+    """Every rows-per-lane count, odd and even, and one or several chunks: 4 pairs
+    per query length, so each work item is planned from one length."""
+    st = synth.Stream(1450 + mode, 1)
+    pairs = []
+    for n in BOUNDARY_LENGTHS:
+        for k in range(4):
+            q = synth.random_codes(st, n, 4)
+            s, _ = synth.mutate(q, np.array([0, n], np.int64), 0.08, 0.02, 0.3, 4, st)
+            if k == 3:
+                s = synth.random_codes(st, int(st.integers(1, n + 30, 1)[0]), 4)
+            pairs.append((q, s))
+    b = synth.from_pairs(pairs)
+    sc_args = (2, -3, -5, -2)
+    res, cigars, _ = gpu_align(pkg, ctx, b, sc_args, mode, force32=force32)
+    assert_cigar_parity(b, res, cigars, sc_args, mode)
