@@ -88,7 +88,10 @@ def sum_over_ranks(ws, x: float, device) -> float:
 
 
 class ClockSampler:
-    """nvidia-smi clocks and throttle reasons sampled every 200 ms."""
+    """nvidia-smi clocks and throttle reasons sampled every 100 ms. start() returns
+    once the sampler has printed its first line; begin() marks the start of the
+    timed region; stop() keeps the samples taken after the mark (all of them if
+    the region was too short for one)."""
     QUERY = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
@@ -97,16 +100,24 @@ class ClockSampler:
         self.gpu = gpu_index
         self.proc = None
         self.lines = []
+        self.mark = 0
 
     def start(self):
         try:
             self.proc = subprocess.Popen(
                 ["nvidia-smi", f"--id={self.gpu}", f"--query-gpu={self.QUERY}", "--format=csv,noheader,nounits",
-                 "-lms", "200"], stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+                 "-lms", "100"], stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
             self.thread = threading.Thread(target=self._read, daemon=True)
             self.thread.start()
         except (OSError, FileNotFoundError):
             self.proc = None
+            return
+        t0 = time.perf_counter()
+        while not self.lines and self.proc.poll() is None and time.perf_counter() - t0 < 3.0:
+            time.sleep(0.005)
+
+    def begin(self):
+        self.mark = len(self.lines)
 
     def _read(self):
         for line in self.proc.stdout:
@@ -121,9 +132,10 @@ class ClockSampler:
         except subprocess.TimeoutExpired:
             self.proc.kill()
         self.thread.join(timeout=2)
+        lines = self.lines[self.mark:] if len(self.lines) > self.mark else self.lines
         sm, smax, reasons = [], [], set()
         names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
-        for ln in self.lines:
+        for ln in lines:
             parts = [p.strip() for p in ln.split(",")]
             if len(parts) < 9:
                 continue
@@ -547,12 +559,13 @@ def main():
         ctx.align_batch(q, q_off, s, s_off, sc, MODE, out=out)
 
     clocks = ClockSampler(local)
-    clocks.start()  # samples warm-up and timed steps (the timed region alone is shorter than the 200 ms period)
+    clocks.start()  # running (first sample printed) before the warm-up
     for _ in range(max(3, args.warmup)):
         step()
     torch.cuda.synchronize()
     barrier(ws)
     torch.cuda.synchronize()
+    clocks.begin()
     step_ms, dp_ms, launches = [], [], 0
     for _ in range(args.steps):
         flush.fill_(1)  # evict L2 between timed steps (outside the events)
