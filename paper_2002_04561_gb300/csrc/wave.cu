@@ -1,8 +1,9 @@
 // Intra-sequence wavefront for one long pair (Sec. IV-C, Sec. VI): global
 // alignment of q[1..n] against s[1..m] in linear space, 32-bit lanes.
 //
-// The rows are cut into stripes of 32 lanes x 16 rows = 512 rows. A warp owns a
-// stripe and walks all m columns; lane l is one step behind lane l-1 and gets
+// The rows are cut into stripes of 32 lanes x WR rows (WR = 16, or 8 for local
+// passes and for problems too small to fill the GPU with 16-row stripes). A
+// warp owns a stripe and walks all m columns; lane l is one step behind lane l-1 and gets
 // its upper neighbours by shfl.up (the anti-diagonal dependency of Sec. III-A).
 // Stripe k reads the last row of stripe k-1 from a border row in global memory
 // and writes its own for stripe k+1 (two border rows, alternating): the first
@@ -15,7 +16,10 @@
 // that makes every other waiter give up too, and the host returns
 // ANYSEQ_ERR_TIMEOUT.
 //
-// Per cell: the same seven instructions as the batched kernel (engine.cuh).
+// Per cell: the batched kernel's cell (engine.cuh) in one of two forms, H as a
+// three-input maximum (six instructions) or as max(diagonal, F) followed by an
+// add-max with E (seven, with a one-instruction chain through the rows);
+// launch_wave picks the form by the number of stripes per SM.
 #include "common.cuh"
 #include "engine.cuh"
 #include "wave.h"
