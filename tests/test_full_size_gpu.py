@@ -6,7 +6,10 @@
   20 kbp pair of the same generator matches the oracle bit for bit;
 * the 65,536 learned-band pairs of 1-10 kbp: the banded route's scores equal
   the full DP's on every pair (the certificate is exact), and a sample of the
-  full DP equals the oracle.
+  full DP equals the oracle;
+* maximum sizes of a batch: 2^21 tiny pairs in one call, and sequences of
+  2^21 - 1 letters (the longest a local or semi-global batch accepts) on
+  either side of a pair, beside short pairs, every pair against the oracle.
 """
 import numpy as np
 import pytest
@@ -77,3 +80,44 @@ def test_band_workload_full_size_scores_equal_full_dp(pkg, ctx):
     idx = np.arange(0, b.n_pairs, 1024)
     want = oracle.score_batch(b.subset(idx), oracle.Scoring(*C4), 0)
     assert np.array_equal(fr["score"][idx], want[0])
+
+
+def _batch_results(pkg, ctx, b, sc_args, mode):
+    sc = pkg.Scoring.make(*sc_args)
+    dev = lambda a: torch.from_numpy(np.ascontiguousarray(a)).cuda()
+    out = torch.zeros(b.n_pairs * 40, dtype=torch.uint8, device="cuda")
+    ctx.align_batch(dev(b.q), dev(b.q_off), dev(b.s), dev(b.s_off), sc, mode, out=out)
+    torch.cuda.synchronize()
+    return out.cpu().numpy().view(pkg.RESULT_DTYPE)
+
+
+def _assert_equal(res, want):
+    for k, name in enumerate(("score", "end_q", "end_s")):
+        bad = np.nonzero(res[name] != want[k])[0]
+        assert len(bad) == 0, f"{len(bad)} pairs differ in {name}; first {int(bad[0])}"
+
+
+def test_two_million_tiny_pairs(pkg, ctx):
+    """2^21 pairs of 0-12 letters in one call: the sort, the work queue and the
+    result scatter at that count; every pair equals the oracle in every mode."""
+    b = synth.random_pairs(2 ** 21, 0, 12, seed=1500, related=0.6)
+    for mode in (0, 1, 2):
+        res = _batch_results(pkg, ctx, b, C4, mode)
+        _assert_equal(res, oracle.score_batch(b, oracle.Scoring(*C4), mode))
+
+
+@pytest.mark.parametrize("mode", [0, 1, 2])
+def test_sequences_at_the_length_limit(pkg, ctx, mode):
+    """A query of 2^21 - 1 letters against 48 and the reverse (one row stripe
+    over 2^21 - 1 columns), with 30 short pairs in the same batch."""
+    st = synth.Stream(1501 + mode, 1)
+    q = synth.random_codes(st, 2 ** 21 - 1, 4)
+    s = q[1000:1048].copy()
+    pairs = [(q, s), (s, q)]
+    pairs += [(synth.random_codes(st, 100, 4), synth.random_codes(st, 120, 4)) for _ in range(30)]
+    b = synth.from_pairs(pairs)
+    res = _batch_results(pkg, ctx, b, C4, mode)
+    want = oracle.score_batch(b, oracle.Scoring(*C4), mode)
+    _assert_equal(res, want)
+    if mode != 0:
+        assert res["score"][0] == 2 * 48 and res["score"][1] == 2 * 48
