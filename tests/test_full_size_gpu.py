@@ -9,7 +9,10 @@
   full DP equals the oracle;
 * maximum sizes of a batch: 2^21 tiny pairs in one call, and sequences of
   2^21 - 1 letters (the longest a local or semi-global batch accepts) on
-  either side of a pair, beside short pairs, every pair against the oracle.
+  either side of a pair, beside short pairs, every pair against the oracle;
+* the longest pair anyseq_align_long accepts on one side (2^23 - 1 letters
+  global, 2^21 - 1 local, against 64), score and optimum cell against the
+  oracle, and one letter more refused.
 """
 import numpy as np
 import pytest
@@ -121,3 +124,30 @@ def test_sequences_at_the_length_limit(pkg, ctx, mode):
     _assert_equal(res, want)
     if mode != 0:
         assert res["score"][0] == 2 * 48 and res["score"][1] == 2 * 48
+
+
+@pytest.mark.parametrize("mode", [0, 1])
+@pytest.mark.parametrize("long_side", ["query", "subject"])
+def test_align_long_at_the_length_limit(pkg, ctx, mode, long_side):
+    """The longest sequence anyseq_align_long takes (global: 2^23 - 1 letters;
+    local: 2^21 - 1, the optimum key's field) against a 64-letter piece of it:
+    thousands of row stripes (long query), or one stripe over all the columns
+    (long subject). One letter more is refused with ERR_ARG."""
+    limit = 2 ** 23 if mode == 0 else 2 ** 21
+    st = synth.Stream(1600 + mode, 1)
+    big = synth.random_codes(st, limit, 4)
+    piece = big[70000:70064].copy()
+    sc = pkg.Scoring.make(*C4)
+    dev = lambda a: torch.from_numpy(np.ascontiguousarray(a)).cuda()
+    longest = big[: limit - 1]
+    q, s = (longest, piece) if long_side == "query" else (piece, longest)
+    r, _ = ctx.align_long(dev(q), dev(s), sc, mode=mode)
+    want = oracle.score_batch(synth.from_pairs([(q, s)]), oracle.Scoring(*C4), mode)
+    got = (int(r["score"][0]), int(r["end_q"][0]), int(r["end_s"][0]))
+    assert got == (int(want[0][0]), int(want[1][0]), int(want[2][0]))
+    if mode == 1:
+        assert got[0] == 2 * 64
+    q, s = (big, piece) if long_side == "query" else (piece, big)
+    with pytest.raises(pkg.AnyseqError) as ei:
+        ctx.align_long(dev(q), dev(s), sc, mode=mode)
+    assert ei.value.status == 1
