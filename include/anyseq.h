@@ -141,9 +141,12 @@ anyseq_status_t anyseq_align_batch(anyseq_ctx *ctx,
  * no CIGAR words and begins at its end. Alphabets of up to 4 letters use 2-bit
  * letters and row profiles; larger alphabets (a substitution matrix, up to 32
  * letters) use byte letters and per-stripe query profiles in shared memory.
- * Arguments as for anyseq_align_batch with one pair of lengths n and m. Errors
- * as there, and ERR_ARG for local and semi-global pairs whose score could
- * reach 2^21 (largest positive substitution score times min(n, m)), and for a
+ * Arguments as for anyseq_align_batch with one pair of lengths n and m:
+ * below 2^23 letters each for global alignment, below 2^21 for local and
+ * semi-global (the optimum cell's fields). Errors as there, and ERR_ARG for a
+ * length at or above those limits, for local and semi-global pairs whose
+ * score could reach 2^21 (largest positive substitution score times
+ * min(n, m)), for a pair whose scores could leave the 32-bit range, and for a
  * scoring with sigma - open - extend (or extend - open - extend) outside
  * [-128, 127].
  */
