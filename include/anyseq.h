@@ -263,7 +263,7 @@ const char *anyseq_version(void);
  * bucket of a work item's longest query); each bin takes the cap with the
  * fewest cycles per cell. Then the whole sample is timed (CUDA events, median
  * of five) under the default shape, each smaller uniform cap and the per-bin
- * table; the fastest is kept if it beats the default by 1 %, else the context
+ * table; the fastest is kept if it beats the default by 3 %, else the context
  * stays untuned. Later calls of the context use the table for the kernels
  * without traceback and substitution matrix; results do not change.
  * anyseq_set_option(ctx, "autotune_reset", 0) drops it; anyseq_autotune_table
