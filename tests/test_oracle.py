@@ -92,6 +92,25 @@ def test_textbook_cases(case):
         assert list(beg) == case["beg"] and list(end) == case["end"]
 
 
+DP_TABLES = os.path.join(os.path.dirname(__file__), "golden", "dp_tables.json")
+
+
+def _dp_tables():
+    with open(DP_TABLES) as f:
+        return json.load(f)["tables"]
+
+
+@pytest.mark.parametrize("case", _dp_tables(), ids=lambda c: c["name"])
+def test_hand_worked_dp_tables(case):
+    """Every cell of a hand-worked global table: H(i, j) is the global score of
+    the prefixes q[1..i], s[1..j] (Eqs. 1-5 with the global initialisation)."""
+    q, s = synth.encode_dna(case["q"]), synth.encode_dna(case["s"])
+    sc = oracle.Scoring(case["match"], case["mismatch"], case["open"], case["extend"])
+    for i, row in enumerate(case["H"]):
+        for j, h in enumerate(row):
+            assert oracle.score(q[:i], s[:j], sc, oracle.GLOBAL)[0] == h, (i, j)
+
+
 def levenshtein(a, b):
     """Wagner-Fischer unit-cost edit distance (textbook)."""
     prev = list(range(len(b) + 1))
