@@ -2,11 +2,17 @@
 
 * features: identical sequences put every hit on the straight line (bin 32);
   a suffix of the query puts every hit on the negative side, with a hit count
-  fixed in closed form; k-mer keys equal a per-position recomputation;
+  fixed in closed form; a query shifted right by 10 letters puts every hit in
+  the hand-computed bin 32 + bucket(10) = 39; the magnitude buckets equal a
+  hand-computed table (tests/golden/band_buckets.json); k-mer keys equal a
+  per-position recomputation;
 * bfloat16 rounding equals torch's float32 -> bfloat16 conversion;
 * network gradients equal central finite differences of the loss;
 * the first Adam step moves each parameter by -lr * g / (|g| + eps).
 """
+import json
+import os
+
 import numpy as np
 import pytest
 
@@ -21,6 +27,31 @@ def test_kmer_keys_by_direct_recomputation():
     keys = F.kmer_keys(q)
     for i in range(len(q) - F.K + 1):
         assert keys[i] == sum(int(q[i + t]) << (2 * t) for t in range(F.K))
+
+
+def test_bucket_table_by_hand():
+    with open(os.path.join(os.path.dirname(__file__), "golden", "band_buckets.json")) as f:
+        rows = json.load(f)["cases"]
+    for x, lg, second, want in rows:
+        assert F.bucket(x) == want, x
+        if x:
+            assert x.bit_length() - 1 == lg  # the table's own arithmetic
+            assert want == min(31, 1 + 2 * lg + second)
+
+
+def test_shifted_copy_hits_one_positive_bin():
+    """s = 10 fresh letters + q[:n - 10] (m = n): the query k-mer at i sits at
+    j = i + 10, so D = (j - i) * n - (m - n) * i = 10 n, |D| / n = 10, bucket 7
+    (floor(log2 10) = 3, second bit 0) and bin 32 + 7 = 39. Sampled starts are
+    i = 0, 4, 8, ... (stride 4 below 16,384 letters); the k-mer at i is in s
+    when i + 10 + 12 <= n."""
+    n = 400
+    st = synth.Stream(3003, 1)
+    q = synth.random_codes(st, n, 4)
+    s = np.concatenate([synth.random_codes(st, 10, 4), q[:n - 10]])
+    counts = F.histogram_counts(q, s)
+    want = len(range(0, n - 22 + 1, 4))
+    assert counts[39] == want and counts.sum() == want
 
 
 def test_identical_sequences_hit_the_diagonal():
