@@ -66,7 +66,8 @@ __device__ __forceinline__ void build_qprofile(const BatchArgs &A, const Slot &s
 __host__ __device__ constexpr int block_cols(int sigp) { return sigp ? 16 : 32; }
 
 template <class C, int MODE, int R, bool TB, int SIGP>
-__device__ __noinline__ void run_slot(const BatchArgs &A, GroupSmemT<4 * block_cols(SIGP)> *sm, const Slot &sl,
+__device__ __noinline__ void run_slot(const BatchArgs &A, GroupSmemT<4 * block_cols(SIGP), block_cols(SIGP)> *sm,
+                                      const Slot &sl,
                                       int nch, int Mit, int g, int64_t gslot, int32_t *res, const int32_t *pid,
                                       uint32_t *qp, const int8_t *tab, uint32_t *lc) {
     typedef typename C::T T;
@@ -390,6 +391,12 @@ __device__ __noinline__ void run_slot(const BatchArgs &A, GroupSmemT<4 * block_c
     }
 }
 
+}  // namespace anyseq
+
+#include "batch_score.cuh"
+
+namespace anyseq {
+
 // Persistent kernel: each warp pulls work items (2 slots of 16 lanes) from the
 // sorted list until it is empty. THREADS = batch_threads (batch.h); the matrix
 // path's per-group query profile lives in dynamic shared memory after a copy
@@ -401,11 +408,11 @@ __host__ __device__ constexpr int rsel(int r) { return r < RMAX ? r : RMAX; }
 template <class C, int MODE, bool TB, int SIGP>
 __global__ void __launch_bounds__(batch_threads(SIGP), batch_min_ctas(SIGP)) batch_kernel(BatchArgs A) {
     constexpr int THREADS = batch_threads(SIGP);
-    __shared__ GroupSmemT<4 * block_cols(SIGP)> smem[THREADS / 16];
+    __shared__ GroupSmemT<4 * block_cols(SIGP), block_cols(SIGP)> smem[THREADS / 16];
     extern __shared__ __align__(16) uint8_t dyn_smem[];
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int grp = lane >> 4, g = lane & 15;
-    GroupSmemT<4 * block_cols(SIGP)> *sm = &smem[warp * 2 + grp];
+    GroupSmemT<4 * block_cols(SIGP), block_cols(SIGP)> *sm = &smem[warp * 2 + grp];
     int8_t *tab = nullptr;
     uint32_t *qp = nullptr;
     if (SIGP) {
@@ -467,25 +474,32 @@ __global__ void __launch_bounds__(batch_threads(SIGP), batch_min_ctas(SIGP)) bat
             // the host sizes the border scratch for every multi-chunk query; never reached
             continue;
         }
-        if (SIGP && TB) {
-            run_slot<C, MODE, TB_R, TB, SIGP>(A, sm, sl, P.nch, P.Mit, g, gslot, res, pid, qp, tab, lc);
+        // the traceback kernels and the local row-profile kernels (whose per-row maxima
+        // and columns leave no registers for the inlined walk) take run_slot
+        if constexpr (TB || (MODE == LOCAL && SIGP == 0)) {
+            if (SIGP && TB) {
+                run_slot<C, MODE, TB_R, TB, SIGP>(A, sm, sl, P.nch, P.Mit, g, gslot, res, pid, qp, tab, lc);
+            } else {
+                switch (P.R) {
+#define ANYSEQ_TB_CASE(RR) \
+    case RR: run_slot<C, MODE, rsel<RMAX>(RR), TB, SIGP>(A, sm, sl, P.nch, P.Mit, g, gslot, res, pid, qp, tab, lc); break;
+                    ANYSEQ_TB_CASE(2) ANYSEQ_TB_CASE(3) ANYSEQ_TB_CASE(4) ANYSEQ_TB_CASE(5) ANYSEQ_TB_CASE(6)
+                    ANYSEQ_TB_CASE(7) ANYSEQ_TB_CASE(8) ANYSEQ_TB_CASE(9) ANYSEQ_TB_CASE(10) ANYSEQ_TB_CASE(11)
+                    ANYSEQ_TB_CASE(12) ANYSEQ_TB_CASE(13) ANYSEQ_TB_CASE(14) ANYSEQ_TB_CASE(15)
+#undef ANYSEQ_TB_CASE
+                    default: run_slot<C, MODE, RMAX, TB, SIGP>(A, sm, sl, P.nch, P.Mit, g, gslot, res, pid, qp, tab, lc); break;
+                }
+            }
         } else {
+            // score only: the lean step loop (batch_score.cuh), one copy per rows-per-lane count
             switch (P.R) {
-                case 2: run_slot<C, MODE, rsel<RMAX>(2), TB, SIGP>(A, sm, sl, P.nch, P.Mit, g, gslot, res, pid, qp, tab, lc); break;
-                case 3: run_slot<C, MODE, rsel<RMAX>(3), TB, SIGP>(A, sm, sl, P.nch, P.Mit, g, gslot, res, pid, qp, tab, lc); break;
-                case 4: run_slot<C, MODE, rsel<RMAX>(4), TB, SIGP>(A, sm, sl, P.nch, P.Mit, g, gslot, res, pid, qp, tab, lc); break;
-                case 5: run_slot<C, MODE, rsel<RMAX>(5), TB, SIGP>(A, sm, sl, P.nch, P.Mit, g, gslot, res, pid, qp, tab, lc); break;
-                case 6: run_slot<C, MODE, rsel<RMAX>(6), TB, SIGP>(A, sm, sl, P.nch, P.Mit, g, gslot, res, pid, qp, tab, lc); break;
-                case 7: run_slot<C, MODE, rsel<RMAX>(7), TB, SIGP>(A, sm, sl, P.nch, P.Mit, g, gslot, res, pid, qp, tab, lc); break;
-                case 8: run_slot<C, MODE, rsel<RMAX>(8), TB, SIGP>(A, sm, sl, P.nch, P.Mit, g, gslot, res, pid, qp, tab, lc); break;
-                case 9: run_slot<C, MODE, rsel<RMAX>(9), TB, SIGP>(A, sm, sl, P.nch, P.Mit, g, gslot, res, pid, qp, tab, lc); break;
-                case 10: run_slot<C, MODE, rsel<RMAX>(10), TB, SIGP>(A, sm, sl, P.nch, P.Mit, g, gslot, res, pid, qp, tab, lc); break;
-                case 11: run_slot<C, MODE, rsel<RMAX>(11), TB, SIGP>(A, sm, sl, P.nch, P.Mit, g, gslot, res, pid, qp, tab, lc); break;
-                case 12: run_slot<C, MODE, rsel<RMAX>(12), TB, SIGP>(A, sm, sl, P.nch, P.Mit, g, gslot, res, pid, qp, tab, lc); break;
-                case 13: run_slot<C, MODE, rsel<RMAX>(13), TB, SIGP>(A, sm, sl, P.nch, P.Mit, g, gslot, res, pid, qp, tab, lc); break;
-                case 14: run_slot<C, MODE, rsel<RMAX>(14), TB, SIGP>(A, sm, sl, P.nch, P.Mit, g, gslot, res, pid, qp, tab, lc); break;
-                case 15: run_slot<C, MODE, rsel<RMAX>(15), TB, SIGP>(A, sm, sl, P.nch, P.Mit, g, gslot, res, pid, qp, tab, lc); break;
-                default: run_slot<C, MODE, RMAX, TB, SIGP>(A, sm, sl, P.nch, P.Mit, g, gslot, res, pid, qp, tab, lc); break;
+#define ANYSEQ_SC_CASE(RR) \
+    case RR: score_slot<C, MODE, rsel<RMAX>(RR), SIGP, RMAX>(A, sm, sl, P.nch, P.Mit, g, lane, gslot, res, qp, tab, lc); break;
+                ANYSEQ_SC_CASE(2) ANYSEQ_SC_CASE(3) ANYSEQ_SC_CASE(4) ANYSEQ_SC_CASE(5) ANYSEQ_SC_CASE(6)
+                ANYSEQ_SC_CASE(7) ANYSEQ_SC_CASE(8) ANYSEQ_SC_CASE(9) ANYSEQ_SC_CASE(10) ANYSEQ_SC_CASE(11)
+                ANYSEQ_SC_CASE(12) ANYSEQ_SC_CASE(13) ANYSEQ_SC_CASE(14) ANYSEQ_SC_CASE(15)
+#undef ANYSEQ_SC_CASE
+                default: score_slot<C, MODE, RMAX, SIGP, RMAX>(A, sm, sl, P.nch, P.Mit, g, lane, gslot, res, qp, tab, lc); break;
             }
         }
         if (A.bin_stats && lane == 0) {

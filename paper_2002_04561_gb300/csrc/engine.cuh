@@ -32,11 +32,15 @@ namespace anyseq {
 // Per-group shared memory: subject selectors, top and bottom border rings of
 // RG columns (four refill blocks: the one being filled, the one being
 // computed, the one the last lanes still finish, the one being drained).
-template <int RG>
+// Each ring has MB entries more: the score kernels keep a copy of ring block 0
+// there (selectors, top) or let the last lane's stores run on past the ring's
+// end (bottom), so a lane walks one refill block with constant offsets from
+// one base address and never wraps.
+template <int RG, int MB = 0>
 struct __align__(16) GroupSmemT {
-    uint32_t sel[RG];
-    int32_t top[2 * RG];  // (Hoe, E) of the row above the chunk
-    int32_t bot[2 * RG];  // (Hoe, E) of the chunk's last row
+    uint32_t sel[RG + MB];
+    int32_t top[2 * (RG + MB)];  // (Hoe, E) of the row above the chunk
+    int32_t bot[2 * (RG + MB)];  // (Hoe, E) of the chunk's last row
 };
 
 // Column-0 value H(i, 0) of padded row with real index i (i <= 0: padding).

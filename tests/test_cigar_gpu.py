@@ -219,3 +219,29 @@ def test_cigar_row_counts_at_chunk_boundaries(pkg, ctx, mode, force32):
     sc_args = (2, -3, -5, -2)
     res, cigars, _ = gpu_align(pkg, ctx, b, sc_args, mode, force32=force32)
     assert_cigar_parity(b, res, cigars, sc_args, mode)
+
+
+def _golden_cases():
+    import json
+    import os
+    with open(os.path.join(os.path.dirname(__file__), "golden", "textbook.json")) as f:
+        return json.load(f)["cases"]
+
+
+@pytest.mark.parametrize("force32", [False, True])
+def test_golden_cases_on_the_gpu(pkg, ctx, force32):
+    """The hand-derived cases of tests/golden/textbook.json (worked examples
+    and the tie rules of the optimum cell and the predecessors) through the
+    batched path with CIGAR, in int16x2 and in 32-bit lanes: score, cells and
+    CIGAR equal the stored hand values, not only the oracle's."""
+    for case in _golden_cases():
+        q = np.array(case["codes_q"], np.uint8) if "codes_q" in case else synth.encode_dna(case["q"])
+        s = np.array(case["codes_s"], np.uint8) if "codes_s" in case else synth.encode_dna(case["s"])
+        b = synth.from_pairs([(q, s)])
+        args = (case["match"], case["mismatch"], case["open"], case["extend"])
+        res, cigars, _ = gpu_align(pkg, ctx, b, args, oracle.MODES[case["mode"]], force32=force32)
+        assert int(res["score"][0]) == case["score"], case["name"]
+        if "cigar" in case:
+            assert oracle.cigar_string(cigars[0]) == case["cigar"], case["name"]
+            assert [int(res["beg_q"][0]), int(res["beg_s"][0])] == case["beg"], case["name"]
+            assert [int(res["end_q"][0]), int(res["end_s"][0])] == case["end"], case["name"]
