@@ -234,9 +234,12 @@ anyseq_status_t anyseq_get_stat(anyseq_ctx *ctx, const char *key, double *value)
  * the synchronisation those calls imply. It runs the same wavefront pass as
  * anyseq_align_long, with all scratch in one fixed device array of the library
  * (about 21 MB on every GPU that loads it, held until the process exits).
- *   q, s    device arrays of codes 0..3, lengths 1 <= n, m <= ANYSEQ_NOALLOC_MAX_LEN
- *           (longer inputs: ANYSEQ_ERR_ARG)
- *   score   device int32 receiving the optimal global score
+ *   q, s    device arrays of codes 0..3 on the current device, lengths
+ *           1 <= n, m <= ANYSEQ_NOALLOC_MAX_LEN
+ *   score   device int32 on the current device receiving the optimal global score
+ * ANYSEQ_ERR_ARG: a length outside those limits, a pointer that is not device
+ * memory of the current device, or a scoring whose values could leave the
+ * 32-bit range on this pair (the same bound as anyseq_align_long).
  * No context is needed. The first call on a device resolves the array's device
  * address (once per device); make that first call before any stream capture.
  * The call returns after its stream has finished (it reads the error flags).
@@ -287,6 +290,22 @@ anyseq_status_t anyseq_gapped(const uint8_t *q, int64_t n, const uint8_t *s, int
                               int32_t beg_q, int32_t beg_s, const uint32_t *cigar, uint32_t cigar_len,
                               const char *letters, int32_t alphabet, char *q_out, char *s_out,
                               int64_t cap, int64_t *len);
+
+/* Share of one batch for rank `rank` of a data-parallel job of `world` ranks
+ * (the paper's inter-sequence parallelism, Sec. VI, spread over GPUs: pairs
+ * are independent, so the only exchange is a gather of the results). Pairs go
+ * by length-balanced round-robin of bins: the 8-bit logarithmic bins of their
+ * cell counts n * m, largest first, index order inside a bin, dealt to the
+ * ranks in snake order (0..W-1, W-1..0, ...). Pair counts per rank differ by
+ * at most one. q_off, s_off: host arrays of n_pairs + 1 offsets (as for
+ * anyseq_align_batch). idx: host array of cap entries receiving the rank's
+ * pair indices in increasing order; *count = their number. Host-only and
+ * deterministic: every rank computes every rank's share without
+ * communication. Errors: ERR_ARG (NULL pointers, rank outside [0, world),
+ * decreasing offsets), ERR_CAPACITY (cap < *count; at most ceil(n_pairs /
+ * world) entries are ever needed). */
+anyseq_status_t anyseq_shard_plan(const int64_t *q_off, const int64_t *s_off, int64_t n_pairs, int32_t world,
+                                  int32_t rank, int64_t *idx, int64_t cap, int64_t *count);
 
 /* ------------------------------------------------------------------------
  * Graph plans (batching, not in the paper): one batch shape of

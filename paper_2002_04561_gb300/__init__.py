@@ -71,7 +71,7 @@ EXPORTS = ["anyseq_create", "anyseq_destroy", "anyseq_align_batch", "anyseq_alig
            "anyseq_server_create", "anyseq_server_submit", "anyseq_server_wait", "anyseq_server_stat",
            "anyseq_server_destroy", "anyseq_plan_create", "anyseq_plan_buffers", "anyseq_plan_run",
            "anyseq_plan_wait", "anyseq_plan_destroy", "anyseq_gapped", "anyseq_autotune",
-           "anyseq_autotune_table", "anyseq_autotune_set_table"]
+           "anyseq_autotune_table", "anyseq_autotune_set_table", "anyseq_shard_plan"]
 NOALLOC_MAX_LEN = 1048576
 BAND_FEATURES = 64
 BAND_PARAMS = 25090
@@ -127,6 +127,7 @@ def load(build_if_missing: bool = False):
     lib.anyseq_autotune_set_table.argtypes = [P, P]
     lib.anyseq_gapped.argtypes = [P, I64, P, I64, I32, I32, P, U32, ctypes.c_char_p, I32, P, P, I64,
                                   ctypes.POINTER(I64)]
+    lib.anyseq_shard_plan.argtypes = [P, P, I64, I32, I32, P, I64, ctypes.POINTER(I64)]
     lib.anyseq_last_error.restype = ctypes.c_char_p
     lib.anyseq_last_error.argtypes = []
     lib.anyseq_version.restype = ctypes.c_char_p
@@ -138,7 +139,7 @@ def load(build_if_missing: bool = False):
                  "anyseq_server_wait", "anyseq_server_stat", "anyseq_server_destroy", "anyseq_plan_create",
                  "anyseq_plan_buffers", "anyseq_plan_run", "anyseq_plan_wait", "anyseq_plan_destroy",
                  "anyseq_gapped", "anyseq_autotune", "anyseq_autotune_table",
-                 "anyseq_autotune_set_table"]:
+                 "anyseq_autotune_set_table", "anyseq_shard_plan"]:
         getattr(lib, name).restype = ctypes.c_int
     _lib = lib
     return lib
@@ -299,8 +300,17 @@ def align_long_noalloc(q, s, scoring: Scoring, score, stream=None):
     callers whose device memory is owned by someone else; see the header)."""
     n = q.numel() if hasattr(q, "numel") else len(q)
     m = s.numel() if hasattr(s, "numel") else len(s)
-    _check(load().anyseq_align_long_noalloc(_ptr(q), n, _ptr(s), m, ctypes.byref(scoring), _ptr(score),
-                                            _stream_handle(stream)))
+    lib = load()
+    dev = getattr(q, "device", None)
+    if dev is not None and dev.type == "cuda":
+        # the library uses the current device's scratch array: make q's device current
+        import torch
+        with torch.cuda.device(dev):
+            _check(lib.anyseq_align_long_noalloc(_ptr(q), n, _ptr(s), m, ctypes.byref(scoring), _ptr(score),
+                                                 _stream_handle(stream)))
+        return
+    _check(lib.anyseq_align_long_noalloc(_ptr(q), n, _ptr(s), m, ctypes.byref(scoring), _ptr(score),
+                                         _stream_handle(stream)))
 
 
 def gapped(q, s, beg_q: int, beg_s: int, cigar, letters: str = "ACGT"):
@@ -314,6 +324,19 @@ def gapped(q, s, beg_q: int, beg_s: int, cigar, letters: str = "ACGT"):
     _check(load().anyseq_gapped(_ptr(q), q.size, _ptr(s), s.size, beg_q, beg_s, _ptr(cigar), cigar.size,
                                 letters.encode(), len(letters), qo, so, cap, ctypes.byref(n)))
     return qo.value.decode(), so.value.decode()
+
+
+def shard_plan(q_off, s_off, world: int, rank: int) -> np.ndarray:
+    """anyseq_shard_plan: the pair indices (int64, increasing) that rank
+    ``rank`` of ``world`` aligns from a batch with these host offsets."""
+    q_off = np.ascontiguousarray(q_off, dtype=np.int64)
+    s_off = np.ascontiguousarray(s_off, dtype=np.int64)
+    n = len(q_off) - 1
+    cap = max(1, -(-n // max(1, world)))
+    idx = np.zeros(cap, dtype=np.int64)
+    count = ctypes.c_int64(0)
+    _check(load().anyseq_shard_plan(_ptr(q_off), _ptr(s_off), n, world, rank, _ptr(idx), cap, ctypes.byref(count)))
+    return idx[:count.value].copy()
 
 
 def encode_dna(text: str) -> np.ndarray:

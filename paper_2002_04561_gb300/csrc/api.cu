@@ -658,7 +658,7 @@ bool anyseq::long_range_ok(const anyseq_scoring_t *sc, int64_t n, int64_t m) {
             int64_t v = sigma_host(sc, a, b);
             smax = v > smax ? v : (-v > smax ? -v : smax);
         }
-    const int64_t bound = 3 * (int64_t)(-sc->gap_open) + (n + m + 2) * (int64_t)(-sc->gap_extend) + smax * (n < m ? n : m + 1);
+    const int64_t bound = 3 * (int64_t)(-sc->gap_open) + (n + m + 2) * (int64_t)(-sc->gap_extend) + smax * ((n < m ? n : m) + 1);
     return bound < (1ll << 28);
 }
 

@@ -48,6 +48,17 @@ __global__ void noalloc_init_kernel(WavePass *pass, WavePass value, int32_t *ctl
     for (int64_t k = t; k < nctl; k += (int64_t)gridDim.x * blockDim.x) ctl[k] = 0;
 }
 
+// True when p is device (or managed) memory of device dev.
+static bool on_device(const void *p, int dev) {
+    cudaPointerAttributes at;
+    if (cudaPointerGetAttributes(&at, p) != cudaSuccess) {
+        cudaGetLastError();
+        return false;
+    }
+    if (at.type == cudaMemoryTypeManaged) return true;
+    return at.type == cudaMemoryTypeDevice && at.device == dev;
+}
+
 __global__ void noalloc_finish_kernel(const int32_t *H, int32_t m, int32_t *score) { *score = H[m]; }
 
 // Device address of the array on the current device, resolved once per device.
@@ -87,18 +98,16 @@ extern "C" anyseq_status_t anyseq_align_long_noalloc(const uint8_t *q, int64_t n
         return fail(ANYSEQ_ERR_ARG, "sequences longer than %lld letters do not fit the fixed scratch array",
                     (long long)NA_MAX);
     if (!q || !s || !score) return fail(ANYSEQ_ERR_ARG, "q, s and score must be device pointers");
-    if (!is_device_ptr(q) || !is_device_ptr(s) || !is_device_ptr(score))
-        return fail(ANYSEQ_ERR_ARG, "q, s and score must be device memory");
-    {
-        int64_t smax = 0;
-        for (int a = 0; a < sc->alphabet; a++)
-            for (int b = 0; b < sc->alphabet; b++) {
-                int64_t v = sigma_host(sc, a, b);
-                smax = v > smax ? v : (-v > smax ? -v : smax);
-            }
-        int64_t bound = 3 * (int64_t)(-sc->gap_open) + (n + m + 2) * (int64_t)(-sc->gap_extend) + smax * (n + 1);
-        if (bound >= (1ll << 28)) return fail(ANYSEQ_ERR_ARG, "scores of this pair may leave the 32-bit range");
+    if (!long_range_ok(sc, n, m)) return fail(ANYSEQ_ERR_ARG, "scores of this pair may leave the 32-bit range");
+    // the scratch array and the launches belong to the current device: inputs and
+    // output must live there too
+    int cur = 0;
+    if (cudaGetDevice(&cur) != cudaSuccess) {
+        cudaGetLastError();
+        return fail(ANYSEQ_ERR_CUDA, "no current CUDA device");
     }
+    if (!on_device(q, cur) || !on_device(s, cur) || !on_device(score, cur))
+        return fail(ANYSEQ_ERR_ARG, "q, s and score must be device memory of the current device (%d)", cur);
     cudaStream_t st = (cudaStream_t)cuda_stream;
     uint8_t *base = nullptr;
     st2 = scratch_address(&base);
@@ -115,9 +124,8 @@ extern "C" anyseq_status_t anyseq_align_long_noalloc(const uint8_t *q, int64_t n
     ps.n = (int32_t)n;
     ps.m = (int32_t)m;
     ps.tb = sc->gap_open;
-    int dev = 0, sms = 1;
-    cudaGetDevice(&dev);
-    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    int sms = 1;
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, cur);
     const int wr = wave_rows_per_lane(n, sms, 1, GLOBAL);
     const int64_t stripes = (n + WAVE_LANES * wr - 1) / (WAVE_LANES * wr);
     noalloc_init_kernel<<<8, 256, 0, st>>>(pass, ps, ctl, stripes + 2, bad);
