@@ -4,17 +4,24 @@ Workload (one step = one anyseq_align_batch call over the whole batch):
 262,144 short-read pairs, query 100-250 bp, target = query with 4 %
 substitutions, 1 % indels and 20-bp flanks; semi-global alignment with affine
 gaps (+1 / -4 / open -6 / extend -1), int16x2 lanes, score and optimum cell.
-Under torchrun every rank aligns its own batch of that shape (weak scaling, no
-data-path collective; the barrier and the max over ranks are timing only).
+The barrier and the max over ranks are timing only.
+
+Under torchrun the ranks split one global batch of N x 262,144 pairs by the
+library's length-balanced round-robin partition (anyseq_shard_plan), so the
+work per GPU stays fixed (weak scaling); after the timed region rank 0
+gathers every pair's record in the caller's order (the path's one exchange).
 
 Prints one JSON line. ``value`` is cell updates per second (GCUPS) with inputs
 resident in device memory; ``e2e`` is the same metric through the C ABI with
 pinned host buffers, host-device copies inside the timed region; ``roofline``
 is the DP kernel's cell rate against the integer-issue bound
-SMs x clock x 64 lane-ops per clock / (3.5 ops per cell for int16x2 affine):
-the DPX add-max, per-half max and byte-permute instructions the recurrence
-needs issue at 64 lanes per clock per SM on GB300 (measured with instruction
-counters; the nominal 128 would halve every fraction, reported beside it);
+SMs x clock x I_SM / I_alg. I_alg = 3.5 algorithmic ops per cell for int16x2
+affine (7 for int32), fixed before measuring. I_SM is the per-SM issue rate of
+the fused cell's instruction mix on the SM's pipes: per lane-word the cell
+issues 4 half-rate ops (byte permute, two DPX add-max, one three-input max:
+64 lanes per clock per SM, measured) and 2 full-rate 32-bit adds (128 lanes
+per clock), under the SM's issue limit of 128 lane-instructions per clock, so
+I_SM = 6 / max(4/64, 2/128, 6/128) = 96 lane-ops per clock;
 ``cpu_baseline`` is the CPU oracle on the host cores on a bounded sample.
 ``--impl reference`` times the CPU oracle itself on the same workload.
 """
@@ -42,8 +49,27 @@ WORKLOAD = "short_reads_262144_semiglobal_affine"
 SCORING = (1, -4, -6, -1)
 MODE = 2  # semi-global
 I_ALG = 3.5  # algorithmic integer ops per cell, int16x2 affine (fixed before measuring)
-LANE_OPS_PER_CLK = 64  # measured issue rate of DPX / VIMNMX / PRMT on sm_103 (lanes per clock per SM)
+I_ALG32 = 7.0  # the same for 32-bit lanes
+# Issue rates per SM in lanes per clock, measured on GB300 (sm_103) with
+# dependent-chain throughput probes: DPX add-max, three-input max and byte
+# permute run at half rate; 32-bit IADD at full rate; the SM issues at most
+# 4 sub-partitions x 32 lanes per clock.
+HALF_RATE, FULL_RATE, ISSUE_RATE = 64, 128, 128
+# instruction mix of the fused cell per lane-word: byte permute (sigma'),
+# add-max (F), three-input max (H), add-max (E) at half rate; the diagonal
+# add and H + open + extend at full rate
+CELL_MIX = {"half": 4, "full": 2}
 NOMINAL_LANE_OPS = 128  # 4 SM sub-partitions x 32 lanes
+
+
+def lane_ops_per_clk(mix=CELL_MIX) -> float:
+    """I_SM: ops of the mix / the clocks its busiest pipe (or the issue port) needs."""
+    ops = mix["half"] + mix["full"]
+    clocks = max(mix["half"] / HALF_RATE, mix["full"] / FULL_RATE, ops / ISSUE_RATE)
+    return ops / clocks
+
+
+LANE_OPS_PER_CLK = lane_ops_per_clk()  # 96
 L2_BYTES = 129 * 2**20
 
 
@@ -414,7 +440,10 @@ def secondary_workloads(pkg, ctx, device):
     r, used = ctx.align_long(qd, sd, sc, want=7, cigar=hcig)
     hb_s = time.perf_counter() - t0
     # the oracle on a 20 kbp pair of the same generator (a 1 Mbp pair is 1e12 cells)
+    peak32 = n_sm * float(measured_peaks().get("sm_max_mhz", 2070.0)) * 1e6 * LANE_OPS_PER_CLK / I_ALG32 / 1e9
     out["long_pair_1Mbp_global_affine"] = {"score_s": ms / 1e3, "score_GCUPS": b.cells() / ms / 1e6,
+                                           "score_roofline_frac": b.cells() / ms / 1e6 / peak32,
+                                           "roofline_peak_GCUPS": peak32,
                                            "cigar_total_s": hb_s, "cigar_words": int(used),
                                            "score": int(r["score"][0]),
                                            "cpu_oracle": oracle_sample(synth.long_pair(n=20_000, inversion=400),
@@ -546,7 +575,15 @@ def main():
     ctx = pkg.Context(local)
     ctx.set_option("profile", 1)
 
-    batch = synth.short_reads(n_pairs=args.pairs, seed=2 + 1000 * rank)
+    # one global batch, this rank's share by the native partition (all pairs at N = 1)
+    batch_all = synth.short_reads(n_pairs=args.pairs * ws, seed=2)
+    mine = pkg.shard_plan(batch_all.q_off, batch_all.s_off, ws, rank)
+    if ws == 1:
+        batch = batch_all
+    else:
+        from paper_2002_04561_gb300.dist import take_pairs
+        batch = synth.Batch(*take_pairs(batch_all.q, batch_all.q_off, mine),
+                            *take_pairs(batch_all.s, batch_all.s_off, mine), batch_all.alphabet)
     cells = batch.cells()
     dev = lambda a: torch.from_numpy(np.ascontiguousarray(a)).to(device)
     q, q_off, s, s_off = dev(batch.q), dev(batch.q_off), dev(batch.s), dev(batch.s_off)
@@ -601,10 +638,20 @@ def main():
     h2d = batch.q.nbytes + batch.s.nbytes + batch.q_off.nbytes + batch.s_off.nbytes
     d2h = hout.numel()
 
-    # results must still match: spot check 2,000 pairs against the oracle (rank 0, untimed)
+    # the host-buffer and device-buffer calls must give the same results (untimed)
     res = out.cpu().numpy().view(pkg.RESULT_DTYPE)
     hres = hout.numpy().view(pkg.RESULT_DTYPE)
     assert np.array_equal(res["score"], hres["score"])
+
+    gathered = None
+    if ws > 1:
+        # the one exchange of the path: every record to rank 0, in the global batch's order
+        from paper_2002_04561_gb300 import dist as pdist
+        recs = pdist.align_batch_sharded(ctx, batch_all.q, batch_all.q_off, batch_all.s, batch_all.s_off, sc, MODE)
+        if rank == 0:
+            assert len(recs) == batch_all.n_pairs
+            assert np.array_equal(recs["score"][mine], hres["score"])
+            gathered = int(len(recs))
 
     peaks = measured_peaks()
     n_sm = torch.cuda.get_device_properties(local).multi_processor_count
@@ -614,8 +661,9 @@ def main():
     achieved = cells / (dp_avg / 1e3) / 1e9
     roof = {"bound": "alu", "achieved": achieved, "peak": peak_gcups, "unit": "GCUPS",
             "frac": achieved / peak_gcups, "traffic": profiled_traffic(),
-            "peak_basis": f"{n_sm} SMs x {f_max / 1e6:.0f} MHz (max) x {LANE_OPS_PER_CLK} lane-ops/clk / "
-                          f"{I_ALG} ops per cell",
+            "peak_basis": f"{n_sm} SMs x {f_max / 1e6:.0f} MHz (max) x I_SM {LANE_OPS_PER_CLK:.0f} lane-ops/clk / "
+                          f"I_alg {I_ALG} ops per cell; I_SM = 6 ops / max(4/{HALF_RATE}, 2/{FULL_RATE}, "
+                          f"6/{ISSUE_RATE}) clk for the cell's 4 half-rate + 2 full-rate ops per lane-word",
             "kernel": "batch_kernel<CellI16x2, SEMIGLOBAL>", "kernel_ms": dp_avg,
             "frac_nominal_128": achieved / (peak_gcups * NOMINAL_LANE_OPS / LANE_OPS_PER_CLK)}
     if clk.get("sm_mhz"):
@@ -629,7 +677,10 @@ def main():
                    "n_pairs_per_gpu": batch.n_pairs, "cells_per_gpu": cells,
                    "query_len": "100-250", "target": "query + 4% sub + 1% indel + 20bp flanks",
                    "scoring": "semiglobal +1/-4 open -6 extend -1", "l2": "flushed between steps (258 MB write)",
-                   "pairs_per_s": batch.n_pairs * ws * args.steps / (total_ms / 1e3)},
+                   "pairs_per_s": batch.n_pairs * ws * args.steps / (total_ms / 1e3),
+                   "parallelism": f"dp{ws}",
+                   "partition": "one global batch, length-balanced round-robin of cell-count bins per rank",
+                   "gathered_pairs": gathered},
         "roofline": roof,
         "e2e": {"value": e2e_value, "unit": "GCUPS", "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
         "gpu_launches": launches,
