@@ -33,7 +33,7 @@ __device__ __forceinline__ void score_slot(const BatchArgs &A, GroupSmemT<4 * bl
                                            int32_t *res, uint32_t *qp, const int8_t *tab, uint32_t *lc) {
     typedef typename C::T T;
     constexpr int B = block_cols(SIGP), RING = 4 * B;
-    constexpr int U = 4;  // unroll of the step loop
+    constexpr int U = 2;  // unroll of the step loop
     const int32_t o = A.o, e = A.e, oe = A.o + A.e;
     const uint32_t e_raw = C::raw(e);
     const uint32_t oe_c = C::cst(oe), e_c = C::cst(e);
@@ -70,8 +70,8 @@ __device__ __forceinline__ void score_slot(const BatchArgs &A, GroupSmemT<4 * bl
         const int32_t rb = ch * CH + g * R + 1;  // padded row of register 0
         uint32_t profA[SIGP ? 1 : R], profB[SIGP ? 1 : R];
         T Hoe[R], F[R];
-        T rowmax[MODE == LOCAL ? R : 1];
-        uint32_t rowj0[MODE == LOCAL ? R : 1], rowj1[MODE == LOCAL ? R : 1];
+        T rowmax[MODE == LOCAL ? R : 1];  // the row maximum of H so far
+        uint32_t rowj0[MODE == LOCAL ? R : 1], rowj1[MODE == LOCAL ? R : 1];  // its first column per half
 #pragma unroll
         for (int r = 0; r < R; r++) {
             int32_t h0[2] = {0, 0};
@@ -193,8 +193,9 @@ __device__ __forceinline__ void score_slot(const BatchArgs &A, GroupSmemT<4 * bl
             __syncwarp();
             const int nst = min(S - s0, B);
             const uint32_t *selp = &sm->sel[(s0 - g) & (RING - 1)];
-            const int2 *topp = &top2[(s0 + 1) & (RING - 1)];
-            int2 *botp = &bot2[(s0 - (GROUP - 1)) & (RING - 1)];
+            // shared-space addresses of lane 15's top load and bottom store at the block's first step
+            const uint32_t topa = (uint32_t)__cvta_generic_to_shared(&top2[(s0 + 1) & (RING - 1)]);
+            const uint32_t bota = (uint32_t)__cvta_generic_to_shared(&bot2[(s0 - (GROUP - 1)) & (RING - 1)]);
             const int c0 = s0 - g;  // this lane's column at the block's first step
 
             auto run = [&](auto careful_tag) {
@@ -261,16 +262,27 @@ __device__ __forceinline__ void score_slot(const BatchArgs &A, GroupSmemT<4 * bl
                                 }
                             }
                         }
-                        if (g == GROUP - 1) {
-                            botp[j] = make_int2((int32_t)C::as_u(xh), (int32_t)C::as_u(xe));
-                            const int2 tv = topp[j];
-                            xh = C::from_u((uint32_t)tv.x);
-                            xe = C::from_u((uint32_t)tv.y);
+                        {
+                            // lane 15: its last row to the bottom ring, lane 0's next border value in;
+                            // predicated shared-memory accesses rather than a branch around them
+                            uint32_t hx = C::as_u(xh), ex = C::as_u(xe);
+                            asm volatile(
+                                "{ .reg .pred p;\n\t"
+                                "setp.eq.u32 p, %4, 15;\n\t"
+                                "@p st.shared.v2.u32 [%2], {%0, %1};\n\t"
+                                "@p ld.shared.v2.u32 {%0, %1}, [%3]; }"
+                                : "+r"(hx), "+r"(ex)
+                                : "r"(bota + 8u * (uint32_t)j), "r"(topa + 8u * (uint32_t)j), "r"(g)
+                                : "memory");
+                            xh = C::from_u(hx);
+                            xe = C::from_u(ex);
                         }
                     }
                 }
             };
-            const bool careful = kb == 0 || (MODE == SEMIGLOBAL && s0 <= evhi && s0 + B > evlo);
+            // local mode keeps one copy of the step loop (the checked one): its code is the
+            // largest, and the second copy cost more in instruction fetch than it saved
+            const bool careful = MODE == LOCAL || kb == 0 || (MODE == SEMIGLOBAL && s0 <= evhi && s0 + B > evlo);
             if (careful) run(std::true_type{});
             else run(std::false_type{});
         }

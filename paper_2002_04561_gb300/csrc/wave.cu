@@ -20,6 +20,8 @@
 // three-input maximum (six instructions) or as max(diagonal, F) followed by an
 // add-max with E (seven, with a one-instruction chain through the rows);
 // launch_wave picks the form by the number of stripes per SM.
+#include <type_traits>
+
 #include "common.cuh"
 #include "engine.cuh"
 #include "wave.h"
@@ -42,10 +44,13 @@ __device__ __forceinline__ void st_release(int32_t *p, int32_t v) {
     asm volatile("st.release.gpu.global.s32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
 }
 
+// Rings of WRING columns plus one more block: the selectors and the top row keep
+// a copy of ring block 0 after the ring's end, and lane 31's bottom stores run
+// on past it, so a lane walks one block from one base address without wrapping.
 struct __align__(16) WaveSmem {
-    uint32_t sel[WRING];
-    int32_t top[2 * WRING];
-    int32_t bot[2 * WRING];
+    uint32_t sel[WRING + BLOCK];
+    int32_t top[2 * (WRING + BLOCK)];
+    int32_t bot[2 * (WRING + BLOCK)];
 };
 
 // Best-cell searches of a mode: over every cell, or over the last row and column.
@@ -212,8 +217,13 @@ __global__ void __launch_bounds__(256, (WR <= 8 && !best_all(MODE)) ? 4 : 2) wav
         auto put = [&](int blk, uint32_t fw, int32_t fsh, int2 ft) {
             const int c = blk * BLOCK + g;
             if (c < m) {
-                sm->sel[c & (WRING - 1)] = MAT ? fw * (uint32_t)WCH : C::selector((fw >> fsh) & 3u, 0);
+                const uint32_t sv = MAT ? fw * (uint32_t)WCH : C::selector((fw >> fsh) & 3u, 0);
+                sm->sel[c & (WRING - 1)] = sv;
                 reinterpret_cast<int2 *>(sm->top)[c & (WRING - 1)] = ft;
+                if ((blk & 3) == 0) {
+                    sm->sel[WRING + (c & (WRING - 1))] = sv;
+                    reinterpret_cast<int2 *>(sm->top)[WRING + (c & (WRING - 1))] = ft;
+                }
             }
         };
         auto fill = [&](int blk) {
@@ -225,10 +235,15 @@ __global__ void __launch_bounds__(256, (WR <= 8 && !best_all(MODE)) ? 4 : 2) wav
         };
         // drain in two halves too: the stores of a finished bottom block, and (after a
         // warp barrier) the release of the progress counter
+        // lane 31 stored column c at step c + 31, at (its block's base column - 31) + offset
+        auto bot_index = [&](int c) {
+            const int sw = (c + WG - 1) & ~(BLOCK - 1);
+            return ((sw - (WG - 1)) & (WRING - 1)) + (c + WG - 1 - sw);
+        };
         auto drain_stores = [&](int blk) {
             int c = blk * BLOCK + g;
             if (blk >= 0 && c < m) {
-                const int2 b2 = reinterpret_cast<const int2 *>(sm->bot)[c & (WRING - 1)];
+                const int2 b2 = reinterpret_cast<const int2 *>(sm->bot)[bot_index(c)];
                 const int32_t hv = b2.x, ev = b2.y;
                 if (!last) {
                     bout[c] = make_int2(hv, ev);
@@ -245,7 +260,7 @@ __global__ void __launch_bounds__(256, (WR <= 8 && !best_all(MODE)) ? 4 : 2) wav
         auto drain = [&](int blk) {
             int c = blk * BLOCK + g;
             if (blk >= 0 && c < m) {
-                const int2 b2 = reinterpret_cast<const int2 *>(sm->bot)[c & (WRING - 1)];
+                const int2 b2 = reinterpret_cast<const int2 *>(sm->bot)[bot_index(c)];
                 const int32_t hv = b2.x, ev = b2.y;
                 if (!last) {
                     bout[c] = make_int2(hv, ev);
@@ -266,21 +281,31 @@ __global__ void __launch_bounds__(256, (WR <= 8 && !best_all(MODE)) ? 4 : 2) wav
         fill(0);
         __syncwarp();
         int drained = 0;
-        T last_hoe = C::NEG, last_e = C::NEG, prev_up = diag0;
-        // one step: column s - g of this lane's rows
-        auto step = [&](const int s) {
+        // exported values: this lane's last row (Hoe, and E of the row below); lane 31,
+        // whose last row goes to the bottom ring, exports lane 0's border value for its
+        // next column instead (the row above the stripe, one column ahead)
+        T xh, xe, prev_up = diag0;
+        {
+            const int2 tv = reinterpret_cast<const int2 *>(sm->top)[0];
+            xh = tv.x;
+            xe = tv.y;
+        }
+        const int src = (g + WG - 1) & (WG - 1);  // lane g-1; lane 0 reads lane 31
+        // base addresses of the current block: this lane's selectors (column s - g at
+        // offset s - s0), lane 31's top loads and bottom stores
+        const uint32_t *selp = sm->sel;
+        uint32_t topa = 0, bota = 0;
+        // one step: column s - g of this lane's rows (j = s - s0). Checked steps (the first
+        // block, where lane g has no column before step g, and the blocks that reach the
+        // last column) skip columns outside the pair and look for the last column's cells.
+        auto step = [&](const int s, const int j, auto careful_tag) {
+            constexpr bool CAREFUL = decltype(careful_tag)::value;
             const int c = s - g;
-            T up_hoe = (T)__shfl_up_sync(0xffffffffu, (uint32_t)last_hoe, 1);
-            T up_e = (T)__shfl_up_sync(0xffffffffu, (uint32_t)last_e, 1);
-            if (g == 0) {
-                // the row above the stripe (row 0 for the first stripe); the ring index is
-                // masked, and invalid columns are not used
-                const int2 tv = reinterpret_cast<const int2 *>(sm->top)[c & (WRING - 1)];
-                up_hoe = tv.x;
-                up_e = tv.y;
-            }
-            if ((unsigned)c < (unsigned)m) {
-                const uint32_t sel = sm->sel[c & (WRING - 1)];
+            const T up_hoe = (T)__shfl_sync(0xffffffffu, (uint32_t)xh, src);
+            const T up_e = (T)__shfl_sync(0xffffffffu, (uint32_t)xe, src);
+            T stE = xe;  // E stored by lane 31: of the row below, or its own in the last stripe
+            if (!CAREFUL || (unsigned)c < (unsigned)m) {
+                const uint32_t sel = selp[j];
                 // this lane's sigma' bytes of the column letter (matrix path)
                 uint32_t wq[MAT ? WR / 4 : 1];
                 if constexpr (MAT) {
@@ -355,7 +380,7 @@ __global__ void __launch_bounds__(256, (WR <= 8 && !best_all(MODE)) ? 4 : 2) wav
                         }
                     }
                 }
-                if (EDGE && c == m - 1) {
+                if (EDGE && CAREFUL && c == m - 1) {
 #pragma unroll
                     for (int r = 0; r < WR; r++) {
                         const int32_t i = rb + r - pad;
@@ -365,13 +390,26 @@ __global__ void __launch_bounds__(256, (WR <= 8 && !best_all(MODE)) ? 4 : 2) wav
                         }
                     }
                 }
-                last_hoe = Hoe[WR - 1];
-                last_e = E;
-                if (g == WG - 1) {
-                    // border for the next stripe: (Hoe, E of the row below); the last
-                    // stripe keeps E of its own last row for the Hirschberg join
-                    reinterpret_cast<int2 *>(sm->bot)[c & (WRING - 1)] = make_int2(last_hoe, last ? Ein : E);
-                }
+                xh = Hoe[WR - 1];
+                xe = E;
+                // border for the next stripe: (Hoe, E of the row below); the last stripe
+                // keeps E of its own last row for the Hirschberg join
+                stE = last ? Ein : E;
+            }
+            {
+                // lane 31: its last row to the bottom ring, then lane 0's next border value
+                // in; predicated shared-memory accesses rather than a branch around them
+                uint32_t hx = (uint32_t)xh, ex = (uint32_t)xe;
+                asm volatile(
+                    "{ .reg .pred p;\n\t"
+                    "setp.eq.u32 p, %5, 31;\n\t"
+                    "@p st.shared.v2.u32 [%2], {%0, %4};\n\t"
+                    "@p ld.shared.v2.u32 {%0, %1}, [%3]; }"
+                    : "+r"(hx), "+r"(ex)
+                    : "r"(bota + 8u * (uint32_t)j), "r"(topa + 8u * (uint32_t)j), "r"((uint32_t)stE), "r"(g)
+                    : "memory");
+                xh = (T)hx;
+                xe = (T)ex;
             }
         };
         for (int s0 = 0; s0 < S && !failed; s0 += BLOCK) {
@@ -388,11 +426,23 @@ __global__ void __launch_bounds__(256, (WR <= 8 && !best_all(MODE)) ? 4 : 2) wav
                 drained = kb - 1;
             }
             const int s1 = min(S, s0 + BLOCK), sm_ = min(s1, s0 + BLOCK / 2);
-            for (int s = s0; s < sm_; s++) step(s);
+            selp = &sm->sel[(s0 - g) & (WRING - 1)];
+            topa = (uint32_t)__cvta_generic_to_shared(&sm->top[2 * ((s0 + 1) & (WRING - 1))]);
+            bota = (uint32_t)__cvta_generic_to_shared(&sm->bot[2 * ((s0 - (WG - 1)) & (WRING - 1))]);
+            const bool careful = kb == 0 || s0 + BLOCK >= m;
+            if (careful) {
+                for (int s = s0; s < sm_; s++) step(s, s - s0, std::true_type{});
+            } else {
+                for (int s = s0; s < sm_; s++) step(s, s - s0, std::false_type{});
+            }
             put(kb + 1, fw, fsh, ft);
             __syncwarp();
             if (released >= 0 && !last && g == 0) st_release(prog_mine, released + 1);
-            for (int s = sm_; s < s1; s++) step(s);
+            if (careful) {
+                for (int s = sm_; s < s1; s++) step(s, s - s0, std::true_type{});
+            } else {
+                for (int s = sm_; s < s1; s++) step(s, s - s0, std::false_type{});
+            }
         }
         __syncwarp();
         for (int b = drained; b <= (m - 1) / BLOCK; b++) drain(b);
