@@ -179,7 +179,7 @@ class ClockSampler:
 
 
 # sources that define the batched DP kernel: its DRAM counters stay valid while these are unchanged
-KERNEL_SOURCES = ("batch_kernel.cuh", "batch.h", "common.cuh", "engine.cuh")
+KERNEL_SOURCES = ("batch_kernel.cuh", "batch_score.cuh", "batch.h", "common.cuh", "engine.cuh")
 
 
 def kernel_source_hash() -> str:
@@ -304,11 +304,14 @@ def timed_events(fn, reps, stream):
     return a.elapsed_time(b) / reps
 
 
-def serving_workload(pkg, n_requests: int = 3000, load: float = 0.8):
+def serving_workload(pkg, n_requests: int = 6000, loads=(0.5, 0.7, 0.9)):
     """The serving mix (70 % 100-300 bp, 25 % 1-10 kbp, 5 % 50-200 kbp, global
     affine +2/-3/-5/-2) through the native request queue: capacity with every
-    request queued at once, then Poisson arrivals at `load` x capacity; latency
-    from submit to completion as the server measures it."""
+    request queued at once, then Poisson arrivals at each fraction of it;
+    latency from submit to completion as the server measures it. A load counts
+    as steady only where the achieved rate is at least 98 % of the offered one
+    (the queue did not grow); the reported p50/p99 are those of the highest
+    steady load."""
     import queue
     import threading
     sc = pkg.Scoring.make(2, -3, -5, -2)
@@ -345,16 +348,28 @@ def serving_workload(pkg, n_requests: int = 3000, load: float = 0.8):
     run(None)  # warm-up: builds the context's scratch
     wall, _, _, _ = run(None)
     capacity = n_requests / wall
-    rate = load * capacity
-    wall, lat, batches, longs = run(arr.times / rate)
-    res = {"requests": n_requests, "capacity_req_per_s": capacity, "capacity_GCUPS": cells / (n_requests / capacity) / 1e9,
-           "offered_req_per_s": rate, "achieved_req_per_s": n_requests / wall,
-           "p50_ms": float(np.percentile(lat, 50)), "p99_ms": float(np.percentile(lat, 99)),
-           "batches": int(batches), "wavefront_pairs": int(longs)}
-    for kind, name in enumerate(("short", "medium", "long")):
-        sel = arr.kind == kind
-        res[f"{name}_p50_ms"] = float(np.percentile(lat[sel], 50))
-        res[f"{name}_p99_ms"] = float(np.percentile(lat[sel], 99))
+    res = {"requests": n_requests, "capacity_req_per_s": capacity,
+           "capacity_GCUPS": cells / (n_requests / capacity) / 1e9, "loads": []}
+    for load in loads:
+        rate = load * capacity
+        wall, lat, batches, longs = run(arr.times / rate)
+        # achieved over the arrival window plus the drain of the last request
+        row = {"load": load, "offered_req_per_s": rate, "achieved_req_per_s": n_requests / wall,
+               "achieved_over_offered": (n_requests / wall) / rate,
+               "p50_ms": float(np.percentile(lat, 50)), "p99_ms": float(np.percentile(lat, 99)),
+               "batches": int(batches), "wavefront_pairs": int(longs)}
+        for kind, name in enumerate(("short", "medium", "long")):
+            sel = arr.kind == kind
+            row[f"{name}_p50_ms"] = float(np.percentile(lat[sel], 50))
+            row[f"{name}_p99_ms"] = float(np.percentile(lat[sel], 99))
+        res["loads"].append(row)
+    steady = [r for r in res["loads"] if r["achieved_over_offered"] >= 0.98]
+    if steady:
+        top = max(steady, key=lambda r: r["load"])
+        res.update({"steady_load": top["load"], "p50_ms": top["p50_ms"], "p99_ms": top["p99_ms"],
+                    "offered_req_per_s": top["offered_req_per_s"], "achieved_req_per_s": top["achieved_req_per_s"]})
+    else:
+        res["steady_load"] = None
     return res
 
 
@@ -472,7 +487,7 @@ def secondary_workloads(pkg, ctx, device):
         "full_dp_GCUPS": b.cells() / ms_full / 1e6, "train_s": train_s, "train_loss": loss,
         "cpu_oracle_full_dp": oracle_sample(b, (2, -3, -5, -2), 0)}
     # serving: Poisson arrivals through the native request queue
-    out["serving_mix_3000_global_affine"] = serving_workload(pkg)
+    out["serving_mix_6000_global_affine"] = serving_workload(pkg)
     return out
 
 

@@ -18,6 +18,8 @@
 //   down:  E(i+1, j) + U(i+1, j) and H(i, j) + Mmax + U(i+1, j+1),
 // the banded score S is the optimum whenever S >= X (S > X when a CIGAR must
 // also be unique). Otherwise the caller widens the band or runs the full DP.
+#include <type_traits>
+
 #include "band.h"
 #include "batch.h"
 #include "common.cuh"
@@ -191,10 +193,13 @@ __device__ __forceinline__ int32_t ubound(int32_t n, int32_t m, int32_t i, int32
     return mmax * mn + e * df;
 }
 
+// Rings of RING columns plus one more block (the step loop's layout of the
+// batched kernel: a copy of ring block 0 after the ring's end for the selectors
+// and the top row, room for lane 15's stores past the end in the bottom ring).
 struct __align__(16) BandSmem {
-    uint32_t sel[RING];
-    int32_t top[2 * RING];
-    int32_t bot[2 * RING];
+    uint32_t sel[RING + BLOCK];
+    int32_t top[2 * (RING + BLOCK)];
+    int32_t bot[2 * (RING + BLOCK)];
 };
 
 // One pair per 16-lane slot (32-bit lanes, global mode), chunks of GROUP * BR
@@ -280,7 +285,9 @@ __device__ __noinline__ void band_slot(const BandArgs &A, BandSmem *sm, int32_t 
                     int cr = blk * BLOCK + g + 16 * k;
                     if (cr < W) {
                         int c = a + cr;
-                        sm->sel[cr & (RING - 1)] = C::selector(code2(A.s2, s0 + c), 0);
+                        const uint32_t sv = C::selector(code2(A.s2, s0 + c), 0);
+                        sm->sel[cr & (RING - 1)] = sv;
+                        if ((blk & 3) == 0) sm->sel[RING + (cr & (RING - 1))] = sv;
                         int2 tv;
                         if (ch > 0) {
                             const bool in = c >= pa && c < pb;
@@ -290,8 +297,14 @@ __device__ __noinline__ void band_slot(const BandArgs &A, BandSmem *sm, int32_t 
                             tv.x = tv.y = o + (c + 1) * e + oe;
                         }
                         reinterpret_cast<int2 *>(sm->top)[cr & (RING - 1)] = tv;
+                        if ((blk & 3) == 0) reinterpret_cast<int2 *>(sm->top)[RING + (cr & (RING - 1))] = tv;
                     }
                 }
+            };
+            // lane 15 stored column cr at step cr + 15, at (its block's base - 15) + offset
+            auto bot_index = [&](int cr) {
+                const int sw = (cr + GROUP - 1) & ~(BLOCK - 1);
+                return ((sw - (GROUP - 1)) & (RING - 1)) + (cr + GROUP - 1 - sw);
             };
             auto drain = [&](int blk) {
 #pragma unroll
@@ -299,7 +312,7 @@ __device__ __noinline__ void band_slot(const BandArgs &A, BandSmem *sm, int32_t 
                     int cr = blk * BLOCK + g + 16 * k;
                     if (blk >= 0 && cr < W) {
                         int c = a + cr;
-                        const int2 b2 = reinterpret_cast<const int2 *>(sm->bot)[cr & (RING - 1)];
+                        const int2 b2 = reinterpret_cast<const int2 *>(sm->bot)[bot_index(cr)];
                         const int32_t hv = b2.x, ev = b2.y;
                         if (!last) {
                             scr[2 * c] = hv;
@@ -327,7 +340,21 @@ __device__ __noinline__ void band_slot(const BandArgs &A, BandSmem *sm, int32_t 
             __syncwarp();
             int drained = 0;
             // prev_up is diag0 until the first valid column
-            T last_hoe = C::NEG, last_e = C::NEG, prev_up = diag0;
+            // exported values: this lane's last row (Hoe, E of the row below); lane 15, whose
+            // last row goes to the bottom ring, exports lane 0's border value for its next
+            // column instead. prev_up is diag0 until the first valid column.
+            T xh, xe, prev_up = diag0;
+            {
+                const int2 tv = reinterpret_cast<const int2 *>(sm->top)[0];
+                xh = tv.x;
+                xe = tv.y;
+            }
+            const int lane = (int)(threadIdx.x & 31);
+            const int src = (lane & 16) | ((lane + GROUP - 1) & (GROUP - 1));  // lane g-1; lane 0 reads lane 15
+            // the warp's steps where a lane reaches the last computed column of its window
+            int wlo = W > 0 ? W - 1 : (1 << 30), whi = W - 1;
+            wlo = min(wlo, __shfl_xor_sync(0xffffffffu, wlo, 16));
+            whi = max(whi, __shfl_xor_sync(0xffffffffu, whi, 16)) + GROUP - 1;
             for (int s0b = 0; s0b < S; s0b += BLOCK) {
               __syncwarp();
               {
@@ -336,19 +363,21 @@ __device__ __noinline__ void band_slot(const BandArgs &A, BandSmem *sm, int32_t 
                 if (kb - 2 >= drained) { drain(kb - 2); drained = kb - 1; }
               }
               __syncwarp();
-              const int s1b = min(S, s0b + BLOCK);
-              for (int s = s0b; s < s1b; s++) {
-                const int cr = s - g;
-                T up_hoe = (T)__shfl_up_sync(0xffffffffu, (uint32_t)last_hoe, 1, GROUP);
-                T up_e = (T)__shfl_up_sync(0xffffffffu, (uint32_t)last_e, 1, GROUP);
-                if (g == 0) {
-                    // the row above the chunk (row 0 for the first); the ring index is masked
-                    const int2 tv = reinterpret_cast<const int2 *>(sm->top)[cr & (RING - 1)];
-                    up_hoe = tv.x;
-                    up_e = tv.y;
-                }
-                if ((unsigned)cr < (unsigned)W) {
-                    const uint32_t sel = sm->sel[cr & (RING - 1)];
+              const int nst = min(S, s0b + BLOCK) - s0b;
+              const uint32_t *selp = &sm->sel[(s0b - g) & (RING - 1)];
+              const uint32_t topa = (uint32_t)__cvta_generic_to_shared(&sm->top[2 * ((s0b + 1) & (RING - 1))]);
+              const uint32_t bota = (uint32_t)__cvta_generic_to_shared(&sm->bot[2 * ((s0b - (GROUP - 1)) & (RING - 1))]);
+              // checked steps: the ramp (no column before step g) and the window's right edge
+              // (the columns past it are left alone, the right exits are taken there); in
+              // between, columns past a narrower window only feed values nobody reads
+              auto run = [&](auto careful_tag) {
+                constexpr bool CAREFUL = decltype(careful_tag)::value;
+                for (int j = 0; j < nst; j++) {
+                  const int cr = s0b + j - g;
+                  const T up_hoe = (T)__shfl_sync(0xffffffffu, (uint32_t)xh, src);
+                  const T up_e = (T)__shfl_sync(0xffffffffu, (uint32_t)xe, src);
+                  if (!CAREFUL || (unsigned)cr < (unsigned)W) {
+                    const uint32_t sel = selp[j];
                     T Ad = C::addc(prev_up, (uint32_t)C::sigma(prof[0], prof[0], sel));
                     prev_up = up_hoe;
                     T E = up_e;
@@ -360,12 +389,10 @@ __device__ __noinline__ void band_slot(const BandArgs &A, BandSmem *sm, int32_t 
                         Hoe[r] = C::addc(Hn, oe_c);
                         E = C::addmax(E, e_raw, Hoe[r]);                       // Eq. 4, row i+1
                     }
-                    last_hoe = Hoe[BR - 1];
-                    last_e = E;
-                    if (g == GROUP - 1)
-                        reinterpret_cast<int2 *>(sm->bot)[cr & (RING - 1)] = make_int2(last_hoe, last_e);
+                    xh = Hoe[BR - 1];
+                    xe = E;
                     // right exits from DP column hi = b (the chunk's last computed column)
-                    if (cr == W - 1 && b < m) {
+                    if (CAREFUL && cr == W - 1 && b < m) {
 #pragma unroll
                         for (int r = 0; r < BR; r++) {
                             int64_t i = (int64_t)rb + r - pad;
@@ -384,8 +411,26 @@ __device__ __noinline__ void band_slot(const BandArgs &A, BandSmem *sm, int32_t 
                             }
                         }
                     }
+                  }
+                  {
+                    // lane 15: its last row to the bottom ring, then lane 0's next border value in
+                    uint32_t hx = (uint32_t)xh, ex = (uint32_t)xe;
+                    asm volatile(
+                        "{ .reg .pred p;\n\t"
+                        "setp.eq.u32 p, %4, 15;\n\t"
+                        "@p st.shared.v2.u32 [%2], {%0, %1};\n\t"
+                        "@p ld.shared.v2.u32 {%0, %1}, [%3]; }"
+                        : "+r"(hx), "+r"(ex)
+                        : "r"(bota + 8u * (uint32_t)j), "r"(topa + 8u * (uint32_t)j), "r"(g)
+                        : "memory");
+                    xh = (T)hx;
+                    xe = (T)ex;
+                  }
                 }
-              }
+              };
+              const bool careful = s0b == 0 || (s0b <= whi && s0b + BLOCK > wlo);
+              if (careful) run(std::true_type{});
+              else run(std::false_type{});
             }
             __syncwarp();
             for (int bk = drained; bk <= (Wmax - 1) / BLOCK; bk++) drain(bk);
