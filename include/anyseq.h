@@ -208,7 +208,10 @@ anyseq_status_t anyseq_band_train(anyseq_ctx *ctx, const uint8_t *q, const int64
  * range test (the full DP runs those two per 32-bit lane); "wave_cell"
  * (default 0) picks the wavefront's cell update in global passes: 0 by the
  * number of stripes side by side, 1 always the three-input maximum, 2 always
- * the two-step form (results are the same); "tb_walker" (default 0) picks the
+ * the two-step form (results are the same); "wave_rows" (default 0) sets the
+ * wavefront's rows per lane (4, 8 or 16; 0 chooses by the number of stripes,
+ * within what each mode has: local passes at most 8, semi-global 4 or 16,
+ * traceback passes 8 or 16; results are the same); "tb_walker" (default 0) picks the
  * batched traceback walk: 0 by batch size, 1 a warp per pair (staged windows),
  * 2 a thread per pair (results are the same). Unknown keys: ANYSEQ_ERR_ARG. */
 anyseq_status_t anyseq_set_option(anyseq_ctx *ctx, const char *key, int64_t value);

@@ -120,6 +120,12 @@ extern "C" anyseq_status_t anyseq_set_option(anyseq_ctx *ctx, const char *key, i
         ctx->tb_walker = (int32_t)value;
         return ANYSEQ_OK;
     }
+    if (!strcmp(key, "wave_rows")) {
+        if (value != 0 && value != 4 && value != 8 && value != 16)
+            return fail(ANYSEQ_ERR_ARG, "wave_rows must be 0, 4, 8 or 16");
+        ctx->wave_rows = (int32_t)value;
+        return ANYSEQ_OK;
+    }
     if (!strcmp(key, "wave_cell")) {
         if (value < 0 || value > 2) return fail(ANYSEQ_ERR_ARG, "wave_cell must be 0, 1 or 2");
         ctx->wave_cell = (int32_t)value;

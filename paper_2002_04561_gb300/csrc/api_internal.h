@@ -46,6 +46,7 @@ struct anyseq_ctx {
     bool tuned = false;
     double tune_gain = 1.0;
     int32_t tb_walker = 0;  // traceback walk: 0 by batch size, 1 a warp per pair, 2 a thread per pair
+    int32_t wave_rows = 0;  // wavefront rows per lane: 0 automatic, or 4, 8, 16 (within what each mode has)
     int32_t wave_cell = 0;  // wavefront cell of global passes: 0 by stripe count, 1 three-input max, 2 two-step  // default time / tuned time on the tuning sample
     std::vector<Buf> bufs;        // device scratch, grown on demand, reused across calls
     std::vector<Buf> pinned;      // pinned host staging

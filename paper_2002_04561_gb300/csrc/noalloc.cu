@@ -126,7 +126,7 @@ extern "C" anyseq_status_t anyseq_align_long_noalloc(const uint8_t *q, int64_t n
     ps.tb = sc->gap_open;
     int sms = 1;
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, cur);
-    const int wr = wave_rows_per_lane(n, sms, 1, GLOBAL);
+    const int wr = wave_rows_per_lane(n, sms, 1, GLOBAL, 0, true);  // the array is sized for 8-row stripes
     const int64_t stripes = (n + WAVE_LANES * wr - 1) / (WAVE_LANES * wr);
     noalloc_init_kernel<<<8, 256, 0, st>>>(pass, ps, ctl, stripes + 2, bad);
     cudaError_t e = cudaGetLastError();

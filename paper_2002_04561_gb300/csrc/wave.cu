@@ -74,7 +74,7 @@ __host__ __device__ constexpr bool best_edge(int mode) { return mode == SEMIGLOB
 // that plane in one vector load. sigma' of row r is then one byte permute, as
 // on the row-profile path.
 template <int WR, bool TB, int MODE, bool TRI, bool MAT>
-__global__ void __launch_bounds__(256, (WR <= 8 && !best_all(MODE)) ? 4 : 2) wave_kernel(WaveArgs A) {
+__global__ void __launch_bounds__(256, (WR <= 4 || (WR <= 8 && !best_all(MODE))) ? 4 : 2) wave_kernel(WaveArgs A) {
     constexpr int INIT = wave_init_mode(MODE);
     constexpr bool ALL = best_all(MODE), EDGE = best_edge(MODE);
     constexpr int WCH = WG * WR;  // rows per stripe
@@ -313,9 +313,11 @@ __global__ void __launch_bounds__(256, (WR <= 8 && !best_all(MODE)) ? 4 : 2) wav
                     if constexpr (WR == 16) {
                         const uint4 v = *reinterpret_cast<const uint4 *>(src);
                         wq[0] = v.x; wq[1] = v.y; wq[2] = v.z; wq[3] = v.w;
-                    } else {
+                    } else if constexpr (WR == 8) {
                         const uint2 v = *reinterpret_cast<const uint2 *>(src);
                         wq[0] = v.x; wq[1] = v.y;
+                    } else {
+                        wq[0] = *reinterpret_cast<const uint32_t *>(src);
                     }
                 }
                 auto sigma_r = [&](int r) -> uint32_t {
@@ -480,6 +482,9 @@ static size_t wave_dyn_smem(bool mat, int wr, int alphabet) {
     return mat ? (size_t)WAVE_SIG_BYTES + 8 * (size_t)alphabet * WG * wr : 0;
 }
 
+// Stripes per SM below which a launch takes 4-row stripes.
+constexpr int WAVE_THIN_STRIPES_PER_SM = 2;
+
 template <int WR, bool TB, int MODE, bool TRI = false, bool MAT = false>
 static int blocks_per_sm(size_t dyn = 0) {
     auto kern = wave_kernel<WR, TB, MODE, TRI, MAT>;
@@ -492,14 +497,31 @@ static int blocks_per_sm(size_t dyn = 0) {
     return nb < 1 ? 1 : nb;
 }
 
-int wave_rows_per_lane(int64_t total_rows, int num_sms, int64_t n_passes, int mode) {
-    if (best_all(mode)) return 8;    // the rows' maxima and columns take registers
-    if (best_edge(mode)) return 16;  // its 8-row variant would spill
-    // 8-row stripes double the stripes (and the pipeline's skew) and run at 64
-    // registers; measured on 100 kbp to 1 Mbp pairs, 16-row stripes win unless
-    // the problem is tiny (a few stripes, as a single pair of a thousand rows)
-    const int64_t stripes16 = total_rows / (WG * 16) + n_passes;  // upper bound of sum(ceil(n / 512))
-    return 16 * stripes16 <= (int64_t)num_sms * blocks_per_sm<16, false, GLOBAL>() * 8 ? 8 : 16;
+int wave_rows_per_lane(int64_t total_rows, int num_sms, int64_t n_passes, int mode, int forced, bool min8) {
+    // stripes of a launch at wr rows per lane (an upper bound of sum(ceil(n / (32 wr))))
+    auto stripes = [&](int wr) { return total_rows / (WG * wr) + n_passes; };
+    int wr;
+    if (forced == 4 || forced == 8 || forced == 16) {
+        wr = forced;
+        if (best_all(mode) && wr == 16) wr = 8;   // the rows' maxima and columns take registers
+        if (best_edge(mode) && wr == 8) wr = 16;  // its 8-row variant would spill
+    } else {
+        if (best_all(mode)) wr = 8;
+        else if (best_edge(mode)) wr = 16;
+        // 8-row stripes double the stripes (and the pipeline's skew) and run at 64
+        // registers; measured on 100 kbp to 1 Mbp pairs, 16-row stripes win unless
+        // the problem is tiny (a few stripes, as a single pair of a thousand rows)
+        else wr = 16 * stripes(16) <= (int64_t)num_sms * blocks_per_sm<16, false, GLOBAL>() * 8 ? 8 : 16;
+        // latency-bound pairs: with fewer than WAVE_THIN_STRIPES_PER_SM stripes per SM each
+        // warp's step is a chain nothing overlaps; 4-row stripes take a quarter of the
+        // cells per step and give four times the warps (100 kbp global: 41.8 -> 32.7 ms).
+        // Not in local passes, whose per-row maxima make a short step cost relatively
+        // more (35,000-residue local pair: 13.7 ms at 8 rows, 19.0 at 4)
+        if (!best_all(mode) && stripes(wr) < (int64_t)WAVE_THIN_STRIPES_PER_SM * num_sms) wr = 4;
+    }
+    // traceback words hold 8 rows; the allocation-free scratch is sized for 8-row stripes
+    if (min8 && wr < 8) wr = 8;
+    return wr;
 }
 
 template <int WR, bool TB, int MODE, bool TRI = false, bool MAT = false>
@@ -519,10 +541,22 @@ cudaError_t launch_wave(const WaveArgs &A, int num_sms, cudaStream_t st) {
     const bool tri = A.mode == GLOBAL && A.rows_per_lane >= 16 && !A.mat &&
                      (A.cell == 1 || (A.cell == 0 && (int64_t)A.n_stripes >= (int64_t)WAVE_TRI_STRIPES_PER_SM * num_sms));
     // the stripe table was built for A.rows_per_lane (from wave_rows_per_lane)
-    if (A.mode != GLOBAL && (tb || A.rows_per_lane != (best_all(A.mode) ? 8 : 16))) return cudaErrorInvalidValue;
+    const int wr = A.rows_per_lane;
+    if (tb && wr != 8 && wr != 16) return cudaErrorInvalidValue;
+    if (A.mode != GLOBAL && (tb || (wr != 4 && wr != (best_all(A.mode) ? 8 : 16)))) return cudaErrorInvalidValue;
+    if (A.mode == GLOBAL && wr != 4 && wr != 8 && wr != 16) return cudaErrorInvalidValue;
     if (A.mat) {
         // the matrix path: letters one byte each, sigma' from shared query profiles
         if (tb || A.alphabet < 1 || A.alphabet > 32 || !A.q8 || !A.s8 || !A.sig) return cudaErrorInvalidValue;
+        if (wr == 4) {
+            if (A.mode == LOCAL) launch_one<4, false, LOCAL, false, true>(A, num_sms, st);
+            else if (A.mode == ANCHORED_LOCAL) launch_one<4, false, ANCHORED_LOCAL, false, true>(A, num_sms, st);
+            else if (A.mode == SEMIGLOBAL) launch_one<4, false, SEMIGLOBAL, false, true>(A, num_sms, st);
+            else if (A.mode == ANCHORED_SEMIGLOBAL) launch_one<4, false, ANCHORED_SEMIGLOBAL, false, true>(A, num_sms, st);
+            else if (A.mode == GLOBAL) launch_one<4, false, GLOBAL, false, true>(A, num_sms, st);
+            else return cudaErrorInvalidValue;
+            return cudaGetLastError();
+        }
         if (A.mode == LOCAL) launch_one<8, false, LOCAL, false, true>(A, num_sms, st);
         else if (A.mode == ANCHORED_LOCAL) launch_one<8, false, ANCHORED_LOCAL, false, true>(A, num_sms, st);
         else if (A.mode == SEMIGLOBAL) launch_one<16, false, SEMIGLOBAL, false, true>(A, num_sms, st);
@@ -530,6 +564,15 @@ cudaError_t launch_wave(const WaveArgs &A, int num_sms, cudaStream_t st) {
         else if (A.mode != GLOBAL) return cudaErrorInvalidValue;
         else if (A.rows_per_lane == 8) launch_one<8, false, GLOBAL, false, true>(A, num_sms, st);
         else launch_one<16, false, GLOBAL, false, true>(A, num_sms, st);
+        return cudaGetLastError();
+    }
+    if (wr == 4) {
+        if (A.mode == LOCAL) launch_one<4, false, LOCAL>(A, num_sms, st);
+        else if (A.mode == ANCHORED_LOCAL) launch_one<4, false, ANCHORED_LOCAL>(A, num_sms, st);
+        else if (A.mode == SEMIGLOBAL) launch_one<4, false, SEMIGLOBAL>(A, num_sms, st);
+        else if (A.mode == ANCHORED_SEMIGLOBAL) launch_one<4, false, ANCHORED_SEMIGLOBAL>(A, num_sms, st);
+        else if (A.mode == GLOBAL) launch_one<4, false, GLOBAL>(A, num_sms, st);
+        else return cudaErrorInvalidValue;
         return cudaGetLastError();
     }
     if (A.mode == LOCAL) {

@@ -33,7 +33,7 @@ struct WaveArgs {
     int32_t *err;                 // zeroed; 1 after a wait gave up
     int32_t *last_H, *last_E;     // optional outputs
     int64_t spin_limit;           // iterations of one wait
-    int32_t rows_per_lane;        // 8 or 16 (stripes of 32 lanes x rows_per_lane rows)
+    int32_t rows_per_lane;        // 4, 8 or 16 (stripes of 32 lanes x rows_per_lane rows; traceback 8 or 16)
     uint32_t *dirs;               // optional: traceback direction words (global mode)
     int32_t mode;                 // GLOBAL, LOCAL, SEMIGLOBAL or an anchored mode (every pass)
     uint64_t *best;               // local / semi-global: per pass the best cell's key (initialised)
@@ -65,7 +65,12 @@ __host__ __device__ constexpr int32_t wave_init_mode(int32_t mode) {
 // each), otherwise 16. total_rows = sum of the passes' row counts.
 // (Local modes: always 8; semi-global modes: always 16.) The stripe table of a launch
 // must be built with this value, and WaveArgs.rows_per_lane set to it.
-int wave_rows_per_lane(int64_t total_rows, int num_sms, int64_t n_passes, int mode);
+// Rows per lane of a launch over total_rows rows in n_passes passes: 16 or 8
+// by the stripe count (8 for local passes, 16 for semi-global ones), 4 when the
+// stripes would leave the SMs latency-bound. forced (4, 8 or 16; 0: automatic)
+// overrides the choice within what each mode has; min8 keeps at least 8 (the
+// traceback's direction words, the allocation-free scratch).
+int wave_rows_per_lane(int64_t total_rows, int num_sms, int64_t n_passes, int mode, int forced = 0, bool min8 = false);
 cudaError_t launch_wave(const WaveArgs &A, int num_sms, cudaStream_t st);
 constexpr int WAVE_LANES = 32;    // lanes per stripe
 constexpr int WAVE_SIG_BYTES = 1024;  // shared copy of the sigma' table (alphabets up to 32)

@@ -301,6 +301,34 @@ def test_long_protein_pairs_with_matrix(pkg, ctx, mode, base):
         ctx.set_option("hirschberg_base_cells", 1 << 16)
 
 
+@pytest.mark.parametrize("rows", [4, 8, 16])
+@pytest.mark.parametrize("mode", [0, 1, 2])
+def test_wavefront_rows_per_lane_match_oracle(pkg, ctx, rows, mode):
+    """Every rows-per-lane count of the wavefront's passes (4-row stripes are
+    the automatic choice for pairs too small to fill the GPU with taller ones;
+    each mode takes the counts it has) gives the oracle's score, cells and
+    linear-space CIGAR, on DNA (2-bit letters) and protein (matrix) pairs that
+    span one to fifteen stripes with ragged last stripes."""
+    mat = synth.protein_matrix(3)
+    cases = [(related(n, extra, seed=4100 + 10 * mode + k), C4, None)
+             for k, (n, extra) in enumerate([(1, 0), (129, 5), (700, -9), (1800, 13)])]
+    cases += [(protein_pair(n, extra, 4200 + 10 * mode + k), PROTEIN, mat)
+              for k, (n, extra) in enumerate([(300, 4), (1500, -7)])]
+    ctx.set_option("wave_rows", rows)
+    try:
+        for (q, s), args, m in cases:
+            cig = np.zeros(len(q) + len(s) + 4, np.uint32)
+            out, used = ctx.align_long(q, s, pkg.Scoring.make(*args, matrix=m), mode=mode,
+                                       want=pkg.WANT_SCORE | pkg.WANT_CIGAR, cigar=cig)
+            r = out[0]
+            got = (int(r["score"]), (int(r["beg_q"]), int(r["beg_s"])), (int(r["end_q"]), int(r["end_s"])))
+            S, beg, end, want = oracle.long_alignment(q, s, oracle.Scoring(*args, matrix=m), mode)
+            assert got == (S, beg, end), (rows, mode, len(q), got, (S, beg, end))
+            assert np.array_equal(cig[:used], want), (rows, mode, len(q))
+    finally:
+        ctx.set_option("wave_rows", 0)
+
+
 @pytest.mark.parametrize("mode", [0, 1, 2])
 def test_matrix_path_equals_row_profiles_on_dna(pkg, ctx, mode):
     """DNA pairs forced through the matrix path (byte letters, shared query
