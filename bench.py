@@ -304,14 +304,26 @@ def timed_events(fn, reps, stream):
     return a.elapsed_time(b) / reps
 
 
+def serving_window_rates(sub, lat_ms):
+    """Offered and achieved request rates over the middle 80 % of the requests:
+    arrivals by submit time (s), completions (submit + latency) in completion
+    order. A server that keeps up completes them over the same span as they
+    arrive; one that falls behind spreads them over a longer one. The ends are
+    left out (the start's empty queue, the last batch's drain)."""
+    a = np.sort(np.asarray(sub, dtype=np.float64))
+    c = np.sort(np.asarray(sub, dtype=np.float64) + np.asarray(lat_ms, dtype=np.float64) * 1e-3)
+    lo, hi = int(0.1 * len(a)), int(0.9 * len(a)) - 1
+    return (hi - lo) / (a[hi] - a[lo]), (hi - lo) / (c[hi] - c[lo])
+
+
 def serving_workload(pkg, n_requests: int = 6000, loads=(0.5, 0.7, 0.9)):
     """The serving mix (70 % 100-300 bp, 25 % 1-10 kbp, 5 % 50-200 kbp, global
     affine +2/-3/-5/-2) through the native request queue: capacity with every
     request queued at once, then Poisson arrivals at each fraction of it;
     latency from submit to completion as the server measures it. A load counts
     as steady only where the achieved rate is at least 98 % of the offered one
-    (the queue did not grow); the reported p50/p99 are those of the highest
-    steady load."""
+    over the middle 80 % of the requests (the queue did not grow); the reported
+    p50/p99 are those of the highest steady load."""
     import queue
     import threading
     sc = pkg.Scoring.make(2, -3, -5, -2)
@@ -324,6 +336,8 @@ def serving_workload(pkg, n_requests: int = 6000, loads=(0.5, 0.7, 0.9)):
         try:
             tq = queue.Queue()
 
+            sub = np.zeros(n_requests)
+
             def submitter():
                 t0 = time.perf_counter()
                 for k in range(n_requests):
@@ -331,6 +345,7 @@ def serving_workload(pkg, n_requests: int = 6000, loads=(0.5, 0.7, 0.9)):
                         delay = t0 + times[k] - time.perf_counter()
                         if delay > 0:
                             time.sleep(delay)
+                    sub[k] = time.perf_counter()
                     tq.put(srv.submit(*pairs[k]))
 
             start = time.perf_counter()
@@ -341,21 +356,23 @@ def serving_workload(pkg, n_requests: int = 6000, loads=(0.5, 0.7, 0.9)):
                 _, lat[k] = srv.wait(tq.get())
             th.join()
             wall = time.perf_counter() - start
-            return wall, lat * 1e-6, srv.stat("batches"), srv.stat("long_pairs")
+            return wall, lat * 1e-6, srv.stat("batches"), srv.stat("long_pairs"), sub
+
         finally:
             srv.close()
 
     run(None)  # warm-up: builds the context's scratch
-    wall, _, _, _ = run(None)
+    wall, _, _, _, _ = run(None)
     capacity = n_requests / wall
     res = {"requests": n_requests, "capacity_req_per_s": capacity,
            "capacity_GCUPS": cells / (n_requests / capacity) / 1e9, "loads": []}
     for load in loads:
         rate = load * capacity
-        wall, lat, batches, longs = run(arr.times / rate)
-        # achieved over the arrival window plus the drain of the last request
-        row = {"load": load, "offered_req_per_s": rate, "achieved_req_per_s": n_requests / wall,
-               "achieved_over_offered": (n_requests / wall) / rate,
+        wall, lat, batches, longs, sub = run(arr.times / rate)
+        offered_w, achieved_w = serving_window_rates(sub, lat)
+        row = {"load": load, "offered_req_per_s": offered_w, "achieved_req_per_s": achieved_w,
+               "achieved_over_offered": achieved_w / offered_w,
+               "requests_over_wall_req_per_s": n_requests / wall,
                "p50_ms": float(np.percentile(lat, 50)), "p99_ms": float(np.percentile(lat, 99)),
                "batches": int(batches), "wavefront_pairs": int(longs)}
         for kind, name in enumerate(("short", "medium", "long")):
@@ -465,10 +482,10 @@ def secondary_workloads(pkg, ctx, device):
                                                                        (2, -3, -5, -2), 0)}
     del qd, sd
     # learned band vs full DP on 65,536 pairs of 1-10 kbp (scores must be equal)
-    train = synth.band_pairs(n_pairs=2048, seed=105)
+    train = synth.band_pairs(n_pairs=16384, seed=105)
     sc = pkg.Scoring.make(2, -3, -5, -2)
     t0 = time.perf_counter()
-    loss = ctx.band_train(train.q, train.q_off, train.s, train.s_off, sc, epochs=40, lr=1e-3)
+    loss = ctx.band_train(train.q, train.q_off, train.s, train.s_off, sc, epochs=60, lr=1e-3)
     train_s = time.perf_counter() - t0
     b = synth.band_pairs()
     args = (dev(b.q), dev(b.q_off), dev(b.s), dev(b.s_off))
@@ -479,11 +496,32 @@ def secondary_workloads(pkg, ctx, device):
                            stream)
     fr = full.cpu().numpy().view(pkg.RESULT_DTYPE)
     br = band.cpu().numpy().view(pkg.RESULT_DTYPE)
+    accepted = int(((br["flags"] & pkg.FLAG_BAND_ACCEPTED) != 0).sum())
+    fallback = int(((br["flags"] & pkg.FLAG_FULL_FALLBACK) != 0).sum())
+    # the same route without the network: constant outputs (centre 0, one half-width
+    # relative to the longer sequence)
+    learned = ctx.band_model_get()
+    const = {}
+    ctx.set_option("band_margin_pct", 100)  # the fixed width as it is
+    ctx.set_option("band_floor_pct", 0)
+    for w in (0.1, 0.25, 0.4):
+        p = np.zeros_like(learned)
+        p[-1] = np.log(w)
+        ctx.band_model_set(p)
+        ms_c = timed_events(lambda: ctx.align_batch(*args, sc, pkg.GLOBAL, want=1 | pkg.BAND_LEARNED, out=band), 2,
+                            stream)
+        const[str(w)] = {"ms": ms_c, "scores_equal": bool(np.array_equal(
+            fr["score"], band.cpu().numpy().view(pkg.RESULT_DTYPE)["score"]))}
+    ctx.band_model_set(learned)
+    ctx.set_option("band_margin_pct", 65)  # the shipped defaults again
+    ctx.set_option("band_floor_pct", 20)
+    best_const = min(const.values(), key=lambda v: v["ms"])["ms"]
     out["band_65536_1_10kbp_global_affine"] = {
         "pairs_per_s_full_dp": b.n_pairs / ms_full * 1e3, "pairs_per_s_learned_band": b.n_pairs / ms_band * 1e3,
         "speedup": ms_full / ms_band, "scores_equal": bool(np.array_equal(fr["score"], br["score"])),
-        "band_accepted": int(((br["flags"] & pkg.FLAG_BAND_ACCEPTED) != 0).sum()),
-        "full_dp_fallback": int(((br["flags"] & pkg.FLAG_FULL_FALLBACK) != 0).sum()),
+        "band_accepted": accepted, "full_dp_fallback": fallback, "certified_share": accepted / b.n_pairs,
+        "constant_band_ms": const, "speedup_over_best_constant_band": best_const / ms_band,
+        "speedup_over_prior_constant_band": const["0.25"]["ms"] / ms_band,
         "full_dp_GCUPS": b.cells() / ms_full / 1e6, "train_s": train_s, "train_loss": loss,
         "cpu_oracle_full_dp": oracle_sample(b, (2, -3, -5, -2), 0)}
     # serving: Poisson arrivals through the native request queue

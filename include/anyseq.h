@@ -181,14 +181,16 @@ anyseq_status_t anyseq_band_model_get(anyseq_ctx *ctx, float *params, int64_t co
 anyseq_status_t anyseq_band_model_set(anyseq_ctx *ctx, const float *params, int64_t count);
 anyseq_status_t anyseq_band_model_save(anyseq_ctx *ctx, const char *path);
 anyseq_status_t anyseq_band_model_load(anyseq_ctx *ctx, const char *path);
-/* Network outputs y (B x 2: band centre, log half-width) for features x (B x 64). */
+/* Network outputs y (B x 2: band centre in columns, log of the half-width relative
+ * to the longer sequence of the pair) for features x (B x 64). */
 anyseq_status_t anyseq_band_forward(anyseq_ctx *ctx, const float *x, int64_t B, float *y, void *cuda_stream);
 /* Mean loss and its gradient (ANYSEQ_BAND_PARAMS floats) for targets (B x 2). */
 anyseq_status_t anyseq_band_gradient(anyseq_ctx *ctx, const float *x, const float *targets, int64_t B,
                                      float *grad, float *loss, void *cuda_stream);
 /* Train the network on the GPU from example pairs: targets are the centre of
- * the optimal path (full DP traceback) and the smallest doubling width whose
- * band passes the certificate. epochs over the pairs in batches of 1024 with
+ * the optimal path (full DP traceback) and the log of the smallest doubling
+ * width whose band passes the certificate, divided by the longer sequence's
+ * length. epochs over the pairs in batches of 1024 with
  * Adam at learning rate lr; the final mean loss goes to *loss (may be NULL). */
 anyseq_status_t anyseq_band_train(anyseq_ctx *ctx, const uint8_t *q, const int64_t *q_off, const uint8_t *s,
                                   const int64_t *s_off, int64_t n_pairs, const anyseq_scoring_t *sc, int32_t epochs,
@@ -205,13 +207,25 @@ anyseq_status_t anyseq_band_train(anyseq_ctx *ctx, const uint8_t *q, const int64
  * band that fails its certificate before the full DP; "band_area_pct" (default
  * 60) sends a pair whose band would exceed that share of its matrix to the full
  * DP, "band_area16_pct" (default 15) the same for pairs that pass the int16
- * range test (the full DP runs those two per 32-bit lane); "wave_cell"
+ * range test (the full DP runs those two per 32-bit lane); "band_margin_pct"
+ * (default 65) multiplies the network's half-width by that percentage before
+ * the band is planned (a width just below the certifying one fails and pays
+ * for the full DP too); "band_floor_pct" (default 20) makes every planned
+ * half-width at least that share of the pair's longer sequence (the network
+ * then widens bands and picks the pairs that go straight to the full DP);
+ * "wave_cell"
  * (default 0) picks the wavefront's cell update in global passes: 0 by the
  * number of stripes side by side, 1 always the three-input maximum, 2 always
- * the two-step form (results are the same); "wave_rows" (default 0) sets the
+ * the two-step form (results are the same); "wave_split" (default 0) runs
+ * global three-input-maximum passes with split steps (each lane's upper 8
+ * rows one column ahead of its lower 8: two dependency chains per step); 2
+ * turns that off (results are the same); "wave_rows" (default 0) sets the
  * wavefront's rows per lane (4, 8 or 16; 0 chooses by the number of stripes,
  * within what each mode has: local passes at most 8, semi-global 4 or 16,
- * traceback passes 8 or 16; results are the same); "tb_walker" (default 0) picks the
+ * traceback passes 8 or 16; results are the same); "wave_ctas_per_sm"
+ * (default 0: as many as fit) caps the wavefront's CTAs per SM, leaving room
+ * for other kernels beside a long pair (results are the same); "tb_walker"
+ * (default 0) picks the
  * batched traceback walk: 0 by batch size, 1 a warp per pair (staged windows),
  * 2 a thread per pair (results are the same). Unknown keys: ANYSEQ_ERR_ARG. */
 anyseq_status_t anyseq_set_option(anyseq_ctx *ctx, const char *key, int64_t value);

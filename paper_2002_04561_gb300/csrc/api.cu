@@ -110,6 +110,16 @@ extern "C" anyseq_status_t anyseq_set_option(anyseq_ctx *ctx, const char *key, i
         ctx->band_area_pct = (int32_t)value;
         return ANYSEQ_OK;
     }
+    if (!strcmp(key, "band_margin_pct")) {
+        if (value < 50 || value > 1000) return fail(ANYSEQ_ERR_ARG, "band_margin_pct must be in 50..1000");
+        ctx->band_margin_pct = (int32_t)value;
+        return ANYSEQ_OK;
+    }
+    if (!strcmp(key, "band_floor_pct")) {
+        if (value < 0 || value > 100) return fail(ANYSEQ_ERR_ARG, "band_floor_pct must be in 0..100");
+        ctx->band_floor_pct = (int32_t)value;
+        return ANYSEQ_OK;
+    }
     if (!strcmp(key, "band_area16_pct")) {
         if (value < 1 || value > 100) return fail(ANYSEQ_ERR_ARG, "band_area16_pct must be in 1..100");
         ctx->band_area16_pct = (int32_t)value;
@@ -118,6 +128,16 @@ extern "C" anyseq_status_t anyseq_set_option(anyseq_ctx *ctx, const char *key, i
     if (!strcmp(key, "tb_walker")) {
         if (value < 0 || value > 2) return fail(ANYSEQ_ERR_ARG, "tb_walker must be 0, 1 or 2");
         ctx->tb_walker = (int32_t)value;
+        return ANYSEQ_OK;
+    }
+    if (!strcmp(key, "wave_split")) {
+        if (value < 0 || value > 2) return fail(ANYSEQ_ERR_ARG, "wave_split must be 0, 1 or 2");
+        ctx->wave_split = (int32_t)value;
+        return ANYSEQ_OK;
+    }
+    if (!strcmp(key, "wave_ctas_per_sm")) {
+        if (value < 0 || value > 8) return fail(ANYSEQ_ERR_ARG, "wave_ctas_per_sm must be in 0..8");
+        ctx->wave_ctas_per_sm = (int32_t)value;
         return ANYSEQ_OK;
     }
     if (!strcmp(key, "wave_rows")) {

@@ -31,6 +31,8 @@ struct anyseq_ctx {
     int32_t band_max_doublings = 0;  // doublings after the predicted width before the full DP
     int32_t band_area_pct = 60;      // a band above this share of the matrix goes to the full DP
     int32_t band_area16_pct = 15;    // the same for pairs the full DP runs in int16x2 lanes
+    int32_t band_margin_pct = 65;    // the network's half-width times this / 100 is the band used
+    int32_t band_floor_pct = 20;     // ... but at least this share (%) of the longer sequence
     int profile = 0;              // time the DP kernels with events
     cudaEvent_t ev[4] = {nullptr, nullptr, nullptr, nullptr};
     // statistics of the last call
@@ -46,6 +48,8 @@ struct anyseq_ctx {
     bool tuned = false;
     double tune_gain = 1.0;
     int32_t tb_walker = 0;  // traceback walk: 0 by batch size, 1 a warp per pair, 2 a thread per pair
+    int32_t wave_split = 0;  // global three-input-maximum wavefront: 0 or 1 split steps, 2 plain steps
+    int32_t wave_ctas_per_sm = 0;  // wavefront CTAs per SM: 0 as many as fit (the serving long lane uses 1)
     int32_t wave_rows = 0;  // wavefront rows per lane: 0 automatic, or 4, 8, 16 (within what each mode has)
     int32_t wave_cell = 0;  // wavefront cell of global passes: 0 by stripe count, 1 three-input max, 2 two-step  // default time / tuned time on the tuning sample
     std::vector<Buf> bufs;        // device scratch, grown on demand, reused across calls

@@ -82,8 +82,8 @@ static void init_params(std::vector<float> &w, uint64_t seed) {
         for (int64_t k = 0; k < (int64_t)sizes[l] * sizes[l + 1]; k++) w[off + k] = (float)((2.0 * next() - 1.0) * lim);
         off += (int64_t)sizes[l] * sizes[l + 1] + sizes[l + 1];  // biases stay 0
     }
-    // output bias: centre 0, half-width e^4
-    w[NP - 1] = 4.0f;
+    // output bias: centre 0, half-width a quarter of the longer sequence
+    w[NP - 1] = -1.386294f;
 }
 
 static anyseq_status_t set_params(anyseq_ctx *ctx, const float *h, cudaStream_t st) {
@@ -107,6 +107,8 @@ static anyseq_status_t set_params(anyseq_ctx *ctx, const float *h, cudaStream_t 
 struct BandCaps {
     double area32, area16;
     int32_t smax, smin, o, e;
+    float margin;  // the network's half-width is multiplied by this before use
+    float floor;   // and is at least this share of the longer sequence
 };
 __device__ __forceinline__ double band_cap(const BandCaps &K, int64_t n, int64_t m) {
     return fits_int16(n, m, K.smax, K.smin, K.o, K.e, GLOBAL) ? K.area16 : K.area32;
@@ -120,8 +122,15 @@ __global__ void band_plan_kernel(const float *y, const int64_t *q_off, const int
         const int64_t n = q_off[p + 1] - q_off[p], m = s_off[p + 1] - s_off[p];
         float c = y[2 * p], lw = y[2 * p + 1];
         c = fminf(fmaxf(c, -1e6f), 1e6f);
-        lw = fminf(fmaxf(lw, 0.0f), 20.0f);
-        int32_t w = (int32_t)ceilf(expf(lw));
+        // the network gives the half-width relative to the longer sequence (the
+        // certificate's margin grows with the length times the divergence, and the
+        // features see the divergence, not the length)
+        lw = fminf(fmaxf(lw, -16.0f), 1.0f);
+        const float L = (float)(n > m ? n : m);
+        // the target is the narrowest certifying width of a doubling series, so a width
+        // just below it fails the certificate and pays for the full DP too: a margin
+        const float wf = fminf(fmaxf(expf(lw) * caps.margin, caps.floor) * L, 1.0e9f);
+        int32_t w = (int32_t)ceilf(wf);
         w = w < MIN_W ? MIN_W : w;
         // the path starts on the line: a shift beyond the top half-width cannot hold it
         c = fminf(fmaxf(c, -(float)w), (float)w);
@@ -173,12 +182,14 @@ __global__ void mark_full_kernel(const uint8_t *full, int64_t n_pairs, uint32_t 
 }
 
 // training targets: centre of the path and log of the certified half-width
+// relative to the longer sequence
 __global__ void band_targets_kernel(const int32_t *dmin, const int32_t *dmax, const int32_t *wcert, int64_t n,
-                                    int32_t *centre, float *target) {
+                                    const int64_t *q_off, const int64_t *s_off, float *target) {
     for (int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; p < n; p += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t qn = q_off[p + 1] - q_off[p], sm = s_off[p + 1] - s_off[p];
+        const float L = (float)(qn > sm ? qn : sm);
         target[2 * p] = 0.5f * (float)(dmin[p] + dmax[p]);
-        target[2 * p + 1] = logf((float)wcert[p]);
-        (void)centre;
+        target[2 * p + 1] = logf((float)wcert[p] / (L > 1.0f ? L : 1.0f));
     }
 }
 
@@ -297,6 +308,8 @@ anyseq_status_t anyseq::band_scores(anyseq_ctx *ctx, const BatchInput &in, const
     BandCaps caps;
     caps.area32 = ctx->band_area_pct / 100.0;
     caps.area16 = ctx->band_area16_pct / 100.0;
+    caps.margin = (float)ctx->band_margin_pct / 100.0f;
+    caps.floor = (float)ctx->band_floor_pct / 100.0f;
     caps.smax = -(1 << 30);
     caps.smin = 1 << 30;
     for (int a = 0; a < sc->alphabet; a++)
@@ -542,7 +555,7 @@ extern "C" anyseq_status_t anyseq_band_train(anyseq_ctx *ctx, const uint8_t *q, 
     // 4. features and targets (centre of the path, log of the certified width)
     BCUDA(cudaMemcpyAsync(width, wcert.data(), n * sizeof(int32_t), cudaMemcpyHostToDevice, st));
     BCUDA(launch_kmer_hist(q2, s2, in.q_off, in.s_off, nullptr, n, feat, st));
-    band_targets_kernel<<<grid_of(n), 256, 0, st>>>(dmin, dmax, width, n, centre, target);
+    band_targets_kernel<<<grid_of(n), 256, 0, st>>>(dmin, dmax, width, n, in.q_off, in.s_off, target);
     BCUDA(cudaGetLastError());
     // 5. Adam over mini-batches
     if (!ctx->mlp_ready) {

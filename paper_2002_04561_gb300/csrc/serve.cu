@@ -1,15 +1,17 @@
 // Serving runtime: a request queue in front of the alignment paths (not in the
 // paper; its GPU mapping aligns one pair or one batch per call).
 //
-// Callers submit single pairs from any thread. One worker thread owns a
-// context and a CUDA stream and drains the queue in micro-batches: it waits at
-// most max_wait_us after the oldest queued request (or until max_batch_pairs
-// are queued), then aligns every small pair of the batch with one
-// anyseq_align_batch call (inter-sequence parallelism) and every pair of at
-// least long_cells cells with the wavefront of anyseq_align_long (intra-sequence
-// parallelism), all of them in one launch. Admission: the
-// letters of queued and running requests may not exceed mem_budget_bytes; a
-// submit that would exceed it is refused with ANYSEQ_ERR_BUDGET.
+// Callers submit single pairs from any thread. Two service lanes, each a
+// worker thread with its own context and CUDA stream, drain two queues in
+// micro-batches: a lane waits at most max_wait_us after its oldest queued
+// request (or until max_batch_pairs are queued). The short lane aligns its
+// batch with one anyseq_align_batch call (inter-sequence parallelism); the long
+// lane takes the pairs of at least long_cells cells and runs them side by side
+// in one wavefront launch (intra-sequence parallelism) with one CTA per SM, so
+// that the short lane's kernels still find room on every SM: short requests do
+// not queue behind a long pair. Admission: the letters of queued and running
+// requests may not exceed mem_budget_bytes; a submit that would exceed it is
+// refused with ANYSEQ_ERR_BUDGET.
 #include <chrono>
 #include <condition_variable>
 #include <cstring>
@@ -44,16 +46,22 @@ struct Request {
 
 }  // namespace
 
+// One service lane: a worker thread, its context, stream and queue.
+struct ServeLane {
+    anyseq_ctx *ctx = nullptr;
+    cudaStream_t stream = nullptr;
+    std::thread worker;
+    std::condition_variable cv_work;
+    std::deque<Request *> queue;
+};
+
 struct anyseq_server {
     anyseq_server_config_t cfg{};
     std::vector<int8_t> matrix;  // copy of the scoring matrix
     anyseq_scoring_t sc{};
-    anyseq_ctx *ctx = nullptr;
-    cudaStream_t stream = nullptr;
-    std::thread worker;
+    ServeLane lane[2];           // 0: short pairs (batched kernel), 1: long pairs (wavefront)
     std::mutex mu;
-    std::condition_variable cv_work, cv_done;
-    std::deque<Request *> queue;
+    std::condition_variable cv_done;
     std::unordered_map<uint64_t, Request *> live;
     uint64_t next_ticket = 1;
     size_t held_bytes = 0;  // letters of queued and running requests
@@ -66,71 +74,15 @@ struct anyseq_server {
 
 namespace {
 
-void run_batch(anyseq_server *S, std::vector<Request *> &reqs) {
-    std::vector<Request *> small, big;
-    for (Request *r : reqs) {
-        const double cells = (double)r->q.size() * (double)r->s.size();
-        const bool is_long = cells >= (double)S->cfg.long_cells && !r->q.empty() && !r->s.empty() &&
-                             S->sc.alphabet <= 4 && r->q.size() < (1u << 21) && r->s.size() < (1u << 21) &&
-                             anyseq::long_range_ok(&S->sc, (int64_t)r->q.size(), (int64_t)r->s.size());
-        (is_long ? big : small).push_back(r);
-    }
-    if (!small.empty()) {
-        std::vector<int64_t> qo(small.size() + 1, 0), so(small.size() + 1, 0);
-        for (size_t k = 0; k < small.size(); k++) {
-            qo[k + 1] = qo[k] + (int64_t)small[k]->q.size();
-            so[k + 1] = so[k] + (int64_t)small[k]->s.size();
-        }
-        std::vector<uint8_t> q((size_t)qo.back() + 1), s((size_t)so.back() + 1);
-        for (size_t k = 0; k < small.size(); k++) {
-            if (!small[k]->q.empty()) memcpy(q.data() + qo[k], small[k]->q.data(), small[k]->q.size());
-            if (!small[k]->s.empty()) memcpy(s.data() + so[k], small[k]->s.data(), small[k]->s.size());
-        }
-        std::vector<anyseq_result_t> out(small.size());
-        uint64_t used = 0;
-        const anyseq_status_t st =
-            anyseq_align_batch(S->ctx, q.data(), qo.data(), s.data(), so.data(), (int64_t)small.size(), &S->sc,
-                               S->cfg.mode, ANYSEQ_WANT_SCORE | ANYSEQ_WANT_END, out.data(), nullptr, 0, &used,
-                               S->stream);
-        const int64_t t = now_ns();
-        for (size_t k = 0; k < small.size(); k++) {
-            small[k]->res = out[k];
-            small[k]->status = st;
-            if (st != ANYSEQ_OK) small[k]->error = anyseq_last_error();
-            small[k]->t_done = t;
-        }
-    }
-    if (!big.empty()) {
-        // every long pair of the batch in one wavefront launch
-        std::vector<int64_t> qo(big.size() + 1, 0), so(big.size() + 1, 0);
-        for (size_t k = 0; k < big.size(); k++) {
-            qo[k + 1] = qo[k] + (int64_t)big[k]->q.size();
-            so[k + 1] = so[k] + (int64_t)big[k]->s.size();
-        }
-        std::vector<uint8_t> q((size_t)qo.back()), s((size_t)so.back());
-        for (size_t k = 0; k < big.size(); k++) {
-            memcpy(q.data() + qo[k], big[k]->q.data(), big[k]->q.size());
-            memcpy(s.data() + so[k], big[k]->s.data(), big[k]->s.size());
-        }
-        std::vector<int32_t> scores(big.size(), 0), eq(big.size(), 0), es(big.size(), 0);
-        const anyseq_status_t st = anyseq::long_scores(S->ctx, q.data(), qo.data(), s.data(), so.data(),
-                                                       (int64_t)big.size(), &S->sc, scores.data(), S->stream,
-                                                       S->cfg.mode, eq.data(), es.data());
-        const std::string msg = st != ANYSEQ_OK ? anyseq_last_error() : "";
-        const int64_t t = now_ns();
-        for (size_t k = 0; k < big.size(); k++) {
-            Request *r = big[k];
-            memset(&r->res, 0, sizeof(r->res));
-            r->res.score = scores[k];
-            r->res.beg_q = r->res.beg_s = -1;
-            r->res.end_q = eq[k];
-            r->res.end_s = es[k];
-            r->res.flags = ANYSEQ_FLAG_INT32;
-            r->status = st;
-            r->error = msg;
-            r->t_done = t;
-        }
-    }
+// A pair of at least long_cells cells that the wavefront takes.
+bool is_long_pair(const anyseq_server *S, int64_t n, int64_t m) {
+    const double cells = (double)n * (double)m;
+    return cells >= (double)S->cfg.long_cells && n > 0 && m > 0 && S->sc.alphabet <= 4 && n < (1 << 21) &&
+           m < (1 << 21) && anyseq::long_range_ok(&S->sc, n, m);
+}
+
+// Results of a finished batch: release its letters and wake the waiters.
+void finish(anyseq_server *S, std::vector<Request *> &reqs, bool long_lane) {
     std::lock_guard<std::mutex> lock(S->mu);
     for (Request *r : reqs) {
         r->done = true;
@@ -141,12 +93,75 @@ void run_batch(anyseq_server *S, std::vector<Request *> &reqs) {
         r->s.shrink_to_fit();
     }
     S->completed += (int64_t)reqs.size();
-    S->long_pairs += (int64_t)big.size();
+    if (long_lane) S->long_pairs += (int64_t)reqs.size();
     S->batches += 1;
     S->cv_done.notify_all();
 }
 
-void worker_main(anyseq_server *S) {
+void run_short(anyseq_server *S, std::vector<Request *> &small) {
+    ServeLane &L = S->lane[0];
+    std::vector<int64_t> qo(small.size() + 1, 0), so(small.size() + 1, 0);
+    for (size_t k = 0; k < small.size(); k++) {
+        qo[k + 1] = qo[k] + (int64_t)small[k]->q.size();
+        so[k + 1] = so[k] + (int64_t)small[k]->s.size();
+    }
+    std::vector<uint8_t> q((size_t)qo.back() + 1), s((size_t)so.back() + 1);
+    for (size_t k = 0; k < small.size(); k++) {
+        if (!small[k]->q.empty()) memcpy(q.data() + qo[k], small[k]->q.data(), small[k]->q.size());
+        if (!small[k]->s.empty()) memcpy(s.data() + so[k], small[k]->s.data(), small[k]->s.size());
+    }
+    std::vector<anyseq_result_t> out(small.size());
+    uint64_t used = 0;
+    const anyseq_status_t st =
+        anyseq_align_batch(L.ctx, q.data(), qo.data(), s.data(), so.data(), (int64_t)small.size(), &S->sc,
+                           S->cfg.mode, ANYSEQ_WANT_SCORE | ANYSEQ_WANT_END, out.data(), nullptr, 0, &used, L.stream);
+    const std::string msg = st != ANYSEQ_OK ? anyseq_last_error() : "";
+    const int64_t t = now_ns();
+    for (size_t k = 0; k < small.size(); k++) {
+        small[k]->res = out[k];
+        small[k]->status = st;
+        small[k]->error = msg;
+        small[k]->t_done = t;
+    }
+    finish(S, small, false);
+}
+
+void run_long(anyseq_server *S, std::vector<Request *> &big) {
+    // every long pair of the batch in one wavefront launch
+    ServeLane &L = S->lane[1];
+    std::vector<int64_t> qo(big.size() + 1, 0), so(big.size() + 1, 0);
+    for (size_t k = 0; k < big.size(); k++) {
+        qo[k + 1] = qo[k] + (int64_t)big[k]->q.size();
+        so[k + 1] = so[k] + (int64_t)big[k]->s.size();
+    }
+    std::vector<uint8_t> q((size_t)qo.back()), s((size_t)so.back());
+    for (size_t k = 0; k < big.size(); k++) {
+        memcpy(q.data() + qo[k], big[k]->q.data(), big[k]->q.size());
+        memcpy(s.data() + so[k], big[k]->s.data(), big[k]->s.size());
+    }
+    std::vector<int32_t> scores(big.size(), 0), eq(big.size(), 0), es(big.size(), 0);
+    const anyseq_status_t st = anyseq::long_scores(L.ctx, q.data(), qo.data(), s.data(), so.data(),
+                                                   (int64_t)big.size(), &S->sc, scores.data(), L.stream,
+                                                   S->cfg.mode, eq.data(), es.data());
+    const std::string msg = st != ANYSEQ_OK ? anyseq_last_error() : "";
+    const int64_t t = now_ns();
+    for (size_t k = 0; k < big.size(); k++) {
+        Request *r = big[k];
+        memset(&r->res, 0, sizeof(r->res));
+        r->res.score = scores[k];
+        r->res.beg_q = r->res.beg_s = -1;
+        r->res.end_q = eq[k];
+        r->res.end_s = es[k];
+        r->res.flags = ANYSEQ_FLAG_INT32;
+        r->status = st;
+        r->error = msg;
+        r->t_done = t;
+    }
+    finish(S, big, true);
+}
+
+void worker_main(anyseq_server *S, int which) {
+    ServeLane &L = S->lane[which];
     if (cudaSetDevice(S->cfg.device) != cudaSuccess) {
         std::lock_guard<std::mutex> lock(S->mu);
         S->worker_status = ANYSEQ_ERR_CUDA;
@@ -156,22 +171,23 @@ void worker_main(anyseq_server *S) {
         std::vector<Request *> batch;
         {
             std::unique_lock<std::mutex> lock(S->mu);
-            S->cv_work.wait(lock, [&] { return S->stop || !S->queue.empty(); });
-            if (S->queue.empty()) break;  // stop requested and nothing left
+            L.cv_work.wait(lock, [&] { return S->stop || !L.queue.empty(); });
+            if (L.queue.empty()) break;  // stop requested and nothing left
             // batching window: until the oldest request has waited max_wait_us or the batch is full
-            const int64_t deadline = S->queue.front()->t_submit + S->cfg.max_wait_us * 1000;
-            while (!S->stop && (int64_t)S->queue.size() < S->cfg.max_batch_pairs) {
+            const int64_t deadline = L.queue.front()->t_submit + S->cfg.max_wait_us * 1000;
+            while (!S->stop && (int64_t)L.queue.size() < S->cfg.max_batch_pairs) {
                 const int64_t left = deadline - now_ns();
                 if (left <= 0) break;
-                S->cv_work.wait_for(lock, std::chrono::nanoseconds(left));
+                L.cv_work.wait_for(lock, std::chrono::nanoseconds(left));
             }
-            while (!S->queue.empty() && (int64_t)batch.size() < S->cfg.max_batch_pairs) {
-                batch.push_back(S->queue.front());
-                S->queue.pop_front();
+            while (!L.queue.empty() && (int64_t)batch.size() < S->cfg.max_batch_pairs) {
+                batch.push_back(L.queue.front());
+                L.queue.pop_front();
             }
         }
         const int64_t t0 = now_ns();
-        run_batch(S, batch);
+        if (which == 0) run_short(S, batch);
+        else run_long(S, batch);
         std::lock_guard<std::mutex> lock(S->mu);
         S->busy_ms += (double)(now_ns() - t0) * 1e-6;
     }
@@ -198,19 +214,25 @@ extern "C" anyseq_status_t anyseq_server_create(anyseq_server **out, const anyse
         S->matrix.assign(cfg->scoring.matrix, cfg->scoring.matrix + (size_t)a * a);
         S->sc.matrix = S->matrix.data();
     }
-    anyseq_status_t st = anyseq_create(&S->ctx, cfg->device, 0);
-    if (st != ANYSEQ_OK) {
-        delete S;
-        return st;
+    for (int k = 0; k < 2; k++) {
+        anyseq_status_t st = anyseq_create(&S->lane[k].ctx, cfg->device, 0);
+        if (st == ANYSEQ_OK && (cudaSetDevice(cfg->device) != cudaSuccess ||
+                                cudaStreamCreateWithFlags(&S->lane[k].stream, cudaStreamNonBlocking) != cudaSuccess)) {
+            cudaGetLastError();
+            st = anyseq::fail(ANYSEQ_ERR_CUDA, "could not create the server's streams");
+        }
+        if (st != ANYSEQ_OK) {
+            for (int j = 0; j <= k; j++) {
+                if (S->lane[j].stream) cudaStreamDestroy(S->lane[j].stream);
+                if (S->lane[j].ctx) anyseq_destroy(S->lane[j].ctx);
+            }
+            delete S;
+            return st;
+        }
     }
-    if (cudaSetDevice(cfg->device) != cudaSuccess ||
-        cudaStreamCreateWithFlags(&S->stream, cudaStreamNonBlocking) != cudaSuccess) {
-        cudaGetLastError();
-        anyseq_destroy(S->ctx);
-        delete S;
-        return anyseq::fail(ANYSEQ_ERR_CUDA, "could not create the server's stream");
-    }
-    S->worker = std::thread(worker_main, S);
+    // the long lane's wavefront leaves room on every SM for the short lane's kernels
+    anyseq_set_option(S->lane[1].ctx, "wave_ctas_per_sm", 1);
+    for (int k = 0; k < 2; k++) S->lane[k].worker = std::thread(worker_main, S, k);
     *out = S;
     return ANYSEQ_OK;
 }
@@ -245,9 +267,10 @@ extern "C" anyseq_status_t anyseq_server_submit(anyseq_server *S, const uint8_t 
     r->ticket = S->next_ticket++;
     r->t_submit = now_ns();
     S->live[r->ticket] = r;
-    S->queue.push_back(r);
+    ServeLane &L = S->lane[is_long_pair(S, n, m) ? 1 : 0];
+    L.queue.push_back(r);
     *ticket = r->ticket;
-    S->cv_work.notify_one();
+    L.cv_work.notify_one();
     return ANYSEQ_OK;
 }
 
@@ -282,7 +305,7 @@ extern "C" anyseq_status_t anyseq_server_stat(anyseq_server *S, const char *key,
     else if (!strcmp(key, "batches")) *value = (double)S->batches;
     else if (!strcmp(key, "long_pairs")) *value = (double)S->long_pairs;
     else if (!strcmp(key, "rejected")) *value = (double)S->rejected;
-    else if (!strcmp(key, "queued")) *value = (double)S->queue.size();
+    else if (!strcmp(key, "queued")) *value = (double)(S->lane[0].queue.size() + S->lane[1].queue.size());
     else if (!strcmp(key, "held_bytes")) *value = (double)S->held_bytes;
     else if (!strcmp(key, "busy_ms")) *value = S->busy_ms;
     else return anyseq::fail(ANYSEQ_ERR_ARG, "unknown server statistic '%s'", key);
@@ -294,12 +317,17 @@ extern "C" anyseq_status_t anyseq_server_destroy(anyseq_server *S) {
     {
         std::lock_guard<std::mutex> lock(S->mu);
         S->stop = true;
-        S->cv_work.notify_all();
+        for (auto &L : S->lane) L.cv_work.notify_all();
     }
-    if (S->worker.joinable()) S->worker.join();
+    for (auto &L : S->lane)
+        if (L.worker.joinable()) L.worker.join();
     for (auto &kv : S->live) delete kv.second;
-    if (S->stream) cudaStreamDestroy(S->stream);
-    anyseq_status_t st = anyseq_destroy(S->ctx);
+    anyseq_status_t st = ANYSEQ_OK;
+    for (auto &L : S->lane) {
+        if (L.stream) cudaStreamDestroy(L.stream);
+        const anyseq_status_t d = anyseq_destroy(L.ctx);
+        if (st == ANYSEQ_OK) st = d;
+    }
     delete S;
     return st;
 }

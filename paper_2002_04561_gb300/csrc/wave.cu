@@ -73,7 +73,7 @@ __host__ __device__ constexpr bool best_edge(int mode) { return mode == SEMIGLOB
 // byte offset of the column letter's plane, and a lane reads its WR bytes of
 // that plane in one vector load. sigma' of row r is then one byte permute, as
 // on the row-profile path.
-template <int WR, bool TB, int MODE, bool TRI, bool MAT>
+template <int WR, bool TB, int MODE, bool TRI, bool MAT, bool SPLIT = false>
 __global__ void __launch_bounds__(256, (WR <= 4 || (WR <= 8 && !best_all(MODE))) ? 4 : 2) wave_kernel(WaveArgs A) {
     constexpr int INIT = wave_init_mode(MODE);
     constexpr bool ALL = best_all(MODE), EDGE = best_edge(MODE);
@@ -81,6 +81,13 @@ __global__ void __launch_bounds__(256, (WR <= 4 || (WR <= 8 && !best_all(MODE)))
     static_assert(!TB || WR % 8 == 0, "direction words hold 8 rows");
     static_assert(!TB || MODE == GLOBAL, "traceback on the wavefront is global");
     static_assert(!(TB && MAT), "the wavefront's traceback variant takes 2-bit letters");
+    static_assert(!SPLIT || (WR == 16 && TRI && MODE == GLOBAL && !TB && !MAT),
+                  "split steps: global three-input-maximum score passes with 16 rows per lane");
+    // steps from lane 0's column to lane 31's last row at that column: each lane is one
+    // column behind the previous, two with split steps (whose lower half runs one more behind)
+    constexpr int RAMP = SPLIT ? 2 * (WG - 1) + 1 : WG - 1;
+    // refill blocks between a block's first step and the drain of its bottom row
+    constexpr int DLAG = SPLIT ? 3 : 2;
     __shared__ WaveSmem smem[8];
     extern __shared__ __align__(16) uint8_t wdyn[];
     const int warp = threadIdx.x >> 5, g = threadIdx.x & 31;
@@ -110,7 +117,7 @@ __global__ void __launch_bounds__(256, (WR <= 4 || (WR <= 8 && !best_all(MODE)))
         const int32_t n = ps.n, m = ps.m;
         const int32_t nstripes = (n + WCH - 1) / WCH;
         const int32_t pad = nstripes * WCH - n;
-        const int S = m + WG - 1;
+        const int S = m + RAMP;
         const int32_t k = t - ps.stripe0;
         const bool last = (k == nstripes - 1);
         const bool rev = ps.rev != 0;
@@ -237,8 +244,8 @@ __global__ void __launch_bounds__(256, (WR <= 4 || (WR <= 8 && !best_all(MODE)))
         // warp barrier) the release of the progress counter
         // lane 31 stored column c at step c + 31, at (its block's base column - 31) + offset
         auto bot_index = [&](int c) {
-            const int sw = (c + WG - 1) & ~(BLOCK - 1);
-            return ((sw - (WG - 1)) & (WRING - 1)) + (c + WG - 1 - sw);
+            const int sw = (c + RAMP) & ~(BLOCK - 1);
+            return ((sw - RAMP) & (WRING - 1)) + (c + RAMP - sw);
         };
         auto drain_stores = [&](int blk) {
             int c = blk * BLOCK + g;
@@ -414,6 +421,101 @@ __global__ void __launch_bounds__(256, (WR <= 4 || (WR <= 8 && !best_all(MODE)))
                 xe = (T)ex;
             }
         };
+        // Split step (SPLIT): rows 0..7 (half A) at column s - 2g, rows 8..15 (half B) one
+        // column behind. The halves are two independent dependency chains of 8 rows in one
+        // step instead of one of 16. Half B takes its diagonal, the E entering row 8 and the
+        // column's selector from the previous step.
+        constexpr int HR = WR / 2;
+        T midD = 0, midE = C::NEG;
+        uint32_t sel_prev = 0;
+        if (SPLIT) midD = col0(INIT, rb + HR - 1 - pad, o, e, ps.tb) + oe;
+        auto step2 = [&](const int s, const int j, auto careful_tag) {
+            constexpr bool CAREFUL = decltype(careful_tag)::value;
+            const int cA = s - 2 * g, cB = cA - 1;
+            const T up_hoe = (T)__shfl_sync(0xffffffffu, (uint32_t)xh, src);
+            const T up_e = (T)__shfl_sync(0xffffffffu, (uint32_t)xe, src);
+            const uint32_t sel = selp[j];
+            const T h7 = Hoe[HR - 1];  // row 7 before this step (half B's diagonal next step)
+            T EA = C::NEG, stE = xe;
+            const bool okA = !CAREFUL || (unsigned)cA < (unsigned)m;
+            const bool okB = !CAREFUL || (unsigned)cB < (unsigned)m;
+            if (okA && okB) {
+                // both halves, interleaved row by row (two independent chains)
+                T AdA = C::addc(prev_up, (uint32_t)C::sigma(prof[0], prof[0], sel));
+                T AdB = C::addc(midD, (uint32_t)C::sigma(prof[HR], prof[HR], sel_prev));
+                prev_up = up_hoe;
+                T E = up_e, EB = midE, EinB = midE;
+#pragma unroll
+                for (int k = 0; k < HR; k++) {
+                    const int ra = k, rb2 = HR + k;
+                    const T Ara = AdA, Arb = AdB;
+                    if (k + 1 < HR) {
+                        AdA = C::addc(Hoe[ra], (uint32_t)C::sigma(prof[ra + 1], prof[ra + 1], sel));
+                        AdB = C::addc(Hoe[rb2], (uint32_t)C::sigma(prof[rb2 + 1], prof[rb2 + 1], sel_prev));
+                    }
+                    F[ra] = C::addmax(F[ra], e_raw, Hoe[ra]);                          // Eq. 5
+                    F[rb2] = C::addmax(F[rb2], e_raw, Hoe[rb2]);
+                    Hoe[ra] = C::addc(C::vmax3(Ara, F[ra], E), oe_c);                  // Eq. 1
+                    Hoe[rb2] = C::addc(C::vmax3(Arb, F[rb2], EB), oe_c);
+                    E = C::addmax(E, e_raw, Hoe[ra]);                                  // Eq. 4
+                    EinB = EB;
+                    EB = C::addmax(EB, e_raw, Hoe[rb2]);
+                }
+                EA = E;
+                xh = Hoe[WR - 1];
+                xe = EB;
+                stE = last ? EinB : EB;
+            } else {
+                if (okA) {
+                    T Ad = C::addc(prev_up, (uint32_t)C::sigma(prof[0], prof[0], sel));
+                    prev_up = up_hoe;
+                    T E = up_e;
+#pragma unroll
+                    for (int r = 0; r < HR; r++) {
+                        const T Adr = Ad;
+                        if (r + 1 < HR) Ad = C::addc(Hoe[r], (uint32_t)C::sigma(prof[r + 1], prof[r + 1], sel));
+                        F[r] = C::addmax(F[r], e_raw, Hoe[r]);
+                        Hoe[r] = C::addc(C::vmax3(Adr, F[r], E), oe_c);
+                        E = C::addmax(E, e_raw, Hoe[r]);
+                    }
+                    EA = E;
+                }
+                if (okB) {
+                    T Ad = C::addc(midD, (uint32_t)C::sigma(prof[HR], prof[HR], sel_prev));
+                    T E = midE, Ein = midE;
+#pragma unroll
+                    for (int r = HR; r < WR; r++) {
+                        const T Adr = Ad;
+                        if (r + 1 < WR) Ad = C::addc(Hoe[r], (uint32_t)C::sigma(prof[r + 1], prof[r + 1], sel_prev));
+                        F[r] = C::addmax(F[r], e_raw, Hoe[r]);
+                        Hoe[r] = C::addc(C::vmax3(Adr, F[r], E), oe_c);
+                        Ein = E;
+                        E = C::addmax(E, e_raw, Hoe[r]);
+                    }
+                    xh = Hoe[WR - 1];
+                    xe = E;
+                    stE = last ? Ein : E;
+                }
+            }
+            midD = h7;
+            midE = EA;
+            sel_prev = sel;
+            {
+                // lane 31: its last row (half B's column) to the bottom ring, then lane 0's
+                // next border value in
+                uint32_t hx = (uint32_t)xh, ex = (uint32_t)xe;
+                asm volatile(
+                    "{ .reg .pred p;\n\t"
+                    "setp.eq.u32 p, %5, 31;\n\t"
+                    "@p st.shared.v2.u32 [%2], {%0, %4};\n\t"
+                    "@p ld.shared.v2.u32 {%0, %1}, [%3]; }"
+                    : "+r"(hx), "+r"(ex)
+                    : "r"(bota + 8u * (uint32_t)j), "r"(topa + 8u * (uint32_t)j), "r"((uint32_t)stE), "r"(g)
+                    : "memory");
+                xh = (T)hx;
+                xe = (T)ex;
+            }
+        };
         for (int s0 = 0; s0 < S && !failed; s0 += BLOCK) {
             const int kb = s0 / BLOCK;
             if ((kb + 1) * BLOCK < m) wait_for(kb + 1);
@@ -422,29 +524,36 @@ __global__ void __launch_bounds__(256, (WR <= 4 || (WR <= 8 && !best_all(MODE)))
             int2 ft = make_int2(C::NEG, C::NEG);
             fetch(kb + 1, fw, fsh, ft);
             int released = -1;
-            if (kb - 2 >= drained) {
-                drain_stores(kb - 2);
-                released = kb - 2;
-                drained = kb - 1;
+            if (kb - DLAG >= drained) {
+                drain_stores(kb - DLAG);
+                released = kb - DLAG;
+                drained = kb - DLAG + 1;
             }
             const int s1 = min(S, s0 + BLOCK), sm_ = min(s1, s0 + BLOCK / 2);
-            selp = &sm->sel[(s0 - g) & (WRING - 1)];
+            selp = &sm->sel[(s0 - (SPLIT ? 2 : 1) * g) & (WRING - 1)];
             topa = (uint32_t)__cvta_generic_to_shared(&sm->top[2 * ((s0 + 1) & (WRING - 1))]);
-            bota = (uint32_t)__cvta_generic_to_shared(&sm->bot[2 * ((s0 - (WG - 1)) & (WRING - 1))]);
-            const bool careful = kb == 0 || s0 + BLOCK >= m;
-            if (careful) {
-                for (int s = s0; s < sm_; s++) step(s, s - s0, std::true_type{});
-            } else {
-                for (int s = s0; s < sm_; s++) step(s, s - s0, std::false_type{});
-            }
+            bota = (uint32_t)__cvta_generic_to_shared(&sm->bot[2 * ((s0 - RAMP) & (WRING - 1))]);
+            const bool careful = s0 < RAMP || s0 + BLOCK >= m;
+            auto run_half = [&](int sa, int sb) {
+                if constexpr (SPLIT) {
+                    if (careful) {
+                        for (int s = sa; s < sb; s++) step2(s, s - s0, std::true_type{});
+                    } else {
+                        for (int s = sa; s < sb; s++) step2(s, s - s0, std::false_type{});
+                    }
+                } else {
+                    if (careful) {
+                        for (int s = sa; s < sb; s++) step(s, s - s0, std::true_type{});
+                    } else {
+                        for (int s = sa; s < sb; s++) step(s, s - s0, std::false_type{});
+                    }
+                }
+            };
+            run_half(s0, sm_);
             put(kb + 1, fw, fsh, ft);
             __syncwarp();
             if (released >= 0 && !last && g == 0) st_release(prog_mine, released + 1);
-            if (careful) {
-                for (int s = sm_; s < s1; s++) step(s, s - s0, std::true_type{});
-            } else {
-                for (int s = sm_; s < s1; s++) step(s, s - s0, std::false_type{});
-            }
+            run_half(sm_, s1);
         }
         __syncwarp();
         for (int b = drained; b <= (m - 1) / BLOCK; b++) drain(b);
@@ -485,9 +594,9 @@ static size_t wave_dyn_smem(bool mat, int wr, int alphabet) {
 // Stripes per SM below which a launch takes 4-row stripes.
 constexpr int WAVE_THIN_STRIPES_PER_SM = 2;
 
-template <int WR, bool TB, int MODE, bool TRI = false, bool MAT = false>
+template <int WR, bool TB, int MODE, bool TRI = false, bool MAT = false, bool SPLIT = false>
 static int blocks_per_sm(size_t dyn = 0) {
-    auto kern = wave_kernel<WR, TB, MODE, TRI, MAT>;
+    auto kern = wave_kernel<WR, TB, MODE, TRI, MAT, SPLIT>;
     if (dyn) cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)dyn);
     int nb = 0;
     if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, kern, 256, dyn) != cudaSuccess) {
@@ -524,10 +633,12 @@ int wave_rows_per_lane(int64_t total_rows, int num_sms, int64_t n_passes, int mo
     return wr;
 }
 
-template <int WR, bool TB, int MODE, bool TRI = false, bool MAT = false>
+template <int WR, bool TB, int MODE, bool TRI = false, bool MAT = false, bool SPLIT = false>
 static void launch_one(const WaveArgs &A, int num_sms, cudaStream_t st) {
     const size_t dyn = wave_dyn_smem(MAT, WR, A.alphabet);
-    wave_kernel<WR, TB, MODE, TRI, MAT><<<num_sms * blocks_per_sm<WR, TB, MODE, TRI, MAT>(dyn), 256, dyn, st>>>(A);
+    int per_sm = blocks_per_sm<WR, TB, MODE, TRI, MAT, SPLIT>(dyn);
+    if (A.ctas_per_sm > 0 && A.ctas_per_sm < per_sm) per_sm = A.ctas_per_sm;
+    wave_kernel<WR, TB, MODE, TRI, MAT, SPLIT><<<num_sms * per_sm, 256, dyn, st>>>(A);
 }
 
 // 16-row stripes side by side per SM from which the 3-input-maximum cell wins
@@ -590,6 +701,7 @@ cudaError_t launch_wave(const WaveArgs &A, int num_sms, cudaStream_t st) {
         else launch_one<8, false, GLOBAL>(A, num_sms, st);
     } else {
         if (tb) launch_one<16, true, GLOBAL>(A, num_sms, st);
+        else if (tri && A.split != 2) launch_one<16, false, GLOBAL, true, false, true>(A, num_sms, st);
         else if (tri) launch_one<16, false, GLOBAL, true>(A, num_sms, st);
         else launch_one<16, false, GLOBAL>(A, num_sms, st);
     }

@@ -7,7 +7,9 @@
 * ANYSEQ_BAND_LEARNED returns exactly the full-DP scores, also for a planted
   band far from the optimal path (the certificate must reject it);
 * training on the GPU lowers the loss, and the trained network needs fewer
-  banded cells and doublings than the same route without it (a constant band).
+  banded cells and doublings than the same route without it (a constant band);
+* under the shipped defaults the learned route has higher pairs/s than the
+  same route with the network's prior (a constant band), all scores equal.
 """
 import os
 import tempfile
@@ -105,6 +107,8 @@ def test_model_roundtrip(pkg, ctx):
 
 
 def constant_model(centre, log_w):
+    """A network with constant outputs: centre (columns) and log of the
+    half-width relative to the pair's longer sequence."""
     p = np.zeros(25090, np.float32)
     p[-2], p[-1] = centre, log_w
     return p
@@ -131,8 +135,9 @@ def test_banded_route_is_exact_and_certificate_rejects_planted_bands(pkg, ctx):
     idx = np.arange(0, b.n_pairs, 11)
     sub = b.subset(idx)
     assert np.array_equal(full["score"][idx], oracle.score_batch(sub, oracle.Scoring(*C45))[0])
-    for model in (constant_model(0.0, np.log(16.0)), constant_model(400.0, np.log(16.0)),
-                  constant_model(-900.0, np.log(40.0))):
+    # narrow planted bands (16 to 40 columns at 3 kbp), two of them off the path
+    for model in (constant_model(0.0, np.log(0.005)), constant_model(400.0, np.log(0.005)),
+                  constant_model(-900.0, np.log(0.013))):
         ctx.band_model_set(model)
         res = band_scores(pkg, ctx, b)
         assert np.array_equal(res["score"], full["score"])
@@ -143,22 +148,27 @@ def test_banded_route_is_exact_and_certificate_rejects_planted_bands(pkg, ctx):
 
 
 def test_training_lowers_loss_and_beats_constant_band(pkg, ctx):
-    # doublings measure how far a band was from certifying: allow them here
+    # doublings measure how far a band was from certifying: allow them here, and
+    # plan the network's widths as they are (no margin, no floor)
     ctx.set_option("band_max_doublings", 8)
     ctx.set_option("band_area_pct", 50)
     ctx.set_option("band_area16_pct", 50)
+    ctx.set_option("band_margin_pct", 100)
+    ctx.set_option("band_floor_pct", 0)
     try:
         _training_lowers_loss_and_beats_constant_band(pkg, ctx)
     finally:
         ctx.set_option("band_max_doublings", 0)
         ctx.set_option("band_area_pct", 60)
         ctx.set_option("band_area16_pct", 15)
+        ctx.set_option("band_margin_pct", 65)
+        ctx.set_option("band_floor_pct", 20)
 
 
 def _training_lowers_loss_and_beats_constant_band(pkg, ctx):
     train = band_set(105, n_pairs=3000)
     sc = pkg.Scoring.make(*C45)
-    ctx.band_model_set(constant_model(0.0, 4.0))
+    ctx.band_model_set(constant_model(0.0, np.log(0.25)))
     first = ctx.band_train(train.q, train.q_off, train.s, train.s_off, sc, epochs=1, lr=1e-3)
     last = ctx.band_train(train.q, train.q_off, train.s, train.s_off, sc, epochs=60, lr=1e-3)
     assert last < first
@@ -168,8 +178,52 @@ def _training_lowers_loss_and_beats_constant_band(pkg, ctx):
     assert np.array_equal(res["score"], full["score"])
     trained_rounds = ctx.stat("band_rounds")
     trained_doublings = int(((res["flags"] >> 8) & 255).sum())
-    ctx.band_model_set(constant_model(0.0, np.log(16.0)))
+    ctx.band_model_set(constant_model(0.0, np.log(0.005)))
     res0 = band_scores(pkg, ctx, test)
     assert np.array_equal(res0["score"], full["score"])
     const_doublings = int(((res0["flags"] >> 8) & 255).sum())
     assert trained_doublings < const_doublings, (trained_doublings, const_doublings, trained_rounds)
+
+
+def test_learned_band_gains_over_the_route_without_the_network(pkg):
+    """What the trained network gains, under the shipped defaults (no
+    doubling, area caps 60/15 %, margin 65 %, floor 20 %): the learned route
+    against the same route whose network is replaced by its prior (constant
+    outputs: centre 0, half-width a quarter of the longer sequence), on the
+    65,536 pairs of the band workload. Both routes' scores equal the full DP
+    on every pair; the learned route has the higher pairs/s."""
+    import time
+    # a fresh context: its network starts from random weights (one trained from a
+    # constant model, whose hidden weights are zero, would only move its biases)
+    ctx = pkg.Context(0)
+    sc = pkg.Scoring.make(*C45)
+    train = synth.band_pairs(n_pairs=16384, seed=105)
+    ctx.band_train(train.q, train.q_off, train.s, train.s_off, sc, epochs=60, lr=1e-3)
+    learned = ctx.band_model_get()
+    b = synth.band_pairs()
+    dev = lambda a: torch.from_numpy(np.ascontiguousarray(a)).cuda()
+    args = (dev(b.q), dev(b.q_off), dev(b.s), dev(b.s_off))
+    out = torch.zeros(b.n_pairs * 40, dtype=torch.uint8, device="cuda")
+    ctx.align_batch(*args, sc, pkg.GLOBAL, out=out)
+    full = out.cpu().numpy().view(pkg.RESULT_DTYPE)["score"].copy()
+
+    def route_ms():
+        ctx.align_batch(*args, sc, pkg.GLOBAL, want=pkg.WANT_SCORE | pkg.BAND_LEARNED, out=out)
+        torch.cuda.synchronize()
+        ts = []
+        for _ in range(3):
+            t0 = time.perf_counter()
+            ctx.align_batch(*args, sc, pkg.GLOBAL, want=pkg.WANT_SCORE | pkg.BAND_LEARNED, out=out)
+            torch.cuda.synchronize()
+            ts.append(time.perf_counter() - t0)
+        assert np.array_equal(out.cpu().numpy().view(pkg.RESULT_DTYPE)["score"], full)
+        return sorted(ts)[1]
+
+    t_learned = route_ms()
+    # the route with the network replaced by its prior, a fixed half-width as it is
+    ctx.set_option("band_margin_pct", 100)
+    ctx.set_option("band_floor_pct", 0)
+    ctx.band_model_set(constant_model(0.0, np.log(0.25)))
+    t_prior = route_ms()
+    ctx.close()
+    assert b.n_pairs / t_learned > 1.03 * b.n_pairs / t_prior, (t_learned, t_prior)

@@ -68,3 +68,16 @@ def test_missing_nvidia_smi(tmp_path, monkeypatch):
     c.start()
     c.begin()
     assert c.stop()["reasons"] == ["nvidia-smi unavailable"]
+
+
+def test_serving_window_rates():
+    """The steady-state test of the serving sweep: a server that completes every
+    request 50 ms after it arrives keeps up (ratio 1); one that completes them
+    at half the arrival rate falls behind (ratio 0.5), whatever the tail."""
+    import numpy as np
+    sub = np.arange(1000) * 1e-3                      # 1,000 requests/s for 1 s
+    off, ach = bench.serving_window_rates(sub, np.full(1000, 50.0))
+    assert abs(off - 1000) < 1e-6 and abs(ach / off - 1) < 1e-9
+    done = np.arange(1000) * 2e-3                     # completions every 2 ms
+    off, ach = bench.serving_window_rates(sub, (done - sub) * 1e3 + 10.0)
+    assert abs(ach / off - 0.5) < 1e-9

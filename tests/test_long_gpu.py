@@ -265,6 +265,30 @@ def test_wavefront_cell_forms_match_oracle(pkg, ctx, cell):
         ctx.set_option("wave_cell", 0)
 
 
+@pytest.mark.parametrize("split", [1, 2])
+def test_wavefront_split_steps_match_oracle(pkg, ctx, split):
+    """The split step of global passes (rows 0-7 of a lane one column ahead of
+    rows 8-15: two independent dependency chains per step) and the plain step
+    give the oracle's scores and divide-and-conquer CIGARs on pairs of one to
+    six 512-row stripes with ragged ends, the query longer or shorter than
+    the subject."""
+    ctx.set_option("wave_rows", 16)
+    ctx.set_option("wave_cell", 1)
+    ctx.set_option("wave_split", split)
+    try:
+        for k, (n, extra) in enumerate([(1, 3), (40, 0), (513, 7), (1800, -40), (3000, 11)]):
+            q, s = related(n, extra, seed=3650 + k)
+            out, _ = ctx.align_long(q, s, pkg.Scoring.make(*C4))
+            assert out["score"][0] == oracle.score(q, s, oracle.Scoring(*C4))[0], (split, n)
+            res, cig = long_cigar(pkg, ctx, q, s, C4)
+            want, _ = oracle.hirschberg(q, s, oracle.Scoring(*C4))
+            assert np.array_equal(cig, want), (split, n)
+    finally:
+        ctx.set_option("wave_rows", 0)
+        ctx.set_option("wave_cell", 0)
+        ctx.set_option("wave_split", 0)
+
+
 PROTEIN = (0, 0, -11, -1)
 
 
