@@ -218,8 +218,9 @@ anyseq_status_t anyseq_band_train(anyseq_ctx *ctx, const uint8_t *q, const int64
  * number of stripes side by side, 1 always the three-input maximum, 2 always
  * the two-step form (results are the same); "wave_split" (default 0) runs
  * global three-input-maximum passes with split steps (each lane's upper 8
- * rows one column ahead of its lower 8: two dependency chains per step); 2
- * turns that off (results are the same); "wave_rows" (default 0) sets the
+ * rows one column ahead of its lower 8: two dependency chains per step): 0
+ * from 12 stripes per SM, 1 always, 2 never (results are the same);
+ * "wave_rows" (default 0) sets the
  * wavefront's rows per lane (4, 8 or 16; 0 chooses by the number of stripes,
  * within what each mode has: local passes at most 8, semi-global 4 or 16,
  * traceback passes 8 or 16; results are the same); "wave_ctas_per_sm"

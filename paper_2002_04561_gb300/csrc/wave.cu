@@ -180,12 +180,17 @@ __global__ void __launch_bounds__(256, (WR <= 4 || (WR <= 8 && !best_all(MODE)))
         uint32_t *dw = TB ? A.dirs + ps.dir_off + (int64_t)k * S * WG * (WR / 8) + g * (WR / 8) : nullptr;
 
         // wait until the previous stripe published border block blk (bounded)
+        // The previous stripe's progress last seen (warp-uniform): blocks below it were
+        // published before the release that the acquire observed, so the warp polls only
+        // when it has caught up (the previous stripe usually runs several blocks ahead).
+        int32_t seen_prog = 0;
         auto wait_for = [&](int blk) {
-            if (k == 0 || failed) return;
+            if (k == 0 || failed || seen_prog >= blk + 1) return;
             int ok = 1;
+            int32_t v = 0;
             if (g == 0) {
                 int64_t spins = 0;
-                while (ld_acquire(prog_prev) < blk + 1) {
+                while ((v = ld_acquire(prog_prev)) < blk + 1) {
                     if (++spins > A.spin_limit || *((volatile int32_t *)A.err)) {
                         atomicExch(A.err, 1);
                         ok = 0;
@@ -195,6 +200,7 @@ __global__ void __launch_bounds__(256, (WR <= 4 || (WR <= 8 && !best_all(MODE)))
                 }
             }
             ok = __shfl_sync(0xffffffffu, ok, 0);
+            seen_prog = __shfl_sync(0xffffffffu, v, 0);
             failed = !ok;
             __syncwarp();
         };
@@ -646,6 +652,10 @@ static void launch_one(const WaveArgs &A, int num_sms, cudaStream_t st) {
 // up to 4 % slower, from 9 per SM 12 % faster; in semi-global passes, where it
 // spills, slower at every size).
 constexpr int WAVE_TRI_STRIPES_PER_SM = 8;
+// ... and from which it runs split steps (two chains per step, one more block of
+// skew per stripe): 1 Mbp (12.9 stripes per SM) 451-455 against 473 ms, 700 kbp (9
+// per SM) 331-360 against 325 ms, on one box.
+constexpr int WAVE_SPLIT_STRIPES_PER_SM = 12;
 
 cudaError_t launch_wave(const WaveArgs &A, int num_sms, cudaStream_t st) {
     const bool tb = A.dirs != nullptr;
@@ -701,7 +711,8 @@ cudaError_t launch_wave(const WaveArgs &A, int num_sms, cudaStream_t st) {
         else launch_one<8, false, GLOBAL>(A, num_sms, st);
     } else {
         if (tb) launch_one<16, true, GLOBAL>(A, num_sms, st);
-        else if (tri && A.split != 2) launch_one<16, false, GLOBAL, true, false, true>(A, num_sms, st);
+        else if (tri && (A.split == 1 || (A.split == 0 && (int64_t)A.n_stripes >= (int64_t)WAVE_SPLIT_STRIPES_PER_SM * num_sms)))
+            launch_one<16, false, GLOBAL, true, false, true>(A, num_sms, st);
         else if (tri) launch_one<16, false, GLOBAL, true>(A, num_sms, st);
         else launch_one<16, false, GLOBAL>(A, num_sms, st);
     }

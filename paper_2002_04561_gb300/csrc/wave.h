@@ -42,7 +42,7 @@ struct WaveArgs {
     // each, and sigma - open - extend per (query, subject) letter pair
     int32_t mat;                  // 0: 2-bit letters and row profiles; 1: the matrix path
     int32_t ctas_per_sm;          // 0: as many CTAs per SM as fit; else at most this many
-    int32_t split;                // global three-input-maximum passes: 0/1 split steps, 2 plain steps
+    int32_t split;                // global three-input-maximum passes: 0 by stripe count, 1 split steps, 2 plain
     int32_t alphabet;
     const uint8_t *q8, *s8;
     const int8_t *sig;            // alphabet x alphabet bytes (device)
