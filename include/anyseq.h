@@ -225,7 +225,10 @@ anyseq_status_t anyseq_band_train(anyseq_ctx *ctx, const uint8_t *q, const int64
  * within what each mode has: local passes at most 8, semi-global 4 or 16,
  * traceback passes 8 or 16; results are the same); "wave_ctas_per_sm"
  * (default 0: as many as fit) caps the wavefront's CTAs per SM, leaving room
- * for other kernels beside a long pair (results are the same); "tb_walker"
+ * for other kernels beside a long pair (results are the same); "wave_spread"
+ * (default 1) holds back the first stripe draws of a wavefront launch so that
+ * its first stripes land on distinct SMs, 0 takes them in plain draw order
+ * (results are the same); "tb_walker"
  * (default 0) picks the
  * batched traceback walk: 0 by batch size, 1 a warp per pair (staged windows),
  * 2 a thread per pair (results are the same). Unknown keys: ANYSEQ_ERR_ARG. */

@@ -135,6 +135,11 @@ extern "C" anyseq_status_t anyseq_set_option(anyseq_ctx *ctx, const char *key, i
         ctx->wave_split = (int32_t)value;
         return ANYSEQ_OK;
     }
+    if (!strcmp(key, "wave_spread")) {
+        if (value != 0 && value != 1) return fail(ANYSEQ_ERR_ARG, "wave_spread must be 0 or 1");
+        ctx->wave_spread = (int32_t)value;
+        return ANYSEQ_OK;
+    }
     if (!strcmp(key, "wave_ctas_per_sm")) {
         if (value < 0 || value > 8) return fail(ANYSEQ_ERR_ARG, "wave_ctas_per_sm must be in 0..8");
         ctx->wave_ctas_per_sm = (int32_t)value;

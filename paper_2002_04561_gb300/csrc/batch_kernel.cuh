@@ -38,8 +38,9 @@ __device__ __forceinline__ void build_qprofile(const BatchArgs &A, const Slot &s
         for (int k = 0; k < 4; k++) {
             const int lane = (w * 4 + k) >> 3, r = (w * 4 + k) & 7;
             int32_t i = ch * GROUP * R + lane * R + r + 1 - sl.pad[h];
+            // codes >= alphabet (an ANYSEQ_ERR_ALPHABET call) are clamped inside the table
             code[k] = (h < C::PAIRS && r < R && i >= 1 && sl.n[h] > 0)
-                          ? (int32_t)A.q8[sl.q0[h] + (sl.rev[h] ? sl.n[h] - i : i - 1)] : -1;
+                          ? min((int32_t)A.q8[sl.q0[h] + (sl.rev[h] ? sl.n[h] - i : i - 1)], alpha - 1) : -1;
         }
         for (int a = 0; a <= alpha; a++) {
             uint32_t word = 0;
@@ -138,8 +139,10 @@ __device__ __noinline__ void run_slot(const BatchArgs &A, GroupSmemT<4 * block_c
                     } else {
                         const uint32_t alpha = (uint32_t)A.alphabet;
                         uint32_t ca = alpha, cb = alpha;
-                        if (c < sl.m[0]) ca = A.s8[sl.s0[0] + (sl.rev[0] ? sl.m[0] - 1 - c : c)];
-                        if (C::PAIRS == 2 && c < sl.m[1]) cb = A.s8[sl.s0[1] + (sl.rev[1] ? sl.m[1] - 1 - c : c)];
+                        // a code >= alphabet (the call then fails with ANYSEQ_ERR_ALPHABET)
+                        // reads the null letter's row, inside the shared profile
+                        if (c < sl.m[0]) ca = min((uint32_t)A.s8[sl.s0[0] + (sl.rev[0] ? sl.m[0] - 1 - c : c)], alpha);
+                        if (C::PAIRS == 2 && c < sl.m[1]) cb = min((uint32_t)A.s8[sl.s0[1] + (sl.rev[1] ? sl.m[1] - 1 - c : c)], alpha);
                         // byte offsets of the two letters' profile rows for this lane
                         sm->sel[c & (RING - 1)] = (ca * QP_ROWS) | (((alpha + 1 + cb) * QP_ROWS) << 16);
                     }

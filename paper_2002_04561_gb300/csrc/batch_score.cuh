@@ -118,8 +118,10 @@ __device__ __forceinline__ void score_slot(const BatchArgs &A, GroupSmemT<4 * bl
                 } else {
                     const uint32_t alpha = (uint32_t)A.alphabet;
                     uint32_t ca = alpha, cb = alpha;
-                    if (c < m0) ca = A.s8[sl.s0[0] + (sl.rev[0] ? m0 - 1 - c : c)];
-                    if (C::PAIRS == 2 && c < m1) cb = A.s8[sl.s0[1] + (sl.rev[1] ? m1 - 1 - c : c)];
+                    // a code >= alphabet (the call then fails with ANYSEQ_ERR_ALPHABET) reads
+                    // the null letter's row, so every profile read stays in shared memory
+                    if (c < m0) ca = min((uint32_t)A.s8[sl.s0[0] + (sl.rev[0] ? m0 - 1 - c : c)], alpha);
+                    if (C::PAIRS == 2 && c < m1) cb = min((uint32_t)A.s8[sl.s0[1] + (sl.rev[1] ? m1 - 1 - c : c)], alpha);
                     selv = (ca * QP_ROWS) | (((alpha + 1 + cb) * QP_ROWS) << 16);
                 }
                 int2 tv;

@@ -304,6 +304,7 @@ anyseq_status_t run_wave_passes(anyseq_ctx *ctx, const uint32_t *q2, const uint3
     W.spin_limit = ctx->spin_limit;
     W.cell = ctx->wave_cell;
     W.ctas_per_sm = ctx->wave_ctas_per_sm;
+    W.no_spread = ctx->wave_spread ? 0 : 1;
     W.split = ctx->wave_split;
     if (mat) {
         W.mat = 1;

@@ -43,6 +43,11 @@ __device__ __forceinline__ int32_t ld_acquire(const int32_t *p) {
 __device__ __forceinline__ void st_release(int32_t *p, int32_t v) {
     asm volatile("st.release.gpu.global.s32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
 }
+__device__ __forceinline__ int32_t ld_relaxed(const int32_t *p) {
+    int32_t v;
+    asm volatile("ld.relaxed.gpu.global.s32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+    return v;
+}
 
 // Rings of WRING columns plus one more block: the selectors and the top row keep
 // a copy of ring block 0 after the ring's end, and lane 31's bottom stores run
@@ -73,8 +78,11 @@ __host__ __device__ constexpr bool best_edge(int mode) { return mode == SEMIGLOB
 // byte offset of the column letter's plane, and a lane reads its WR bytes of
 // that plane in one vector load. sigma' of row r is then one byte permute, as
 // on the row-profile path.
+// Two CTAs of 8 warps per SM (up to 128 registers a thread): 4- and 8-row stripes are
+// picked only when a launch has few stripes per SM, so more resident warps would
+// not run, and at 64 registers those variants spilled.
 template <int WR, bool TB, int MODE, bool TRI, bool MAT, bool SPLIT = false>
-__global__ void __launch_bounds__(256, (WR <= 4 || (WR <= 8 && !best_all(MODE))) ? 4 : 2) wave_kernel(WaveArgs A) {
+__global__ void __launch_bounds__(256, 2) wave_kernel(WaveArgs A) {
     constexpr int INIT = wave_init_mode(MODE);
     constexpr bool ALL = best_all(MODE), EDGE = best_edge(MODE);
     constexpr int WCH = WG * WR;  // rows per stripe
@@ -96,12 +104,27 @@ __global__ void __launch_bounds__(256, (WR <= 4 || (WR <= 8 && !best_all(MODE)))
     uint8_t *qp = wdyn + WAVE_SIG_BYTES + (size_t)warp * A.alphabet * WCH;
     if (MAT) {
         for (int x = threadIdx.x; x < A.alphabet * A.alphabet; x += blockDim.x) stab[x] = A.sig[x];
+        // selectors are read one step ahead, also at ring slots no column of the stripe
+        // has filled yet: every slot holds a valid plane offset from the start
+        for (int x = g; x < WRING + BLOCK; x += WG) sm->sel[x] = 0;
         __syncthreads();
     }
     typedef CellI32 C;
     typedef int32_t T;
     const int32_t o = A.o, e = A.e, oe = A.o + A.e;
     const uint32_t e_raw = C::raw(e), oe_raw = C::raw(oe), oe_c = C::cst(oe), e_c = C::cst(e);
+    // Stripes go to warps in the order they draw them. Consecutive stripes on one SM
+    // compete for its issue slots and shared-memory pipe while other SMs idle, so a
+    // warp holds back its first draw by its rank (1 us each): the warp index times the
+    // CTAs per SM, plus its CTA's launch wave (blockIdx / SMs). With CTAs dispatched
+    // breadth-first over the SMs, the warps of one rank sit on distinct SMs. A warp
+    // stops waiting once every stripe is taken. (A 35,000-residue protein pair, 137
+    // stripes: 14.2 -> 7.3 ms; 100 kbp global, 781 stripes: 32.6 -> 25.9 ms.)
+    if (!A.no_spread && A.grid_sms > 0 && g == 0) {
+        const int rank = warp * (int)(gridDim.x / (unsigned)A.grid_sms) + (int)(blockIdx.x / (unsigned)A.grid_sms);
+        for (int z = 0; z < rank && ld_relaxed(A.stripe_counter) < A.n_stripes; z++) __nanosleep(1000);
+    }
+    __syncwarp();
     for (;;) {
         int32_t t = 0;
         if (g == 0) t = atomicAdd(A.stripe_counter, 1);
@@ -141,7 +164,8 @@ __global__ void __launch_bounds__(256, (WR <= 4 || (WR <= 8 && !best_all(MODE)))
 #pragma unroll
             for (int r = 0; r < WR; r++) {
                 const int32_t i = rb + r - pad;
-                qa[r] = i >= 1 ? (int32_t)A.q8[ps.q0 + (rev ? (int64_t)(n - i) : (int64_t)(i - 1))] : -1;
+                // codes >= alphabet (an ANYSEQ_ERR_ALPHABET call) are clamped inside the table
+                qa[r] = i >= 1 ? min((int32_t)A.q8[ps.q0 + (rev ? (int64_t)(n - i) : (int64_t)(i - 1))], A.alphabet - 1) : -1;
             }
             for (int a = 0; a < A.alphabet; a++) {
 #pragma unroll
@@ -213,7 +237,9 @@ __global__ void __launch_bounds__(256, (WR <= 4 || (WR <= 8 && !best_all(MODE)))
             if (c < m) {
                 const int64_t pos = ps.s0 + (rev ? (int64_t)(m - 1 - c) : (int64_t)c);
                 if (MAT) {
-                    fw = A.s8[pos];
+                    // a code >= alphabet (an ANYSEQ_ERR_ALPHABET call) is clamped, so that
+                    // the profile read it selects stays in shared memory
+                    fw = min((uint32_t)A.s8[pos], (uint32_t)A.alphabet - 1u);
                 } else {
                     fw = A.s2[pos >> 4];
                     fsh = 2 * (int32_t)(pos & 15);
@@ -308,6 +334,34 @@ __global__ void __launch_bounds__(256, (WR <= 4 || (WR <= 8 && !best_all(MODE)))
         // offset s - s0), lane 31's top loads and bottom stores
         const uint32_t *selp = sm->sel;
         uint32_t topa = 0, bota = 0;
+        // loaded one step ahead, so that no shared-memory latency sits in a step's chain:
+        // the next step's selector (and on the matrix path this lane's sigma' bytes of
+        // its letter), and on lane 31 the top value lane 0 takes after the next step
+        uint32_t nsel = sm->sel[(0 - (SPLIT ? 2 : 1) * g) & (WRING - 1)];
+        uint32_t nwq[MAT ? WR / 4 : 1];
+        auto load_wq = [&](uint32_t sv, uint32_t (&w)[MAT ? WR / 4 : 1]) {
+            if constexpr (MAT) {
+                const uint8_t *p = qp + sv + g * WR;
+                if constexpr (WR == 16) {
+                    const uint4 v = *reinterpret_cast<const uint4 *>(p);
+                    w[0] = v.x; w[1] = v.y; w[2] = v.z; w[3] = v.w;
+                } else if constexpr (WR == 8) {
+                    const uint2 v = *reinterpret_cast<const uint2 *>(p);
+                    w[0] = v.x; w[1] = v.y;
+                } else {
+                    w[0] = *reinterpret_cast<const uint32_t *>(p);
+                }
+            } else {
+                w[0] = 0;
+            }
+        };
+        load_wq(nsel, nwq);
+        uint32_t ph, pe;
+        {
+            const int2 tv = reinterpret_cast<const int2 *>(sm->top)[1];
+            ph = (uint32_t)tv.x;
+            pe = (uint32_t)tv.y;
+        }
         // one step: column s - g of this lane's rows (j = s - s0). Checked steps (the first
         // block, where lane g has no column before step g, and the blocks that reach the
         // last column) skip columns outside the pair and look for the last column's cells.
@@ -317,22 +371,16 @@ __global__ void __launch_bounds__(256, (WR <= 4 || (WR <= 8 && !best_all(MODE)))
             const T up_hoe = (T)__shfl_sync(0xffffffffu, (uint32_t)xh, src);
             const T up_e = (T)__shfl_sync(0xffffffffu, (uint32_t)xe, src);
             T stE = xe;  // E stored by lane 31: of the row below, or its own in the last stripe
+            // this step's selector and sigma' bytes (matrix path); the next step's are
+            // loaded now (selp[j + 1] stays inside the ring's extra block)
+            const uint32_t sel = nsel;
+            (void)sel;  // the matrix path reads its sigma' bytes instead
+            uint32_t wq[MAT ? WR / 4 : 1];
+#pragma unroll
+            for (int w = 0; w < (MAT ? WR / 4 : 1); w++) wq[w] = nwq[w];
+            nsel = selp[j + 1];
+            load_wq(nsel, nwq);
             if (!CAREFUL || (unsigned)c < (unsigned)m) {
-                const uint32_t sel = selp[j];
-                // this lane's sigma' bytes of the column letter (matrix path)
-                uint32_t wq[MAT ? WR / 4 : 1];
-                if constexpr (MAT) {
-                    const uint8_t *src = qp + sel + g * WR;
-                    if constexpr (WR == 16) {
-                        const uint4 v = *reinterpret_cast<const uint4 *>(src);
-                        wq[0] = v.x; wq[1] = v.y; wq[2] = v.z; wq[3] = v.w;
-                    } else if constexpr (WR == 8) {
-                        const uint2 v = *reinterpret_cast<const uint2 *>(src);
-                        wq[0] = v.x; wq[1] = v.y;
-                    } else {
-                        wq[0] = *reinterpret_cast<const uint32_t *>(src);
-                    }
-                }
                 auto sigma_r = [&](int r) -> uint32_t {
                     if constexpr (MAT) {
                         const uint32_t b = (uint32_t)(r & 3);  // byte b, sign-extended
@@ -412,16 +460,19 @@ __global__ void __launch_bounds__(256, (WR <= 4 || (WR <= 8 && !best_all(MODE)))
                 stE = last ? Ein : E;
             }
             {
-                // lane 31: its last row to the bottom ring, then lane 0's next border value
-                // in; predicated shared-memory accesses rather than a branch around them
+                // lane 31: its last row to the bottom ring; it then exports lane 0's next
+                // border value (loaded a step ago) and loads the one after. Predicated
+                // shared-memory accesses rather than a branch around them
                 uint32_t hx = (uint32_t)xh, ex = (uint32_t)xe;
                 asm volatile(
                     "{ .reg .pred p;\n\t"
-                    "setp.eq.u32 p, %5, 31;\n\t"
-                    "@p st.shared.v2.u32 [%2], {%0, %4};\n\t"
-                    "@p ld.shared.v2.u32 {%0, %1}, [%3]; }"
-                    : "+r"(hx), "+r"(ex)
-                    : "r"(bota + 8u * (uint32_t)j), "r"(topa + 8u * (uint32_t)j), "r"((uint32_t)stE), "r"(g)
+                    "setp.eq.u32 p, %7, 31;\n\t"
+                    "@p st.shared.v2.u32 [%4], {%0, %6};\n\t"
+                    "@p mov.b32 %0, %2;\n\t"
+                    "@p mov.b32 %1, %3;\n\t"
+                    "@p ld.shared.v2.u32 {%2, %3}, [%5]; }"
+                    : "+r"(hx), "+r"(ex), "+r"(ph), "+r"(pe)
+                    : "r"(bota + 8u * (uint32_t)j), "r"(topa + 8u * (uint32_t)(j + 1)), "r"((uint32_t)stE), "r"(g)
                     : "memory");
                 xh = (T)hx;
                 xe = (T)ex;
@@ -440,7 +491,8 @@ __global__ void __launch_bounds__(256, (WR <= 4 || (WR <= 8 && !best_all(MODE)))
             const int cA = s - 2 * g, cB = cA - 1;
             const T up_hoe = (T)__shfl_sync(0xffffffffu, (uint32_t)xh, src);
             const T up_e = (T)__shfl_sync(0xffffffffu, (uint32_t)xe, src);
-            const uint32_t sel = selp[j];
+            const uint32_t sel = nsel;
+            nsel = selp[j + 1];  // the next step's, one step ahead
             const T h7 = Hoe[HR - 1];  // row 7 before this step (half B's diagonal next step)
             T EA = C::NEG, stE = xe;
             const bool okA = !CAREFUL || (unsigned)cA < (unsigned)m;
@@ -507,16 +559,19 @@ __global__ void __launch_bounds__(256, (WR <= 4 || (WR <= 8 && !best_all(MODE)))
             midE = EA;
             sel_prev = sel;
             {
-                // lane 31: its last row (half B's column) to the bottom ring, then lane 0's
-                // next border value in
+                // lane 31: its last row (half B's column) to the bottom ring; it then
+                // exports lane 0's next border value (loaded a step ago) and loads the
+                // one after
                 uint32_t hx = (uint32_t)xh, ex = (uint32_t)xe;
                 asm volatile(
                     "{ .reg .pred p;\n\t"
-                    "setp.eq.u32 p, %5, 31;\n\t"
-                    "@p st.shared.v2.u32 [%2], {%0, %4};\n\t"
-                    "@p ld.shared.v2.u32 {%0, %1}, [%3]; }"
-                    : "+r"(hx), "+r"(ex)
-                    : "r"(bota + 8u * (uint32_t)j), "r"(topa + 8u * (uint32_t)j), "r"((uint32_t)stE), "r"(g)
+                    "setp.eq.u32 p, %7, 31;\n\t"
+                    "@p st.shared.v2.u32 [%4], {%0, %6};\n\t"
+                    "@p mov.b32 %0, %2;\n\t"
+                    "@p mov.b32 %1, %3;\n\t"
+                    "@p ld.shared.v2.u32 {%2, %3}, [%5]; }"
+                    : "+r"(hx), "+r"(ex), "+r"(ph), "+r"(pe)
+                    : "r"(bota + 8u * (uint32_t)j), "r"(topa + 8u * (uint32_t)(j + 1)), "r"((uint32_t)stE), "r"(g)
                     : "memory");
                 xh = (T)hx;
                 xe = (T)ex;
@@ -597,8 +652,8 @@ static size_t wave_dyn_smem(bool mat, int wr, int alphabet) {
     return mat ? (size_t)WAVE_SIG_BYTES + 8 * (size_t)alphabet * WG * wr : 0;
 }
 
-// Stripes per SM below which a launch takes 4-row stripes.
-constexpr int WAVE_THIN_STRIPES_PER_SM = 2;
+// Stripes for every four SMs from which a launch takes a taller stripe.
+constexpr int WAVE_MIN_STRIPES_PER_4_SMS = 3;
 
 template <int WR, bool TB, int MODE, bool TRI = false, bool MAT = false, bool SPLIT = false>
 static int blocks_per_sm(size_t dyn = 0) {
@@ -620,19 +675,19 @@ int wave_rows_per_lane(int64_t total_rows, int num_sms, int64_t n_passes, int mo
         wr = forced;
         if (best_all(mode) && wr == 16) wr = 8;   // the rows' maxima and columns take registers
         if (best_edge(mode) && wr == 8) wr = 16;  // its 8-row variant would spill
+    } else if (best_all(mode)) {
+        // local passes: the rows' maxima and columns make a short step cost relatively
+        // more (35,000-residue local pair: 6.5 ms at 8 rows, 7.2 at 4)
+        wr = 8;
     } else {
-        if (best_all(mode)) wr = 8;
-        else if (best_edge(mode)) wr = 16;
-        // 8-row stripes double the stripes (and the pipeline's skew) and run at 64
-        // registers; measured on 100 kbp to 1 Mbp pairs, 16-row stripes win unless
-        // the problem is tiny (a few stripes, as a single pair of a thousand rows)
-        else wr = 16 * stripes(16) <= (int64_t)num_sms * blocks_per_sm<16, false, GLOBAL>() * 8 ? 8 : 16;
-        // latency-bound pairs: with fewer than WAVE_THIN_STRIPES_PER_SM stripes per SM each
-        // warp's step is a chain nothing overlaps; 4-row stripes take a quarter of the
-        // cells per step and give four times the warps (100 kbp global: 41.8 -> 32.7 ms).
-        // Not in local passes, whose per-row maxima make a short step cost relatively
-        // more (35,000-residue local pair: 13.7 ms at 8 rows, 19.0 at 4)
-        if (!best_all(mode) && stripes(wr) < (int64_t)WAVE_THIN_STRIPES_PER_SM * num_sms) wr = 4;
+        // the tallest stripes that still give about three stripes for every four SMs:
+        // a stripe moves at the speed of its warp's chain, so taller stripes do more
+        // per step, and too few leave SMs idle (global pairs, ms at 16 / 8 / 4 rows:
+        // 35 kbp 5.65 / 5.05 / 5.91, 100 kbp 16.2 / 18.9 / 20.5)
+        const int64_t want = (int64_t)num_sms * WAVE_MIN_STRIPES_PER_4_SMS / 4;
+        if (stripes(16) >= want) wr = 16;
+        else if (!best_edge(mode) && stripes(8) >= want) wr = 8;
+        else wr = 4;
     }
     // traceback words hold 8 rows; the allocation-free scratch is sized for 8-row stripes
     if (min8 && wr < 8) wr = 8;
@@ -644,7 +699,9 @@ static void launch_one(const WaveArgs &A, int num_sms, cudaStream_t st) {
     const size_t dyn = wave_dyn_smem(MAT, WR, A.alphabet);
     int per_sm = blocks_per_sm<WR, TB, MODE, TRI, MAT, SPLIT>(dyn);
     if (A.ctas_per_sm > 0 && A.ctas_per_sm < per_sm) per_sm = A.ctas_per_sm;
-    wave_kernel<WR, TB, MODE, TRI, MAT, SPLIT><<<num_sms * per_sm, 256, dyn, st>>>(A);
+    WaveArgs B = A;
+    B.grid_sms = num_sms;
+    wave_kernel<WR, TB, MODE, TRI, MAT, SPLIT><<<num_sms * per_sm, 256, dyn, st>>>(B);
 }
 
 // 16-row stripes side by side per SM from which the 3-input-maximum cell wins

@@ -47,6 +47,8 @@ struct WaveArgs {
     const uint8_t *q8, *s8;
     const int8_t *sig;            // alphabet x alphabet bytes (device)
     int32_t sig_pad;              // sigma' of the padding rows above a pass
+    int32_t no_spread;            // 0: hold back first draws so that the first stripes land on distinct SMs
+    int32_t grid_sms;             // set by launch_wave: the SMs the grid was sized for
 };
 
 // Wavefront-only modes of the start-cell pass of a local or semi-global
@@ -62,16 +64,13 @@ __host__ __device__ constexpr int32_t wave_init_mode(int32_t mode) {
     return (mode == LOCAL || mode == SEMIGLOBAL) ? mode : GLOBAL;
 }
 
-// Rows per lane of a launch: 8 when 16-row stripes would fill less than a
-// sixteenth of the resident warps (twice the stripes, half the per-step chain
-// each), otherwise 16. total_rows = sum of the passes' row counts.
-// (Local modes: always 8; semi-global modes: always 16.) The stripe table of a launch
+// Rows per lane of a launch over total_rows rows (the sum of the passes' row
+// counts) in n_passes passes: the tallest stripes (16, 8, then 4 rows per lane)
+// that still give about three stripes for every four SMs; local passes always 8,
+// semi-global passes 16 or 4. forced (4, 8 or 16; 0: automatic) overrides the
+// choice within what each mode has; min8 keeps at least 8 (the traceback's
+// direction words, the allocation-free scratch). The stripe table of a launch
 // must be built with this value, and WaveArgs.rows_per_lane set to it.
-// Rows per lane of a launch over total_rows rows in n_passes passes: 16 or 8
-// by the stripe count (8 for local passes, 16 for semi-global ones), 4 when the
-// stripes would leave the SMs latency-bound. forced (4, 8 or 16; 0: automatic)
-// overrides the choice within what each mode has; min8 keeps at least 8 (the
-// traceback's direction words, the allocation-free scratch).
 int wave_rows_per_lane(int64_t total_rows, int num_sms, int64_t n_passes, int mode, int forced = 0, bool min8 = false);
 cudaError_t launch_wave(const WaveArgs &A, int num_sms, cudaStream_t st);
 constexpr int WAVE_LANES = 32;    // lanes per stripe

@@ -146,6 +146,36 @@ def test_bad_letter_is_rejected(pkg, ctx):
     assert ei.value.status == 2
 
 
+def test_bad_protein_letter_is_rejected(pkg, ctx):
+    """A code at or above a 20-letter alphabet, in the query or the subject, on
+    the matrix paths (batched score and traceback kernels, and the long-pair
+    wavefront): the kernels read a clamped letter (every shared-memory read
+    stays inside the profile) and the call fails with ANYSEQ_ERR_ALPHABET;
+    the context keeps working."""
+    mat = synth.protein_matrix(3)
+    sc = pkg.Scoring.make(0, 0, -11, -1, matrix=mat)
+    for which, code in (("q", 200), ("s", 255), ("s", 20)):
+        b = synth.random_pairs(64, 20, 300, alphabet=20, seed=702)
+        getattr(b, which)[157] = code
+        for want in (pkg.WANT_SCORE, pkg.WANT_SCORE | pkg.WANT_CIGAR):
+            cig = np.zeros(int(b.q_len().sum() + b.s_len().sum() + b.n_pairs), np.uint32)
+            with pytest.raises(pkg.AnyseqError) as ei:
+                ctx.align_batch(b.q, b.q_off, b.s, b.s_off, sc, 1, want=want, cigar=cig)
+            assert ei.value.status == 2, (which, code, want)
+    st = synth.Stream(703, 1)
+    q = synth.random_codes(st, 3000, 20)
+    s = synth.random_codes(st, 2500, 20)
+    s[1234] = 240
+    for mode in (0, 1, 2):
+        with pytest.raises(pkg.AnyseqError) as ei:
+            ctx.align_long(q, s, sc, mode=mode)
+        assert ei.value.status == 2
+    good = synth.random_pairs(16, 20, 100, alphabet=20, seed=704)
+    got = run(pkg, ctx, good, (0, 0, -11, -1, mat), 1)
+    want = oracle.score_batch(good, oracle.Scoring(0, 0, -11, -1, matrix=mat), 1)
+    assert np.array_equal(got["score"], want[0])
+
+
 def test_bad_arguments_are_rejected(pkg, ctx):
     b = synth.random_pairs(4, 5, 20, seed=701)
     sc = pkg.Scoring.make(1, -1, 2, -1)  # positive open

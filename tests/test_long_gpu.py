@@ -289,6 +289,31 @@ def test_wavefront_split_steps_match_oracle(pkg, ctx, split):
         ctx.set_option("wave_split", 0)
 
 
+@pytest.mark.parametrize("spread", [0, 1])
+@pytest.mark.parametrize("mode", [0, 1, 2])
+def test_wavefront_draw_order_matches_oracle(pkg, ctx, spread, mode):
+    """Stripes drawn in plain order and with held-back first draws (the first
+    stripes of a launch on distinct SMs) give the oracle's score, optimum
+    cell, start cell and linear-space CIGAR, on pairs of 1 to 47 four-row
+    stripes."""
+    ctx.set_option("wave_spread", spread)
+    ctx.set_option("wave_rows", 4)
+    try:
+        for k, (n, extra) in enumerate([(90, 2), (2500, -17), (6000, 9)]):
+            q, s = related(n, extra, seed=4400 + 10 * mode + k)
+            cig = np.zeros(len(q) + len(s) + 4, np.uint32)
+            out, used = ctx.align_long(q, s, pkg.Scoring.make(*C4), mode=mode,
+                                       want=pkg.WANT_SCORE | pkg.WANT_CIGAR, cigar=cig)
+            r = out[0]
+            got = (int(r["score"]), (int(r["beg_q"]), int(r["beg_s"])), (int(r["end_q"]), int(r["end_s"])))
+            S, beg, end, want = oracle.long_alignment(q, s, oracle.Scoring(*C4), mode)
+            assert got == (S, beg, end), (spread, mode, n, got, (S, beg, end))
+            assert np.array_equal(cig[:used], want), (spread, mode, n)
+    finally:
+        ctx.set_option("wave_rows", 0)
+        ctx.set_option("wave_spread", 1)
+
+
 PROTEIN = (0, 0, -11, -1)
 
 
