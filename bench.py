@@ -586,6 +586,31 @@ def profile_cigar(n_pairs: int):
     print(json.dumps({"profile_cigar": n_pairs, "cells": b.cells(), "dp_ms": ctx.stat("dp_ms"), "cigar_words": used}))
 
 
+def profile_band(n_pairs: int):
+    """The first n_pairs pairs of the band workload through the learned-band route
+    with a constant network (half-width 0.4 x the longer sequence), twice (a case
+    for ncu captures of the banded kernel)."""
+    import torch
+    import paper_2002_04561_gb300 as pkg
+    pkg.load(build_if_missing=True)
+    ctx = pkg.Context(0)
+    b = synth.band_pairs(n_pairs=n_pairs)
+    p = np.zeros(pkg.BAND_PARAMS, dtype=np.float32)
+    p[-1] = np.log(0.4)
+    ctx.band_model_set(p)
+    ctx.set_option("band_margin_pct", 100)
+    ctx.set_option("band_floor_pct", 0)
+    dev = lambda a: torch.from_numpy(np.ascontiguousarray(a)).cuda()
+    args = (dev(b.q), dev(b.q_off), dev(b.s), dev(b.s_off))
+    sc = pkg.Scoring.make(2, -3, -5, -2)
+    res = torch.zeros(b.n_pairs * 40, dtype=torch.uint8, device="cuda")
+    for _ in range(2):
+        ctx.align_batch(*args, sc, pkg.GLOBAL, want=pkg.WANT_SCORE | pkg.BAND_LEARNED, out=res)
+    torch.cuda.synchronize()
+    print(json.dumps({"profile_band": n_pairs, "band_cells": ctx.stat("band_cells"),
+                      "band_pass_ms": ctx.stat("band_pass_ms"), "accepted": ctx.stat("band_accepted")}))
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -601,6 +626,8 @@ def main():
                     help="profiling case: only the protein local scores of the first N pairs, twice")
     ap.add_argument("--profile-cigar", type=int, default=0, metavar="N",
                     help="profiling case: only the first N short reads with CIGAR, twice")
+    ap.add_argument("--profile-band", type=int, default=0, metavar="N",
+                    help="profiling case: only the first N band pairs through the banded route, twice")
     args = ap.parse_args()
     ws, rank, local = dist_env()
 
@@ -612,6 +639,9 @@ def main():
         return
     if args.profile_cigar:
         profile_cigar(args.profile_cigar)
+        return
+    if args.profile_band:
+        profile_band(args.profile_band)
         return
 
     if args.impl == "reference":

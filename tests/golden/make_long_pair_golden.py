@@ -7,7 +7,8 @@ pair has 1e12 DP cells, so the two oracle calls run as two processes side by
 side, each single-threaded: the linear-space score pass of Sec. III-A (score
 only, Fig. 1 right) and the Myers-Miller divide-and-conquer traceback (the
 linear-space traceback of Sec. III-A, about 2e12 cells). On one core of an
-x86 host at about 0.2 G cells/s this takes roughly three hours.
+x86 host the oracle relaxes about 0.1 G cells/s in the score pass and 0.13 G
+cells/s in the traceback, so this takes about four and a half hours.
 
 Run from the repository root:  python tests/golden/make_long_pair_golden.py
 """
