@@ -112,13 +112,15 @@ struct Runs {
 
 // One warp per pair: the walk from the optimum cell is sequential and every
 // step moves up or left, so the warp stages a window of direction words ahead of
-// the walker into shared memory (rows i-31..i, columns j-31..j: one load per
-// lane and row group of 8 rows, all independent) and lane 0 walks inside it;
-// leaving the window triggers the next load. This turns one dependent global
-// load per step into one per window.
-constexpr int TBW = 32;                  // window height and width (cells)
+// the walker into shared memory (rows i-63..i, columns j-63..j: each lane loads
+// the words of two columns, all issued before the first is stored, so a window
+// costs one global latency) and lane 0 walks inside it; leaving the window
+// triggers the next load. This turns one dependent global load per step into
+// one per window. (A 1,000 x 1,100 pair: 32 x 32 windows filled one word at a
+// time took 313 us.)
+constexpr int TBW = 64;                  // window height and width (cells)
 constexpr int TBG = TBW / 2 + 1;         // word units a window can touch (lanes of 2 rows at least)
-constexpr int TB_WARPS = 8;              // warps per block of the walk
+constexpr int TB_WARPS = 4;              // warps per block of the walk
 
 __global__ void __launch_bounds__(TB_WARPS * 32) tb_walk_kernel(TbWalkArgs W) {
     __shared__ uint32_t win[TB_WARPS][TBG][TBW];
@@ -154,13 +156,27 @@ __global__ void __launch_bounds__(TB_WARPS * 32) tb_walk_kernel(TbWalkArgs W) {
                 const int32_t i_lo = max(1, i - TBW + 1), j_lo = max(1, j - TBW + 1);
                 const int32_t rg_lo = tb_unit(L, tb_cursor(L, i_lo));  // word unit of the window's top row
                 if (i >= 1 && j >= 1) {
-                    const int32_t rg_hi = tb_unit(L, tb_cursor(L, i));
-                    const int32_t jj = j - lane, per_chunk = L.lpc * L.wpl;
-                    if (jj >= j_lo) {
-                        for (int32_t rg = rg_lo; rg <= rg_hi; rg++) {
-                            const int32_t rem = rg % per_chunk;
-                            wn[rg - rg_lo][lane] = dw[tb_word_index(L, rg / per_chunk, rem / L.wpl, rem % L.wpl, jj)];
+                    const int32_t nu = tb_unit(L, tb_cursor(L, i)) - rg_lo + 1;  // units of the window (<= TBG)
+                    const TbCursor c0 = tb_cursor(L, i_lo);
+#pragma unroll
+                    for (int half = 0; half < TBW / 32; half++) {
+                        const int32_t col = lane + 32 * half, jj = j - col;
+                        uint32_t v[TBG];
+                        int32_t ch = c0.ch, gl = c0.gl, sub = c0.rr >> 3;  // unit rg_lo, then upwards
+#pragma unroll
+                        for (int u = 0; u < TBG; u++) {
+                            v[u] = (u < nu && jj >= j_lo) ? dw[tb_word_index(L, ch, gl, sub, jj)] : 0u;
+                            if (++sub == L.wpl) {
+                                sub = 0;
+                                if (++gl == L.lpc) {
+                                    gl = 0;
+                                    ch++;
+                                }
+                            }
                         }
+#pragma unroll
+                        for (int u = 0; u < TBG; u++)
+                            if (u < nu) wn[u][col] = v[u];
                     }
                 }
                 __syncwarp();
