@@ -262,8 +262,8 @@ anyseq_status_t anyseq_get_stat(anyseq_ctx *ctx, const char *key, double *value)
  * memory of the current device, or a scoring whose values could leave the
  * 32-bit range on this pair (the same bound as anyseq_align_long).
  * No context is needed. The first call on a device resolves the array's device
- * address (once per device); make that first call before any stream capture.
- * The call returns after its stream has finished (it reads the error flags).
+ * address (once per device). The call returns after its stream has finished
+ * (it reads the error flags).
  * All calls share the array: calls that overlap on the GPU race on it.
  */
 #define ANYSEQ_NOALLOC_MAX_LEN 1048576
