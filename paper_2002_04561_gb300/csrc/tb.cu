@@ -182,13 +182,22 @@ __global__ void __launch_bounds__(TB_WARPS * 32) tb_walk_kernel(TbWalkArgs W) {
                 __syncwarp();
                 if (lane == 0) {
                     const int32_t jtop = j;  // the window's right column (j moves while walking)
-                    TbCursor cur = tb_cursor(L, i);  // row i; follows i downwards
-                    // the word of (i, jj) inside the window, r = its row bit
-                    auto word = [&](int32_t jj, int32_t &r) -> uint32_t {
-                        r = cur.rr & 7;
-                        return wn[tb_unit(L, cur) - rg_lo][jtop - jj];
+                    // row i's word unit (as a window row), its bit, and the window column of j,
+                    // all followed by increments: a move up leaves the unit only from a word's
+                    // first row, and units are numbered in row order
+                    TbCursor cur = tb_cursor(L, i);
+                    int32_t urow = tb_unit(L, cur) - rg_lo, r = cur.rr & 7, col = 0;
+                    auto up = [&]() {
+                        if (r == 0) {
+                            tb_up(L, cur);
+                            urow--;
+                            r = cur.rr & 7;
+                        } else {
+                            cur.rr--;
+                            r--;
+                        }
+                        i--;
                     };
-                    auto inside = [&](int32_t ii, int32_t jj) { return ii >= i_lo && jj >= j_lo && jj <= jtop; };
                     for (; guard > 0; guard--) {
                         if (state != 0 && (i <= 0 || j <= 0)) { done = true; break; }
                         if (state == 0) {
@@ -199,27 +208,31 @@ __global__ void __launch_bounds__(TB_WARPS * 32) tb_walk_kernel(TbWalkArgs W) {
                                 if (j == 0) { rl.push(1u, (uint32_t)i); i = 0; done = true; break; }
                                 if (i == 0) { rl.push(2u, (uint32_t)j); j = 0; done = true; break; }
                             }
-                            if (!inside(i, j)) break;  // next window
-                            int32_t r;
-                            const uint32_t w = word(j, r);
-                            const uint32_t s0 = (w >> r) & 1u, s1 = (w >> (8 + r)) & 1u;
-                            if (W.mode == LOCAL && s0 && s1) { done = true; break; }  // H = 0: the alignment starts here
-                            if (s0) { rl.push(0u, 1u); i--; j--; tb_up(L, cur); }
-                            else state = s1 ? 1 : 2;
-                        } else {
-                            if (!inside(i, j)) break;
-                            int32_t r;
-                            const uint32_t w = word(j, r);
-                            if (state == 1) {
-                                rl.push(1u, 1u);
-                                if ((w >> (16 + r)) & 1u) state = 0;
-                                i--;
-                                tb_up(L, cur);
-                            } else {
-                                rl.push(2u, 1u);
-                                if ((w >> (24 + r)) & 1u) state = 0;
+                        }
+                        if (i < i_lo || j < j_lo) break;  // next window
+                        // (i, j)'s bits at positions 0 (s0), 8 (s1), 16 (E opened), 24 (F opened)
+                        const uint32_t w = wn[urow][col] >> r;
+                        if (state == 0) {
+                            if (W.mode == LOCAL && (w & 0x101u) == 0x101u) { done = true; break; }  // H = 0: the start
+                            if (w & 1u) {
+                                rl.push(0u, 1u);
+                                up();
                                 j--;
+                                col++;
+                                continue;
                             }
+                            // H from E or F: take that gap's step from the same cell now
+                            state = (w & 0x100u) ? 1 : 2;
+                        }
+                        if (state == 1) {
+                            rl.push(1u, 1u);
+                            if ((w >> 16) & 1u) state = 0;
+                            up();
+                        } else {
+                            rl.push(2u, 1u);
+                            if ((w >> 24) & 1u) state = 0;
+                            j--;
+                            col++;
                         }
                     }
                     if (guard <= 0) done = true;
