@@ -122,6 +122,33 @@ constexpr int TBW = 64;                  // window height and width (cells)
 constexpr int TBG = TBW / 2 + 1;         // word units a window can touch (lanes of 2 rows at least)
 constexpr int TB_WARPS = 4;              // warps per block of the walk
 
+// Stage one window: each lane loads units 0..nu-1 (from the window's top row up)
+// of its two columns j - lane and j - lane - 32, all loads before any store.
+template <int MU>
+__device__ __forceinline__ void stage_window(const TbLayout &L, const uint32_t *dw, const TbCursor &c0, int32_t nu,
+                                             int32_t j, int32_t j_lo, int lane, uint32_t (*wn)[TBW]) {
+#pragma unroll
+    for (int half = 0; half < TBW / 32; half++) {
+        const int32_t col = lane + 32 * half, jj = j - col;
+        uint32_t v[MU];
+        int32_t ch = c0.ch, gl = c0.gl, sub = c0.rr >> 3;  // the window's first unit, then upwards
+#pragma unroll
+        for (int u = 0; u < MU; u++) {
+            v[u] = (u < nu && jj >= j_lo) ? dw[tb_word_index(L, ch, gl, sub, jj)] : 0u;
+            if (++sub == L.wpl) {
+                sub = 0;
+                if (++gl == L.lpc) {
+                    gl = 0;
+                    ch++;
+                }
+            }
+        }
+#pragma unroll
+        for (int u = 0; u < MU; u++)
+            if (u < nu) wn[u][col] = v[u];
+    }
+}
+
 __global__ void __launch_bounds__(TB_WARPS * 32) tb_walk_kernel(TbWalkArgs W) {
     __shared__ uint32_t win[TB_WARPS][TBG][TBW];
     const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
@@ -158,26 +185,10 @@ __global__ void __launch_bounds__(TB_WARPS * 32) tb_walk_kernel(TbWalkArgs W) {
                 if (i >= 1 && j >= 1) {
                     const int32_t nu = tb_unit(L, tb_cursor(L, i)) - rg_lo + 1;  // units of the window (<= TBG)
                     const TbCursor c0 = tb_cursor(L, i_lo);
-#pragma unroll
-                    for (int half = 0; half < TBW / 32; half++) {
-                        const int32_t col = lane + 32 * half, jj = j - col;
-                        uint32_t v[TBG];
-                        int32_t ch = c0.ch, gl = c0.gl, sub = c0.rr >> 3;  // unit rg_lo, then upwards
-#pragma unroll
-                        for (int u = 0; u < TBG; u++) {
-                            v[u] = (u < nu && jj >= j_lo) ? dw[tb_word_index(L, ch, gl, sub, jj)] : 0u;
-                            if (++sub == L.wpl) {
-                                sub = 0;
-                                if (++gl == L.lpc) {
-                                    gl = 0;
-                                    ch++;
-                                }
-                            }
-                        }
-#pragma unroll
-                        for (int u = 0; u < TBG; u++)
-                            if (u < nu) wn[u][col] = v[u];
-                    }
+                    // lanes of 8 rows or more (the wavefront's layout, most batched items)
+                    // touch at most TBW / 8 + 1 units: a short unrolled copy for them
+                    if (nu <= TBW / 8 + 1) stage_window<TBW / 8 + 1>(L, dw, c0, nu, j, j_lo, lane, wn);
+                    else stage_window<TBG>(L, dw, c0, nu, j, j_lo, lane, wn);
                 }
                 __syncwarp();
                 if (lane == 0) {
