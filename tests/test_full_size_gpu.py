@@ -1,9 +1,11 @@
 """Parity at the full sizes the benchmark times, on GPU:
 
-* the 1 Mbp x 1 Mbp global affine pair (1e12 cells, beyond the oracle): the
-  divide-and-conquer CIGAR consumes both sequences and re-scores exactly to the
-  wavefront's score, which equals the allocation-free entry point's score; a
-  20 kbp pair of the same generator matches the oracle bit for bit;
+* the 1 Mbp x 1 Mbp global affine pair (1e12 cells): the wavefront score and
+  the divide-and-conquer CIGAR equal, word for word, the oracle's score and
+  Myers-Miller CIGAR stored in tests/golden/long_pair_1mbp.json (written by
+  tests/golden/make_long_pair_golden.py, which calls only the oracle); the
+  CIGAR also consumes both sequences and re-scores to the score, which the
+  allocation-free entry point reproduces;
 * the 65,536 learned-band pairs of 1-10 kbp: the banded route's scores equal
   the full DP's on every pair (the certificate is exact), and a sample of the
   full DP equals the oracle;
@@ -43,9 +45,23 @@ def ctx(pkg):
     c.close()
 
 
-def test_long_pair_1mbp_cigar_rescores_to_wavefront_score(pkg, ctx):
+def _long_pair_golden():
+    import hashlib
+    import json
+    import os
+    with open(os.path.join(os.path.dirname(__file__), "golden", "long_pair_1mbp.json")) as f:
+        g = json.load(f)
+    digest = lambda a: hashlib.sha256(np.ascontiguousarray(a, dtype=np.uint8).tobytes()).hexdigest()
+    return g, digest
+
+
+def test_long_pair_1mbp_equals_the_oracle(pkg, ctx):
+    golden, digest = _long_pair_golden()
     b = synth.long_pair()
     q, s = b.pair(0)
+    # the stored values belong to exactly these letters
+    assert (digest(q), digest(s)) == (golden["q_sha256"], golden["s_sha256"])
+    assert (golden["n"], golden["m"]) == (len(q), len(s))
     sc = pkg.Scoring.make(*C4)
     qd, sd = torch.from_numpy(q).cuda(), torch.from_numpy(s).cuda()
     res, _ = ctx.align_long(qd, sd, sc)
@@ -55,14 +71,13 @@ def test_long_pair_1mbp_cigar_rescores_to_wavefront_score(pkg, ctx):
     assert int(r2["score"][0]) == score
     got, eq, es = rescore_cigar(cig[:used], q, s, (0, 0), oracle.Scoring(*C4))
     assert (got, eq, es) == (score, len(q), len(s))
+    assert score == golden["score"]
+    assert oracle.cigar_string(cig[:used]) == golden["cigar"]
+    assert used == golden["cigar_words"]
     out = torch.zeros(1, dtype=torch.int32, device="cuda")
     pkg.align_long_noalloc(qd, sd, sc, out)
     torch.cuda.synchronize()
     assert int(out.item()) == score
-    small = synth.long_pair(n=20_000, inversion=400)
-    qs, ss = small.pair(0)
-    r3, _ = ctx.align_long(qs, ss, sc)
-    assert int(r3["score"][0]) == oracle.score(qs, ss, oracle.Scoring(*C4))[0]
 
 
 def test_band_workload_full_size_scores_equal_full_dp(pkg, ctx):

@@ -337,3 +337,41 @@ def test_long_alignment_agrees_with_full_traceback(mode):
         assert (S, end) == (S2, end2)
         assert rescore_cigar(cig, q, s, beg, sc) == (S, end[0], end[1])
         assert rescore_cigar(cig2, q, s, beg2, sc) == (S2, end2[0], end2[1])
+
+
+def test_long_pair_golden_is_self_consistent():
+    """The stored 1 Mbp record (written by tests/golden/make_long_pair_golden.py
+    from two separate oracle computations: the linear-space score pass and the
+    Myers-Miller traceback, Sec. III-A) belongs to the generator's letters, its
+    CIGAR consumes both sequences and re-scores (Eqs. 1-5, affine gaps of
+    length L costing open + L * extend) to the stored score, and the traceback
+    relaxed at most twice the matrix's cells."""
+    import hashlib
+    import re
+    with open(os.path.join(os.path.dirname(__file__), "golden", "long_pair_1mbp.json")) as f:
+        g = json.load(f)
+    q, s = synth.long_pair().pair(0)
+    digest = lambda a: hashlib.sha256(np.ascontiguousarray(a, dtype=np.uint8).tobytes()).hexdigest()
+    assert (digest(q), digest(s)) == (g["q_sha256"], g["s_sha256"])
+    assert (g["n"], g["m"]) == (len(q), len(s)) and g["end"] == [len(q), len(s)]
+    sc = g["scoring"]
+    runs = [(int(k), op) for k, op in re.findall(r"(\d+)([MID])", g["cigar"])]
+    assert len(runs) == g["cigar_words"]
+    assert "".join(f"{k}{op}" for k, op in runs) == g["cigar"]
+    i = j = 0
+    score = 0
+    for k, op in runs:
+        if op == "M":
+            same = int(np.count_nonzero(q[i:i + k] == s[j:j + k]))
+            score += sc["match"] * same + sc["mismatch"] * (k - same)
+            i += k
+            j += k
+        else:
+            score += sc["gap_open"] + k * sc["gap_extend"]
+            if op == "I":
+                i += k
+            else:
+                j += k
+    assert (i, j) == (len(q), len(s))
+    assert score == g["score"]
+    assert len(q) * len(s) <= g["cells_relaxed"] <= 2 * len(q) * len(s)
