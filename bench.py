@@ -494,10 +494,13 @@ def secondary_workloads(pkg, ctx, device):
     ms_full = timed_events(lambda: ctx.align_batch(*args, sc, pkg.GLOBAL, out=full), 2, stream)
     ms_band = timed_events(lambda: ctx.align_batch(*args, sc, pkg.GLOBAL, want=1 | pkg.BAND_LEARNED, out=band), 2,
                            stream)
+    band_pass_cells = float(ctx.stat("band_cells"))  # cells of the last call's banded pass
     fr = full.cpu().numpy().view(pkg.RESULT_DTYPE)
     br = band.cpu().numpy().view(pkg.RESULT_DTYPE)
     accepted = int(((br["flags"] & pkg.FLAG_BAND_ACCEPTED) != 0).sum())
-    fallback = int(((br["flags"] & pkg.FLAG_FULL_FALLBACK) != 0).sum())
+    fb = (br["flags"] & pkg.FLAG_FULL_FALLBACK) != 0
+    fallback = int(fb.sum())
+    fallback_cells = float((b.q_len().astype(np.float64) * b.s_len())[fb].sum())
     # the same route without the network: constant outputs (centre 0, one half-width
     # relative to the longer sequence)
     learned = ctx.band_model_get()
@@ -522,7 +525,13 @@ def secondary_workloads(pkg, ctx, device):
         "band_accepted": accepted, "full_dp_fallback": fallback, "certified_share": accepted / b.n_pairs,
         "constant_band_ms": const, "speedup_over_best_constant_band": best_const / ms_band,
         "speedup_over_prior_constant_band": const["0.25"]["ms"] / ms_band,
-        "full_dp_GCUPS": b.cells() / ms_full / 1e6, "train_s": train_s, "train_loss": loss,
+        "full_dp_GCUPS": b.cells() / ms_full / 1e6,
+        # the learned route as full-DP-equivalent cells per second, and as the cells it
+        # relaxed (banded pass plus the fallback pairs' full DP) per second
+        "learned_band_full_dp_equivalent_GCUPS": b.cells() / ms_band / 1e6,
+        "learned_band_true_GCUPS": (band_pass_cells + fallback_cells) / ms_band / 1e6,
+        "learned_band_cells": band_pass_cells + fallback_cells,
+        "train_s": train_s, "train_loss": loss,
         "cpu_oracle_full_dp": oracle_sample(b, (2, -3, -5, -2), 0)}
     # serving: Poisson arrivals through the native request queue
     out["serving_mix_6000_global_affine"] = serving_workload(pkg)
