@@ -46,13 +46,13 @@ struct anyseq_ctx {
     uint8_t *d_tune_tab = nullptr;
     unsigned long long *d_bin_stats = nullptr;
     bool tuned = false;
-    double tune_gain = 1.0;
+    double tune_gain = 1.0;       // default time / tuned time on the tuning sample
     int32_t tb_walker = 0;  // traceback walk: 0 by batch size, 1 a warp per pair, 2 a thread per pair
     int32_t wave_split = 0;  // global three-input-maximum wavefront: 0 by stripe count, 1 split steps, 2 plain
     int32_t wave_spread = 1;       // wavefront: first stripes of a launch on distinct SMs
     int32_t wave_ctas_per_sm = 0;  // wavefront CTAs per SM: 0 as many as fit (the serving long lane uses 1)
     int32_t wave_rows = 0;  // wavefront rows per lane: 0 automatic, or 4, 8, 16 (within what each mode has)
-    int32_t wave_cell = 0;  // wavefront cell of global passes: 0 by stripe count, 1 three-input max, 2 two-step  // default time / tuned time on the tuning sample
+    int32_t wave_cell = 0;  // wavefront cell of global passes: 0 by stripe count, 1 three-input max, 2 two-step
     std::vector<Buf> bufs;        // device scratch, grown on demand, reused across calls
     std::vector<Buf> pinned;      // pinned host staging
     // Named device buffer of at least 'bytes'; contents are not preserved on growth.
