@@ -112,6 +112,11 @@ anyseq_status_t anyseq_destroy(anyseq_ctx *ctx);
  *                 out[p].cigar_off; *cigar_used (host) receives the total. Too small a buffer
  *                 returns ANYSEQ_ERR_CAPACITY with *cigar_used = words needed; NULL/0 allowed otherwise.
  *   cuda_stream   cudaStream_t (NULL = legacy default stream)
+ * Any pointer may be host or device memory. Host letters in pinned memory of a
+ * 2-bit alphabet (at most 4 letters) are read in place by the device over the
+ * host link (option "host_in_place", default 1; 0 copies them first); other host
+ * letters are copied. Either way the host buffers must stay unchanged until the
+ * call's work on cuda_stream has finished, as with any asynchronous copy.
  * Errors: ERR_ARG (null pointers, decreasing offsets, open/extend > 0, alphabet out of
  * range, mode unknown, a pair of 2^21 letters or more, and in local and
  * semi-global mode a pair whose score could reach 2^21: largest positive
@@ -228,7 +233,9 @@ anyseq_status_t anyseq_band_train(anyseq_ctx *ctx, const uint8_t *q, const int64
  * for other kernels beside a long pair (results are the same); "wave_spread"
  * (default 1) holds back the first stripe draws of a wavefront launch so that
  * its first stripes land on distinct SMs, 0 takes them in plain draw order
- * (results are the same); "tb_walker"
+ * (results are the same); "host_in_place" (default 1) lets 2-bit batches read
+ * pinned host letters in place, 0 copies them to the device first (results are
+ * the same); "tb_walker"
  * (default 0) picks the
  * batched traceback walk: 0 by batch size, 1 a warp per pair (staged windows),
  * 2 a thread per pair (results are the same). Unknown keys: ANYSEQ_ERR_ARG. */

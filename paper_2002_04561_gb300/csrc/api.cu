@@ -135,6 +135,11 @@ extern "C" anyseq_status_t anyseq_set_option(anyseq_ctx *ctx, const char *key, i
         ctx->wave_split = (int32_t)value;
         return ANYSEQ_OK;
     }
+    if (!strcmp(key, "host_in_place")) {
+        if (value != 0 && value != 1) return fail(ANYSEQ_ERR_ARG, "host_in_place must be 0 or 1");
+        ctx->host_in_place = (int)value;
+        return ANYSEQ_OK;
+    }
     if (!strcmp(key, "wave_spread")) {
         if (value != 0 && value != 1) return fail(ANYSEQ_ERR_ARG, "wave_spread must be 0 or 1");
         ctx->wave_spread = (int32_t)value;
@@ -514,8 +519,21 @@ anyseq_status_t anyseq::batch_scores(anyseq_ctx *ctx, const BatchInput &in, cons
     return ANYSEQ_OK;
 }
 
+// The device address of pinned host memory that kernels can read in place (a
+// mapped allocation in the unified address space), or nullptr.
+static const void *mapped_host_ptr(const void *p) {
+    if (!p) return nullptr;
+    cudaPointerAttributes at;
+    if (cudaPointerGetAttributes(&at, p) != cudaSuccess) {
+        cudaGetLastError();
+        return nullptr;
+    }
+    return at.type == cudaMemoryTypeHost ? at.devicePointer : nullptr;
+}
+
 anyseq_status_t anyseq::stage_batch(anyseq_ctx *ctx, const uint8_t *q, const int64_t *q_off, const uint8_t *s,
-                                    const int64_t *s_off, int64_t n_pairs, BatchInput &in, cudaStream_t st) {
+                                    const int64_t *s_off, int64_t n_pairs, BatchInput &in, cudaStream_t st,
+                                    bool read_in_place) {
     anyseq_status_t s2 = ANYSEQ_OK;
     in.n_pairs = n_pairs;
     const void *dq_off, *ds_off;
@@ -545,9 +563,13 @@ anyseq_status_t anyseq::stage_batch(anyseq_ctx *ctx, const uint8_t *q, const int
     in.q_len = hstats[4];
     in.s_len = hstats[5];
     if ((in.q_len > 0 && !q) || (in.s_len > 0 && !s)) return fail(ANYSEQ_ERR_ARG, "q or s is NULL");
-    const void *dq, *ds;
-    TRY(stage_input(ctx, "in_q", q, (size_t)in.q_len, st, &dq));
-    TRY(stage_input(ctx, "in_s", s, (size_t)in.s_len, st, &ds));
+    // Letters in pinned host memory whose only reader is the 2-bit packing kernel stay
+    // where they are: the kernel reads them over the host link as it packs them, in
+    // place of a separate copy followed by a pass over device memory.
+    const void *dq = read_in_place && in.q_len > 0 ? mapped_host_ptr(q) : nullptr;
+    const void *ds = read_in_place && in.s_len > 0 ? mapped_host_ptr(s) : nullptr;
+    if (!dq) TRY(stage_input(ctx, "in_q", q, (size_t)in.q_len, st, &dq));
+    if (!ds) TRY(stage_input(ctx, "in_s", s, (size_t)in.s_len, st, &ds));
     in.q = (const uint8_t *)dq;
     in.s = (const uint8_t *)ds;
 
@@ -572,7 +594,8 @@ extern "C" anyseq_status_t anyseq_align_batch(anyseq_ctx *ctx, const uint8_t *q,
     // offsets: stage, then read totals and maxima
     ctx->launches = 0;
     BatchInput in;
-    TRY(stage_batch(ctx, q, q_off, s, s_off, n_pairs, in, st));
+    TRY(stage_batch(ctx, q, q_off, s, s_off, n_pairs, in, st,
+                    ctx->host_in_place && sc->alphabet <= 4 && !ctx->force_matrix));
     if (mode != ANYSEQ_GLOBAL && !key_range_ok(sc, in.max_min))
         return fail(ANYSEQ_ERR_ARG, "local / semi-global scores of a pair may reach 2^21 (the optimum key's range)");
 

@@ -34,6 +34,7 @@ struct anyseq_ctx {
     int32_t band_margin_pct = 65;    // the network's half-width times this / 100 is the band used
     int32_t band_floor_pct = 20;     // ... but at least this share (%) of the longer sequence
     int profile = 0;              // time the DP kernels with events
+    int host_in_place = 1;        // 2-bit batches: pinned host letters read in place by the packing kernel
     cudaEvent_t ev[4] = {nullptr, nullptr, nullptr, nullptr};
     // statistics of the last call
     int64_t launches = 0;
@@ -104,8 +105,12 @@ anyseq_status_t wave_batch(anyseq_ctx *ctx, const BatchInput &in, const anyseq_s
 anyseq_status_t long_pairs_split(anyseq_ctx *ctx, const BatchInput &in, const anyseq_scoring_t *sc, int32_t mode,
                                  int32_t *score, int32_t *eq, int32_t *es, uint32_t *flags, cudaStream_t st,
                                  BatchInput &rest, bool *all_done);
+// read_in_place: letters in pinned (mapped) host memory are left there for the
+// device to read through the host link (callers whose only letter reader is the
+// 2-bit packing kernel)
 anyseq_status_t stage_batch(anyseq_ctx *ctx, const uint8_t *q, const int64_t *q_off, const uint8_t *s,
-                            const int64_t *s_off, int64_t n_pairs, BatchInput &in, cudaStream_t st);
+                            const int64_t *s_off, int64_t n_pairs, BatchInput &in, cudaStream_t st,
+                            bool read_in_place = false);
 anyseq_status_t band_scores(anyseq_ctx *ctx, const BatchInput &in, const anyseq_scoring_t *sc, int32_t *score,
                             int32_t *eq, int32_t *es, uint32_t *flags, cudaStream_t st);
 bool long_range_ok(const anyseq_scoring_t *sc, int64_t n, int64_t m);

@@ -138,6 +138,36 @@ def test_host_buffers_match_device_buffers(pkg, ctx):
         assert np.array_equal(a["score"], h["score"]) and np.array_equal(a["end_s"], h["end_s"])
 
 
+@pytest.mark.parametrize("in_place", [0, 1])
+def test_pinned_host_letters_read_in_place_or_copied(pkg, ctx, in_place):
+    """Host letters in pinned memory, read in place by the packing kernel or
+    copied first, give the device-input results and the oracle's, for short
+    reads in all three modes (2-bit path) and for a 20-letter batch (always
+    copied)."""
+    b = synth.random_pairs(3000, 0, 300, seed=710, related=0.7)
+    pin = lambda a: torch.from_numpy(np.ascontiguousarray(a)).pin_memory()
+    ctx.set_option("host_in_place", in_place)
+    try:
+        for mode in (0, 1, 2):
+            sc = pkg.Scoring.make(2, -3, -5, -2)
+            hout = torch.zeros(b.n_pairs * 40, dtype=torch.uint8).pin_memory()
+            ctx.align_batch(pin(b.q), pin(b.q_off), pin(b.s), pin(b.s_off), sc, mode, out=hout)
+            got = hout.numpy().view(pkg.RESULT_DTYPE)
+            dres = run(pkg, ctx, b, (2, -3, -5, -2), mode)
+            assert np.array_equal(got["score"], dres["score"]) and np.array_equal(got["end_s"], dres["end_s"])
+            want = oracle.score_batch(b, oracle.Scoring(2, -3, -5, -2), mode)
+            assert np.array_equal(got["score"], want[0]), mode
+        p = synth.random_pairs(500, 20, 200, alphabet=20, seed=711)
+        mat = synth.protein_matrix(3)
+        hout = torch.zeros(p.n_pairs * 40, dtype=torch.uint8).pin_memory()
+        ctx.align_batch(pin(p.q), pin(p.q_off), pin(p.s), pin(p.s_off), pkg.Scoring.make(0, 0, -11, -1, matrix=mat),
+                        1, out=hout)
+        want = oracle.score_batch(p, oracle.Scoring(0, 0, -11, -1, matrix=mat), 1)
+        assert np.array_equal(hout.numpy().view(pkg.RESULT_DTYPE)["score"], want[0])
+    finally:
+        ctx.set_option("host_in_place", 1)
+
+
 def test_bad_letter_is_rejected(pkg, ctx):
     b = synth.random_pairs(10, 5, 20, seed=700)
     b.q[3] = 7
