@@ -209,18 +209,27 @@ __global__ void __launch_bounds__(TB_WARPS * 32) tb_walk_kernel(TbWalkArgs W) {
                         }
                         i--;
                     };
-                    for (; guard > 0; guard--) {
-                        if (state != 0 && (i <= 0 || j <= 0)) { done = true; break; }
-                        if (state == 0) {
-                            if (i == 0 && j == 0) { done = true; break; }
-                            if (W.mode != GLOBAL) {
-                                if (i == 0 || j == 0) { done = true; break; }
-                            } else {
-                                if (j == 0) { rl.push(1u, (uint32_t)i); i = 0; done = true; break; }
-                                if (i == 0) { rl.push(2u, (uint32_t)j); j = 0; done = true; break; }
-                            }
+                    // the matrix's first row or column ends the walk; a window starts at
+                    // rows and columns from 1, so inside one only its edges need a test
+                    if (state != 0 && (i <= 0 || j <= 0)) {
+                        done = true;
+                    } else if (state == 0) {
+                        if (i == 0 && j == 0) {
+                            done = true;
+                        } else if (W.mode != GLOBAL) {
+                            if (i == 0 || j == 0) done = true;
+                        } else if (j == 0) {
+                            rl.push(1u, (uint32_t)i);
+                            i = 0;
+                            done = true;
+                        } else if (i == 0) {
+                            rl.push(2u, (uint32_t)j);
+                            j = 0;
+                            done = true;
                         }
-                        if (i < i_lo || j < j_lo) break;  // next window
+                    }
+                    for (; !done && guard > 0; guard--) {
+                        if (i < i_lo || j < j_lo) break;  // next window (or the first row or column)
                         // (i, j)'s bits at positions 0 (s0), 8 (s1), 16 (E opened), 24 (F opened)
                         const uint32_t w = wn[urow][col] >> r;
                         if (state == 0) {
@@ -246,7 +255,7 @@ __global__ void __launch_bounds__(TB_WARPS * 32) tb_walk_kernel(TbWalkArgs W) {
                             col++;
                         }
                     }
-                    if (guard <= 0) done = true;
+                    if (!done && guard <= 0) done = true;
                 }
                 __syncwarp();
                 i = __shfl_sync(0xffffffffu, i, 0);
