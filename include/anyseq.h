@@ -228,7 +228,7 @@ anyseq_status_t anyseq_band_train(anyseq_ctx *ctx, const uint8_t *q, const int64
  * "wave_rows" (default 0) sets the
  * wavefront's rows per lane (4, 8 or 16; 0 chooses by the number of stripes,
  * within what each mode has: local passes at most 8, semi-global 4 or 16,
- * traceback passes 8 or 16; results are the same); "wave_ctas_per_sm"
+ * traceback passes 4, 8 or 16; results are the same); "wave_ctas_per_sm"
  * (default 0: as many as fit) caps the wavefront's CTAs per SM, leaving room
  * for other kernels beside a long pair (results are the same); "wave_spread"
  * (default 1) holds back the first stripe draws of a wavefront launch so that

@@ -253,7 +253,7 @@ anyseq_status_t run_wave_passes(anyseq_ctx *ctx, const uint32_t *q2, const uint3
     anyseq_status_t s2st = ANYSEQ_OK;
     int64_t border = 0, rows = 0;
     for (const auto &p : passes) rows += p.n;
-    const int wr = wave_rows_per_lane(rows, ctx->num_sms, (int64_t)passes.size(), mode, ctx->wave_rows, tb != nullptr);
+    const int wr = wave_rows_per_lane(rows, ctx->num_sms, (int64_t)passes.size(), mode, ctx->wave_rows, false);
     const int stripe_rows = WAVE_LANES * wr;
     int32_t stripes = 0;
     int64_t dir_words = 0;
@@ -264,7 +264,7 @@ anyseq_status_t run_wave_passes(anyseq_ctx *ctx, const uint32_t *q2, const uint3
         const int32_t ns = (p.n + stripe_rows - 1) / stripe_rows;
         stripes += ns;
         p.dir_off = dir_words;
-        if (tb) dir_words += (int64_t)ns * (p.m + WAVE_LANES - 1) * WAVE_LANES * (wr / 8);
+        if (tb) dir_words += (int64_t)ns * (p.m + WAVE_LANES - 1) * WAVE_LANES * ((wr + 7) / 8);
     }
     WaveArgs W;
     memset(&W, 0, sizeof(W));

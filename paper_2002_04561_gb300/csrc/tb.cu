@@ -185,9 +185,11 @@ __global__ void __launch_bounds__(TB_WARPS * 32) tb_walk_kernel(TbWalkArgs W) {
                 if (i >= 1 && j >= 1) {
                     const int32_t nu = tb_unit(L, tb_cursor(L, i)) - rg_lo + 1;  // units of the window (<= TBG)
                     const TbCursor c0 = tb_cursor(L, i_lo);
-                    // lanes of 8 rows or more (the wavefront's layout, most batched items)
-                    // touch at most TBW / 8 + 1 units: a short unrolled copy for them
+                    // lanes of 8 rows or more (most batched items, the wavefront's 8- and
+                    // 16-row layouts) touch at most TBW / 8 + 1 units, lanes of 4 rows
+                    // TBW / 4 + 1: shorter unrolled copies for them
                     if (nu <= TBW / 8 + 1) stage_window<TBW / 8 + 1>(L, dw, c0, nu, j, j_lo, lane, wn);
+                    else if (nu <= TBW / 4 + 1) stage_window<TBW / 4 + 1>(L, dw, c0, nu, j, j_lo, lane, wn);
                     else stage_window<TBG>(L, dw, c0, nu, j, j_lo, lane, wn);
                 }
                 __syncwarp();

@@ -86,7 +86,8 @@ __global__ void __launch_bounds__(256, 2) wave_kernel(WaveArgs A) {
     constexpr int INIT = wave_init_mode(MODE);
     constexpr bool ALL = best_all(MODE), EDGE = best_edge(MODE);
     constexpr int WCH = WG * WR;  // rows per stripe
-    static_assert(!TB || WR % 8 == 0, "direction words hold 8 rows");
+    static_assert(!TB || WR == 4 || WR % 8 == 0, "direction words hold 8 rows (4 in the low half of each byte)");
+    constexpr int WPL = (WR + 7) / 8;  // direction words per lane and step
     static_assert(!TB || MODE == GLOBAL, "traceback on the wavefront is global");
     static_assert(!(TB && MAT), "the wavefront's traceback variant takes 2-bit letters");
     static_assert(!SPLIT || (WR == 16 && TRI && MODE == GLOBAL && !TB && !MAT),
@@ -201,7 +202,7 @@ __global__ void __launch_bounds__(256, 2) wave_kernel(WaveArgs A) {
         int32_t *prog_mine = A.prog + t;
         bool failed = false;
         // this stripe's direction words: [step][lane][WR / 8]
-        uint32_t *dw = TB ? A.dirs + ps.dir_off + (int64_t)k * S * WG * (WR / 8) + g * (WR / 8) : nullptr;
+        uint32_t *dw = TB ? A.dirs + ps.dir_off + (int64_t)k * S * WG * WPL + g * WPL : nullptr;
 
         // wait until the previous stripe published border block blk (bounded)
         // The previous stripe's progress last seen (warp-uniform): blocks below it were
@@ -436,10 +437,12 @@ __global__ void __launch_bounds__(256, 2) wave_kernel(WaveArgs A) {
                         pl_eo = (pl_eo >> 1) | (fEo & FM);
                         pl_fo = (pl_fo >> 1) | (fFo & FM);
                         hup = Hoe[r];
-                        if ((r & 7) == 7) {
-                            // rows r-7..r: bytes s0, s1, E opened, F opened (bit k = row r-7+k)
-                            dw[(int64_t)s * WG * (WR / 8) + (r >> 3)] =
-                                prmt(prmt(pl_s0, pl_s1, 0x7351u), prmt(pl_eo, pl_fo, 0x7351u), 0x7632u);
+                        if ((r & 7) == 7 || r == WR - 1) {
+                            // rows (r & ~7)..r: bytes s0, s1, E opened, F opened (bit k = row
+                            // (r & ~7) + k); a word of fewer than 8 rows shifts them down to bit 0
+                            const int sh = 7 - (r & 7);
+                            dw[(int64_t)s * WG * WPL + (r >> 3)] =
+                                prmt(prmt(pl_s0 >> sh, pl_s1 >> sh, 0x7351u), prmt(pl_eo >> sh, pl_fo >> sh, 0x7351u), 0x7632u);
                         }
                     }
                 }
@@ -689,7 +692,7 @@ int wave_rows_per_lane(int64_t total_rows, int num_sms, int64_t n_passes, int mo
         else if (!best_edge(mode) && stripes(8) >= want) wr = 8;
         else wr = 4;
     }
-    // traceback words hold 8 rows; the allocation-free scratch is sized for 8-row stripes
+    // the allocation-free scratch is sized for 8-row stripes
     if (min8 && wr < 8) wr = 8;
     return wr;
 }
@@ -720,7 +723,7 @@ cudaError_t launch_wave(const WaveArgs &A, int num_sms, cudaStream_t st) {
                      (A.cell == 1 || (A.cell == 0 && (int64_t)A.n_stripes >= (int64_t)WAVE_TRI_STRIPES_PER_SM * num_sms));
     // the stripe table was built for A.rows_per_lane (from wave_rows_per_lane)
     const int wr = A.rows_per_lane;
-    if (tb && wr != 8 && wr != 16) return cudaErrorInvalidValue;
+    if (tb && wr != 4 && wr != 8 && wr != 16) return cudaErrorInvalidValue;
     if (A.mode != GLOBAL && (tb || (wr != 4 && wr != (best_all(A.mode) ? 8 : 16)))) return cudaErrorInvalidValue;
     if (A.mode == GLOBAL && wr != 4 && wr != 8 && wr != 16) return cudaErrorInvalidValue;
     if (A.mat) {
@@ -749,6 +752,7 @@ cudaError_t launch_wave(const WaveArgs &A, int num_sms, cudaStream_t st) {
         else if (A.mode == ANCHORED_LOCAL) launch_one<4, false, ANCHORED_LOCAL>(A, num_sms, st);
         else if (A.mode == SEMIGLOBAL) launch_one<4, false, SEMIGLOBAL>(A, num_sms, st);
         else if (A.mode == ANCHORED_SEMIGLOBAL) launch_one<4, false, ANCHORED_SEMIGLOBAL>(A, num_sms, st);
+        else if (A.mode == GLOBAL && tb) launch_one<4, true, GLOBAL>(A, num_sms, st);
         else if (A.mode == GLOBAL) launch_one<4, false, GLOBAL>(A, num_sms, st);
         else return cudaErrorInvalidValue;
         return cudaGetLastError();

@@ -68,8 +68,8 @@ __host__ __device__ constexpr int32_t wave_init_mode(int32_t mode) {
 // counts) in n_passes passes: the tallest stripes (16, 8, then 4 rows per lane)
 // that still give about three stripes for every four SMs; local passes always 8,
 // semi-global passes 16 or 4. forced (4, 8 or 16; 0: automatic) overrides the
-// choice within what each mode has; min8 keeps at least 8 (the traceback's
-// direction words, the allocation-free scratch). The stripe table of a launch
+// choice within what each mode has; min8 keeps at least 8 (the allocation-free
+// scratch is sized for 8-row stripes). The stripe table of a launch
 // must be built with this value, and WaveArgs.rows_per_lane set to it.
 int wave_rows_per_lane(int64_t total_rows, int num_sms, int64_t n_passes, int mode, int forced = 0, bool min8 = false);
 cudaError_t launch_wave(const WaveArgs &A, int num_sms, cudaStream_t st);

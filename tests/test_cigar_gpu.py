@@ -180,6 +180,30 @@ def test_small_global_batches_on_the_wavefront(pkg, ctx, sc_args):
         assert_cigar_parity(b, res, cigars, sc_args, 0)
 
 
+@pytest.mark.parametrize("rows", [4, 8, 16])
+def test_wavefront_traceback_rows_per_lane(pkg, ctx, rows):
+    """The wavefront's traceback variant at 4, 8 and 16 rows per lane (4-row
+    direction words fill the low half of each byte): CIGARs and cells equal
+    the oracle's full traceback on small global batches, including pairs of
+    one stripe, ragged last stripes and an empty pair."""
+    st = synth.Stream(9500 + rows, 1)
+    pairs = []
+    for n, extra in ((1, 2), (127, 0), (129, 5), (700, -30), (2100, 11)):
+        q = synth.random_codes(st, n, 4)
+        s, _ = synth.mutate(q, np.array([0, n], np.int64), 0.06, 0.02, 0.3, 4, st)
+        pairs.append((q, s[: max(1, len(s) + extra)]))
+    pairs.append((synth.random_codes(st, 300, 4), np.zeros(0, np.uint8)))
+    ctx.set_option("wave_rows", rows)
+    try:
+        for sc_args in ((2, -3, -5, -2), (2, -1, 0, -2)):
+            # each batch holds a pair above the wavefront's size threshold
+            for b in (synth.from_pairs(pairs[:3] + [pairs[4]]), synth.from_pairs(pairs[3:]), synth.single_pair()):
+                res, cigars, _ = gpu_align(pkg, ctx, b, sc_args, 0)
+                assert_cigar_parity(b, res, cigars, sc_args, 0)
+    finally:
+        ctx.set_option("wave_rows", 0)
+
+
 @pytest.mark.parametrize("walker", [1, 2])
 @pytest.mark.parametrize("mode", [0, 1, 2])
 def test_both_walkers_match_oracle(pkg, ctx, mode, walker):
