@@ -365,15 +365,16 @@ anyseq_status_t anyseq_plan_wait(anyseq_plan *plan, void *cuda_stream);
 anyseq_status_t anyseq_plan_destroy(anyseq_plan *plan);
 
 /* ------------------------------------------------------------------------
- * Serving (not in the paper, whose interface aligns one pair per call): a
- * request queue drained by one worker thread that owns a context and a CUDA
- * stream. Pairs are submitted one at a time from any thread and aligned in
- * micro-batches: the worker waits at most max_wait_us after the oldest queued
- * request (or until max_batch_pairs are queued), then aligns the batch's small
- * pairs with one anyseq_align_batch call and every pair of at least long_cells
- * cells with the wavefront of anyseq_align_long, all of them in
- * one launch (their stripes run side by side). Results carry score and optimum
- * cell.
+ * Serving (not in the paper, whose interface aligns one pair per call):
+ * request queues drained by two service lanes, each a worker thread that owns
+ * a context and a CUDA stream. Pairs are submitted one at a time from any
+ * thread; a pair of at least long_cells cells goes to the long lane, any other
+ * to the short lane. Each lane aligns in micro-batches: it waits at most
+ * max_wait_us after its oldest queued request (or until max_batch_pairs are
+ * queued). The short lane aligns a batch with one anyseq_align_batch call;
+ * the long lane runs its pairs side by side in one wavefront launch of
+ * anyseq_align_long's kind, at one CTA per SM, which leaves room on every SM
+ * for the short lane's kernels. Results carry score and optimum cell.
  * Admission: the letters of queued and running requests never exceed
  * mem_budget_bytes; a submit beyond it returns ANYSEQ_ERR_BUDGET and queues
  * nothing (the caller may retry later). Device scratch is the context's,
