@@ -223,17 +223,24 @@ static anyseq_status_t pack_batch(anyseq_ctx *ctx, const BatchInput &in, int32_t
     return ANYSEQ_OK;
 }
 
-// Order a pass's pairs longest first (query, then subject length): the two
-// slots of a warp share its chunk count and step count, so pairs of similar
-// size side by side keep both busy, as the length binning of the full DP does.
-static anyseq_status_t sort_by_length(const std::vector<int64_t> &hq, const std::vector<int64_t> &hs, int32_t *list,
-                                      int64_t n_list, cudaStream_t st) {
+// Order a pass's pairs so that the two slots of a warp hold pairs of one chunk
+// count and similar band: the warp runs as many chunks as its longer query needs
+// and as many steps per chunk as its wider window, and the other slot computes
+// columns nobody reads meanwhile. So: queries in 64-row classes (the shortest
+// chunk) longest first, then within a class the band width, widest first, then
+// the lengths. (Sorted by lengths alone, two pairs of one length could differ
+// several-fold in band width.)
+static anyseq_status_t sort_pass(const std::vector<int64_t> &hq, const std::vector<int64_t> &hs, const int32_t *width,
+                                 int64_t n_pairs, int32_t *list, int64_t n_list, cudaStream_t st) {
     if (n_list < 2) return ANYSEQ_OK;
-    std::vector<int32_t> h((size_t)n_list);
+    std::vector<int32_t> h((size_t)n_list), hw((size_t)n_pairs);
     BCUDA(cudaMemcpyAsync(h.data(), list, (size_t)n_list * sizeof(int32_t), cudaMemcpyDeviceToHost, st));
+    BCUDA(cudaMemcpyAsync(hw.data(), width, (size_t)n_pairs * sizeof(int32_t), cudaMemcpyDeviceToHost, st));
     BCUDA(cudaStreamSynchronize(st));
     std::stable_sort(h.begin(), h.end(), [&](int32_t a, int32_t b) {
         const int64_t na = hq[a + 1] - hq[a], nb = hq[b + 1] - hq[b];
+        if (na / 64 != nb / 64) return na > nb;
+        if (hw[a] != hw[b]) return hw[a] > hw[b];
         if (na != nb) return na > nb;
         return hs[a + 1] - hs[a] > hs[b + 1] - hs[b];
     });
@@ -338,7 +345,7 @@ anyseq_status_t anyseq::band_scores(anyseq_ctx *ctx, const BatchInput &in, const
     BCUDA(cudaMemcpyAsync(hs.data(), in.s_off, ((size_t)n + 1) * sizeof(int64_t), cudaMemcpyDeviceToHost, st));
     BCUDA(cudaStreamSynchronize(st));
     while (n_list > 0) {
-        BTRY(sort_by_length(hq, hs, listA, n_list, st));
+        BTRY(sort_pass(hq, hs, width, n, listA, n_list, st));
         BTRY(banded_pass(ctx, in, sc, q2, s2, listA, n_list, centre, width, false, bscore, accept, st));
         BCUDA(cudaMemsetAsync(cnt + 1, 0, sizeof(int64_t), st));
         band_round_kernel<<<grid_of(n_list), 256, 0, st>>>(listA, n_list, in.q_off, in.s_off, bscore, accept, width,
