@@ -517,7 +517,7 @@ def secondary_workloads(pkg, ctx, device):
             fr["score"], band.cpu().numpy().view(pkg.RESULT_DTYPE)["score"]))}
     ctx.band_model_set(learned)
     ctx.set_option("band_margin_pct", 65)  # the shipped defaults again
-    ctx.set_option("band_floor_pct", 20)
+    ctx.set_option("band_floor_pct", 30)
     best_const = min(const.values(), key=lambda v: v["ms"])["ms"]
     out["band_65536_1_10kbp_global_affine"] = {
         "pairs_per_s_full_dp": b.n_pairs / ms_full * 1e3, "pairs_per_s_learned_band": b.n_pairs / ms_band * 1e3,

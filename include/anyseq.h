@@ -215,7 +215,7 @@ anyseq_status_t anyseq_band_train(anyseq_ctx *ctx, const uint8_t *q, const int64
  * range test (the full DP runs those two per 32-bit lane); "band_margin_pct"
  * (default 65) multiplies the network's half-width by that percentage before
  * the band is planned (a width just below the certifying one fails and pays
- * for the full DP too); "band_floor_pct" (default 20) makes every planned
+ * for the full DP too); "band_floor_pct" (default 30) makes every planned
  * half-width at least that share of the pair's longer sequence (the network
  * then widens bands and picks the pairs that go straight to the full DP);
  * "wave_cell"

@@ -738,13 +738,14 @@ __global__ void scatter_results_kernel(int64_t k, const int64_t *idx, const int3
 // the long pairs of a score-only batch run as one multi-pass wavefront launch,
 // their stripes side by side, and the batched kernel takes the rest through
 // its pair selection. A pair is long from 2^18 cells in a batch of at most
-// WAVE_BATCH_PAIRS pairs, otherwise from max(2^24, 4 x the batch's cells / the
-// resident 16-lane groups); it must also pass the wavefront's range tests.
+// WAVE_BATCH_PAIRS pairs, otherwise from max(2^24, tail_factor x the batch's
+// cells / the resident 16-lane groups); it must also pass the wavefront's range
+// tests. With in.select, only the selected pairs count and move.
 // *all_done: every pair ran on the wavefront; rest: the batch with the other
 // pairs selected.
 anyseq_status_t anyseq::long_pairs_split(anyseq_ctx *ctx, const BatchInput &in, const anyseq_scoring_t *sc,
                                          int32_t mode, int32_t *score, int32_t *eq, int32_t *es, uint32_t *flags,
-                                         cudaStream_t st, BatchInput &rest, bool *all_done) {
+                                         cudaStream_t st, BatchInput &rest, bool *all_done, double tail_factor) {
     *all_done = false;
     rest = in;
     const int64_t n = in.n_pairs;
@@ -753,17 +754,26 @@ anyseq_status_t anyseq::long_pairs_split(anyseq_ctx *ctx, const BatchInput &in, 
     if ((double)in.max_n * (double)in.max_m < (n <= WAVE_BATCH_PAIRS ? small_batch_cells : big_batch_cells))
         return ANYSEQ_OK;
     std::vector<int64_t> hq((size_t)n + 1), hs((size_t)n + 1);
+    std::vector<uint8_t> hsel(in.select ? (size_t)n : 0);
     CUDA_TRY(cudaMemcpyAsync(hq.data(), in.q_off, ((size_t)n + 1) * sizeof(int64_t), cudaMemcpyDeviceToHost, st));
     CUDA_TRY(cudaMemcpyAsync(hs.data(), in.s_off, ((size_t)n + 1) * sizeof(int64_t), cudaMemcpyDeviceToHost, st));
+    if (in.select) CUDA_TRY(cudaMemcpyAsync(hsel.data(), in.select, (size_t)n, cudaMemcpyDeviceToHost, st));
     CUDA_TRY(cudaStreamSynchronize(st));
+    auto taken = [&](int64_t p) { return !in.select || hsel[(size_t)p] != 0; };
     double total = 0;
-    for (int64_t p = 0; p < n; p++) total += (double)(hq[p + 1] - hq[p]) * (double)(hs[p + 1] - hs[p]);
+    int64_t n_taken = 0;
+    for (int64_t p = 0; p < n; p++)
+        if (taken(p)) {
+            total += (double)(hq[p + 1] - hq[p]) * (double)(hs[p + 1] - hs[p]);
+            n_taken++;
+        }
     const double groups = (double)ctx->num_sms * batch_min_ctas(0) * (batch_threads(0) / GROUP);
-    const double thr = n <= WAVE_BATCH_PAIRS ? small_batch_cells : std::max(big_batch_cells, 4.0 * total / groups);
+    const double thr =
+        n_taken <= WAVE_BATCH_PAIRS ? small_batch_cells : std::max(big_batch_cells, tail_factor * total / groups);
     std::vector<int64_t> idx;
     for (int64_t p = 0; p < n; p++) {
         const int64_t qn = hq[p + 1] - hq[p], sm = hs[p + 1] - hs[p];
-        if (qn == 0 || sm == 0 || (double)qn * (double)sm < thr) continue;
+        if (!taken(p) || qn == 0 || sm == 0 || (double)qn * (double)sm < thr) continue;
         if (!long_range_ok(sc, qn, sm) || (mode != ANYSEQ_GLOBAL && !key_range_ok(sc, qn < sm ? qn : sm))) continue;
         idx.push_back(p);
     }
@@ -827,13 +837,14 @@ anyseq_status_t anyseq::long_pairs_split(anyseq_ctx *ctx, const BatchInput &in, 
                                                                                              es, flags);
     CUDA_TRY(cudaGetLastError());
     ctx->launches += 1;
-    if (k == n) {
+    if (k == n_taken) {
         *all_done = true;
         ctx->pairs16 = 0;
-        ctx->pairs32 = n;
+        ctx->pairs32 = k;
     } else {
         // the batched kernel takes the other pairs
         std::vector<uint8_t> sel((size_t)n, 1);
+        if (in.select) sel = hsel;
         for (int64_t p : idx) sel[(size_t)p] = 0;
         uint8_t *dsel = arena<uint8_t>(ctx, "wb_sel", (size_t)n + 16, &s2);
         if (s2 != ANYSEQ_OK) return s2;

@@ -32,7 +32,7 @@ struct anyseq_ctx {
     int32_t band_area_pct = 60;      // a band above this share of the matrix goes to the full DP
     int32_t band_area16_pct = 15;    // the same for pairs the full DP runs in int16x2 lanes
     int32_t band_margin_pct = 65;    // the network's half-width times this / 100 is the band used
-    int32_t band_floor_pct = 20;     // ... but at least this share (%) of the longer sequence
+    int32_t band_floor_pct = 30;     // ... but at least this share (%) of the longer sequence
     int profile = 0;              // time the DP kernels with events
     int host_in_place = 1;        // 2-bit batches: pinned host letters read in place by the packing kernel
     cudaEvent_t ev[4] = {nullptr, nullptr, nullptr, nullptr};
@@ -101,10 +101,12 @@ anyseq_status_t wave_batch(anyseq_ctx *ctx, const BatchInput &in, const anyseq_s
                            int32_t *score, int32_t *eq, int32_t *es, uint32_t *flags, cudaStream_t st, TbOut *tb,
                            bool *used);
 // Long pairs of a score-only batch on the wavefront (see api.cu); rest: the
-// batch with the other pairs selected, *all_done when none is left.
+// batch with the other pairs selected, *all_done when none is left. Only pairs
+// that in.select keeps (all without one) take part; tail_factor: a pair is long
+// from this many times the batch's cells per resident 16-lane group.
 anyseq_status_t long_pairs_split(anyseq_ctx *ctx, const BatchInput &in, const anyseq_scoring_t *sc, int32_t mode,
                                  int32_t *score, int32_t *eq, int32_t *es, uint32_t *flags, cudaStream_t st,
-                                 BatchInput &rest, bool *all_done);
+                                 BatchInput &rest, bool *all_done, double tail_factor = 4.0);
 // read_in_place: letters in pinned (mapped) host memory are left there for the
 // device to read through the host link (callers whose only letter reader is the
 // 2-bit packing kernel)

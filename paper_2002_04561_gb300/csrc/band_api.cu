@@ -364,10 +364,17 @@ anyseq_status_t anyseq::band_scores(anyseq_ctx *ctx, const BatchInput &in, const
     }
     const double t_bands = now_ms();
     ctx->band_pass_ms = t_bands - t_plan;
-    // everything not accepted: the full DP, restricted to the marked pairs
+    // everything not accepted: the full DP, restricted to the marked pairs. The few
+    // fallback pairs far above the others' size would each hold one 16-lane group
+    // for longer than the rest of the launch takes, so pairs above the selection's
+    // cells per resident group run on the wavefront first.
     BatchInput sub = in;
     sub.select = full;
-    BTRY(batch_scores(ctx, sub, sc, ANYSEQ_GLOBAL, score, eq, es, flags, st));
+    BatchInput rest = sub;
+    bool all_wave = false;
+    if (!ctx->force32)
+        BTRY(long_pairs_split(ctx, sub, sc, ANYSEQ_GLOBAL, score, eq, es, flags, st, rest, &all_wave, 1.0));
+    if (!all_wave) BTRY(batch_scores(ctx, rest, sc, ANYSEQ_GLOBAL, score, eq, es, flags, st));
     mark_full_kernel<<<grid_of(n), 256, 0, st>>>(full, n, flags, round);
     BCUDA(cudaGetLastError());
     ctx->launches += 1;

@@ -162,7 +162,7 @@ def test_training_lowers_loss_and_beats_constant_band(pkg, ctx):
         ctx.set_option("band_area_pct", 60)
         ctx.set_option("band_area16_pct", 15)
         ctx.set_option("band_margin_pct", 65)
-        ctx.set_option("band_floor_pct", 20)
+        ctx.set_option("band_floor_pct", 30)
 
 
 def _training_lowers_loss_and_beats_constant_band(pkg, ctx):
@@ -187,7 +187,7 @@ def _training_lowers_loss_and_beats_constant_band(pkg, ctx):
 
 def test_learned_band_gains_over_the_route_without_the_network(pkg):
     """What the trained network gains, under the shipped defaults (no
-    doubling, area caps 60/15 %, margin 65 %, floor 20 %): the learned route
+    doubling, area caps 60/15 %, margin 65 %, floor 30 %): the learned route
     against the same route whose network is replaced by its prior (constant
     outputs: centre 0, half-width a quarter of the longer sequence), on the
     65,536 pairs of the band workload. Both routes' scores equal the full DP
