@@ -230,7 +230,9 @@ anyseq_status_t anyseq_band_train(anyseq_ctx *ctx, const uint8_t *q, const int64
  * within what each mode has: local passes at most 8, semi-global 4 or 16,
  * traceback passes 4, 8 or 16; results are the same); "wave_ctas_per_sm"
  * (default 0: as many as fit) caps the wavefront's CTAs per SM, leaving room
- * for other kernels beside a long pair (results are the same); "wave_spread"
+ * for other kernels beside a long pair (results are the same);
+ * "batch_ctas_per_sm" (default 0: as many as fit) caps the batched DP kernel's
+ * persistent CTAs per SM likewise (results are the same); "wave_spread"
  * (default 1) holds back the first stripe draws of a wavefront launch so that
  * its first stripes land on distinct SMs, 0 takes them in plain draw order
  * (results are the same); "host_in_place" (default 1) lets 2-bit batches read
@@ -373,8 +375,11 @@ anyseq_status_t anyseq_plan_destroy(anyseq_plan *plan);
  * max_wait_us after its oldest queued request (or until max_batch_pairs are
  * queued). The short lane aligns a batch with one anyseq_align_batch call;
  * the long lane runs its pairs side by side in one wavefront launch of
- * anyseq_align_long's kind, at one CTA per SM, which leaves room on every SM
- * for the short lane's kernels. Results carry score and optimum cell.
+ * anyseq_align_long's kind. The lanes' kernels are capped so that both fit on
+ * every SM at once (the long lane's wavefront at one CTA per SM, the short
+ * lane's batched kernel at two and its wavefront launches at one), and a
+ * short batch never waits for a long launch to leave the SMs. Results carry
+ * score and optimum cell.
  * Admission: the letters of queued and running requests never exceed
  * mem_budget_bytes; a submit beyond it returns ANYSEQ_ERR_BUDGET and queues
  * nothing (the caller may retry later). Device scratch is the context's,

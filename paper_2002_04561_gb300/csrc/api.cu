@@ -36,12 +36,24 @@ void *anyseq_ctx::get(const char *name, size_t bytes, anyseq_status_t *st) {
     for (auto &b : bufs) {
         if (b.name == name) {
             if (b.cap >= bytes) return b.p;
-            cudaFree(b.p);
-            used -= b.cap;
+            // The old buffer may still be read by this context's queued work, and
+            // cudaFree would wait for every stream of the device (another context's
+            // long kernel included), so it is retired rather than freed; the retired
+            // buffers are freed when the budget needs their room, and at destroy.
+            if (b.p) retired.push_back(b);
             b.p = nullptr;
             b.cap = 0;
-            size_t want = bytes + bytes / 4;
+            size_t want = bytes + bytes / 2;
             if (used + want > budget) want = bytes;
+            if (used + want > budget && !retired.empty()) {
+                for (auto &r : retired) {
+                    cudaFree(r.p);
+                    used -= r.cap;
+                }
+                retired.clear();
+                want = bytes + bytes / 2;
+                if (used + want > budget) want = bytes;
+            }
             if (used + want > budget) {
                 *st = fail(ANYSEQ_ERR_BUDGET, "scratch '%s' of %zu bytes exceeds the memory budget (%zu of %zu used)",
                            name, bytes, used, budget);
@@ -49,8 +61,20 @@ void *anyseq_ctx::get(const char *name, size_t bytes, anyseq_status_t *st) {
             }
             if (cudaMalloc(&b.p, want) != cudaSuccess) {
                 cudaGetLastError();
-                *st = fail(ANYSEQ_ERR_BUDGET, "cudaMalloc of %zu bytes for '%s' failed", want, name);
-                return nullptr;
+                b.p = nullptr;
+                // the device is full: give back the retired buffers and try once more
+                for (auto &r : retired) {
+                    cudaFree(r.p);
+                    used -= r.cap;
+                }
+                const bool had_retired = !retired.empty();
+                retired.clear();
+                if (!had_retired || cudaMalloc(&b.p, want) != cudaSuccess) {
+                    cudaGetLastError();
+                    b.p = nullptr;
+                    *st = fail(ANYSEQ_ERR_BUDGET, "cudaMalloc of %zu bytes for '%s' failed", want, name);
+                    return nullptr;
+                }
             }
             b.cap = want;
             used += want;
@@ -84,6 +108,7 @@ extern "C" anyseq_status_t anyseq_destroy(anyseq_ctx *ctx) {
     if (!ctx) return ANYSEQ_OK;
     cudaSetDevice(ctx->device);
     for (auto &b : ctx->bufs) cudaFree(b.p);
+    for (auto &b : ctx->retired) cudaFree(b.p);
     for (auto &h : ctx->pinned) cudaFreeHost(h.p);
     for (auto &e : ctx->ev) if (e) cudaEventDestroy(e);
     if (ctx->mlp) cudaFree(ctx->mlp);
@@ -143,6 +168,11 @@ extern "C" anyseq_status_t anyseq_set_option(anyseq_ctx *ctx, const char *key, i
     if (!strcmp(key, "wave_spread")) {
         if (value != 0 && value != 1) return fail(ANYSEQ_ERR_ARG, "wave_spread must be 0 or 1");
         ctx->wave_spread = (int32_t)value;
+        return ANYSEQ_OK;
+    }
+    if (!strcmp(key, "batch_ctas_per_sm")) {
+        if (value < 0 || value > 16) return fail(ANYSEQ_ERR_ARG, "batch_ctas_per_sm must be in 0..16");
+        ctx->batch_ctas_per_sm = (int32_t)value;
         return ANYSEQ_OK;
     }
     if (!strcmp(key, "wave_ctas_per_sm")) {
@@ -475,7 +505,9 @@ anyseq_status_t anyseq::batch_scores(anyseq_ctx *ctx, const BatchInput &in, cons
         tb->dir_words = total;
     }
     for (int cell32 = 0; cell32 < 2; cell32++) {
-        const int grid = ctx->num_sms * batch_blocks_per_sm(cell32, mode, tb != nullptr, sigp, sc->alphabet);
+        int per_sm = batch_blocks_per_sm(cell32, mode, tb != nullptr, sigp, sc->alphabet);
+        if (ctx->batch_ctas_per_sm > 0 && ctx->batch_ctas_per_sm < per_sm) per_sm = ctx->batch_ctas_per_sm;
+        const int grid = ctx->num_sms * per_sm;
         A.list = cell32 ? P.list32 : P.list16;
         A.n_list = P.counts + cell32;
         A.scratch = nullptr;

@@ -51,10 +51,14 @@ struct anyseq_ctx {
     int32_t tb_walker = 0;  // traceback walk: 0 by batch size, 1 a warp per pair, 2 a thread per pair
     int32_t wave_split = 0;  // global three-input-maximum wavefront: 0 by stripe count, 1 split steps, 2 plain
     int32_t wave_spread = 1;       // wavefront: first stripes of a launch on distinct SMs
-    int32_t wave_ctas_per_sm = 0;  // wavefront CTAs per SM: 0 as many as fit (the serving long lane uses 1)
+    int32_t wave_ctas_per_sm = 0;  // wavefront CTAs per SM: 0 as many as fit (the serving lanes use 1)
+    int32_t batch_ctas_per_sm = 0;  // batched DP CTAs per SM: 0 as many as fit (the serving short lane uses 2)
     int32_t wave_rows = 0;  // wavefront rows per lane: 0 automatic, or 4, 8, 16 (within what each mode has)
     int32_t wave_cell = 0;  // wavefront cell of global passes: 0 by stripe count, 1 three-input max, 2 two-step
     std::vector<Buf> bufs;        // device scratch, grown on demand, reused across calls
+    // buffers replaced by larger ones, freed only under budget pressure or at
+    // destroy: cudaFree waits for the whole device, including other contexts' work
+    std::vector<Buf> retired;
     std::vector<Buf> pinned;      // pinned host staging
     // Named device buffer of at least 'bytes'; contents are not preserved on growth.
     void *get(const char *name, size_t bytes, anyseq_status_t *st);

@@ -230,8 +230,15 @@ extern "C" anyseq_status_t anyseq_server_create(anyseq_server **out, const anyse
             return st;
         }
     }
-    // the long lane's wavefront leaves room on every SM for the short lane's kernels
+    // Both lanes' persistent kernels must fit on every SM at once: a CTA that does
+    // not fit waits for the other lane's persistent kernel to finish, and its own
+    // launch ends only after it has run. The long lane's wavefront takes one CTA per
+    // SM (8 warps, 32K registers). The short lane's batched kernel takes two (16K
+    // registers each), and the wavefront launch it makes for a batch's larger pairs
+    // one as well.
     anyseq_set_option(S->lane[1].ctx, "wave_ctas_per_sm", 1);
+    anyseq_set_option(S->lane[0].ctx, "wave_ctas_per_sm", 1);
+    anyseq_set_option(S->lane[0].ctx, "batch_ctas_per_sm", 2);
     for (int k = 0; k < 2; k++) S->lane[k].worker = std::thread(worker_main, S, k);
     *out = S;
     return ANYSEQ_OK;
