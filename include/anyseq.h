@@ -346,7 +346,14 @@ anyseq_status_t anyseq_shard_plan(const int64_t *q_off, const int64_t *s_off, in
  *   1. anyseq_plan_create: host offsets (copied), scoring (copied), mode.
  *   2. anyseq_plan_buffers: device pointers of the plan's letter arrays
  *      (q_off[n_pairs] and s_off[n_pairs] bytes) and of its n_pairs results.
- *      Fill the letters (any stream, ordered before the run) before each run.
+ *      Fill the letters (any stream, ordered before the run) before each run,
+ *      or with anyseq_plan_upload: an asynchronous copy of q_off[n_pairs] and
+ *      s_off[n_pairs] bytes from q and s (host or device memory; pinned host
+ *      memory keeps the copy asynchronous) on cuda_stream.
+ *   After a run, anyseq_plan_download copies the n_pairs result records to
+ *   out (host or device) asynchronously on cuda_stream; they are valid after
+ *   anyseq_plan_wait. Two plans of one shape on two streams let one batch's
+ *   copies overlap the other's run.
  *   3. anyseq_plan_run: enqueue one run on cuda_stream. The first run executes
  *      the batched path once (sizing the scratch; it synchronises), then
  *      captures it; every later run is one graph launch and does not
@@ -362,7 +369,9 @@ anyseq_status_t anyseq_plan_create(anyseq_plan **plan, int device, const int64_t
                                    const anyseq_scoring_t *sc, int32_t mode);
 anyseq_status_t anyseq_plan_buffers(anyseq_plan *plan, uint8_t **q, uint8_t **s,
                                     anyseq_result_t **out);
+anyseq_status_t anyseq_plan_upload(anyseq_plan *plan, const uint8_t *q, const uint8_t *s, void *cuda_stream);
 anyseq_status_t anyseq_plan_run(anyseq_plan *plan, void *cuda_stream);
+anyseq_status_t anyseq_plan_download(anyseq_plan *plan, anyseq_result_t *out, void *cuda_stream);
 anyseq_status_t anyseq_plan_wait(anyseq_plan *plan, void *cuda_stream);
 anyseq_status_t anyseq_plan_destroy(anyseq_plan *plan);
 

@@ -71,7 +71,8 @@ EXPORTS = ["anyseq_create", "anyseq_destroy", "anyseq_align_batch", "anyseq_alig
            "anyseq_server_create", "anyseq_server_submit", "anyseq_server_wait", "anyseq_server_stat",
            "anyseq_server_destroy", "anyseq_plan_create", "anyseq_plan_buffers", "anyseq_plan_run",
            "anyseq_plan_wait", "anyseq_plan_destroy", "anyseq_gapped", "anyseq_autotune",
-           "anyseq_autotune_table", "anyseq_autotune_set_table", "anyseq_shard_plan"]
+           "anyseq_autotune_table", "anyseq_autotune_set_table", "anyseq_shard_plan", "anyseq_plan_upload",
+           "anyseq_plan_download"]
 NOALLOC_MAX_LEN = 1048576
 BAND_FEATURES = 64
 BAND_PARAMS = 25090
@@ -120,6 +121,8 @@ def load(build_if_missing: bool = False):
     lib.anyseq_plan_create.argtypes = [ctypes.POINTER(P), ctypes.c_int, P, P, I64, P, I32]
     lib.anyseq_plan_buffers.argtypes = [P, ctypes.POINTER(P), ctypes.POINTER(P), ctypes.POINTER(P)]
     lib.anyseq_plan_run.argtypes = [P, P]
+    lib.anyseq_plan_upload.argtypes = [P, P, P, P]
+    lib.anyseq_plan_download.argtypes = [P, P, P]
     lib.anyseq_plan_wait.argtypes = [P, P]
     lib.anyseq_plan_destroy.argtypes = [P]
     lib.anyseq_autotune.argtypes = [P, P, P, P, P, I64, P, I32, P]
@@ -139,7 +142,7 @@ def load(build_if_missing: bool = False):
                  "anyseq_server_wait", "anyseq_server_stat", "anyseq_server_destroy", "anyseq_plan_create",
                  "anyseq_plan_buffers", "anyseq_plan_run", "anyseq_plan_wait", "anyseq_plan_destroy",
                  "anyseq_gapped", "anyseq_autotune", "anyseq_autotune_table",
-                 "anyseq_autotune_set_table", "anyseq_shard_plan"]:
+                 "anyseq_autotune_set_table", "anyseq_shard_plan", "anyseq_plan_upload", "anyseq_plan_download"]:
         getattr(lib, name).restype = ctypes.c_int
     _lib = lib
     return lib
@@ -430,6 +433,16 @@ class Plan:
 
     def run(self, stream=None):
         _check(load().anyseq_plan_run(self.h, _stream_handle(stream)))
+
+    def upload(self, q, s, stream=None):
+        """anyseq_plan_upload: the letters of the next run from q and s (torch
+        tensors or numpy arrays, host or device), asynchronously on the stream."""
+        _check(load().anyseq_plan_upload(self.h, _ptr(q), _ptr(s), _stream_handle(stream)))
+
+    def download(self, out, stream=None):
+        """anyseq_plan_download: the last run's result records into out (n_pairs x 40
+        bytes, host or device), asynchronously on the stream; valid after wait()."""
+        _check(load().anyseq_plan_download(self.h, _ptr(out), _stream_handle(stream)))
 
     def wait(self, stream=None):
         _check(load().anyseq_plan_wait(self.h, _stream_handle(stream)))

@@ -186,6 +186,34 @@ extern "C" anyseq_status_t anyseq_plan_run(anyseq_plan *P, void *cuda_stream) {
     return ANYSEQ_OK;
 }
 
+extern "C" anyseq_status_t anyseq_plan_upload(anyseq_plan *P, const uint8_t *q, const uint8_t *s,
+                                              void *cuda_stream) {
+    if (!P) return fail(ANYSEQ_ERR_ARG, "plan is NULL");
+    if ((P->in.q_len > 0 && !q) || (P->in.s_len > 0 && !s)) return fail(ANYSEQ_ERR_ARG, "q or s is NULL");
+    cudaStream_t st = (cudaStream_t)cuda_stream;
+    if (cudaSetDevice(P->ctx->device) != cudaSuccess) return fail(ANYSEQ_ERR_CUDA, "cudaSetDevice failed");
+    cudaError_t e = cudaSuccess;
+    if (P->in.q_len > 0) e = cudaMemcpyAsync(P->q, q, (size_t)P->in.q_len, cudaMemcpyDefault, st);
+    if (e == cudaSuccess && P->in.s_len > 0) e = cudaMemcpyAsync(P->s, s, (size_t)P->in.s_len, cudaMemcpyDefault, st);
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        return fail(ANYSEQ_ERR_CUDA, "plan upload: %s", cudaGetErrorString(e));
+    }
+    return ANYSEQ_OK;
+}
+
+extern "C" anyseq_status_t anyseq_plan_download(anyseq_plan *P, anyseq_result_t *out, void *cuda_stream) {
+    if (!P || !out) return fail(ANYSEQ_ERR_ARG, "plan or out is NULL");
+    if (cudaSetDevice(P->ctx->device) != cudaSuccess) return fail(ANYSEQ_ERR_CUDA, "cudaSetDevice failed");
+    const cudaError_t e = cudaMemcpyAsync(out, P->out, (size_t)P->in.n_pairs * sizeof(anyseq_result_t),
+                                          cudaMemcpyDefault, (cudaStream_t)cuda_stream);
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        return fail(ANYSEQ_ERR_CUDA, "plan download: %s", cudaGetErrorString(e));
+    }
+    return ANYSEQ_OK;
+}
+
 extern "C" anyseq_status_t anyseq_plan_wait(anyseq_plan *P, void *cuda_stream) {
     if (!P) return fail(ANYSEQ_ERR_ARG, "plan is NULL");
     const cudaError_t e = cudaStreamSynchronize((cudaStream_t)cuda_stream);

@@ -78,3 +78,49 @@ def test_plan_replay_reports_bad_letter(pkg):
         plan.run(); plan.wait()     # good letters again
     finally:
         plan.close()
+
+
+def test_two_plans_alternating_with_upload_and_download(pkg):
+    """Two plans of one shape on two streams, each step uploading its letters
+    from pinned host memory, replaying and downloading its records (one
+    batch's copies overlapping the other's run), give every batch the
+    results of anyseq_align_batch and the oracle's scores on a sample."""
+    sc_args = (1, -4, -6, -1)
+    b0 = synth.random_pairs(900, 0, 300, seed=9300, related=0.7, p_sub=0.05, p_indel=0.02)
+    batches = []
+    for k in range(6):
+        st = synth.Stream(9400 + k, 1)
+        q = synth.random_codes(st, len(b0.q), 4)
+        s, _ = synth.mutate(q, b0.q_off, 0.05, 0.02, 0.5, 4, st)
+        s = np.resize(s, len(b0.s)).astype(np.uint8)  # the subject letters of the shape's lengths
+        batches.append(synth.Batch(q, b0.q_off, s, b0.s_off, 4))
+    sc = pkg.Scoring.make(*sc_args)
+    plans = [pkg.Plan(b0.q_off, b0.s_off, sc, 2), pkg.Plan(b0.q_off, b0.s_off, sc, 2)]
+    streams = [torch.cuda.Stream(), torch.cuda.Stream()]
+    pin = lambda a: torch.from_numpy(np.ascontiguousarray(a)).pin_memory()
+    hq = [pin(b.q) for b in batches]
+    hs = [pin(b.s) for b in batches]
+    outs = [torch.zeros(b0.n_pairs * 40, dtype=torch.uint8).pin_memory() for _ in batches]
+    ctx = pkg.Context(0)
+    try:
+        for k, b in enumerate(batches):
+            i = k & 1
+            if k >= 2:
+                plans[i].wait(streams[i])
+            plans[i].upload(hq[k], hs[k], streams[i])
+            plans[i].run(streams[i])
+            plans[i].download(outs[k], streams[i])
+        for i in range(2):
+            plans[i].wait(streams[i])
+        for k, b in enumerate(batches):
+            got = outs[k].numpy().view(pkg.RESULT_DTYPE)
+            want, _ = ctx.align_batch(b.q, b.q_off, b.s, b.s_off, sc, 2)
+            assert np.array_equal(got["score"], want["score"]), k
+            assert np.array_equal(got["end_q"], want["end_q"]) and np.array_equal(got["end_s"], want["end_s"]), k
+        idx = np.arange(0, b0.n_pairs, 29)
+        o = oracle.score_batch(batches[3].subset(idx), oracle.Scoring(*sc_args), 2)
+        assert np.array_equal(outs[3].numpy().view(pkg.RESULT_DTYPE)["score"][idx], o[0])
+    finally:
+        for p in plans:
+            p.close()
+        ctx.close()
