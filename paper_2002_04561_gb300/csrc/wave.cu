@@ -707,15 +707,16 @@ static void launch_one(const WaveArgs &A, int num_sms, cudaStream_t st) {
     wave_kernel<WR, TB, MODE, TRI, MAT, SPLIT><<<num_sms * per_sm, 256, dyn, st>>>(B);
 }
 
-// 16-row stripes side by side per SM from which the 3-input-maximum cell wins
-// in global passes (measured on single pairs: up to 6.4 stripes per SM it was
-// up to 4 % slower, from 9 per SM 12 % faster; in semi-global passes, where it
-// spills, slower at every size).
-constexpr int WAVE_TRI_STRIPES_PER_SM = 8;
-// ... and from which it runs split steps (two chains per step, one more block of
-// skew per stripe): 1 Mbp (12.9 stripes per SM) 451-455 against 473 ms, 700 kbp (9
-// per SM) 331-360 against 325 ms, on one box.
-constexpr int WAVE_SPLIT_STRIPES_PER_SM = 12;
+// 16-row stripes side by side per SM from which global passes take the
+// 3-input-maximum cell with split steps (two chains per step, one more block of
+// skew per stripe). Measured on single pairs, ms, two-step cell / 3-input cell /
+// 3-input cell with split steps: 100 kbp (1.3 stripes per SM) 17 / 23 / 19, 300 kbp
+// (3.9) 76 / 85 / 74, 500 kbp (6.4) 142-146 / 146-152 / 135-136, 700 kbp (9.0)
+// - / 275-293 / 238-254, 1 Mbp (12.9) - / 460-470 / 403-405. The 3-input cell
+// without split steps no longer wins anywhere; in semi-global passes, where it
+// spills, it is never taken.
+constexpr int WAVE_TRI_STRIPES_PER_SM = 3;
+constexpr int WAVE_SPLIT_STRIPES_PER_SM = 3;
 
 cudaError_t launch_wave(const WaveArgs &A, int num_sms, cudaStream_t st) {
     const bool tb = A.dirs != nullptr;
