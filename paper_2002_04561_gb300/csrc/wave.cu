@@ -717,11 +717,20 @@ static void launch_one(const WaveArgs &A, int num_sms, cudaStream_t st) {
 // spills, it is never taken.
 constexpr int WAVE_TRI_STRIPES_PER_SM = 3;
 constexpr int WAVE_SPLIT_STRIPES_PER_SM = 3;
+// Launches capped below the CTAs that fit (the serving lanes: one CTA per SM) run
+// many small passes side by side on at most 8 warps per SM; there the lower
+// thresholds cut the serving sweep's capacity from about 3,800 to 2,680 requests/s,
+// so they keep the earlier ones.
+constexpr int WAVE_TRI_STRIPES_PER_SM_CAPPED = 8;
+constexpr int WAVE_SPLIT_STRIPES_PER_SM_CAPPED = 12;
 
 cudaError_t launch_wave(const WaveArgs &A, int num_sms, cudaStream_t st) {
     const bool tb = A.dirs != nullptr;
+    const bool capped = A.ctas_per_sm > 0;
+    const int64_t tri_from = capped ? WAVE_TRI_STRIPES_PER_SM_CAPPED : WAVE_TRI_STRIPES_PER_SM;
+    const int64_t split_from = capped ? WAVE_SPLIT_STRIPES_PER_SM_CAPPED : WAVE_SPLIT_STRIPES_PER_SM;
     const bool tri = A.mode == GLOBAL && A.rows_per_lane >= 16 && !A.mat &&
-                     (A.cell == 1 || (A.cell == 0 && (int64_t)A.n_stripes >= (int64_t)WAVE_TRI_STRIPES_PER_SM * num_sms));
+                     (A.cell == 1 || (A.cell == 0 && (int64_t)A.n_stripes >= tri_from * num_sms));
     // the stripe table was built for A.rows_per_lane (from wave_rows_per_lane)
     const int wr = A.rows_per_lane;
     if (tb && wr != 4 && wr != 8 && wr != 16) return cudaErrorInvalidValue;
@@ -773,7 +782,7 @@ cudaError_t launch_wave(const WaveArgs &A, int num_sms, cudaStream_t st) {
         else launch_one<8, false, GLOBAL>(A, num_sms, st);
     } else {
         if (tb) launch_one<16, true, GLOBAL>(A, num_sms, st);
-        else if (tri && (A.split == 1 || (A.split == 0 && (int64_t)A.n_stripes >= (int64_t)WAVE_SPLIT_STRIPES_PER_SM * num_sms)))
+        else if (tri && (A.split == 1 || (A.split == 0 && (int64_t)A.n_stripes >= split_from * num_sms)))
             launch_one<16, false, GLOBAL, true, false, true>(A, num_sms, st);
         else if (tri) launch_one<16, false, GLOBAL, true>(A, num_sms, st);
         else launch_one<16, false, GLOBAL>(A, num_sms, st);
