@@ -194,7 +194,6 @@ __global__ void __launch_bounds__(TB_WARPS * 32) tb_walk_kernel(TbWalkArgs W) {
                 }
                 __syncwarp();
                 if (lane == 0) {
-                    const int32_t jtop = j;  // the window's right column (j moves while walking)
                     // row i's word unit (as a window row), its bit, and the window column of j,
                     // all followed by increments: a move up leaves the unit only from a word's
                     // first row, and units are numbered in row order

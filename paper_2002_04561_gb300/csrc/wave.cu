@@ -148,12 +148,13 @@ __global__ void __launch_bounds__(256, 2) wave_kernel(WaveArgs A) {
         int32_t *outH = A.last_H ? A.last_H + ps.out_off : nullptr;
         int32_t *outE = A.last_E ? A.last_E + ps.out_off : nullptr;
         const int32_t rb = k * WCH + g * WR + 1;
-        uint32_t prof[MAT ? 1 : WR];
+        uint32_t prof[WR];  // row profiles (unused on the matrix path)
         T Hoe[WR], F[WR];
 #pragma unroll
         for (int r = 0; r < WR; r++) {
             int32_t i = rb + r - pad;
             if constexpr (!MAT) prof[r] = (i >= 1) ? A.rowprof[wletter(A.q2, ps.q0, n, i - 1, rev)] : A.rowprof[4];
+            else prof[r] = 0;
             Hoe[r] = col0(INIT, i, o, e, ps.tb) + oe;
             F[r] = C::NEG;
         }
